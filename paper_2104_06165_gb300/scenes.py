@@ -1,0 +1,313 @@
+"""Seeded synthetic multi-view scenes (input generator only).
+
+Stands in for the ETH3D high-resolution scenes of the paper's experiments
+(Sec. IV), which are not available here.  A scene is a set of planar quads
+(one large background plane, textured quads and texture-less quads) seen by
+one reference camera and several source cameras.  Images are rendered by
+ray casting in double precision; textures are band-limited sums of
+sinusoids in plane coordinates; intensities are mapped to [20, 235] and
+rounded half-to-even to uint8.  Ground-truth depth (z-depth) and normals of
+the reference view come with the render.
+
+This module holds no arithmetic of the depth-estimation method itself; it
+feeds both the CUDA library and the CPU oracle with the same arrays.
+Random numbers of the method are drawn inside the method (Philox); the seeds
+here only shape the scene.
+"""
+from __future__ import annotations
+
+import math
+import os
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Quad:
+    center: np.ndarray        # world point
+    normal: np.ndarray        # unit world normal
+    e1: np.ndarray            # in-plane unit axes
+    e2: np.ndarray
+    half: tuple               # half extents along e1, e2
+    textured: bool
+    flat_value: float = 128.0
+    freqs: np.ndarray = None  # (K, 2) cycles per world unit
+    phases: np.ndarray = None
+    amps: np.ndarray = None
+
+
+@dataclass
+class Scene:
+    K: np.ndarray             # (n, 3, 3)
+    R: np.ndarray             # (n, 3, 3) world -> camera
+    t: np.ndarray             # (n, 3)
+    images: list              # uint8 (H, W) per view (or float64 in [0,1])
+    gt_depth: np.ndarray      # reference view z-depth (H, W), 0 = nothing hit
+    gt_normal: np.ndarray     # reference view normals (H, W, 3), facing the camera
+    gt_textured: np.ndarray   # bool (H, W): reference pixel lies on a textured quad
+    d_lo: float
+    d_hi: float
+    quads: list = field(default_factory=list)
+
+    @property
+    def n_views(self):
+        return len(self.images)
+
+
+def intrinsics(W, H, f):
+    return np.array([[f, 0.0, (W - 1) / 2.0], [0.0, f, (H - 1) / 2.0], [0.0, 0.0, 1.0]])
+
+
+def look_at(C, target, down=(0.0, 1.0, 0.0)):
+    """Rotation (world -> camera, rows = camera axes x right, y down, z
+    forward) and translation of a camera at C looking at target."""
+    C = np.asarray(C, float)
+    z = np.asarray(target, float) - C
+    z /= np.linalg.norm(z)
+    x = np.cross(np.asarray(down, float), z)
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    R = np.stack([x, y, z])
+    return R, -R @ C
+
+
+def _plane_axes(n):
+    a = np.array([1.0, 0.0, 0.0]) if abs(n[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = np.cross(n, a)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(n, e1)
+    return e1, e2
+
+
+def _texture(rng, depth, f, n_sin=32, lam_px=(4.0, 32.0), std=38.0):
+    """Band-limited texture: n_sin sinusoids with wavelengths log-uniform in
+    lam_px pixels at the given depth."""
+    lam = np.exp(rng.uniform(np.log(lam_px[0]), np.log(lam_px[1]), n_sin)) * depth / f
+    ang = rng.uniform(0, np.pi, n_sin)
+    freqs = np.stack([np.cos(ang), np.sin(ang)], 1) / lam[:, None]
+    phases = rng.uniform(0, 2 * np.pi, n_sin)
+    amps = rng.uniform(0.5, 1.0, n_sin)
+    amps *= std / math.sqrt(0.5 * np.sum(amps ** 2))
+    return freqs, phases, amps
+
+
+def _random_normal(rng, max_tilt_deg):
+    """Unit normal facing the reference camera (negative z), tilted up to
+    max_tilt_deg from the optical axis."""
+    tilt = math.radians(rng.uniform(0, max_tilt_deg))
+    az = rng.uniform(0, 2 * math.pi)
+    return np.array([math.sin(tilt) * math.cos(az), math.sin(tilt) * math.sin(az), -math.cos(tilt)])
+
+
+def _ray_dirs(K, R, W, H, y0, y1):
+    v, u = np.mgrid[y0:y1, 0:W].astype(np.float64)
+    pix = np.stack([u, v, np.ones_like(u)], -1)
+    d_cam = pix @ np.linalg.inv(K).T
+    return d_cam @ R  # world directions (rows): R^T d
+
+
+def _render_rows(quads, K, R, t, W, H, y0, y1, want_gt):
+    C = -R.T @ t
+    dirs = _ray_dirs(K, R, W, H, y0, y1)
+    best = np.full(dirs.shape[:2], np.inf)
+    idx = np.full(dirs.shape[:2], -1, np.int32)
+    for qi, q in enumerate(quads):
+        den = dirs @ q.normal
+        with np.errstate(divide="ignore", invalid="ignore"):
+            lam = ((q.center - C) @ q.normal) / den
+        P = C + lam[..., None] * dirs
+        rel = P - q.center
+        s1, s2 = rel @ q.e1, rel @ q.e2
+        hit = (lam > 1e-9) & (np.abs(s1) <= q.half[0]) & (np.abs(s2) <= q.half[1]) & (lam < best)
+        best = np.where(hit, lam, best)
+        idx = np.where(hit, qi, idx)
+    img = np.full(dirs.shape[:2], 128.0)
+    for qi, q in enumerate(quads):
+        m = idx == qi
+        if not m.any():
+            continue
+        if not q.textured:
+            img[m] = q.flat_value
+            continue
+        P = C + best[m][:, None] * dirs[m]
+        rel = P - q.center
+        s1, s2 = rel @ q.e1, rel @ q.e2
+        acc = np.zeros(s1.shape)
+        for k in range(len(q.amps)):
+            acc += q.amps[k] * np.sin(2 * np.pi * (q.freqs[k, 0] * s1 + q.freqs[k, 1] * s2) + q.phases[k])
+        img[m] = 128.0 + acc
+    out = {"img": img}
+    if want_gt:
+        P = C + np.where(np.isfinite(best), best, 0.0)[..., None] * dirs
+        Pc = P @ R.T + t
+        depth = np.where(idx >= 0, Pc[..., 2], 0.0)
+        nrm = np.zeros(dirs.shape[:2] + (3,))
+        tex = np.zeros(dirs.shape[:2], bool)
+        for qi, q in enumerate(quads):
+            m = idx == qi
+            nc = R @ q.normal
+            nrm[m] = nc
+            tex[m] = q.textured
+        ray_c = np.stack(np.meshgrid(np.arange(W, dtype=float), np.arange(y0, y1, dtype=float)), -1)
+        ray_c = np.concatenate([ray_c, np.ones(ray_c.shape[:2] + (1,))], -1) @ np.linalg.inv(K).T
+        flip = np.sum(nrm * ray_c, -1) > 0
+        nrm[flip] *= -1
+        out.update(depth=depth, normal=nrm, textured=tex)
+    return out
+
+
+def render(quads, K, R, t, W, H, quantise=True, want_gt=False, threads=None):
+    if threads is None:
+        threads = 1 if W * H < 500_000 else min(16, os.cpu_count() or 1)
+    step = max(8, (H + threads * 4 - 1) // (threads * 4))
+    chunks = [(y, min(H, y + step)) for y in range(0, H, step)]
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(lambda c: _render_rows(quads, K, R, t, W, H, c[0], c[1], want_gt), chunks))
+    img = np.concatenate([p["img"] for p in parts], 0)
+    if quantise:
+        img = np.rint(np.clip(img, 20.0, 235.0)).astype(np.uint8)
+    else:
+        img = np.clip(img, 20.0, 235.0) / 255.0
+    out = {"img": img}
+    if want_gt:
+        for k in ("depth", "normal", "textured"):
+            out[k] = np.concatenate([p[k] for p in parts], 0)
+    return out
+
+
+def _quad_facing(rng, K, W, H, depth, u, v, size_px, textured, f, tilt=50.0, flat_value=None):
+    """Quad whose centre projects to reference pixel (u, v) at the given
+    depth, roughly size_px pixels across, tilted up to `tilt` degrees."""
+    ray = np.linalg.inv(K) @ np.array([u, v, 1.0])
+    center = depth * ray
+    n = _random_normal(rng, tilt)
+    e1, e2 = _plane_axes(n)
+    half = size_px * depth / f / 2.0
+    q = Quad(center=center, normal=n, e1=e1, e2=e2, half=(half, half * rng.uniform(0.6, 1.0)),
+             textured=textured)
+    if textured:
+        q.freqs, q.phases, q.amps = _texture(rng, depth, f)
+    else:
+        q.flat_value = float(flat_value if flat_value is not None else rng.uniform(70, 190))
+    return q
+
+
+def _sources_ring(n_src, z_c, angles_deg, rng):
+    """Source camera centres at the given viewing angles to the scene
+    centre (0, 0, z_c), azimuths spread around the reference axis."""
+    cams = []
+    for k in range(n_src):
+        a = math.radians(angles_deg[k])
+        b = 2 * math.pi * k / n_src + rng.uniform(-0.2, 0.2)
+        C = np.array([0.0, 0.0, z_c]) + z_c * np.array([math.sin(a) * math.cos(b), math.sin(a) * math.sin(b),
+                                                        -math.cos(a)])
+        cams.append(look_at(C, [0.0, 0.0, z_c]))
+    return cams
+
+
+def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_angles=None,
+               n_textured=3, n_flat=1, flat_frac=None, d_lo=2.0, d_hi=8.0, quantise=True, threads=None):
+    """Scene of planar quads in front of a textured background plane.
+
+    Default shape: W x H reference, focal f = 300 * W / 320 px (same field of
+    view at every resolution), n_src source views.  With view_angles=None the
+    sources sit on a ring of radius baseline_frac * 5 around the reference
+    optical axis; otherwise at the given viewing angles (degrees) to the
+    scene centre.  flat_frac sizes the texture-less quads so that roughly that
+    fraction of the reference image is texture-less."""
+    rng = np.random.default_rng(seed)
+    f = f if f is not None else 300.0 * W / 320.0
+    K = intrinsics(W, H, f)
+    z_c = 5.0
+    quads = []
+    # background: large textured plane at depth ~7, mildly tilted
+    bg_depth = 7.0
+    n_bg = _random_normal(rng, 15.0)
+    e1, e2 = _plane_axes(n_bg)
+    bg = Quad(center=np.array([0.0, 0.0, bg_depth]), normal=n_bg, e1=e1, e2=e2, half=(40.0, 40.0), textured=True)
+    bg.freqs, bg.phases, bg.amps = _texture(rng, bg_depth, f)
+    quads.append(bg)
+    placed = []
+    flat_size = None
+    if flat_frac:
+        flat_size = math.sqrt(flat_frac * W * H / max(n_flat, 1)) * 1.1
+    for k in range(n_textured + n_flat):
+        textured = k < n_textured
+        for _ in range(50):
+            u = rng.uniform(0.15 * W, 0.85 * W)
+            v = rng.uniform(0.15 * H, 0.85 * H)
+            if all((u - pu) ** 2 + (v - pv) ** 2 > (0.18 * W) ** 2 for pu, pv in placed):
+                break
+        placed.append((u, v))
+        depth = rng.uniform(3.0, 5.8)
+        size = rng.uniform(0.3, 0.45) * W if (textured or flat_size is None) else flat_size
+        quads.append(_quad_facing(rng, K, W, H, depth, u, v, size, textured, f,
+                                  tilt=50.0 if textured else 35.0))
+    Ks, Rs, ts = [K], [np.eye(3)], [np.zeros(3)]
+    if view_angles is None:
+        b = baseline_frac * z_c
+        for k in range(n_src):
+            a = 2 * math.pi * k / n_src
+            R, t = look_at([b * math.cos(a), b * math.sin(a), 0.0], [0.0, 0.0, z_c])
+            Ks.append(K); Rs.append(R); ts.append(t)
+    else:
+        for R, t in _sources_ring(n_src, z_c, view_angles, rng):
+            Ks.append(K); Rs.append(R); ts.append(t)
+    images = []
+    gt = None
+    for v in range(len(Ks)):
+        out = render(quads, Ks[v], Rs[v], ts[v], W, H, quantise=quantise, want_gt=(v == 0), threads=threads)
+        images.append(out["img"])
+        if v == 0:
+            gt = out
+    return Scene(K=np.stack(Ks), R=np.stack(Rs), t=np.stack(ts), images=images, gt_depth=gt["depth"],
+                 gt_normal=gt["normal"], gt_textured=gt["textured"], d_lo=d_lo, d_hi=d_hi, quads=quads)
+
+
+def make_plane_scene(W=64, H=48, f=None, n_src=2, seed=0, depth=4.0, normal=(0.0, 0.0, -1.0),
+                     baseline=0.2, quantise=True, textured=True, flat_value=128.0, lam_px=(4.0, 16.0)):
+    """A single infinite-extent textured plane through (0, 0, depth) with the
+    given world normal, sources translated along x (and y) from the
+    reference without rotation."""
+    rng = np.random.default_rng(seed)
+    f = f if f is not None else 300.0 * W / 320.0
+    K = intrinsics(W, H, f)
+    n = np.asarray(normal, float)
+    n /= np.linalg.norm(n)
+    e1, e2 = _plane_axes(n)
+    q = Quad(center=np.array([0.0, 0.0, depth]), normal=n, e1=e1, e2=e2, half=(1e3, 1e3), textured=textured,
+             flat_value=flat_value)
+    if textured:
+        q.freqs, q.phases, q.amps = _texture(rng, depth, f, lam_px=lam_px)
+    Ks, Rs, ts = [K], [np.eye(3)], [np.zeros(3)]
+    for k in range(n_src):
+        a = 2 * math.pi * k / n_src
+        C = np.array([baseline * math.cos(a), baseline * math.sin(a), 0.0])
+        Ks.append(K); Rs.append(np.eye(3)); ts.append(-C)
+    images, gt = [], None
+    for v in range(len(Ks)):
+        out = render([q], Ks[v], Rs[v], ts[v], W, H, quantise=quantise, want_gt=(v == 0), threads=1)
+        images.append(out["img"])
+        if v == 0:
+            gt = out
+    return Scene(K=np.stack(Ks), R=np.stack(Rs), t=np.stack(ts), images=images, gt_depth=gt["depth"],
+                 gt_normal=gt["normal"], gt_textured=gt["textured"], d_lo=2.0, d_hi=8.0, quads=[q])
+
+
+# ---------------------------------------------------------------------------
+# Workload shapes (stand-ins for the paper's ETH3D high-resolution inputs)
+# ---------------------------------------------------------------------------
+def scene_small(seed=0, **kw):
+    """320 x 240, 4 sources at baseline 0.1 x scene depth, 3 textured quads
+    + 1 texture-less quad in front of a textured background, depth [2, 8]."""
+    return make_scene(W=320, H=240, n_src=4, seed=seed, baseline_frac=0.1, n_textured=3, n_flat=1, **kw)
+
+
+def scene_highres(seed=0, W=3072, H=2048, n_src=10, **kw):
+    """3072 x 2048 reference + 10 sources at 15..40 degree viewing angles,
+    about 30 % of the reference covered by texture-less quads."""
+    angles = list(np.linspace(15.0, 40.0, n_src))
+    return make_scene(W=W, H=H, n_src=n_src, seed=seed, view_angles=angles, n_textured=4, n_flat=2,
+                      flat_frac=0.30, **kw)
