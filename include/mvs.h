@@ -1,0 +1,219 @@
+/*
+ * mvs.h -- C ABI of the GB300 PatchMatch multi-view-stereo library
+ * (depth-map path of PHI-MVS, Sun et al., arXiv 2104.06165).
+ *
+ * The library estimates, for every pixel x of a reference image, a depth d_x
+ * and a unit normal n_x (Sec. III: "estimate depth and normal values for each
+ * pixel on each reference image") from images and calibrated cameras
+ * (Sec. I: "3D structure using 2D images and camera parameters").
+ *
+ * General rules
+ *   - Every entry point returns an mvs_status; nothing throws or aborts across
+ *     the ABI.  On failure the context keeps a message (mvs_last_error).
+ *   - One context is used by one host thread at a time.
+ *   - All GPU work is ordered on the context's CUDA stream (the stream given
+ *     to mvs_create).  Calls whose outputs are device pointers return after
+ *     enqueueing; calls with host outputs synchronise that stream.
+ *   - Arrays are row-major; pixel (x, y) of a W x H view is element y*W + x.
+ *     Pixel centres sit at integer coordinates.
+ *   - Device pointers must be allocated on the context's device; the caller
+ *     owns every buffer it passes.  The library owns its context memory.
+ *   - Plane maps hold 4 floats per pixel: (n.x, n.y, n.z, depth) with the
+ *     normal in the reference camera frame facing the camera
+ *     (n . K^-1 (x, y, 1) < 0) and depth the camera z-depth; depth 0 marks a
+ *     pixel without a depth.
+ */
+#ifndef MVS_H
+#define MVS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MVS_OK = 0,
+    MVS_EINVAL = 1,       /* bad argument (NULL pointer, size, index, range) */
+    MVS_ENOMEM = 2,       /* device or host allocation failed               */
+    MVS_ECUDA = 3,        /* a CUDA call failed (message has the CUDA error) */
+    MVS_ETIMEOUT = 4,     /* a bounded device wait ran out                   */
+    MVS_ESTATE = 5,       /* a needed depth map was never computed           */
+    MVS_EUNSUPPORTED = 6  /* parameter combination not built                 */
+} mvs_status;
+
+/* Calibrated pinhole camera: x_cam = R * X_world + t, pixel = K * x_cam. */
+typedef struct {
+    double K[9];          /* row-major intrinsics, last row (0, 0, 1)        */
+    double R[9];          /* row-major rotation world -> camera              */
+    double t[3];
+    int32_t width, height;
+} mvs_camera;
+
+typedef struct mvs_ctx mvs_ctx;   /* opaque, owned by the library */
+
+enum { MVS_MEM_DEVICE = 0, MVS_MEM_HOST = 1 };
+enum { MVS_INIT_RANDOM = 0,       /* Sec. III-B random initialisation        */
+       MVS_INIT_GIVEN = 1,        /* start from out->plane and out->cost     */
+       MVS_INIT_GIVEN_RECOST = 2  /* start from out->plane, compute its cost */
+};
+
+/* PatchMatch parameters (Sec. III-B, III-C; defaults in Sec. IV). */
+typedef struct {
+    float win_radius;      /* r_orig: half side of the matching window, px   */
+    int32_t win_samples;   /* samples per axis n = 2 r_now + 1 (2..22); the
+                              offsets are s*k, k = -r_now..r_now, s = r_orig /
+                              r_now (Sec. III-C, dilated window)             */
+    float sigma_s;         /* bilateral spatial sigma in px; <= 0: none      */
+    float sigma_c;         /* bilateral colour sigma on the [0,1] intensity
+                              scale; <= 0 together with sigma_s <= 0 gives
+                              the unweighted ZNCC of Eq. 4                   */
+    float d_lo, d_hi;      /* depth range of initialisation / refinement    */
+    int32_t iters;         /* iterations (one = red phase + black phase)     */
+    int32_t phase_begin;   /* first half-iteration to run (0 = red of it. 0) */
+    int32_t phase_end;     /* one past the last half-iteration; < 0 means
+                              2 * iters                                      */
+    int32_t init_mode;     /* MVS_INIT_*                                     */
+    uint64_t seed;         /* Philox4x64-10 key word 0 (word 1 = ref index)  */
+    int32_t precision;     /* 0 = FP32 (only value built)                    */
+    int32_t reserved[7];
+} mvs_pm_params;
+
+/* Depth-map buffers supplied by the caller. */
+typedef struct {
+    float* plane;          /* H*W*4: (n.x, n.y, n.z, depth)                  */
+    float* cost;           /* H*W aggregated cost C(x) of Eq. 5              */
+    int32_t mem;           /* MVS_MEM_DEVICE or MVS_MEM_HOST                 */
+} mvs_depth_map;
+
+/* Geometric-consistency filter parameters (Sec. III-D). */
+typedef struct {
+    float depth_tol;       /* 0.02                                           */
+    int32_t depth_relative;/* 0: |d_j(x'_j) - z_j(X)| (paper); 1: relative   */
+    float max_angle_deg;   /* 30                                             */
+    float max_reproj_px;   /* 1                                              */
+    int32_t min_consistent;/* "more than one" consistent view: 2             */
+} mvs_filter_params;
+
+/* Plane hypothesis inference parameters (Sec. III-E, Sec. IV). */
+typedef struct {
+    float kappa1, kappa2, kappa3;  /* Eq. 6 / Eq. 7: 4, 0.5, 2               */
+    int32_t n_fit;         /* closest reconstructed pixels per line fit: 6   */
+    int32_t fit_inverse;   /* 0: fit depth (paper); 1: fit 1/depth           */
+    int32_t trw_iters;     /* TRW iterations (forward + backward pass): 1    */
+    float hole_cost;       /* with keep_mask == NULL, pixels whose stored
+                              cost >= hole_cost (or without depth) are holes */
+} mvs_phi_params;
+
+/* ------------------------------------------------------------------------ */
+
+/* Create a context and copy the images to the device.
+ *   cams[n_views], images[n_views]: host pointers to uint8 grayscale images of
+ *   cams[i].width x cams[i].height, pitch = width.  The images are copied (the
+ *   caller keeps its buffers).  cuda_stream: a cudaStream_t or NULL for the
+ *   legacy default stream.  The context uses the current CUDA device.
+ * Errors: MVS_EINVAL (NULL pointers, n_views < 2, sizes <= 0 or > 32768),
+ *   MVS_ENOMEM, MVS_ECUDA. */
+mvs_status mvs_create(const mvs_camera* cams, const uint8_t* const* images, int32_t n_views,
+                      void* cuda_stream, mvs_ctx** out);
+
+/* Release everything the context owns.  NULL-safe.  Synchronises its stream. */
+void mvs_destroy(mvs_ctx* ctx);
+
+/* Message of the last failed call on ctx (or of the last failed mvs_create
+ * when ctx is NULL); valid until the next call on ctx. */
+const char* mvs_last_error(const mvs_ctx* ctx);
+
+/* Depth and normal map of reference view `ref` from source views srcs[n_src]
+ * by checkerboard PatchMatch (Sec. III-B random init, Sec. III-C Eq. 4 ZNCC
+ * with dilated window and plane-induced homography, Eq. 5 aggregation, red-
+ * black propagation and four-candidate random refinement).
+ *   Runs half-iterations [phase_begin, phase_end) after the initialisation
+ *   chosen by init_mode; the counter-based random numbers make a run split
+ *   into several calls (MVS_INIT_GIVEN) identical to one uninterrupted run.
+ *   out: caller buffers of the reference's size; with MVS_INIT_GIVEN* they
+ *   also carry the starting state.  The result is kept in the context for
+ *   mvs_geo_filter / mvs_plane_infer.
+ * Errors: MVS_EINVAL (bad index, duplicate or self source, n_src outside
+ *   1..32, window outside 2..22 samples, d_lo >= d_hi, NULL buffers),
+ *   MVS_EUNSUPPORTED (precision != 0), MVS_ENOMEM, MVS_ECUDA. */
+mvs_status mvs_patchmatch(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_t n_src,
+                          const mvs_pm_params* params, mvs_depth_map* out);
+
+/* Aggregated cost (Eq. 4/5) of a given plane map of view `ref`.
+ *   plane: H*W*4 input, cost: H*W output, view_cost: H*W*n_src output of the
+ *   per-view costs C(x, j) (C_max = 2 for an excluded view) or NULL.  All
+ *   three live in `mem` (device or host).
+ * Errors as mvs_patchmatch. */
+mvs_status mvs_plane_cost(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_t n_src,
+                          const mvs_pm_params* params, const float* plane, float* cost, float* view_cost,
+                          int32_t mem);
+
+/* Geometric-consistency filter of view `ref` against srcs (Sec. III-D):
+ *   keep_mask[H*W] (in `mem`) receives 1 for pixels consistent with at least
+ *   min_consistent source maps, else 0; count (H*W int32, may be NULL)
+ *   receives the number of consistent views.
+ * Errors: MVS_ESTATE if ref or a source has no depth map in the context,
+ *   MVS_EINVAL, MVS_ECUDA. */
+mvs_status mvs_geo_filter(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_t n_src,
+                          const mvs_filter_params* fp, uint8_t* keep_mask, int32_t* count, int32_t mem);
+
+/* Plane hypothesis inference (Sec. III-E) on view `ref`: four line-fit
+ * hypotheses per hole, their matching cost through the sources, a pairwise
+ * MRF (Eq. 6-9) decoded by TRW at half resolution, closest-hypothesis
+ * selection, Eq. 10 normals.
+ *   keep_mask[H*W] (in `mem`): 1 = reconstructed; NULL derives holes from
+ *   the stored cost (cost >= hole_cost or no depth).  inout: the depth map
+ *   (MVS_INIT_GIVEN state of the view); on return holes that were filled
+ *   carry their plane, remaining holes and dropped pixels have depth 0.  The
+ *   context's copy of the view is updated.  pm gives the window / ZNCC
+ *   parameters for the hypothesis costs.
+ * Errors: MVS_ESTATE if the view has no depth map, MVS_EINVAL, MVS_ECUDA. */
+mvs_status mvs_plane_infer(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_t n_src,
+                           const mvs_pm_params* pm, const mvs_phi_params* phi, const uint8_t* keep_mask,
+                           mvs_depth_map* inout);
+
+/* Stages of mvs_plane_infer, exposed for stage-by-stage checking.
+ * All buffers are in `mem`.
+ *  mvs_phi_hypotheses: depth[H*W] and known[H*W] (1 = reconstructed) ->
+ *    hyp[H*W*4] depths of the four directions (horizontal, vertical, 45 deg
+ *    below, 45 deg above), valid[H*W*4] flags.
+ *  mvs_phi_cost: hypothesis depths -> hcost[H*W*4] (Eq. 5 cost of the
+ *    fronto-parallel plane at that depth, C_max where invalid).
+ *  mvs_phi_mrf: half-resolution MRF from (known, depth, hyp, valid, hcost) ->
+ *    label[gh*gw] (chosen hypothesis index 0..3, -1 for a reconstructed node,
+ *    -2 for a node without labels), gw = (W+1)/2, gh = (H+1)/2.
+ *  mvs_phi_select: labels -> plane[H*W*4] filled with the closest hypothesis
+ *    and its Eq. 10 normal (known pixels keep their plane). */
+mvs_status mvs_phi_hypotheses(mvs_ctx* ctx, int32_t W, int32_t H, const float* depth, const uint8_t* known,
+                              const mvs_phi_params* phi, float d_lo, float d_hi, float* hyp, uint8_t* valid,
+                              int32_t mem);
+mvs_status mvs_phi_cost(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_t n_src,
+                        const mvs_pm_params* pm, const float* hyp, const uint8_t* valid, float* hcost,
+                        int32_t mem);
+mvs_status mvs_phi_mrf(mvs_ctx* ctx, int32_t W, int32_t H, const uint8_t* known, const float* depth,
+                       const float* hyp, const uint8_t* valid, const float* hcost, const mvs_phi_params* phi,
+                       int32_t* label, int32_t mem);
+mvs_status mvs_phi_select(mvs_ctx* ctx, int32_t ref, const uint8_t* known, const float* hyp,
+                          const uint8_t* valid, const int32_t* label, float* plane, int32_t mem);
+
+/* Measurement hooks (no counterpart in the paper).
+ *  mvs_profile(ctx, enable): enable != 0 makes mvs_patchmatch bracket every
+ *    checkerboard-phase kernel with CUDA events on the context stream; any
+ *    call resets the accumulated figures.
+ *  mvs_profile_read: synchronises the context stream and returns the summed
+ *    event time of the phase kernels in ms and their number since the last
+ *    reset, the number of kernels the library launched (all contexts) since
+ *    the last reset, and the number of (pixel, hypothesis, source view) ZNCC
+ *    evaluations the phase kernels performed (views whose window left the
+ *    source image and pixels with a flat reference patch are not evaluated).
+ *    Any of the pointers may be NULL.
+ * Errors: MVS_EINVAL for a NULL ctx, MVS_ECUDA. */
+mvs_status mvs_profile(mvs_ctx* ctx, int32_t enable);
+mvs_status mvs_profile_read(mvs_ctx* ctx, double* phase_ms, int64_t* phase_launches, int64_t* kernel_launches,
+                            int64_t* phase_evals);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MVS_H */

@@ -1,0 +1,674 @@
+// C ABI of the library (declared in include/mvs.h): context management,
+// argument checking, per-view constants in double precision, and the
+// stream-ordered sequencing of the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mvs.h"
+#include "mvs_internal.h"
+
+namespace {
+
+struct ViewData {
+    mvs_camera cam;
+    double Kinv[9];
+    uint8_t* img = nullptr;
+    float4* tex = nullptr;
+    float4* plane = nullptr;   // depth map state (library-owned)
+    float* cost = nullptr;
+    bool has_map = false;
+};
+
+struct Scratch {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+std::atomic<long long> g_kernel_launches{0};
+
+struct mvs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<ViewData> views;
+    std::string err;
+    Scratch scratch[6];
+    // measurement hooks
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    long long launches0 = 0;
+    unsigned long long* evals = nullptr;   // device counter of evaluated (pixel, hypothesis, view)
+};
+
+namespace {
+
+mvs_status fail(mvs_ctx* c, mvs_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+#define CK(c, call)                                                                                     \
+    do {                                                                                                \
+        cudaError_t _e = (call);                                                                        \
+        if (_e != cudaSuccess)                                                                          \
+            return fail((c), _e == cudaErrorMemoryAllocation ? MVS_ENOMEM : MVS_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(_e), __FILE__, __LINE__);                             \
+    } while (0)
+
+void m3_mul(const double* A, const double* B, double* C) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+            C[3 * i + j] = s;
+        }
+}
+void m3_inv(const double* A, double* B) {
+    double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    B[0] = c00 / det; B[1] = (A[2] * A[7] - A[1] * A[8]) / det; B[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    B[3] = c01 / det; B[4] = (A[0] * A[8] - A[2] * A[6]) / det; B[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    B[6] = c02 / det; B[7] = (A[1] * A[6] - A[0] * A[7]) / det; B[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+}
+// X_j = Rr X_ref + tr
+void rel_pose(const mvs_camera& r, const mvs_camera& j, double* Rr, double* tr) {
+    double RrT[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) RrT[3 * b + a] = r.R[3 * a + b];
+    m3_mul(j.R, RrT, Rr);
+    for (int a = 0; a < 3; ++a) tr[a] = j.t[a] - (Rr[3 * a] * r.t[0] + Rr[3 * a + 1] * r.t[1] + Rr[3 * a + 2] * r.t[2]);
+}
+
+void* scratch(mvs_ctx* c, int slot, size_t bytes, cudaError_t* e) {
+    Scratch& s = c->scratch[slot];
+    *e = cudaSuccess;
+    if (s.bytes >= bytes) return s.p;
+    if (s.p) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(s.p);
+        s.p = nullptr;
+        s.bytes = 0;
+    }
+    *e = cudaMalloc(&s.p, bytes);
+    if (*e != cudaSuccess) { s.p = nullptr; return nullptr; }
+    s.bytes = bytes;
+    return s.p;
+}
+
+mvs_status check_view(mvs_ctx* c, int32_t v) {
+    if (!c) return MVS_EINVAL;
+    if (v < 0 || v >= (int32_t)c->views.size()) return fail(c, MVS_EINVAL, "view index %d out of range", v);
+    return MVS_OK;
+}
+
+mvs_status check_pm(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src, const mvs_pm_params* p) {
+    mvs_status st = check_view(c, ref);
+    if (st != MVS_OK) return st;
+    if (!p) return fail(c, MVS_EINVAL, "params is NULL");
+    if (!srcs || n_src < 1 || n_src > MVS_MAX_SRC)
+        return fail(c, MVS_EINVAL, "need 1..%d source views (got %d)", MVS_MAX_SRC, n_src);
+    for (int i = 0; i < n_src; ++i) {
+        if (srcs[i] < 0 || srcs[i] >= (int32_t)c->views.size() || srcs[i] == ref)
+            return fail(c, MVS_EINVAL, "bad source view %d", srcs[i]);
+        for (int k = 0; k < i; ++k)
+            if (srcs[k] == srcs[i]) return fail(c, MVS_EINVAL, "duplicate source view %d", srcs[i]);
+    }
+    if (p->win_samples < 2 || p->win_samples > MVS_MAX_WIN)
+        return fail(c, MVS_EINVAL, "win_samples must be in 2..%d", MVS_MAX_WIN);
+    if (!(p->win_radius > 0.0f) || !(p->win_radius <= 64.0f))
+        return fail(c, MVS_EINVAL, "win_radius must be in (0, 64]");
+    if (!(p->d_lo > 0.0f) || !(p->d_hi > p->d_lo) || !std::isfinite(p->d_hi))
+        return fail(c, MVS_EINVAL, "need 0 < d_lo < d_hi");
+    if (p->precision != 0) return fail(c, MVS_EUNSUPPORTED, "precision %d not built", p->precision);
+    if (p->iters < 0) return fail(c, MVS_EINVAL, "iters < 0");
+    return MVS_OK;
+}
+
+void make_refconst(const mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src, const mvs_pm_params* p,
+                   RefConst& rc) {
+    std::memset(&rc, 0, sizeof rc);
+    const ViewData& R = c->views[ref];
+    rc.W = R.cam.width;
+    rc.H = R.cam.height;
+    rc.ref_index = ref;
+    rc.n_src = n_src;
+    for (int i = 0; i < 9; ++i) rc.Kinv[i] = (float)R.Kinv[i];
+    rc.tex = R.tex;
+    rc.img = R.img;
+    rc.pitch = rc.W + 1;
+    rc.n_tex = (uint32_t)((rc.W + 1) * (rc.H + 1));
+    rc.n = p->win_samples;
+    double r_now = 0.5 * (p->win_samples - 1);
+    rc.step = (float)(p->win_radius / r_now);
+    rc.sp_coef = p->sigma_s > 0 ? (float)(-1.0 / (2.0 * (double)p->sigma_s * p->sigma_s)) : 0.0f;
+    double sc = 255.0 * p->sigma_c;
+    rc.col_coef = p->sigma_c > 0 ? (float)(-1.0 / (2.0 * sc * sc)) : 0.0f;
+    rc.d_lo = p->d_lo;
+    rc.d_hi = p->d_hi;
+    rc.seed = p->seed;
+    rc.plane = R.plane;
+    rc.cost = R.cost;
+    for (int j = 0; j < n_src; ++j) {
+        const ViewData& S = c->views[srcs[j]];
+        double Rr[9], tr[3], T[9], A[9];
+        rel_pose(R.cam, S.cam, Rr, tr);
+        m3_mul(S.cam.K, Rr, T);
+        m3_mul(T, R.Kinv, A);
+        PairConst& P = rc.pair[j];
+        for (int i = 0; i < 9; ++i) P.A[i] = (float)A[i];
+        for (int a = 0; a < 3; ++a)
+            P.b[a] = (float)(S.cam.K[3 * a] * tr[0] + S.cam.K[3 * a + 1] * tr[1] + S.cam.K[3 * a + 2] * tr[2]);
+        P.tex = S.tex;
+        P.W = S.cam.width;
+        P.H = S.cam.height;
+        P.pitch = P.W + 1;
+        P.n_tex = (uint32_t)((P.W + 1) * (P.H + 1));
+    }
+}
+
+mvs_status ensure_map(mvs_ctx* c, int32_t v) {
+    ViewData& V = c->views[v];
+    if (V.plane) return MVS_OK;
+    size_t n = (size_t)V.cam.width * V.cam.height;
+    CK(c, cudaMalloc(&V.plane, n * sizeof(float4)));
+    CK(c, cudaMalloc(&V.cost, n * sizeof(float)));
+    return MVS_OK;
+}
+
+cudaMemcpyKind kind_in(int32_t mem) { return mem == MVS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+cudaMemcpyKind kind_out(int32_t mem) { return mem == MVS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+
+}  // namespace
+
+extern "C" {
+
+mvs_status mvs_create(const mvs_camera* cams, const uint8_t* const* images, int32_t n_views, void* cuda_stream,
+                      mvs_ctx** out) {
+    if (!out) return fail(nullptr, MVS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cams || !images) return fail(nullptr, MVS_EINVAL, "cams or images is NULL");
+    if (n_views < 2) return fail(nullptr, MVS_EINVAL, "need at least 2 views");
+    for (int i = 0; i < n_views; ++i) {
+        if (!images[i]) return fail(nullptr, MVS_EINVAL, "image %d is NULL", i);
+        if (cams[i].width < 2 || cams[i].height < 2 || cams[i].width > 32768 || cams[i].height > 32768)
+            return fail(nullptr, MVS_EINVAL, "view %d: size %dx%d outside 2..32768", i, cams[i].width,
+                        cams[i].height);
+        const double* K = cams[i].K;
+        double det = K[0] * (K[4] * K[8] - K[5] * K[7]) - K[1] * (K[3] * K[8] - K[5] * K[6]) +
+                     K[2] * (K[3] * K[7] - K[4] * K[6]);
+        if (!(std::fabs(det) > 0) || !std::isfinite(det))
+            return fail(nullptr, MVS_EINVAL, "view %d: singular or non-finite K", i);
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(cams[i].R[k])) return fail(nullptr, MVS_EINVAL, "view %d: non-finite R", i);
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(cams[i].t[k])) return fail(nullptr, MVS_EINVAL, "view %d: non-finite t", i);
+    }
+    mvs_ctx* c = new (std::nothrow) mvs_ctx();
+    if (!c) return fail(nullptr, MVS_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, MVS_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+    c->stream = (cudaStream_t)cuda_stream;
+    c->views.resize(n_views);
+    for (int i = 0; i < n_views; ++i) {
+        ViewData& V = c->views[i];
+        V.cam = cams[i];
+        m3_inv(V.cam.K, V.Kinv);
+        size_t n = (size_t)V.cam.width * V.cam.height;
+        size_t nt = (size_t)(V.cam.width + 1) * (V.cam.height + 1);
+        e = cudaMalloc(&V.img, n);
+        if (e == cudaSuccess) e = cudaMalloc(&V.tex, nt * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(V.img, images[i], n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = launch_build_texture(V.img, V.cam.width, V.cam.height, V.tex, c->stream);
+        if (e != cudaSuccess) {
+            mvs_status st = e == cudaErrorMemoryAllocation ? MVS_ENOMEM : MVS_ECUDA;
+            fail(nullptr, st, "view %d upload: %s", i, cudaGetErrorString(e));
+            mvs_destroy(c);
+            return st;
+        }
+    }
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        fail(nullptr, MVS_ECUDA, "upload: %s", cudaGetErrorString(e));
+        mvs_destroy(c);
+        return MVS_ECUDA;
+    }
+    *out = c;
+    return MVS_OK;
+}
+
+void mvs_destroy(mvs_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto& V : c->views) {
+        cudaFree(V.img);
+        cudaFree(V.tex);
+        cudaFree(V.plane);
+        cudaFree(V.cost);
+    }
+    for (auto& s : c->scratch) cudaFree(s.p);
+    for (auto e : c->ev) cudaEventDestroy(e);
+    cudaFree(c->evals);
+    delete c;
+}
+
+const char* mvs_last_error(const mvs_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+mvs_status mvs_patchmatch(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src, const mvs_pm_params* p,
+                          mvs_depth_map* out) {
+    mvs_status st = check_pm(c, ref, srcs, n_src, p);
+    if (st != MVS_OK) return st;
+    if (!out || !out->plane || !out->cost) return fail(c, MVS_EINVAL, "out buffers are NULL");
+    if (((uintptr_t)out->plane & 15u) || ((uintptr_t)out->cost & 3u))
+        return fail(c, MVS_EINVAL, "plane must be 16-byte and cost 4-byte aligned");
+    if (out->mem != MVS_MEM_DEVICE && out->mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    if (p->init_mode < MVS_INIT_RANDOM || p->init_mode > MVS_INIT_GIVEN_RECOST)
+        return fail(c, MVS_EINVAL, "bad init_mode");
+    int pend = p->phase_end < 0 ? 2 * p->iters : p->phase_end;
+    if (p->phase_begin < 0 || pend < p->phase_begin) return fail(c, MVS_EINVAL, "bad phase range");
+    CK(c, cudaSetDevice(c->device));
+    if ((st = ensure_map(c, ref)) != MVS_OK) return st;
+    ViewData& V = c->views[ref];
+    size_t n = (size_t)V.cam.width * V.cam.height;
+    RefConst rc;
+    make_refconst(c, ref, srcs, n_src, p, rc);
+    if (p->init_mode == MVS_INIT_RANDOM) {
+        CK(c, launch_init(rc, nullptr, c->stream));
+    } else {
+        CK(c, cudaMemcpyAsync(V.plane, out->plane, n * sizeof(float4), kind_in(out->mem), c->stream));
+        if (p->init_mode == MVS_INIT_GIVEN)
+            CK(c, cudaMemcpyAsync(V.cost, out->cost, n * sizeof(float), kind_in(out->mem), c->stream));
+        else
+            CK(c, launch_cost(rc, V.plane, V.cost, nullptr, c->stream));
+    }
+    RefConst rcp = rc;
+    if (c->prof) rcp.eval_counter = c->evals;
+    for (int ph = p->phase_begin; ph < pend; ++ph) {
+        if (c->prof) {
+            while (c->ev.size() < c->ev_used + 2) {
+                cudaEvent_t e;
+                CK(c, cudaEventCreate(&e));
+                c->ev.push_back(e);
+            }
+            CK(c, cudaEventRecord(c->ev[c->ev_used], c->stream));
+        }
+        CK(c, launch_phase(rcp, ph, c->stream));
+        if (c->prof) {
+            CK(c, cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+            c->ev_used += 2;
+        }
+    }
+    V.has_map = true;
+    CK(c, cudaMemcpyAsync(out->plane, V.plane, n * sizeof(float4), kind_out(out->mem), c->stream));
+    CK(c, cudaMemcpyAsync(out->cost, V.cost, n * sizeof(float), kind_out(out->mem), c->stream));
+    if (out->mem == MVS_MEM_HOST) CK(c, cudaStreamSynchronize(c->stream));
+    return MVS_OK;
+}
+
+mvs_status mvs_plane_cost(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src, const mvs_pm_params* p,
+                          const float* plane, float* cost, float* view_cost, int32_t mem) {
+    mvs_status st = check_pm(c, ref, srcs, n_src, p);
+    if (st != MVS_OK) return st;
+    if (!plane || !cost) return fail(c, MVS_EINVAL, "plane or cost is NULL");
+    if (((uintptr_t)plane & 15u) || ((uintptr_t)cost & 3u) || ((uintptr_t)view_cost & 3u))
+        return fail(c, MVS_EINVAL, "plane must be 16-byte and costs 4-byte aligned");
+    if (mem != MVS_MEM_DEVICE && mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    CK(c, cudaSetDevice(c->device));
+    ViewData& V = c->views[ref];
+    size_t n = (size_t)V.cam.width * V.cam.height;
+    RefConst rc;
+    make_refconst(c, ref, srcs, n_src, p, rc);
+    const float4* pl_d = (const float4*)plane;
+    float* cost_d = cost;
+    float* vc_d = view_cost;
+    cudaError_t e;
+    if (mem == MVS_MEM_HOST) {
+        char* buf = (char*)scratch(c, 0, n * (sizeof(float4) + sizeof(float) * (1 + n_src)), &e);
+        CK(c, e);
+        pl_d = (const float4*)buf;
+        cost_d = (float*)(buf + n * sizeof(float4));
+        vc_d = view_cost ? cost_d + n : nullptr;
+        CK(c, cudaMemcpyAsync((void*)pl_d, plane, n * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(c, launch_cost(rc, pl_d, cost_d, vc_d, c->stream));
+    if (mem == MVS_MEM_HOST) {
+        CK(c, cudaMemcpyAsync(cost, cost_d, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        if (view_cost)
+            CK(c, cudaMemcpyAsync(view_cost, vc_d, n * n_src * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return MVS_OK;
+}
+
+mvs_status mvs_geo_filter(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src, const mvs_filter_params* fp,
+                          uint8_t* keep_mask, int32_t* count, int32_t mem) {
+    mvs_status st = check_view(c, ref);
+    if (st != MVS_OK) return st;
+    if (!fp || !keep_mask) return fail(c, MVS_EINVAL, "params or keep_mask is NULL");
+    if (!srcs || n_src < 1 || n_src > MVS_MAX_SRC) return fail(c, MVS_EINVAL, "need 1..%d sources", MVS_MAX_SRC);
+    if (mem != MVS_MEM_DEVICE && mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    for (int i = 0; i < n_src; ++i)
+        if (srcs[i] < 0 || srcs[i] >= (int32_t)c->views.size() || srcs[i] == ref)
+            return fail(c, MVS_EINVAL, "bad source view %d", srcs[i]);
+    if (!c->views[ref].has_map) return fail(c, MVS_ESTATE, "view %d has no depth map", ref);
+    for (int i = 0; i < n_src; ++i)
+        if (!c->views[srcs[i]].has_map) return fail(c, MVS_ESTATE, "source view %d has no depth map", srcs[i]);
+    CK(c, cudaSetDevice(c->device));
+    const ViewData& V = c->views[ref];
+    FilterConst fc;
+    std::memset(&fc, 0, sizeof fc);
+    fc.W = V.cam.width;
+    fc.H = V.cam.height;
+    for (int i = 0; i < 9; ++i) { fc.K[i] = (float)V.cam.K[i]; fc.Kinv[i] = (float)V.Kinv[i]; }
+    fc.plane = V.plane;
+    fc.n_src = n_src;
+    for (int j = 0; j < n_src; ++j) {
+        const ViewData& S = c->views[srcs[j]];
+        double Rr[9], tr[3];
+        rel_pose(V.cam, S.cam, Rr, tr);
+        auto& s = fc.src[j];
+        for (int i = 0; i < 9; ++i) { s.R[i] = (float)Rr[i]; s.K[i] = (float)S.cam.K[i]; s.Kinv[i] = (float)S.Kinv[i]; }
+        for (int i = 0; i < 3; ++i) s.t[i] = (float)tr[i];
+        s.plane = S.plane;
+        s.W = S.cam.width;
+        s.H = S.cam.height;
+    }
+    fc.depth_tol = fp->depth_tol;
+    fc.depth_relative = fp->depth_relative;
+    fc.cos_max = (float)std::cos(fp->max_angle_deg * 3.14159265358979323846 / 180.0);
+    fc.max_reproj = fp->max_reproj_px;
+    fc.min_consistent = fp->min_consistent;
+    size_t n = (size_t)fc.W * fc.H;
+    uint8_t* keep_d = keep_mask;
+    int32_t* cnt_d = count;
+    cudaError_t e;
+    if (mem == MVS_MEM_HOST) {
+        char* buf = (char*)scratch(c, 0, n * (1 + sizeof(int32_t)) + 16, &e);
+        CK(c, e);
+        cnt_d = (int32_t*)buf;
+        keep_d = (uint8_t*)(buf + n * sizeof(int32_t));
+    }
+    CK(c, launch_geo_filter(fc, keep_d, cnt_d, c->stream));
+    if (mem == MVS_MEM_HOST) {
+        CK(c, cudaMemcpyAsync(keep_mask, keep_d, n, cudaMemcpyDeviceToHost, c->stream));
+        if (count) CK(c, cudaMemcpyAsync(count, cnt_d, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return MVS_OK;
+}
+
+mvs_status mvs_phi_hypotheses(mvs_ctx* c, int32_t W, int32_t H, const float* depth, const uint8_t* known,
+                              const mvs_phi_params* phi, float d_lo, float d_hi, float* hyp, uint8_t* valid,
+                              int32_t mem) {
+    if (!c) return MVS_EINVAL;
+    if (!depth || !known || !phi || !hyp || !valid) return fail(c, MVS_EINVAL, "NULL argument");
+    if (W < 2 || H < 2 || W > 32768 || H > 32768) return fail(c, MVS_EINVAL, "bad size");
+    if (phi->n_fit < 2 || phi->n_fit > 32) return fail(c, MVS_EINVAL, "n_fit must be in 2..32");
+    if (mem != MVS_MEM_DEVICE && mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    CK(c, cudaSetDevice(c->device));
+    size_t n = (size_t)W * H;
+    cudaError_t e;
+    int32_t* work = (int32_t*)scratch(c, 1, n * 8 * sizeof(int32_t), &e);
+    CK(c, e);
+    const float* dd = depth;
+    const uint8_t* kd = known;
+    float* hd = hyp;
+    uint8_t* vd = valid;
+    if (mem == MVS_MEM_HOST) {
+        char* buf = (char*)scratch(c, 0, n * (sizeof(float) * 5 + 5) + 64, &e);
+        CK(c, e);
+        hd = (float*)buf;
+        float* dd2 = hd + 4 * n;
+        uint8_t* kd2 = (uint8_t*)(dd2 + n);
+        vd = kd2 + n;
+        CK(c, cudaMemcpyAsync(dd2, depth, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(kd2, known, n, cudaMemcpyHostToDevice, c->stream));
+        dd = dd2;
+        kd = kd2;
+    }
+    CK(c, launch_phi_hypotheses(W, H, dd, kd, phi->n_fit, phi->fit_inverse, d_lo, d_hi, hd, vd, work, c->stream));
+    if (mem == MVS_MEM_HOST) {
+        CK(c, cudaMemcpyAsync(hyp, hd, n * 4 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaMemcpyAsync(valid, vd, n * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return MVS_OK;
+}
+
+mvs_status mvs_phi_cost(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src, const mvs_pm_params* pm,
+                        const float* hyp, const uint8_t* valid, float* hcost, int32_t mem) {
+    mvs_status st = check_pm(c, ref, srcs, n_src, pm);
+    if (st != MVS_OK) return st;
+    if (!hyp || !valid || !hcost) return fail(c, MVS_EINVAL, "NULL argument");
+    if (mem != MVS_MEM_DEVICE && mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    CK(c, cudaSetDevice(c->device));
+    const ViewData& V = c->views[ref];
+    size_t n = (size_t)V.cam.width * V.cam.height;
+    RefConst rc;
+    make_refconst(c, ref, srcs, n_src, pm, rc);
+    const float* hd = hyp;
+    const uint8_t* vd = valid;
+    float* cd = hcost;
+    cudaError_t e;
+    if (mem == MVS_MEM_HOST) {
+        char* buf = (char*)scratch(c, 0, n * (8 * sizeof(float) + 4) + 64, &e);
+        CK(c, e);
+        float* h2 = (float*)buf;
+        cd = h2 + 4 * n;
+        uint8_t* v2 = (uint8_t*)(cd + 4 * n);
+        CK(c, cudaMemcpyAsync(h2, hyp, n * 4 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(v2, valid, n * 4, cudaMemcpyHostToDevice, c->stream));
+        hd = h2;
+        vd = v2;
+    }
+    CK(c, launch_phi_cost(rc, hd, vd, cd, c->stream));
+    if (mem == MVS_MEM_HOST) {
+        CK(c, cudaMemcpyAsync(hcost, cd, n * 4 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return MVS_OK;
+}
+
+mvs_status mvs_phi_mrf(mvs_ctx* c, int32_t W, int32_t H, const uint8_t* known, const float* depth, const float* hyp,
+                       const uint8_t* valid, const float* hcost, const mvs_phi_params* phi, int32_t* label,
+                       int32_t mem) {
+    if (!c) return MVS_EINVAL;
+    if (!known || !depth || !hyp || !valid || !hcost || !phi || !label) return fail(c, MVS_EINVAL, "NULL argument");
+    if (W < 2 || H < 2 || W > 32768 || H > 32768) return fail(c, MVS_EINVAL, "bad size");
+    if (phi->trw_iters < 0 || phi->trw_iters > 1000) return fail(c, MVS_EINVAL, "trw_iters outside 0..1000");
+    if (!(phi->kappa1 > 0) || !(phi->kappa2 > 0) || !(phi->kappa3 > 1))
+        return fail(c, MVS_EINVAL, "need kappa1 > 0, kappa2 > 0, kappa3 > 1");
+    if (mem != MVS_MEM_DEVICE && mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    CK(c, cudaSetDevice(c->device));
+    size_t n = (size_t)W * H;
+    int gw = (W + 1) / 2, gh = (H + 1) / 2;
+    size_t g = (size_t)gw * gh;
+    cudaError_t e;
+    float* work = (float*)scratch(c, 2, phi_mrf_work_floats(W, H) * sizeof(float), &e);
+    CK(c, e);
+    const uint8_t* kd = known;
+    const float* dd = depth;
+    const float* hd = hyp;
+    const uint8_t* vd = valid;
+    const float* cd = hcost;
+    int32_t* ld = label;
+    if (mem == MVS_MEM_HOST) {
+        char* buf = (char*)scratch(c, 0, n * (9 * sizeof(float) + 5) + g * sizeof(int32_t) + 64, &e);
+        CK(c, e);
+        float* h2 = (float*)buf;
+        float* c2 = h2 + 4 * n;
+        float* d2 = c2 + 4 * n;
+        int32_t* l2 = (int32_t*)(d2 + n);
+        uint8_t* k2 = (uint8_t*)(l2 + g);
+        uint8_t* v2 = k2 + n;
+        CK(c, cudaMemcpyAsync(h2, hyp, n * 4 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c2, hcost, n * 4 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(d2, depth, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(k2, known, n, cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(v2, valid, n * 4, cudaMemcpyHostToDevice, c->stream));
+        kd = k2; dd = d2; hd = h2; vd = v2; cd = c2; ld = l2;
+    }
+    CK(c, launch_phi_mrf(W, H, kd, dd, hd, vd, cd, phi->kappa1, phi->kappa2, phi->kappa3, phi->trw_iters, ld, work,
+                         c->stream));
+    if (mem == MVS_MEM_HOST) {
+        CK(c, cudaMemcpyAsync(label, ld, g * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return MVS_OK;
+}
+
+mvs_status mvs_phi_select(mvs_ctx* c, int32_t ref, const uint8_t* known, const float* hyp, const uint8_t* valid,
+                          const int32_t* label, float* plane, int32_t mem) {
+    mvs_status st = check_view(c, ref);
+    if (st != MVS_OK) return st;
+    if (!known || !hyp || !valid || !label || !plane) return fail(c, MVS_EINVAL, "NULL argument");
+    if (((uintptr_t)plane & 15u) || ((uintptr_t)hyp & 3u) || ((uintptr_t)label & 3u))
+        return fail(c, MVS_EINVAL, "plane must be 16-byte, hyp and label 4-byte aligned");
+    if (mem != MVS_MEM_DEVICE && mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    CK(c, cudaSetDevice(c->device));
+    const ViewData& V = c->views[ref];
+    int W = V.cam.width, H = V.cam.height;
+    size_t n = (size_t)W * H;
+    size_t g = (size_t)((W + 1) / 2) * ((H + 1) / 2);
+    RefConst rc;
+    std::memset(&rc, 0, sizeof rc);
+    rc.W = W;
+    rc.H = H;
+    for (int i = 0; i < 9; ++i) rc.Kinv[i] = (float)V.Kinv[i];
+    cudaError_t e;
+    float* newd = (float*)scratch(c, 3, n * sizeof(float), &e);
+    CK(c, e);
+    const uint8_t* kd = known;
+    const float* hd = hyp;
+    const uint8_t* vd = valid;
+    const int32_t* ld = label;
+    float4* pd = (float4*)plane;
+    if (mem == MVS_MEM_HOST) {
+        char* buf = (char*)scratch(c, 0, n * (8 * sizeof(float) + 5) + g * sizeof(int32_t) + 64, &e);
+        CK(c, e);
+        float4* p2 = (float4*)buf;
+        float* h2 = (float*)(p2 + n);
+        int32_t* l2 = (int32_t*)(h2 + 4 * n);
+        uint8_t* k2 = (uint8_t*)(l2 + g);
+        uint8_t* v2 = k2 + n;
+        CK(c, cudaMemcpyAsync(p2, plane, n * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(h2, hyp, n * 4 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(l2, label, g * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(k2, known, n, cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(v2, valid, n * 4, cudaMemcpyHostToDevice, c->stream));
+        kd = k2; hd = h2; vd = v2; ld = l2; pd = p2;
+    }
+    CK(c, launch_phi_select(rc, kd, hd, vd, ld, pd, newd, c->stream));
+    if (mem == MVS_MEM_HOST) {
+        CK(c, cudaMemcpyAsync(plane, pd, n * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return MVS_OK;
+}
+
+mvs_status mvs_plane_infer(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src, const mvs_pm_params* pm,
+                           const mvs_phi_params* phi, const uint8_t* keep_mask, mvs_depth_map* inout) {
+    mvs_status st = check_pm(c, ref, srcs, n_src, pm);
+    if (st != MVS_OK) return st;
+    if (!phi || !inout || !inout->plane || !inout->cost) return fail(c, MVS_EINVAL, "NULL argument");
+    if (((uintptr_t)inout->plane & 15u) || ((uintptr_t)inout->cost & 3u))
+        return fail(c, MVS_EINVAL, "plane must be 16-byte and cost 4-byte aligned");
+    if (inout->mem != MVS_MEM_DEVICE && inout->mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    if (phi->n_fit < 2 || phi->n_fit > 32) return fail(c, MVS_EINVAL, "n_fit must be in 2..32");
+    if (phi->trw_iters < 0 || phi->trw_iters > 1000) return fail(c, MVS_EINVAL, "trw_iters outside 0..1000");
+    if (!(phi->kappa1 > 0) || !(phi->kappa2 > 0) || !(phi->kappa3 > 1))
+        return fail(c, MVS_EINVAL, "need kappa1 > 0, kappa2 > 0, kappa3 > 1");
+    CK(c, cudaSetDevice(c->device));
+    if ((st = ensure_map(c, ref)) != MVS_OK) return st;
+    ViewData& V = c->views[ref];
+    int W = V.cam.width, H = V.cam.height;
+    size_t n = (size_t)W * H;
+    size_t g = (size_t)((W + 1) / 2) * ((H + 1) / 2);
+    int32_t mem = inout->mem;
+    CK(c, cudaMemcpyAsync(V.plane, inout->plane, n * sizeof(float4), kind_in(mem), c->stream));
+    CK(c, cudaMemcpyAsync(V.cost, inout->cost, n * sizeof(float), kind_in(mem), c->stream));
+    cudaError_t e;
+    // layout of scratch slot 4: hyp(4n f) hcost(4n f) depth(n f) newd(n f) label(g i) known(n) valid(4n)
+    char* buf = (char*)scratch(c, 4, n * (10 * sizeof(float) + 5) + g * sizeof(int32_t) + 256, &e);
+    CK(c, e);
+    float* hyp = (float*)buf;
+    float* hcost = hyp + 4 * n;
+    float* depth = hcost + 4 * n;
+    float* newd = depth + n;
+    int32_t* label = (int32_t*)(newd + n);
+    uint8_t* known = (uint8_t*)(label + g);
+    uint8_t* valid = known + n;
+    int32_t* work = (int32_t*)scratch(c, 1, n * 8 * sizeof(int32_t), &e);
+    CK(c, e);
+    float* mwork = (float*)scratch(c, 2, phi_mrf_work_floats(W, H) * sizeof(float), &e);
+    CK(c, e);
+    if (keep_mask) {
+        CK(c, cudaMemcpyAsync(known, keep_mask, n, kind_in(mem), c->stream));
+        CK(c, launch_depth_of(W, H, V.plane, known, depth, c->stream));
+    } else {
+        CK(c, launch_known_from_cost(W, H, V.plane, V.cost, phi->hole_cost, known, depth, c->stream));
+    }
+    RefConst rc;
+    make_refconst(c, ref, srcs, n_src, pm, rc);
+    CK(c, launch_phi_hypotheses(W, H, depth, known, phi->n_fit, phi->fit_inverse, pm->d_lo, pm->d_hi, hyp, valid,
+                                work, c->stream));
+    CK(c, launch_phi_cost(rc, hyp, valid, hcost, c->stream));
+    CK(c, launch_phi_mrf(W, H, known, depth, hyp, valid, hcost, phi->kappa1, phi->kappa2, phi->kappa3,
+                         phi->trw_iters, label, mwork, c->stream));
+    CK(c, launch_phi_select(rc, known, hyp, valid, label, V.plane, newd, c->stream));
+    V.has_map = true;
+    CK(c, cudaMemcpyAsync(inout->plane, V.plane, n * sizeof(float4), kind_out(mem), c->stream));
+    if (mem == MVS_MEM_HOST) CK(c, cudaStreamSynchronize(c->stream));
+    return MVS_OK;
+}
+
+mvs_status mvs_profile(mvs_ctx* c, int32_t enable) {
+    if (!c) return MVS_EINVAL;
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->prof = enable != 0;
+    c->ev_used = 0;
+    c->launches0 = g_kernel_launches.load();
+    if (!c->evals) CK(c, cudaMalloc(&c->evals, sizeof(unsigned long long)));
+    CK(c, cudaMemsetAsync(c->evals, 0, sizeof(unsigned long long), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return MVS_OK;
+}
+
+mvs_status mvs_profile_read(mvs_ctx* c, double* phase_ms, int64_t* phase_launches, int64_t* kernel_launches,
+                            int64_t* phase_evals) {
+    if (!c) return MVS_EINVAL;
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (phase_evals) {
+        unsigned long long v = 0;
+        if (c->evals) CK(c, cudaMemcpy(&v, c->evals, sizeof v, cudaMemcpyDeviceToHost));
+        *phase_evals = (int64_t)v;
+    }
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+        float t = 0.0f;
+        CK(c, cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
+        ms += t;
+    }
+    if (phase_ms) *phase_ms = ms;
+    if (phase_launches) *phase_launches = (int64_t)(c->ev_used / 2);
+    if (kernel_launches) *kernel_launches = (int64_t)(g_kernel_launches.load() - c->launches0);
+    return MVS_OK;
+}
+
+}  // extern "C"

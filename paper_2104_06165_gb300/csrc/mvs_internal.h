@@ -1,0 +1,106 @@
+// Internal data layout shared by the host and device translation units of
+// the library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define MVS_MAX_SRC 32
+#define MVS_MAX_WIN 22
+
+// One source view as seen from a reference view.
+//   A = K_j R_rel K_ref^-1, b = K_j t_rel (row-major, float, computed in double
+//   on the host), so that the plane-induced homography of a plane (n, d) at
+//   reference pixel x is H = A + b m^T with m = K_ref^-T n / rho,
+//   rho = d n.K_ref^-1 x  (Sec. III-C homography mapping).
+struct PairConst {
+    float A[9];
+    float b[3];
+    const float4* tex;   // bilinear-coefficient texels of the source, see below
+    int W, H;            // source image size
+    int pitch;           // texel row pitch = W + 1
+    uint32_t n_tex;      // (W + 1) * (H + 1)
+};
+
+// Per reference-view launch constants (kernel parameter, < 4 KB).
+struct RefConst {
+    int W, H;
+    int ref_index;
+    int n_src;
+    float Kinv[9];
+    const float4* tex;         // reference bilinear-coefficient texels
+    const uint8_t* img;        // reference image (uint8)
+    int pitch;                 // W + 1
+    uint32_t n_tex;
+    // window (Sec. III-C): n samples per axis, offsets step * (k - (n-1)/2)
+    int n;
+    float step;
+    float sp_coef;             // -1 / (2 sigma_s^2) (0 = no spatial weight)
+    float col_coef;            // -1 / (2 (255 sigma_c)^2) (0 = no colour weight)
+    float d_lo, d_hi;
+    unsigned long long seed;
+    float4* plane;             // state: (n.x, n.y, n.z, depth) per pixel
+    float* cost;               // state: aggregated cost per pixel
+    unsigned long long* eval_counter;  // measurement: evaluated (pixel, hypothesis, view) triples, or null
+    PairConst pair[MVS_MAX_SRC];
+};
+
+// Bilinear-coefficient texel layout.  Texel (i, j), i in [-1, W-1],
+// j in [-1, H-1], stored at ((j + 1) * (W + 1) + (i + 1)), holds, for the
+// clamped taps p00 = I(i, j), p01 = I(i+1, j), p10 = I(i, j+1),
+// p11 = I(i+1, j+1) on the [0, 255] scale:
+//   .x = (p00 + p01 + p10 + p11) / 4
+//   .y = ((p01 - p00) + (p11 - p10)) / 2
+//   .z = ((p10 - p00) + (p11 - p01)) / 2
+//   .w = p00 - p01 - p10 + p11
+// so that the bilinear value at (i + 0.5 + u, j + 0.5 + v), |u|,|v| <= 1/2,
+// is x + u y + v z + u v w (every coefficient is a multiple of 1/4 and exact).
+
+// Status word written by kernels (bounded waits, bounds checks).
+enum { MVS_DEV_OK = 0, MVS_DEV_TIMEOUT = 1, MVS_DEV_BOUNDS = 2 };
+
+// Number of kernels the library has launched (all contexts); every launcher
+// adds its launches so that a caller can count the kernels of a timed region.
+#include <atomic>
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launch(long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Host-side launchers (pm_kernels.cu / phi_kernels.cu).
+cudaError_t launch_build_texture(const uint8_t* img, int W, int H, float4* tex, cudaStream_t s);
+cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s);
+cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, float* view_cost, cudaStream_t s);
+cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s);
+int pm_group_lanes(int n_samples);
+
+struct FilterConst {
+    int W, H;
+    float K[9], Kinv[9];
+    const float4* plane;
+    int n_src;
+    struct Src {
+        float R[9], t[3];      // X_j = R X_ref + t
+        float K[9], Kinv[9];
+        const float4* plane;
+        int W, H;
+    } src[MVS_MAX_SRC];
+    float depth_tol;
+    int depth_relative;
+    float cos_max;
+    float max_reproj;
+    int min_consistent;
+};
+cudaError_t launch_geo_filter(const FilterConst& fc, uint8_t* keep, int32_t* count, cudaStream_t s);
+
+cudaError_t launch_phi_hypotheses(int W, int H, const float* depth, const uint8_t* known, int n_fit, int inverse,
+                                  float d_lo, float d_hi, float* hyp, uint8_t* valid, int32_t* scratch,
+                                  cudaStream_t s);
+cudaError_t launch_phi_cost(const RefConst& rc, const float* hyp, const uint8_t* valid, float* hcost,
+                            cudaStream_t s);
+cudaError_t launch_phi_mrf(int W, int H, const uint8_t* known, const float* depth, const float* hyp,
+                           const uint8_t* valid, const float* hcost, float k1, float k2, float k3, int iters,
+                           int32_t* label, float* work, cudaStream_t s);
+size_t phi_mrf_work_floats(int W, int H);
+cudaError_t launch_phi_select(const RefConst& rc, const uint8_t* known, const float* hyp, const uint8_t* valid,
+                              const int32_t* label, float4* plane, float* newdepth, cudaStream_t s);
+cudaError_t launch_known_from_cost(int W, int H, const float4* plane, const float* cost, float hole_cost,
+                                   uint8_t* known, float* depth, cudaStream_t s);
+cudaError_t launch_depth_of(int W, int H, const float4* plane, const uint8_t* known, float* depth, cudaStream_t s);

@@ -1,0 +1,551 @@
+// Geometric-consistency filter (Sec. III-D) and plane hypothesis inference
+// (Sec. III-E): four-direction line-fit hypotheses, their matching cost, the
+// pairwise MRF of Eq. 6-9 decoded by tree-reweighted message passing at half
+// resolution, closest-hypothesis selection and Eq. 10 normals.
+#include "pm_device.cuh"
+
+using namespace mvsdev;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Sec. III-D: geometric consistency.  Reading: the z-depth of X in view j is
+// compared with the bilinear depth of view j at x'_j (a tap without depth
+// makes the view inconsistent); the normal of view j at the rounded x'_j is
+// rotated into the reference frame and compared sign-agnostically; the
+// reprojection goes back through d_j(x'_j).  Kept with >= min_consistent.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mat3v(const float* M, float a, float b, float c, float& o0, float& o1, float& o2) {
+    o0 = fmaf(M[0], a, fmaf(M[1], b, M[2] * c));
+    o1 = fmaf(M[3], a, fmaf(M[4], b, M[5] * c));
+    o2 = fmaf(M[6], a, fmaf(M[7], b, M[8] * c));
+}
+
+__global__ void k_geo_filter(const __grid_constant__ FilterConst fc, uint8_t* __restrict__ keep,
+                             int32_t* __restrict__ count) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)fc.W * fc.H) return;
+    int x = (int)(i % fc.W), y = (int)(i / fc.W);
+    float4 pl = fc.plane[i];
+    int cnt = 0;
+    if (pl.w > 0.0f) {
+        float r0, r1, r2;
+        mat3v(fc.Kinv, (float)x, (float)y, 1.0f, r0, r1, r2);
+        float X0 = pl.w * r0, X1 = pl.w * r1, X2 = pl.w * r2;
+        for (int jj = 0; jj < fc.n_src; ++jj) {
+            const FilterConst::Src& S = fc.src[jj];
+            float Y0, Y1, Y2;
+            mat3v(S.R, X0, X1, X2, Y0, Y1, Y2);
+            Y0 += S.t[0]; Y1 += S.t[1]; Y2 += S.t[2];
+            if (!(Y2 > 0.0f)) continue;
+            float q0, q1, q2;
+            mat3v(S.K, Y0, Y1, Y2, q0, q1, q2);
+            float u = q0 / q2, v = q1 / q2;
+            if (!(u >= 0.0f && u <= (float)(S.W - 1) && v >= 0.0f && v <= (float)(S.H - 1))) continue;
+            int x0 = (int)floorf(u), y0 = (int)floorf(v);
+            int x1 = min(x0 + 1, S.W - 1), y1 = min(y0 + 1, S.H - 1);
+            float da = S.plane[(long long)y0 * S.W + x0].w, db = S.plane[(long long)y0 * S.W + x1].w;
+            float dc = S.plane[(long long)y1 * S.W + x0].w, de = S.plane[(long long)y1 * S.W + x1].w;
+            if (!(da > 0.0f && db > 0.0f && dc > 0.0f && de > 0.0f)) continue;
+            float fx = u - (float)x0, fy = v - (float)y0;
+            float dj = (1.0f - fy) * ((1.0f - fx) * da + fx * db) + fy * ((1.0f - fx) * dc + fx * de);
+            float diff = fabsf(dj - Y2);
+            if (fc.depth_relative) diff /= Y2;
+            if (!(diff < fc.depth_tol)) continue;
+            int xn = min((int)floorf(u + 0.5f), S.W - 1), yn = min((int)floorf(v + 0.5f), S.H - 1);
+            float4 nj = S.plane[(long long)yn * S.W + xn];
+            // R^T n_j
+            float m0 = S.R[0] * nj.x + S.R[3] * nj.y + S.R[6] * nj.z;
+            float m1 = S.R[1] * nj.x + S.R[4] * nj.y + S.R[7] * nj.z;
+            float m2 = S.R[2] * nj.x + S.R[5] * nj.y + S.R[8] * nj.z;
+            float cs = fabsf(pl.x * m0 + pl.y * m1 + pl.z * m2) /
+                       sqrtf((pl.x * pl.x + pl.y * pl.y + pl.z * pl.z) * (m0 * m0 + m1 * m1 + m2 * m2));
+            if (!(cs > fc.cos_max)) continue;
+            float s0, s1, s2;
+            mat3v(S.Kinv, u, v, 1.0f, s0, s1, s2);
+            float Z0 = dj * s0 - S.t[0], Z1 = dj * s1 - S.t[1], Z2 = dj * s2 - S.t[2];
+            float B0 = S.R[0] * Z0 + S.R[3] * Z1 + S.R[6] * Z2;
+            float B1 = S.R[1] * Z0 + S.R[4] * Z1 + S.R[7] * Z2;
+            float B2 = S.R[2] * Z0 + S.R[5] * Z1 + S.R[8] * Z2;
+            if (!(B2 > 0.0f)) continue;
+            float e0, e1, e2;
+            mat3v(fc.K, B0, B1, B2, e0, e1, e2);
+            float eu = e0 / e2 - (float)x, ev = e1 / e2 - (float)y;
+            if (!(sqrtf(eu * eu + ev * ev) < fc.max_reproj)) continue;
+            cnt++;
+        }
+    }
+    if (count) count[i] = cnt;
+    keep[i] = (uint8_t)(pl.w > 0.0f && cnt >= fc.min_consistent);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. III-E hypotheses.  Direction k: 0 horizontal (1,0), 1 vertical (0,1),
+// 2 diagonal 45 deg below (1,1), 3 diagonal 45 deg above (1,-1).  A line of
+// direction k is indexed by its first pixel; gap[k][side][p] holds the
+// distance in steps from p to the nearest reconstructed pixel strictly
+// before (side 0) or after (side 1) p along the line, 0 if there is none.
+// ---------------------------------------------------------------------------
+__constant__ int c_dir[4][2] = {{1, 0}, {0, 1}, {1, 1}, {1, -1}};
+
+__device__ __forceinline__ int n_lines(int k, int W, int H) { return k == 0 ? H : (k == 1 ? W : W + H - 1); }
+
+// start pixel of line l of direction k
+__device__ __forceinline__ void line_start(int k, int l, int W, int H, int& x, int& y) {
+    if (k == 0) { x = 0; y = l; }
+    else if (k == 1) { x = l; y = 0; }
+    else if (k == 2) {          // step (1,1): starts on the left column (bottom up) then the top row
+        if (l < H) { x = 0; y = H - 1 - l; } else { x = l - H + 1; y = 0; }
+    } else {                    // step (1,-1): starts on the left column then the bottom row
+        if (l < H) { x = 0; y = l; } else { x = l - H + 1; y = H - 1; }
+    }
+}
+
+__global__ void k_line_gaps(int W, int H, const uint8_t* __restrict__ known, int32_t* __restrict__ gaps) {
+    const long long N = (long long)W * H;
+    int k = blockIdx.y;
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n_lines(k, W, H)) return;
+    int sx = c_dir[k][0], sy = c_dir[k][1];
+    int x0, y0;
+    line_start(k, l, W, H, x0, y0);
+    int32_t* before = gaps + (long long)(2 * k) * N;
+    int32_t* after = gaps + (long long)(2 * k + 1) * N;
+    // forward walk: distance to the previous reconstructed pixel
+    int last = -1, t = 0;
+    for (int x = x0, y = y0; x >= 0 && x < W && y >= 0 && y < H; x += sx, y += sy, ++t) {
+        long long p = (long long)y * W + x;
+        before[p] = last >= 0 ? t - last : 0;
+        if (known[p]) last = t;
+    }
+    // backward walk: distance to the next reconstructed pixel
+    int len = t;
+    last = -1;
+    for (int s = len - 1; s >= 0; --s) {
+        int x = x0 + s * sx, y = y0 + s * sy;
+        long long p = (long long)y * W + x;
+        after[p] = last >= 0 ? last - s : 0;
+        if (known[p]) last = s;
+    }
+}
+
+// least-squares line v = a + b t through the n_fit reconstructed pixels
+// nearest along the line (negative side first at equal distance), value at
+// t = 0; centred normal equations in float
+__global__ void k_line_fit(int W, int H, const float* __restrict__ depth, const uint8_t* __restrict__ known,
+                           const int32_t* __restrict__ gaps, int n_fit, int inverse, float d_lo, float d_hi,
+                           float* __restrict__ hyp, uint8_t* __restrict__ valid) {
+    const long long N = (long long)W * H;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int x = (int)(i % W), y = (int)(i / W);
+    bool hole = !known[i];
+    for (int k = 0; k < 4; ++k) {
+        float h = 0.0f;
+        bool ok = false;
+        if (hole) {
+            const int32_t* before = gaps + (long long)(2 * k) * N;
+            const int32_t* after = gaps + (long long)(2 * k + 1) * N;
+            int sx = c_dir[k][0], sy = c_dir[k][1];
+            int dl = before[i], dr = after[i];   // distances of the next candidates on each side (0 = none)
+            float ts[32], vs[32];
+            int m = 0;
+            float tsum = 0.0f;
+            while (m < n_fit && (dl > 0 || dr > 0)) {
+                bool take_left = dl > 0 && (dr == 0 || dl <= dr);
+                int dist = take_left ? dl : dr;
+                int side = take_left ? -1 : 1;
+                long long q = (long long)(y + side * dist * sy) * W + (x + side * dist * sx);
+                float dv = depth[q];
+                ts[m] = (float)(side * dist);
+                vs[m] = inverse ? 1.0f / dv : dv;
+                tsum += ts[m];
+                m++;
+                if (take_left) {
+                    int g = before[q];
+                    dl = g > 0 ? dl + g : 0;
+                } else {
+                    int g = after[q];
+                    dr = g > 0 ? dr + g : 0;
+                }
+            }
+            if (m >= 2) {
+                float tm = tsum / (float)m, vm = 0.0f;
+                for (int a = 0; a < m; ++a) vm += vs[a];
+                vm /= (float)m;
+                float stt = 0.0f, stv = 0.0f;
+                for (int a = 0; a < m; ++a) {
+                    float dt = ts[a] - tm;
+                    stt = fmaf(dt, dt, stt);
+                    stv = fmaf(dt, vs[a] - vm, stv);
+                }
+                float b = stv / stt;
+                float av = vm - b * tm;
+                h = inverse ? 1.0f / av : av;
+                ok = h >= d_lo && h <= d_hi;
+            }
+        }
+        hyp[4 * i + k] = ok ? h : 0.0f;
+        valid[4 * i + k] = ok ? 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// hypothesis cost: fronto-parallel plane z = h, n = (0, 0, -1) (Sec. III-E)
+// ---------------------------------------------------------------------------
+constexpr int kBlock = 128;
+
+template <int G, int S>
+__global__ void __launch_bounds__(kBlock) k_phi_cost(const __grid_constant__ RefConst rc, const float* __restrict__ hyp,
+                                                      const uint8_t* __restrict__ valid, float* __restrict__ hcost) {
+    const int lane = threadIdx.x & 31;
+    const long long npix = (long long)rc.W * rc.H;
+    const long long a = ((long long)blockIdx.x * kBlock + threadIdx.x) / G;
+    if (((long long)blockIdx.x * kBlock + (threadIdx.x & ~31)) / G >= npix) return;
+    const bool exists = a < npix;
+    const int px = exists ? (int)(a % rc.W) : 0, py = exists ? (int)(a / rc.W) : 0;
+    uint32_t vmask = 0u;
+    if (exists)
+        for (int k = 0; k < 4; ++k) vmask |= (uint32_t)(valid[4 * a + k] != 0) << (8 * k);
+    if (!__any_sync(0xffffffffu, vmask != 0u)) {
+        if (exists && (lane & (G - 1)) == 0)
+            for (int k = 0; k < 4; ++k) hcost[4 * a + k] = kCmax;
+        return;
+    }
+    PixWin<S> pw;
+    build_window<G, S>(rc, px, py, exists, pw);
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        bool v = ((vmask >> (8 * k)) & 0xFFu) != 0u;
+        float h = exists ? hyp[4 * a + k] : 1.0f;
+        unsigned nev = 0;
+        float c = eval_hyp<G, S, false>(rc, pw, px, py, 0.0f, 0.0f, -1.0f, h, v, nullptr, nev);
+        if (exists && (lane & (G - 1)) == 0) hcost[4 * a + k] = v ? c : kCmax;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// MRF (Eq. 6-9) at half resolution (node (gx, gy) <- pixel (2gx, 2gy)).
+// Reading: TRW = sequential tree-reweighted min-sum message passing with
+// rows and columns as monotonic chains (node weight 1 / max(#earlier,
+// #later present neighbours)); one iteration = forward pass in raster order +
+// backward pass; decode = per-node argmin of the belief (lowest label on a
+// tie).  The raster order is run as anti-diagonal wavefronts (a node only
+// depends on its up / left neighbours in the forward pass and on its down /
+// right neighbours in the backward pass), which gives the same result as the
+// sequential sweep: tiles of T x T nodes are processed one tile-diagonal per
+// launch and, inside a tile, one node-diagonal per __syncthreads step.
+// ---------------------------------------------------------------------------
+constexpr int kT = 32;
+
+struct MrfBufs {
+    int gw, gh;
+    int8_t* nlab;     // labels per node (0 = absent)
+    int8_t* lmap;     // [4] hypothesis index of each label (-1 = reconstructed pixel)
+    float* lab;       // [4] label depths
+    float* un;        // [4] unary energies -log phi_n
+    float* msg;       // [4 dir][4 lab] incoming messages (dir 0 up, 1 down, 2 left, 3 right)
+};
+
+__global__ void k_mrf_setup(int W, int H, MrfBufs mb, const uint8_t* __restrict__ known,
+                            const float* __restrict__ depth, const float* __restrict__ hyp,
+                            const uint8_t* __restrict__ valid, const float* __restrict__ hcost, float k1, float k2) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)mb.gw * mb.gh) return;
+    int gx = (int)(g % mb.gw), gy = (int)(g / mb.gw);
+    long long i = (long long)(2 * gy) * W + 2 * gx;
+    int L = 0;
+    if (known[i]) {
+        mb.lab[4 * g] = depth[i];
+        mb.un[4 * g] = 0.0f;
+        mb.lmap[4 * g] = -1;
+        L = 1;
+    } else {
+        for (int k = 0; k < 4; ++k)
+            if (valid[4 * i + k]) {
+                mb.lab[4 * g + L] = hyp[4 * i + k];
+                mb.un[4 * g + L] = -logf((kCmax - hcost[4 * i + k]) / k1 + k2);   // Eq. 6
+                mb.lmap[4 * g + L] = (int8_t)k;
+                L++;
+            }
+    }
+    mb.nlab[g] = (int8_t)L;
+    for (int k = 0; k < 16; ++k) mb.msg[16 * g + k] = 0.0f;
+}
+
+// -log of Eq. 7: phi_e = [k3 - min(1, relative difference)]^2
+__device__ __forceinline__ float pair_energy(float h1, float h2, float k3) {
+    float rel = h1 > h2 ? (h1 - h2) / h2 : (h2 - h1) / h1;
+    return -2.0f * logf(k3 - fminf(1.0f, rel));
+}
+
+__device__ void trw_node(const MrfBufs& mb, int x, int y, bool forward, float k3) {
+    long long i = (long long)y * mb.gw + x;
+    int L = mb.nlab[i];
+    if (!L) return;
+    const int nbx[4] = {0, 0, -1, 1}, nby[4] = {-1, 1, 0, 0};
+    float bel[4];
+    for (int l = 0; l < 4; ++l) {
+        float b = mb.un[4 * i + l];
+        for (int d = 0; d < 4; ++d) b += mb.msg[16 * i + 4 * d + l];
+        bel[l] = b;
+    }
+    int before = 0, after = 0;
+    bool pres[4];
+    for (int d = 0; d < 4; ++d) {
+        int qx = x + nbx[d], qy = y + nby[d];
+        pres[d] = qx >= 0 && qx < mb.gw && qy >= 0 && qy < mb.gh && mb.nlab[(long long)qy * mb.gw + qx] > 0;
+        if (pres[d]) { if (d == 0 || d == 2) before++; else after++; }
+    }
+    int mx = max(before, after);
+    float gamma = mx > 0 ? 1.0f / (float)mx : 1.0f;
+    for (int d = 0; d < 4; ++d) {
+        bool later = (d == 1 || d == 3);
+        if (later != forward || !pres[d]) continue;
+        long long q = (long long)(y + nby[d]) * mb.gw + (x + nbx[d]);
+        int Lq = mb.nlab[q];
+        float out[4], mn = 3.0e38f;
+        for (int lq = 0; lq < Lq; ++lq) {
+            float best = 3.0e38f;
+            for (int l = 0; l < L; ++l) {
+                float e = gamma * bel[l] - mb.msg[16 * i + 4 * d + l] + pair_energy(mb.lab[4 * i + l], mb.lab[4 * q + lq], k3);
+                best = fminf(best, e);
+            }
+            out[lq] = best;
+            mn = fminf(mn, best);
+        }
+        int od = d ^ 1;
+        for (int lq = 0; lq < Lq; ++lq) mb.msg[16 * q + 4 * od + lq] = out[lq] - mn;
+    }
+}
+
+__global__ void __launch_bounds__(kT) k_trw_diag(MrfBufs mb, int tile_diag, bool forward, float k3) {
+    int ntx = (mb.gw + kT - 1) / kT, nty = (mb.gh + kT - 1) / kT;
+    int D = forward ? tile_diag : (ntx + nty - 2 - tile_diag);
+    int ty_lo = max(0, D - (ntx - 1));
+    int ty = ty_lo + blockIdx.x;
+    int tx = D - ty;
+    if (ty >= nty || tx < 0) return;
+    for (int s = 0; s < 2 * kT - 1; ++s) {
+        int l = forward ? s : (2 * kT - 2 - s);
+        int lx = threadIdx.x, ly = l - lx;
+        if (ly >= 0 && ly < kT) {
+            int x = tx * kT + lx, y = ty * kT + ly;
+            if (x < mb.gw && y < mb.gh) trw_node(mb, x, y, forward, k3);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_trw_decode(MrfBufs mb, int32_t* __restrict__ label) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)mb.gw * mb.gh) return;
+    int L = mb.nlab[i];
+    if (!L) { label[i] = -2; return; }
+    int best = 0;
+    float bv = 3.0e38f;
+    for (int l = 0; l < L; ++l) {
+        float b = mb.un[4 * i + l];
+        for (int d = 0; d < 4; ++d) b += mb.msg[16 * i + 4 * d + l];
+        if (b < bv) { bv = b; best = l; }
+    }
+    label[i] = mb.lmap[4 * i + best];
+}
+
+// ---------------------------------------------------------------------------
+// selection: nearest up-sampled decoded depth is the reference; the closest
+// valid hypothesis (lowest k on a tie) becomes the new depth of a hole
+// ---------------------------------------------------------------------------
+__global__ void k_select(int W, int H, const uint8_t* __restrict__ known, const float* __restrict__ hyp,
+                         const uint8_t* __restrict__ valid, const int32_t* __restrict__ label,
+                         const float4* __restrict__ plane, float* __restrict__ newd) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)W * H) return;
+    int x = (int)(i % W), y = (int)(i / W);
+    if (known[i]) { newd[i] = plane[i].w; return; }
+    int gw = (W + 1) / 2;
+    long long g = (long long)(y / 2) * gw + (x / 2);
+    int lb = label[g];
+    float nd = 0.0f;
+    if (lb >= -1) {
+        long long ni = (long long)(2 * (y / 2)) * W + 2 * (x / 2);
+        float rd = lb == -1 ? plane[ni].w : hyp[4 * ni + lb];
+        float bd = 3.0e38f;
+        for (int k = 0; k < 4; ++k)
+            if (valid[4 * i + k]) {
+                float e = fabsf(hyp[4 * i + k] - rd);
+                if (e < bd) { bd = e; nd = hyp[4 * i + k]; }
+            }
+    }
+    newd[i] = nd;
+}
+
+// Eq. 10 normal from the back-projected 4-neighbours (reading: unit length,
+// oriented towards the camera); a hole without all four neighbours stays
+// empty
+__global__ void k_eq10(const __grid_constant__ RefConst rc, const uint8_t* __restrict__ known,
+                       const float* __restrict__ newd, float4* __restrict__ plane) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int W = rc.W, H = rc.H;
+    if (i >= (long long)W * H) return;
+    if (known[i]) return;
+    int x = (int)(i % W), y = (int)(i / W);
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    float d = newd[i];
+    if (d > 0.0f && x >= 1 && y >= 1 && x <= W - 2 && y <= H - 2) {
+        const int nx[4] = {x, x, x - 1, x + 1}, ny[4] = {y - 1, y + 1, y, y};
+        float P[4][3];
+        bool ok = true;
+        for (int k = 0; k < 4; ++k) {
+            float dk = newd[(long long)ny[k] * W + nx[k]];
+            if (!(dk > 0.0f)) { ok = false; break; }
+            float r0, r1, r2;
+            mat3v(rc.Kinv, (float)nx[k], (float)ny[k], 1.0f, r0, r1, r2);
+            P[k][0] = dk * r0; P[k][1] = dk * r1; P[k][2] = dk * r2;
+        }
+        if (ok) {
+            float a0 = P[0][0] - P[1][0], a1 = P[0][1] - P[1][1], a2 = P[0][2] - P[1][2];
+            float b0 = P[2][0] - P[3][0], b1 = P[2][1] - P[3][1], b2 = P[2][2] - P[3][2];
+            float n0 = a1 * b2 - a2 * b1, n1 = a2 * b0 - a0 * b2, n2 = a0 * b1 - a1 * b0;
+            float len = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+            if (len > 0.0f) {
+                n0 /= len; n1 /= len; n2 /= len;
+                float r0, r1, r2;
+                mat3v(rc.Kinv, (float)x, (float)y, 1.0f, r0, r1, r2);
+                if (n0 * r0 + n1 * r1 + n2 * r2 > 0.0f) { n0 = -n0; n1 = -n1; n2 = -n2; }
+                out = make_float4(n0, n1, n2, d);
+            }
+        }
+    }
+    plane[i] = out;
+}
+
+__global__ void k_known_from_cost(long long n, const float4* __restrict__ plane, const float* __restrict__ cost,
+                                  float hole_cost, uint8_t* __restrict__ known, float* __restrict__ depth) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float d = plane[i].w;
+    bool k = d > 0.0f && cost[i] < hole_cost;
+    known[i] = k ? 1 : 0;
+    depth[i] = k ? d : 0.0f;
+}
+
+__global__ void k_depth_of(long long n, const float4* __restrict__ plane, const uint8_t* __restrict__ known,
+                           float* __restrict__ depth) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    depth[i] = known[i] ? plane[i].w : 0.0f;
+}
+
+unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t launch_geo_filter(const FilterConst& fc, uint8_t* keep, int32_t* count, cudaStream_t s) {
+    long long n = (long long)fc.W * fc.H;
+    k_geo_filter<<<blocks_for(n, 256), 256, 0, s>>>(fc, keep, count);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi_hypotheses(int W, int H, const float* depth, const uint8_t* known, int n_fit, int inverse,
+                                  float d_lo, float d_hi, float* hyp, uint8_t* valid, int32_t* scratch,
+                                  cudaStream_t s) {
+    int maxl = W + H - 1;
+    dim3 grid(blocks_for(maxl, 128), 4);
+    k_line_gaps<<<grid, 128, 0, s>>>(W, H, known, scratch);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    long long n = (long long)W * H;
+    k_line_fit<<<blocks_for(n, 128), 128, 0, s>>>(W, H, depth, known, scratch, n_fit, inverse, d_lo, d_hi, hyp,
+                                                  valid);
+    count_launch();
+    return cudaGetLastError();
+}
+
+#define MVS_DISPATCH(n, CALL)                       \
+    do {                                            \
+        int _s = (n) * (n);                         \
+        if (_s <= 16) { CALL(4, 4); }               \
+        else if (_s <= 36) { CALL(4, 9); }          \
+        else if (_s <= 64) { CALL(8, 8); }          \
+        else if (_s <= 128) { CALL(8, 16); }        \
+        else if (_s <= 256) { CALL(16, 16); }       \
+        else { CALL(32, 16); }                      \
+    } while (0)
+
+cudaError_t launch_phi_cost(const RefConst& rc, const float* hyp, const uint8_t* valid, float* hcost,
+                            cudaStream_t s) {
+    long long npix = (long long)rc.W * rc.H;
+#define CALL(G, S) k_phi_cost<G, S><<<(unsigned)((npix * G + kBlock - 1) / kBlock), kBlock, 0, s>>>(rc, hyp, valid, hcost)
+    MVS_DISPATCH(rc.n, CALL);
+#undef CALL
+    count_launch();
+    return cudaGetLastError();
+}
+
+size_t phi_mrf_work_floats(int W, int H) {
+    size_t g = (size_t)((W + 1) / 2) * ((H + 1) / 2);
+    // msg 16, lab 4, un 4 floats; nlab 1 + lmap 4 bytes (rounded up to 2 floats)
+    return g * (16 + 4 + 4 + 2) + 64;
+}
+
+cudaError_t launch_phi_mrf(int W, int H, const uint8_t* known, const float* depth, const float* hyp,
+                           const uint8_t* valid, const float* hcost, float k1, float k2, float k3, int iters,
+                           int32_t* label, float* work, cudaStream_t s) {
+    MrfBufs mb;
+    mb.gw = (W + 1) / 2;
+    mb.gh = (H + 1) / 2;
+    long long g = (long long)mb.gw * mb.gh;
+    mb.msg = work;
+    mb.lab = mb.msg + 16 * g;
+    mb.un = mb.lab + 4 * g;
+    mb.lmap = (int8_t*)(mb.un + 4 * g);
+    mb.nlab = mb.lmap + 4 * g;
+    k_mrf_setup<<<blocks_for(g, 256), 256, 0, s>>>(W, H, mb, known, depth, hyp, valid, hcost, k1, k2);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int ntx = (mb.gw + kT - 1) / kT, nty = (mb.gh + kT - 1) / kT;
+    for (int it = 0; it < iters; ++it)
+        for (int pass = 0; pass < 2; ++pass)
+            for (int D = 0; D < ntx + nty - 1; ++D) {
+                int Dd = pass == 0 ? D : (ntx + nty - 2 - D);
+                int ty_lo = max(0, Dd - (ntx - 1)), ty_hi = min(nty - 1, Dd);
+                k_trw_diag<<<ty_hi - ty_lo + 1, kT, 0, s>>>(mb, D, pass == 0, k3);
+                count_launch();
+                e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+            }
+    k_trw_decode<<<blocks_for(g, 256), 256, 0, s>>>(mb, label);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi_select(const RefConst& rc, const uint8_t* known, const float* hyp, const uint8_t* valid,
+                              const int32_t* label, float4* plane, float* newdepth, cudaStream_t s) {
+    long long n = (long long)rc.W * rc.H;
+    k_select<<<blocks_for(n, 256), 256, 0, s>>>(rc.W, rc.H, known, hyp, valid, label, plane, newdepth);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_eq10<<<blocks_for(n, 256), 256, 0, s>>>(rc, known, newdepth, plane);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_known_from_cost(int W, int H, const float4* plane, const float* cost, float hole_cost,
+                                   uint8_t* known, float* depth, cudaStream_t s) {
+    long long n = (long long)W * H;
+    k_known_from_cost<<<blocks_for(n, 256), 256, 0, s>>>(n, plane, cost, hole_cost, known, depth);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_depth_of(int W, int H, const float4* plane, const uint8_t* known, float* depth, cudaStream_t s) {
+    long long n = (long long)W * H;
+    k_depth_of<<<blocks_for(n, 256), 256, 0, s>>>(n, plane, known, depth);
+    count_launch();
+    return cudaGetLastError();
+}

@@ -1,0 +1,296 @@
+// Device building blocks of the PatchMatch path: Philox4x64-10, the dilated
+// support window, the plane-induced homography and the weighted ZNCC of one
+// plane hypothesis against all source views (Sec. III-C, Eq. 4, Eq. 5).
+//
+// Work layout: a group of G consecutive lanes of a warp owns one reference
+// pixel; the n*n window samples are dealt round-robin to the G lanes (S slots
+// per lane, sample k = slot * G + lane_in_group).  The reference side of the
+// window (bilateral weights, centred intensities) stays in registers for
+// every hypothesis and view of the pixel; each (hypothesis, view) pair costs
+// S bilinear gathers per lane and two group reductions (two-pass moments).
+#pragma once
+#include <cstdint>
+#include "mvs_internal.h"
+
+namespace mvsdev {
+
+constexpr float kCmax = 2.0f;                       // C_max = 1 - Z_min, Z_min = -1
+constexpr float kEpsC = 1e-6f;                      // floor of C(x,j) in the weights of Eq. 5
+constexpr float kTauVar = 1e-6f * 255.0f * 255.0f;  // flat-patch variance limit, [0,255] scale
+constexpr float kGraze = 1e-3f;                     // grazing-plane limit |n.r| / |r|
+constexpr float kMagic = 12582912.0f;               // 1.5 * 2^23: float -> nearest integer
+constexpr int kMagicBits = 0x4B400000;
+constexpr float kPi = 3.14159265358979323846f;
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Philox4x64-10 (Salmon et al., SC'11).
+__device__ __forceinline__ void philox4x64(unsigned long long c[4], unsigned long long k0,
+                                           unsigned long long k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+        unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B97F4A7C15ULL;
+        k1 += 0xBB67AE8584CAA73BULL;
+    }
+}
+
+// Uniform in [0, 1) from the top 24 bits of a Philox word (exact in float).
+__device__ __forceinline__ float u24(unsigned long long w) {
+    return (float)(unsigned)(w >> 40) * (1.0f / 16777216.0f);
+}
+
+// Three uniforms for pixel `pix` in phase `phase` (-1 = initialisation):
+// counter (pix, phase + 1, 0, 0), key (seed, reference index).
+__device__ __forceinline__ void draws3(const RefConst& rc, long long pix, int phase, float u[3]) {
+    unsigned long long c[4] = {(unsigned long long)pix, (unsigned long long)(long long)(phase + 1), 0ULL, 0ULL};
+    philox4x64(c, rc.seed, (unsigned long long)rc.ref_index);
+    u[0] = u24(c[0]);
+    u[1] = u24(c[1]);
+    u[2] = u24(c[2]);
+}
+
+template <int G>
+__device__ __forceinline__ float gsum(float v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+    return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+}
+
+// Bilinear sample of a coefficient texture at (xs + 0.5, ys + 0.5): the
+// caller passes coordinates already shifted by -1/2.  The texel index is
+// clamped into the array, so any input (even NaN) reads inside the buffer.
+__device__ __forceinline__ float tex_sample(const float4* __restrict__ tex, int pitch, uint32_t n_tex, float xs,
+                                            float ys) {
+    float tx = __fadd_rn(xs, kMagic), ty = __fadd_rn(ys, kMagic);
+    float u = __fsub_rn(xs, __fsub_rn(tx, kMagic));
+    float v = __fsub_rn(ys, __fsub_rn(ty, kMagic));
+    uint32_t idx = (uint32_t)__float_as_int(ty) * (uint32_t)pitch + (uint32_t)__float_as_int(tx) +
+                   (uint32_t)(pitch + 1) * (uint32_t)(1 - kMagicBits);
+    idx = min(idx, n_tex - 1u);
+    float4 c = __ldg(tex + idx);
+    return fmaf(v, fmaf(u, c.w, c.z), fmaf(u, c.y, c.x));
+}
+
+// Reference side of the window of one pixel, held by the G lanes of its group.
+template <int S>
+struct PixWin {
+    float ou[S], ov[S];   // sample offsets (0 for padding / excluded samples)
+    float w[S];           // bilateral weights (0 for padding / excluded)
+    float wr[S];          // w * (I_ref - weighted mean)
+    float inv_wsum;       // 1 / sum w over the group
+    float srr;            // sum w (I_ref - mean)^2 over the group
+    float wsum;
+    float cu, cv;         // this lane's corner of the included sample rectangle
+    float rx0, rx1, rx2;  // K^-1 (x, y, 1)
+    float rc0, rc1, rc2;  // K^-1 (x + cu, y + cv, 1)
+    bool ok;              // pixel exists and its reference patch is not flat
+};
+
+// Window offsets s*(k - r_now) (Sec. III-C); samples outside the reference
+// image are left out of the window.
+template <int G, int S>
+__device__ __forceinline__ void build_window(const RefConst& rc, int px, int py, bool exists, PixWin<S>& pw) {
+    const int lane = threadIdx.x & 31, lg = lane & (G - 1);
+    const int n = rc.n;
+    const float half = 0.5f * (float)(n - 1);
+    int ku_lo = n, ku_hi = -1, kv_lo = n, kv_hi = -1;
+    for (int k = 0; k < n; ++k) {
+        float o = rc.step * ((float)k - half);
+        float eu = (float)px + o, ev = (float)py + o;
+        if (eu >= 0.0f && eu <= (float)(rc.W - 1)) { ku_lo = min(ku_lo, k); ku_hi = max(ku_hi, k); }
+        if (ev >= 0.0f && ev <= (float)(rc.H - 1)) { kv_lo = min(kv_lo, k); kv_hi = max(kv_hi, k); }
+    }
+    const float rcen = exists ? (float)__ldg(rc.img + (long long)py * rc.W + px) : 0.0f;
+    float sw = 0.0f, swr = 0.0f;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        int k = s * G + lg;
+        int ku = k % n, kv = k / n;
+        bool in = exists && k < n * n && ku >= ku_lo && ku <= ku_hi && kv >= kv_lo && kv <= kv_hi;
+        float ou = rc.step * ((float)ku - half), ov = rc.step * ((float)kv - half);
+        float r = 0.0f, w = 0.0f;
+        if (in) {
+            r = tex_sample(rc.tex, rc.pitch, rc.n_tex, (float)px + ou - 0.5f, (float)py + ov - 0.5f);
+            float dc = r - rcen;
+            w = expf(rc.sp_coef * (ou * ou + ov * ov)) * expf(rc.col_coef * dc * dc);
+        }
+        pw.ou[s] = in ? ou : 0.0f;
+        pw.ov[s] = in ? ov : 0.0f;
+        pw.w[s] = w;
+        pw.wr[s] = r;   // temporarily the intensity
+        sw += w;
+        swr = fmaf(w, r, swr);
+    }
+    sw = gsum<G>(sw);
+    swr = gsum<G>(swr);
+    float mu = sw > 0.0f ? swr / sw : 0.0f;
+    float srr = 0.0f;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        float d = pw.wr[s] - mu;
+        float t = pw.w[s] * d;
+        pw.wr[s] = t;
+        srr = fmaf(t, d, srr);
+    }
+    srr = gsum<G>(srr);
+    pw.wsum = sw;
+    pw.inv_wsum = sw > 0.0f ? 1.0f / sw : 0.0f;
+    pw.srr = srr;
+    pw.ok = exists && sw > 0.0f && srr >= kTauVar * sw && ku_hi >= 0 && kv_hi >= 0;
+    const int c = lg & 3;
+    int ku = (c & 1) ? ku_hi : ku_lo, kv = (c & 2) ? kv_hi : kv_lo;
+    pw.cu = rc.step * ((float)ku - half);
+    pw.cv = rc.step * ((float)kv - half);
+    const float* Ki = rc.Kinv;
+    float x = (float)px, y = (float)py;
+    pw.rx0 = fmaf(Ki[0], x, fmaf(Ki[1], y, Ki[2]));
+    pw.rx1 = fmaf(Ki[3], x, fmaf(Ki[4], y, Ki[5]));
+    pw.rx2 = fmaf(Ki[6], x, fmaf(Ki[7], y, Ki[8]));
+    float xc = x + pw.cu, yc = y + pw.cv;
+    pw.rc0 = fmaf(Ki[0], xc, fmaf(Ki[1], yc, Ki[2]));
+    pw.rc1 = fmaf(Ki[3], xc, fmaf(Ki[4], yc, Ki[5]));
+    pw.rc2 = fmaf(Ki[6], xc, fmaf(Ki[7], yc, Ki[8]));
+}
+
+// Cost C(x) (Eq. 5) of plane hypothesis (n, d) at the group's pixel.  Must be
+// called by all 32 lanes of the warp (warp-uniform control flow); lanes of
+// groups whose hypothesis is invalid take part with discarded results.
+// Reading of the paper's silent points: the hypothesis is invalid (cost
+// C_max) unless d > 0, n.r < -1e-3 |r| at the pixel and n.r < 0 at every
+// window sample (plane in front of the reference camera); a view is excluded
+// when a sample leaves the source image or falls behind it (Sec. III-C), or
+// when its weighted variance is below 1e-6 on the [0,1] scale.
+template <int G, int S, bool VIEWS>
+__device__ __forceinline__ float eval_hyp(const RefConst& rc, const PixWin<S>& pw, int px, int py, float n0,
+                                          float n1, float n2, float d, bool want, float* view_cost,
+                                          unsigned& n_evals) {
+    const int lane = threadIdx.x & 31;
+    const unsigned gm = group_mask<G>(lane);
+    const float* Ki = rc.Kinv;
+    float nr = n0 * pw.rx0 + n1 * pw.rx1 + n2 * pw.rx2;
+    float rlen = sqrtf(pw.rx0 * pw.rx0 + pw.rx1 * pw.rx1 + pw.rx2 * pw.rx2);
+    float nrc = n0 * pw.rc0 + n1 * pw.rc1 + n2 * pw.rc2;
+    bool hv = want && pw.ok && d > 0.0f && d < 3.0e38f && nr < -kGraze * rlen && nrc < 0.0f;
+    hv = ((__ballot_sync(0xffffffffu, hv) & gm) == gm);
+    if (!__any_sync(0xffffffffu, hv)) {
+        if (VIEWS && hv == false && (lane & (G - 1)) == 0 && view_cost)
+            for (int j = 0; j < rc.n_src; ++j) view_cost[j] = kCmax;
+        return kCmax;
+    }
+    // m = K^-T n / rho, rho = d (n . r_x); p0 = A x + b / d
+    float inv_rho = hv ? 1.0f / (d * nr) : 0.0f;
+    float m0 = (Ki[0] * n0 + Ki[3] * n1 + Ki[6] * n2) * inv_rho;
+    float m1 = (Ki[1] * n0 + Ki[4] * n1 + Ki[7] * n2) * inv_rho;
+    float invd = hv ? 1.0f / d : 0.0f;
+    const float x = (float)px, y = (float)py;
+    int cnt = 0;
+    float inv_sum = 0.0f;
+    for (int j = 0; j < rc.n_src; ++j) {
+        const PairConst& P = rc.pair[j];
+        float h0x = fmaf(P.b[0], m0, P.A[0]), h0y = fmaf(P.b[1], m0, P.A[3]), h0z = fmaf(P.b[2], m0, P.A[6]);
+        float h1x = fmaf(P.b[0], m1, P.A[1]), h1y = fmaf(P.b[1], m1, P.A[4]), h1z = fmaf(P.b[2], m1, P.A[7]);
+        float p0x = fmaf(P.b[0], invd, fmaf(P.A[0], x, fmaf(P.A[1], y, P.A[2])));
+        float p0y = fmaf(P.b[1], invd, fmaf(P.A[3], x, fmaf(P.A[4], y, P.A[5])));
+        float p0z = fmaf(P.b[2], invd, fmaf(P.A[6], x, fmaf(P.A[7], y, P.A[8])));
+        // this lane's corner of the window (exact convexity test: the window
+        // maps into the source image iff its four corners do, w > 0 included)
+        float cx = fmaf(pw.cu, h0x, fmaf(pw.cv, h1x, p0x));
+        float cy = fmaf(pw.cu, h0y, fmaf(pw.cv, h1y, p0y));
+        float cz = fmaf(pw.cu, h0z, fmaf(pw.cv, h1z, p0z));
+        float icz = 1.0f / cz;
+        float xs = cx * icz, ys = cy * icz;
+        bool cok = hv && cz > 0.0f && xs >= 0.0f && xs <= (float)(P.W - 1) && ys >= 0.0f && ys <= (float)(P.H - 1);
+        bool vok = ((__ballot_sync(0xffffffffu, cok) & gm) == gm);
+        if (!__any_sync(0xffffffffu, vok)) {
+            if (VIEWS && (lane & (G - 1)) == 0 && view_cost) view_cost[j] = kCmax;
+            continue;
+        }
+        // sample coordinates shifted by -1/2 for tex_sample
+        h0x = fmaf(-0.5f, h0z, h0x);
+        h0y = fmaf(-0.5f, h0z, h0y);
+        h1x = fmaf(-0.5f, h1z, h1x);
+        h1y = fmaf(-0.5f, h1z, h1y);
+        p0x = fmaf(-0.5f, p0z, p0x);
+        p0y = fmaf(-0.5f, p0z, p0y);
+        float sv[S];
+        float s1 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            float X = fmaf(pw.ou[k], h0x, fmaf(pw.ov[k], h1x, p0x));
+            float Y = fmaf(pw.ou[k], h0y, fmaf(pw.ov[k], h1y, p0y));
+            float Z = fmaf(pw.ou[k], h0z, fmaf(pw.ov[k], h1z, p0z));
+            float iz = rcp_approx(Z);
+            float v = tex_sample(P.tex, P.pitch, P.n_tex, __fmul_rn(X, iz), __fmul_rn(Y, iz));
+            sv[k] = v;
+            s1 = fmaf(pw.w[k], v, s1);
+        }
+        s1 = gsum<G>(s1);
+        float mu = s1 * pw.inv_wsum;
+        float sdd = 0.0f, srd = 0.0f;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            float dv = sv[k] - mu;
+            float t = pw.w[k] * dv;
+            sdd = fmaf(t, dv, sdd);
+            srd = fmaf(pw.wr[k], dv, srd);
+        }
+        sdd = gsum<G>(sdd);
+        srd = gsum<G>(srd);
+        float cj = kCmax;
+        n_evals += (vok && (lane & (G - 1)) == 0) ? 1u : 0u;
+        if (vok && sdd >= kTauVar * pw.wsum) {
+            float z = srd * rsqrtf(pw.srr * sdd);
+            z = fminf(1.0f, fmaxf(-1.0f, z));
+            cj = 1.0f - z;
+            if (cj < kCmax) {
+                cnt++;
+                inv_sum += 1.0f / fmaxf(cj, kEpsC);
+            } else {
+                cj = kCmax;
+            }
+        }
+        if (VIEWS && (lane & (G - 1)) == 0 && view_cost) view_cost[j] = cj;
+    }
+    return (hv && cnt > 0) ? (float)cnt / inv_sum : kCmax;
+}
+
+// adds the warp's evaluated (pixel, hypothesis, view) count to the counter
+__device__ __forceinline__ void flush_evals(unsigned long long* counter, unsigned n) {
+    unsigned t = __reduce_add_sync(0xffffffffu, n);
+    if (counter && (threadIdx.x & 31) == 0 && t) atomicAdd(counter, (unsigned long long)t);
+}
+
+// Sec. III-B: n = (cos t sin p, sin t sin p, cos p), turned to face the camera.
+__device__ __forceinline__ void normal_from_angles(float th, float ph, float rx0, float rx1, float rx2, float& n0,
+                                                   float& n1, float& n2) {
+    float st, ct, sp, cp;
+    sincosf(th, &st, &ct);
+    sincosf(ph, &sp, &cp);
+    n0 = ct * sp;
+    n1 = st * sp;
+    n2 = cp;
+    if (n0 * rx0 + n1 * rx1 + n2 * rx2 > 0.0f) {
+        n0 = -n0;
+        n1 = -n1;
+        n2 = -n2;
+    }
+}
+
+}  // namespace mvsdev

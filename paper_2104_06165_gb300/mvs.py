@@ -1,0 +1,325 @@
+"""Thin ctypes binding of libmvs.so (the C ABI declared in include/mvs.h).
+
+Argument marshalling only: every step of the depth-map path runs in the
+library's CUDA kernels.  Buffers may be torch CUDA tensors (device memory,
+work is enqueued on the context's stream) or numpy arrays (host memory, the
+call synchronises).  There is no CPU fallback: if the compiled library is
+missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmvs.so")
+
+MVS_OK, MVS_EINVAL, MVS_ENOMEM, MVS_ECUDA, MVS_ETIMEOUT, MVS_ESTATE, MVS_EUNSUPPORTED = range(7)
+MVS_MEM_DEVICE, MVS_MEM_HOST = 0, 1
+MVS_INIT_RANDOM, MVS_INIT_GIVEN, MVS_INIT_GIVEN_RECOST = 0, 1, 2
+STATUS_NAMES = ["MVS_OK", "MVS_EINVAL", "MVS_ENOMEM", "MVS_ECUDA", "MVS_ETIMEOUT", "MVS_ESTATE",
+                "MVS_EUNSUPPORTED"]
+
+
+class MvsError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+
+
+class mvs_camera(C.Structure):
+    _fields_ = [("K", C.c_double * 9), ("R", C.c_double * 9), ("t", C.c_double * 3), ("width", C.c_int32),
+                ("height", C.c_int32)]
+
+
+class mvs_pm_params(C.Structure):
+    _fields_ = [("win_radius", C.c_float), ("win_samples", C.c_int32), ("sigma_s", C.c_float),
+                ("sigma_c", C.c_float), ("d_lo", C.c_float), ("d_hi", C.c_float), ("iters", C.c_int32),
+                ("phase_begin", C.c_int32), ("phase_end", C.c_int32), ("init_mode", C.c_int32),
+                ("seed", C.c_uint64), ("precision", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class mvs_depth_map(C.Structure):
+    _fields_ = [("plane", C.c_void_p), ("cost", C.c_void_p), ("mem", C.c_int32)]
+
+
+class mvs_filter_params(C.Structure):
+    _fields_ = [("depth_tol", C.c_float), ("depth_relative", C.c_int32), ("max_angle_deg", C.c_float),
+                ("max_reproj_px", C.c_float), ("min_consistent", C.c_int32)]
+
+
+class mvs_phi_params(C.Structure):
+    _fields_ = [("kappa1", C.c_float), ("kappa2", C.c_float), ("kappa3", C.c_float), ("n_fit", C.c_int32),
+                ("fit_inverse", C.c_int32), ("trw_iters", C.c_int32), ("hole_cost", C.c_float)]
+
+
+@dataclass
+class PMParams:
+    """PatchMatch parameters; defaults follow Sec. IV (r_now = 5, r_orig = 7,
+    8 iterations) with the bilateral weights sigma_s = 5 px, sigma_c = 0.2."""
+    win_radius: float = 7.0
+    win_samples: int = 11
+    sigma_s: float = 5.0
+    sigma_c: float = 0.2
+    d_lo: float = 2.0
+    d_hi: float = 8.0
+    iters: int = 8
+    phase_begin: int = 0
+    phase_end: int = -1
+    init_mode: int = MVS_INIT_RANDOM
+    seed: int = 0
+    precision: int = 0
+
+    def c(self):
+        return mvs_pm_params(self.win_radius, self.win_samples, self.sigma_s, self.sigma_c, self.d_lo, self.d_hi,
+                             self.iters, self.phase_begin, self.phase_end, self.init_mode,
+                             int(self.seed) & 0xFFFFFFFFFFFFFFFF, self.precision)
+
+
+@dataclass
+class FilterParams:
+    """Sec. III-D: 0.02 depth, 30 degrees, 1 px, more than one view."""
+    depth_tol: float = 0.02
+    depth_relative: int = 0
+    max_angle_deg: float = 30.0
+    max_reproj_px: float = 1.0
+    min_consistent: int = 2
+
+    def c(self):
+        return mvs_filter_params(self.depth_tol, self.depth_relative, self.max_angle_deg, self.max_reproj_px,
+                                 self.min_consistent)
+
+
+@dataclass
+class PhiParams:
+    """Sec. III-E / Sec. IV: kappa = (4, 0.5, 2), six closest pixels, one
+    TRW iteration."""
+    kappa1: float = 4.0
+    kappa2: float = 0.5
+    kappa3: float = 2.0
+    n_fit: int = 6
+    fit_inverse: int = 0
+    trw_iters: int = 1
+    hole_cost: float = 0.5
+
+    def c(self):
+        return mvs_phi_params(self.kappa1, self.kappa2, self.kappa3, self.n_fit, self.fit_inverse, self.trw_iters,
+                              self.hole_cost)
+
+
+_lib = None
+
+
+def load():
+    """Load libmvs.so (built in-tree by build.py); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, ip, u8p, fp = C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p
+    L.mvs_create.restype = i32
+    L.mvs_create.argtypes = [C.POINTER(mvs_camera), C.POINTER(C.c_void_p), i32, vp, C.POINTER(C.c_void_p)]
+    L.mvs_destroy.restype = None
+    L.mvs_destroy.argtypes = [vp]
+    L.mvs_last_error.restype = C.c_char_p
+    L.mvs_last_error.argtypes = [vp]
+    L.mvs_patchmatch.restype = i32
+    L.mvs_patchmatch.argtypes = [vp, i32, ip, i32, C.POINTER(mvs_pm_params), C.POINTER(mvs_depth_map)]
+    L.mvs_plane_cost.restype = i32
+    L.mvs_plane_cost.argtypes = [vp, i32, ip, i32, C.POINTER(mvs_pm_params), fp, fp, fp, i32]
+    L.mvs_geo_filter.restype = i32
+    L.mvs_geo_filter.argtypes = [vp, i32, ip, i32, C.POINTER(mvs_filter_params), u8p, vp, i32]
+    L.mvs_plane_infer.restype = i32
+    L.mvs_plane_infer.argtypes = [vp, i32, ip, i32, C.POINTER(mvs_pm_params), C.POINTER(mvs_phi_params), u8p,
+                                  C.POINTER(mvs_depth_map)]
+    L.mvs_phi_hypotheses.restype = i32
+    L.mvs_phi_hypotheses.argtypes = [vp, i32, i32, fp, u8p, C.POINTER(mvs_phi_params), C.c_float, C.c_float, fp,
+                                     u8p, i32]
+    L.mvs_phi_cost.restype = i32
+    L.mvs_phi_cost.argtypes = [vp, i32, ip, i32, C.POINTER(mvs_pm_params), fp, u8p, fp, i32]
+    L.mvs_phi_mrf.restype = i32
+    L.mvs_phi_mrf.argtypes = [vp, i32, i32, u8p, fp, fp, u8p, fp, C.POINTER(mvs_phi_params), vp, i32]
+    L.mvs_phi_select.restype = i32
+    L.mvs_phi_select.argtypes = [vp, i32, u8p, fp, u8p, vp, fp, i32]
+    L.mvs_profile.restype = i32
+    L.mvs_profile.argtypes = [vp, i32]
+    L.mvs_profile_read.restype = i32
+    L.mvs_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int64)]
+    _lib = L
+    return L
+
+
+def _check(status, ctx=None):
+    if status != MVS_OK:
+        msg = load().mvs_last_error(ctx)
+        raise MvsError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, mem kind) of a torch CUDA tensor or a numpy array."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("numpy buffers must be C-contiguous")
+        return a.ctypes.data, MVS_MEM_HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor buffers must be contiguous")
+        return a.data_ptr(), (MVS_MEM_DEVICE if a.is_cuda else MVS_MEM_HOST)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _mem(*bufs):
+    kinds = {k for _, k in (_ptr(b) for b in bufs if b is not None)}
+    if len(kinds) != 1:
+        raise ValueError("all buffers of one call must be in the same memory (all device or all host)")
+    return kinds.pop()
+
+
+def _srcs(srcs):
+    a = (C.c_int32 * len(srcs))(*[int(s) for s in srcs])
+    return a, len(srcs)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def mvs_create(cams, images, stream=None):
+    """cams: list of (K, R, t) with x_cam = R X + t; images: uint8 (H, W)
+    numpy arrays.  Returns the context handle."""
+    L = load()
+    n = len(images)
+    carr = (mvs_camera * n)()
+    keep = []
+    ptrs = (C.c_void_p * n)()
+    for i, ((K, R, t), im) in enumerate(zip(cams, images)):
+        im = np.ascontiguousarray(im, dtype=np.uint8)
+        keep.append(im)
+        carr[i].K[:] = [float(v) for v in np.asarray(K, float).ravel()]
+        carr[i].R[:] = [float(v) for v in np.asarray(R, float).ravel()]
+        carr[i].t[:] = [float(v) for v in np.asarray(t, float).ravel()]
+        carr[i].height, carr[i].width = im.shape
+        ptrs[i] = im.ctypes.data
+    h = C.c_void_p()
+    _check(L.mvs_create(carr, ptrs, n, _stream_handle(stream), C.byref(h)), None)
+    return h
+
+
+def mvs_destroy(ctx):
+    load().mvs_destroy(ctx)
+
+
+def mvs_patchmatch(ctx, ref, srcs, params: PMParams, plane, cost):
+    """Run PatchMatch for view `ref`; plane (H, W, 4) float32 and cost (H, W)
+    float32 buffers receive the result (and carry the start state for
+    MVS_INIT_GIVEN*)."""
+    pp, _ = _ptr(plane)
+    cp, _ = _ptr(cost)
+    mem = _mem(plane, cost)
+    s, ns = _srcs(srcs)
+    out = mvs_depth_map(pp, cp, mem)
+    cpar = params.c()
+    _check(load().mvs_patchmatch(ctx, ref, s, ns, C.byref(cpar), C.byref(out)), ctx)
+
+
+def mvs_plane_cost(ctx, ref, srcs, params: PMParams, plane, cost, view_cost=None):
+    mem = _mem(plane, cost, view_cost)
+    s, ns = _srcs(srcs)
+    cpar = params.c()
+    _check(load().mvs_plane_cost(ctx, ref, s, ns, C.byref(cpar), _ptr(plane)[0], _ptr(cost)[0],
+                                 _ptr(view_cost)[0], mem), ctx)
+
+
+def mvs_geo_filter(ctx, ref, srcs, fparams: FilterParams, keep, count=None):
+    mem = _mem(keep, count)
+    s, ns = _srcs(srcs)
+    cpar = fparams.c()
+    _check(load().mvs_geo_filter(ctx, ref, s, ns, C.byref(cpar), _ptr(keep)[0], _ptr(count)[0], mem), ctx)
+
+
+def mvs_plane_infer(ctx, ref, srcs, pm: PMParams, phi: PhiParams, keep_mask, plane, cost):
+    mem = _mem(plane, cost, keep_mask)
+    s, ns = _srcs(srcs)
+    out = mvs_depth_map(_ptr(plane)[0], _ptr(cost)[0], mem)
+    a, b = pm.c(), phi.c()
+    _check(load().mvs_plane_infer(ctx, ref, s, ns, C.byref(a), C.byref(b), _ptr(keep_mask)[0], C.byref(out)), ctx)
+
+
+def mvs_phi_hypotheses(ctx, depth, known, phi: PhiParams, d_lo, d_hi, hyp, valid):
+    mem = _mem(depth, known, hyp, valid)
+    H, W = depth.shape
+    b = phi.c()
+    _check(load().mvs_phi_hypotheses(ctx, W, H, _ptr(depth)[0], _ptr(known)[0], C.byref(b), d_lo, d_hi,
+                                     _ptr(hyp)[0], _ptr(valid)[0], mem), ctx)
+
+
+def mvs_phi_cost(ctx, ref, srcs, pm: PMParams, hyp, valid, hcost):
+    mem = _mem(hyp, valid, hcost)
+    s, ns = _srcs(srcs)
+    a = pm.c()
+    _check(load().mvs_phi_cost(ctx, ref, s, ns, C.byref(a), _ptr(hyp)[0], _ptr(valid)[0], _ptr(hcost)[0], mem),
+           ctx)
+
+
+def mvs_phi_mrf(ctx, known, depth, hyp, valid, hcost, phi: PhiParams, label):
+    mem = _mem(known, depth, hyp, valid, hcost, label)
+    H, W = depth.shape
+    b = phi.c()
+    _check(load().mvs_phi_mrf(ctx, W, H, _ptr(known)[0], _ptr(depth)[0], _ptr(hyp)[0], _ptr(valid)[0],
+                              _ptr(hcost)[0], C.byref(b), _ptr(label)[0], mem), ctx)
+
+
+def mvs_phi_select(ctx, ref, known, hyp, valid, label, plane):
+    mem = _mem(known, hyp, valid, label, plane)
+    _check(load().mvs_phi_select(ctx, ref, _ptr(known)[0], _ptr(hyp)[0], _ptr(valid)[0], _ptr(label)[0],
+                                 _ptr(plane)[0], mem), ctx)
+
+
+def mvs_profile(ctx, enable):
+    _check(load().mvs_profile(ctx, int(bool(enable))), ctx)
+
+
+def mvs_profile_read(ctx):
+    """(phase kernel ms, phase launches, kernel launches, ZNCC evaluations)"""
+    ms = C.c_double()
+    a, b, e = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().mvs_profile_read(ctx, C.byref(ms), C.byref(a), C.byref(b), C.byref(e)), ctx)
+    return ms.value, a.value, b.value, e.value
+
+
+class Context:
+    """Owns an mvs_ctx for a scene (cameras + uint8 images)."""
+
+    def __init__(self, K, R, t, images, stream=None):
+        cams = [(K[i], R[i], t[i]) for i in range(len(images))]
+        self.h = mvs_create(cams, images, stream)
+        self.shapes = [np.asarray(im).shape for im in images]
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            mvs_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
