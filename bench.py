@@ -31,6 +31,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(W=3072, H=2048, n_src=10, win_radius=10.0, win_samples=11, iters=8, sigma_s=5.0, sigma_c=0.2)
+# smaller case of the same kernels for profiler captures (inputs still larger than L2)
+WORKLOADS = {"highres": WORKLOAD, "mid": dict(WORKLOAD, W=1536, H=1024)}
 FLOP_PER_SAMPLE = 26          # algorithmic FP32 flops per window sample of one ZNCC (FMA = 2)
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
@@ -87,10 +89,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_params(mvs, seed):
+def make_params(mvs, seed, lanes=0):
     w = WORKLOAD
     return mvs.PMParams(win_radius=w["win_radius"], win_samples=w["win_samples"], sigma_s=w["sigma_s"],
-                        sigma_c=w["sigma_c"], d_lo=2.0, d_hi=8.0, iters=w["iters"], seed=seed)
+                        sigma_c=w["sigma_c"], d_lo=2.0, d_hi=8.0, iters=w["iters"], seed=seed,
+                        lanes_per_pixel=lanes)
 
 
 # ---------------------------------------------------------------------------
@@ -180,7 +183,7 @@ def run_ours(args):
     t_render = time.perf_counter() - t0
     H, W = sc.images[0].shape
     srcs = list(range(1, len(sc.images)))
-    params = make_params(mvs, seed=1 + rank)
+    params = make_params(mvs, seed=1 + rank, lanes=args.lanes)
     phi = mvs.PhiParams()
     stream = torch.cuda.current_stream(dev)
     ctx = mvs.Context(sc.K, sc.R, sc.t, sc.images, stream=stream)
@@ -262,8 +265,9 @@ def run_ours(args):
         "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "highres 3072x2048 uint8 ref + 10 sources, 21x21 window dil 2 (11x11 samples), "
-                               "8 iterations, PHI + 4-label MRF", "parallelism": f"replicas{world}",
+        "config": {"workload": f"{args.workload} {W}x{H} uint8 ref + {len(srcs)} sources, 21x21 window dil 2 "
+                               "(11x11 samples), 8 iterations, PHI + 4-label MRF", "parallelism": f"replicas{world}",
+                   "lanes_per_pixel": args.lanes,
                    "l2": "inputs larger than L2 (11 x 100 MB textures)", "render_s": round(t_render, 1)},
         "e2e": {"value": world * mpix / e2e_s, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -297,7 +301,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per pixel group of the ZNCC kernels (0 = default)")
+    ap.add_argument("--workload", default="highres", choices=sorted(WORKLOADS),
+                    help="highres = the measured workload; mid = 1536x1024 case for profiler captures")
     args = ap.parse_args()
+    WORKLOAD.update(WORKLOADS[args.workload])
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -76,7 +76,11 @@ typedef struct {
     int32_t init_mode;     /* MVS_INIT_*                                     */
     uint64_t seed;         /* Philox4x64-10 key word 0 (word 1 = ref index)  */
     int32_t precision;     /* 0 = FP32 (only value built)                    */
-    int32_t reserved[7];
+    int32_t lanes_per_pixel; /* work layout of the ZNCC kernels: lanes that
+                              share one window (4, 8, 16 or 32; 0 = default).
+                              Results are identical for every choice up to
+                              float rounding of the group reductions.        */
+    int32_t reserved[6];
 } mvs_pm_params;
 
 /* Depth-map buffers supplied by the caller. */

@@ -87,7 +87,10 @@ def lib():
             L.or_line_fit_at.restype = C.c_double
             L.or_line_fit_at.argtypes = [dp, up, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                          C.c_double, C.c_double, ip]
-            L.or_phi_cost.argtypes = [vp, C.c_int, ip, C.c_int, C.POINTER(_PM), dp, up, dp]
+            L.or_phi_cost.argtypes = [vp, C.c_int, ip, C.c_int, C.POINTER(_PM), dp, up, dp, dp]
+            L.or_phi_mrf.argtypes = [C.c_int, C.c_int, up, dp, dp, up, dp, C.c_double, C.c_double, C.c_double,
+                                     C.c_int, ip, dp]
+            L.or_phi_select.argtypes = [vp, C.c_int, up, dp, up, ip, dp, up, dp]
             L.or_phi_unary.restype = C.c_double
             L.or_phi_unary.argtypes = [C.c_double, C.c_double, C.c_double]
             L.or_phi_pair.restype = C.c_double
@@ -299,14 +302,42 @@ def line_fit_at(depth, known, x, y, k, n_fit=6, inverse=False, d_lo=0.0, d_hi=np
     return (h if ok.value else None)
 
 
-def phi_cost(scene, ref, srcs, p, hyp, valid):
+def phi_cost(scene, ref, srcs, p, hyp, valid, with_margin=False):
+    """Sec. III-E hypothesis costs (fronto-parallel plane at each depth)."""
     H, W = scene.shape(ref)
     s = _srcs(srcs)
     hyp = _f64(hyp)
     valid = np.ascontiguousarray(valid, dtype=np.uint8)
     out = np.zeros((H, W, 4), np.float64)
-    lib().or_phi_cost(scene.h, ref, _i(s), len(s), C.byref(_pm(p)), _d(hyp), _u8(valid), _d(out))
-    return out
+    mg = np.zeros((H, W, 4), np.float64)
+    lib().or_phi_cost(scene.h, ref, _i(s), len(s), C.byref(_pm(p)), _d(hyp), _u8(valid), _d(out), _d(mg))
+    return (out, mg) if with_margin else out
+
+
+def phi_mrf(known, depth, hyp, valid, hcost, k1=4.0, k2=0.5, k3=2.0, iters=1):
+    """Sec. III-E MRF at half resolution from full-resolution inputs; returns
+    labels (gh, gw) (-1 reconstructed node, -2 absent) and belief gaps."""
+    known = np.ascontiguousarray(known, dtype=np.uint8)
+    H, W = known.shape
+    gw, gh = (W + 1) // 2, (H + 1) // 2
+    label = np.zeros((gh, gw), np.int32)
+    gap = np.zeros((gh, gw), np.float64)
+    lib().or_phi_mrf(W, H, _u8(known), _d(_f64(depth)), _d(_f64(hyp)),
+                     _u8(np.ascontiguousarray(valid, dtype=np.uint8)), _d(_f64(hcost)), k1, k2, k3, iters,
+                     _i(label), _d(gap))
+    return label, gap
+
+
+def phi_select(scene, ref, known, hyp, valid, label, plane):
+    """Sec. III-E selection + Eq. 10 normals; returns (plane, filled)."""
+    H, W = scene.shape(ref)
+    pl = _f64(plane).reshape(H, W, 4).copy()
+    filled = np.zeros((H, W), np.uint8)
+    refd = np.zeros((H, W), np.float64)
+    lib().or_phi_select(scene.h, ref, _u8(np.ascontiguousarray(known, dtype=np.uint8)), _d(_f64(hyp)),
+                        _u8(np.ascontiguousarray(valid, dtype=np.uint8)),
+                        _i(np.ascontiguousarray(label, dtype=np.int32)), _d(pl), _u8(filled), _d(refd))
+    return pl, filled
 
 
 def phi_unary(c, k1=4.0, k2=0.5):

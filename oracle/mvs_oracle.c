@@ -747,7 +747,7 @@ double or_line_fit_at(const double* depth, const unsigned char* known, int W, in
  * projected into the sources (Sec. III-E); this is the homography of the
  * fronto-parallel plane z = h, n = (0, 0, -1) (reading) */
 void or_phi_cost(const or_scene* s, int ref, const int* srcs, int ns, const or_pm* p, const double* hyp,
-                 const unsigned char* valid, double* hcost) {
+                 const unsigned char* valid, double* hcost, double* margin_out) {
     const or_view* V = &s->v[ref];
     or_window* win = (or_window*)malloc(sizeof(or_window));
     double n[3] = {0, 0, -1};
@@ -757,10 +757,13 @@ void or_phi_cost(const or_scene* s, int ref, const int* srcs, int ns, const or_p
             int any = 0;
             for (int k = 0; k < 4; ++k) any |= valid[4 * i + k];
             if (any) ref_window(s, ref, p, x, y, win);
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < 4; ++k) {
+                double mg = 1e300;
                 hcost[4 * i + k] = valid[4 * i + k]
-                    ? pixel_cost(s, ref, srcs, ns, p, x, y, n, hyp[4 * i + k], win, NULL, NULL)
+                    ? pixel_cost(s, ref, srcs, ns, p, x, y, n, hyp[4 * i + k], win, NULL, &mg)
                     : OR_CMAX;
+                if (margin_out) margin_out[4 * i + k] = mg;
+            }
         }
     free(win);
 }
@@ -906,31 +909,23 @@ typedef struct {
     int trw_iters;         /* 1                                              */
 } or_phi;
 
-/* The whole PHI step for one reference view.
- * plane (in/out) H*W*4; known H*W (1 = reconstructed, kept).  On return
- * holes that received a hypothesis and an Eq. 10 normal carry it; others
- * are zero.  Intermediate results go to the optional outputs. */
-void or_plane_infer(const or_scene* s, int ref, const int* srcs, int ns, const or_pm* p, const or_phi* q,
-                    const unsigned char* known, double* plane, double* hyp_out, unsigned char* valid_out,
-                    double* hcost_out, int* label_out, double* refdepth_out, unsigned char* filled_out) {
-    const or_view* V = &s->v[ref];
-    int W = V->W, H = V->H;
-    long N = (long)W * H;
-    double* depth = (double*)malloc(sizeof(double) * N);
-    for (long i = 0; i < N; ++i) depth[i] = known[i] ? plane[4 * i + 3] : 0.0;
-    double* hyp = (double*)malloc(sizeof(double) * 4 * N);
-    unsigned char* valid = (unsigned char*)malloc(4 * N);
-    double* hcost = (double*)malloc(sizeof(double) * 4 * N);
-    or_phi_hypotheses(W, H, depth, known, q->n_fit, q->inverse, p->d_lo, p->d_hi, hyp, valid);
-    or_phi_cost(s, ref, srcs, ns, p, hyp, valid, hcost);
-
-    /* reading: half resolution by taking pixel (2i, 2j) */
+/* MRF stage of Sec. III-E from full-resolution inputs: nodes at pixels
+ * (2i, 2j) (reading: half resolution by sub-sampling); a reconstructed pixel
+ * is a one-label node carrying its depth, a hole carries its valid
+ * hypotheses with unary -log phi_n (Eq. 6), a hole without hypotheses is
+ * absent.  label_out[g] = chosen hypothesis index (0..3), -1 for a
+ * reconstructed node, -2 for an absent node; gap_out[g] (optional) = belief
+ * difference between the best and the second-best label (1e300 for one
+ * label). */
+void or_phi_mrf(int W, int H, const unsigned char* known, const double* depth, const double* hyp,
+                const unsigned char* valid, const double* hcost, double k1, double k2, double k3, int iters,
+                int* label_out, double* gap_out) {
     int gw = (W + 1) / 2, gh = (H + 1) / 2;
     long G = (long)gw * gh;
     int* nlab = (int*)calloc((size_t)G, sizeof(int));
     double* lab = (double*)calloc((size_t)G * 4, sizeof(double));
     double* un = (double*)calloc((size_t)G * 4, sizeof(double));
-    int* lmap = (int*)calloc((size_t)G * 4, sizeof(int));   /* node label -> hypothesis index */
+    int* lmap = (int*)calloc((size_t)G * 4, sizeof(int));
     for (int gy = 0; gy < gh; ++gy)
         for (int gx = 0; gx < gw; ++gx) {
             long g = (long)gy * gw + gx, i = (long)(2 * gy) * W + 2 * gx;
@@ -945,7 +940,7 @@ void or_plane_infer(const or_scene* s, int ref, const int* srcs, int ns, const o
             for (int k = 0; k < 4; ++k)
                 if (valid[4 * i + k]) {
                     lab[4 * g + L] = hyp[4 * i + k];
-                    un[4 * g + L] = -log(or_phi_unary(hcost[4 * i + k], q->k1, q->k2));
+                    un[4 * g + L] = -log(or_phi_unary(hcost[4 * i + k], k1, k2));
                     lmap[4 * g + L] = k;
                     L++;
                 }
@@ -953,18 +948,43 @@ void or_plane_infer(const or_scene* s, int ref, const int* srcs, int ns, const o
         }
     double* msg = (double*)malloc(sizeof(double) * G * 16);
     int* label = (int*)malloc(sizeof(int) * G);
-    or_trw(gw, gh, nlab, lab, un, q->k3, q->trw_iters, msg, label);
+    or_trw(gw, gh, nlab, lab, un, k3, iters, msg, label);
+    for (long g = 0; g < G; ++g) {
+        label_out[g] = nlab[g] ? lmap[4 * g + label[g]] : -2;
+        if (gap_out) {
+            double b1 = 1e300, b2 = 1e300;
+            for (int l = 0; l < nlab[g]; ++l) {
+                double b = un[4 * g + l];
+                for (int dir = 0; dir < 4; ++dir) b += msg[(4 * g + dir) * 4 + l];
+                if (b < b1) { b2 = b1; b1 = b; } else if (b < b2) b2 = b;
+            }
+            gap_out[g] = b2 - b1;
+        }
+    }
+    free(nlab); free(lab); free(un); free(lmap); free(msg); free(label);
+}
 
-    /* up-sample (nearest) the decoded depths as the reference map and pick
-     * the closest hypothesis per hole (lowest k on a tie) */
+/* Selection stage of Sec. III-E: the decoded depth of node (x/2, y/2)
+ * (nearest up-sampling) is the reference; each hole takes its valid
+ * hypothesis closest to it (lowest k on a tie); then Eq. 10 normals for the
+ * filled pixels.  plane (in/out): reconstructed pixels keep their plane,
+ * holes get (n, d) or zeros. */
+void or_phi_select(const or_scene* s, int ref, const unsigned char* known, const double* hyp,
+                   const unsigned char* valid, const int* label, double* plane, unsigned char* filled_out,
+                   double* refdepth_out) {
+    const or_view* V = &s->v[ref];
+    int W = V->W, H = V->H, gw = (W + 1) / 2;
+    long N = (long)W * H;
     double* newd = (double*)calloc((size_t)N, sizeof(double));
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             long i = (long)y * W + x, g = (long)(y / 2) * gw + (x / 2);
-            double rd = label[g] >= 0 ? lab[4 * g + label[g]] : 0.0;
+            long ni = (long)(2 * (y / 2)) * W + 2 * (x / 2);
+            int lb = label[g];
+            double rd = lb == -1 ? plane[4 * ni + 3] : (lb >= 0 ? hyp[4 * ni + lb] : 0.0);
             if (refdepth_out) refdepth_out[i] = rd;
-            if (known[i]) { newd[i] = depth[i]; continue; }
-            if (label[g] < 0) continue;
+            if (known[i]) { newd[i] = plane[4 * i + 3]; continue; }
+            if (lb < -1) continue;
             int bk = -1;
             double bd = 1e300;
             for (int k = 0; k < 4; ++k)
@@ -974,14 +994,11 @@ void or_plane_infer(const or_scene* s, int ref, const int* srcs, int ns, const o
                 }
             if (bk >= 0) newd[i] = hyp[4 * i + bk];
         }
-    /* Eq. 10 normals for the filled pixels, from the selected depth map */
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             long i = (long)y * W + x;
             unsigned char filled = 0;
-            if (known[i]) {
-                plane[4 * i + 3] = depth[i];
-            } else {
+            if (!known[i]) {
                 double n[3];
                 if (newd[i] > 0 && eq10_normal(V, newd, x, y, n)) {
                     plane[4 * i] = n[0]; plane[4 * i + 1] = n[1]; plane[4 * i + 2] = n[2];
@@ -993,12 +1010,36 @@ void or_plane_infer(const or_scene* s, int ref, const int* srcs, int ns, const o
             }
             if (filled_out) filled_out[i] = filled;
         }
+    free(newd);
+}
+
+
+/* The whole PHI step for one reference view: hypotheses, their costs, MRF,
+ * selection and Eq. 10 normals.  plane (in/out) H*W*4; known H*W
+ * (1 = reconstructed, kept).  Intermediate results go to the optional
+ * outputs. */
+void or_plane_infer(const or_scene* s, int ref, const int* srcs, int ns, const or_pm* p, const or_phi* q,
+                    const unsigned char* known, double* plane, double* hyp_out, unsigned char* valid_out,
+                    double* hcost_out, int* label_out, double* refdepth_out, unsigned char* filled_out) {
+    const or_view* V = &s->v[ref];
+    int W = V->W, H = V->H;
+    long N = (long)W * H;
+    long G = (long)((W + 1) / 2) * ((H + 1) / 2);
+    double* depth = (double*)malloc(sizeof(double) * N);
+    for (long i = 0; i < N; ++i) depth[i] = known[i] ? plane[4 * i + 3] : 0.0;
+    double* hyp = (double*)malloc(sizeof(double) * 4 * N);
+    unsigned char* valid = (unsigned char*)malloc(4 * N);
+    double* hcost = (double*)malloc(sizeof(double) * 4 * N);
+    int* label = (int*)malloc(sizeof(int) * G);
+    or_phi_hypotheses(W, H, depth, known, q->n_fit, q->inverse, p->d_lo, p->d_hi, hyp, valid);
+    or_phi_cost(s, ref, srcs, ns, p, hyp, valid, hcost, NULL);
+    or_phi_mrf(W, H, known, depth, hyp, valid, hcost, q->k1, q->k2, q->k3, q->trw_iters, label, NULL);
+    for (long i = 0; i < N; ++i)
+        if (known[i]) plane[4 * i + 3] = depth[i];
+    or_phi_select(s, ref, known, hyp, valid, label, plane, filled_out, refdepth_out);
     if (hyp_out) memcpy(hyp_out, hyp, sizeof(double) * 4 * N);
     if (valid_out) memcpy(valid_out, valid, 4 * N);
     if (hcost_out) memcpy(hcost_out, hcost, sizeof(double) * 4 * N);
-    if (label_out) {
-        for (long g = 0; g < G; ++g) label_out[g] = label[g] >= 0 ? lmap[4 * g + label[g]] : -2;
-    }
-    free(depth); free(hyp); free(valid); free(hcost); free(nlab); free(lab); free(un); free(lmap);
-    free(msg); free(label); free(newd);
+    if (label_out) memcpy(label_out, label, sizeof(int) * G);
+    free(depth); free(hyp); free(valid); free(hcost); free(label);
 }

@@ -135,6 +135,9 @@ mvs_status check_pm(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src,
         return fail(c, MVS_EINVAL, "need 0 < d_lo < d_hi");
     if (p->precision != 0) return fail(c, MVS_EUNSUPPORTED, "precision %d not built", p->precision);
     if (p->iters < 0) return fail(c, MVS_EINVAL, "iters < 0");
+    if (p->lanes_per_pixel != 0 && p->lanes_per_pixel != 4 && p->lanes_per_pixel != 8 &&
+        p->lanes_per_pixel != 16 && p->lanes_per_pixel != 32)
+        return fail(c, MVS_EINVAL, "lanes_per_pixel must be 0, 4, 8, 16 or 32");
     return MVS_OK;
 }
 
@@ -160,6 +163,7 @@ void make_refconst(const mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n
     rc.d_lo = p->d_lo;
     rc.d_hi = p->d_hi;
     rc.seed = p->seed;
+    rc.lanes_hint = p->lanes_per_pixel;
     rc.plane = R.plane;
     rc.cost = R.cost;
     for (int j = 0; j < n_src; ++j) {

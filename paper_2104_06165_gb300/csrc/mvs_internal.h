@@ -41,6 +41,7 @@ struct RefConst {
     float4* plane;             // state: (n.x, n.y, n.z, depth) per pixel
     float* cost;               // state: aggregated cost per pixel
     unsigned long long* eval_counter;  // measurement: evaluated (pixel, hypothesis, view) triples, or null
+    int lanes_hint;            // lanes per pixel group (0 = default)
     PairConst pair[MVS_MAX_SRC];
 };
 
@@ -70,6 +71,8 @@ cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s);
 cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, float* view_cost, cudaStream_t s);
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s);
 int pm_group_lanes(int n_samples);
+// blocks of 128 threads for a grid-stride kernel over `units` warps of work
+unsigned pm_grid_for(const void* kernel, long long units);
 
 struct FilterConst {
     int W, H;

@@ -194,33 +194,37 @@ __global__ void k_line_fit(int W, int H, const float* __restrict__ depth, const 
 // hypothesis cost: fronto-parallel plane z = h, n = (0, 0, -1) (Sec. III-E)
 // ---------------------------------------------------------------------------
 constexpr int kBlock = 128;
+constexpr int kWarps = kBlock / 32;
+struct BlockSm {
+    ViewSm views[MVS_MAX_SRC];
+    uint16_t list[kWarps][8 * MVS_MAX_SRC];
+};
 
+// one warp per pixel, the four hypotheses of a pixel in lanes 0..3
 template <int G, int S>
-__global__ void __launch_bounds__(kBlock) k_phi_cost(const __grid_constant__ RefConst rc, const float* __restrict__ hyp,
+__global__ void __launch_bounds__(kBlock, 3) k_phi_cost(const __grid_constant__ RefConst rc, const float* __restrict__ hyp,
                                                       const uint8_t* __restrict__ valid, float* __restrict__ hcost) {
-    const int lane = threadIdx.x & 31;
+    __shared__ BlockSm sm;
+    load_views(rc, sm.views);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long npix = (long long)rc.W * rc.H;
-    const long long a = ((long long)blockIdx.x * kBlock + threadIdx.x) / G;
-    if (((long long)blockIdx.x * kBlock + (threadIdx.x & ~31)) / G >= npix) return;
-    const bool exists = a < npix;
-    const int px = exists ? (int)(a % rc.W) : 0, py = exists ? (int)(a / rc.W) : 0;
-    uint32_t vmask = 0u;
-    if (exists)
-        for (int k = 0; k < 4; ++k) vmask |= (uint32_t)(valid[4 * a + k] != 0) << (8 * k);
-    if (!__any_sync(0xffffffffu, vmask != 0u)) {
-        if (exists && (lane & (G - 1)) == 0)
-            for (int k = 0; k < 4; ++k) hcost[4 * a + k] = kCmax;
-        return;
-    }
-    PixWin<S> pw;
-    build_window<G, S>(rc, px, py, exists, pw);
-#pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
-        bool v = ((vmask >> (8 * k)) & 0xFFu) != 0u;
-        float h = exists ? hyp[4 * a + k] : 1.0f;
-        unsigned nev = 0;
-        float c = eval_hyp<G, S, false>(rc, pw, px, py, 0.0f, 0.0f, -1.0f, h, v, nullptr, nev);
-        if (exists && (lane & (G - 1)) == 0) hcost[4 * a + k] = v ? c : kCmax;
+    unsigned nev = 0;
+    for (long long a = (long long)blockIdx.x * kWarps + warp; a < npix; a += (long long)gridDim.x * kWarps) {
+        bool v = lane < 4 && valid[4 * a + lane] != 0;
+        if (!__any_sync(0xffffffffu, v)) {
+            if (lane < 4) hcost[4 * a + lane] = kCmax;
+            continue;
+        }
+        const int px = (int)(a % rc.W), py = (int)(a / rc.W);
+        PixWin<S> pw;
+        build_window<G, S>(rc, px, py, true, pw);
+        float h = lane < 4 ? hyp[4 * a + lane] : 1.0f;
+        float c = kCmax;
+        if (pw.ok) {
+            Cand my = make_cand(rc, pw, 0.0f, 0.0f, -1.0f, h, v);
+            c = eval_batch<G, S, false>(rc, sm.views, pw, px, py, my, 4, sm.list[warp], nullptr, nev);
+        }
+        if (lane < 4) hcost[4 * a + lane] = v ? c : kCmax;
     }
 }
 
@@ -478,7 +482,7 @@ cudaError_t launch_phi_hypotheses(int W, int H, const float* depth, const uint8_
 cudaError_t launch_phi_cost(const RefConst& rc, const float* hyp, const uint8_t* valid, float* hcost,
                             cudaStream_t s) {
     long long npix = (long long)rc.W * rc.H;
-#define CALL(G, S) k_phi_cost<G, S><<<(unsigned)((npix * G + kBlock - 1) / kBlock), kBlock, 0, s>>>(rc, hyp, valid, hcost)
+#define CALL(G, S) k_phi_cost<G, S><<<pm_grid_for((const void*)k_phi_cost<G, S>, npix), kBlock, 0, s>>>(rc, hyp, valid, hcost)
     MVS_DISPATCH(rc.n, CALL);
 #undef CALL
     count_launch();

@@ -2,12 +2,16 @@
 // support window, the plane-induced homography and the weighted ZNCC of one
 // plane hypothesis against all source views (Sec. III-C, Eq. 4, Eq. 5).
 //
-// Work layout: a group of G consecutive lanes of a warp owns one reference
-// pixel; the n*n window samples are dealt round-robin to the G lanes (S slots
-// per lane, sample k = slot * G + lane_in_group).  The reference side of the
-// window (bilateral weights, centred intensities) stays in registers for
-// every hypothesis and view of the pixel; each (hypothesis, view) pair costs
-// S bilinear gathers per lane and two group reductions (two-pass moments).
+// Work layout: one warp owns one reference pixel.  The warp is split into
+// 32/G groups of G lanes; the n*n window samples are dealt round-robin to the
+// G lanes of a group (S slots per lane, sample k = slot * G + lane_in_group)
+// and every group keeps the reference side of the window (bilateral weights,
+// centred intensities) in registers.  The (hypothesis, view) pairs of a
+// batch of hypotheses whose window lands inside the source image are listed
+// first, then each group evaluates one listed pair at a time: S bilinear
+// gathers per lane and two group reductions (two-pass moments).  Pairs that
+// fall outside a source and pixels with a flat reference patch therefore
+// cost no gathers and leave no lane idle.
 #pragma once
 #include <cstdint>
 #include "mvs_internal.h"
@@ -88,18 +92,18 @@ __device__ __forceinline__ float tex_sample(const float4* __restrict__ tex, int 
     return fmaf(v, fmaf(u, c.w, c.z), fmaf(u, c.y, c.x));
 }
 
-// Reference side of the window of one pixel, held by the G lanes of its group.
+// Reference side of the window of one pixel.  Every group of G lanes of the
+// warp holds the same pixel's window (sample k = slot * G + lane_in_group).
 template <int S>
 struct PixWin {
     float ou[S], ov[S];   // sample offsets (0 for padding / excluded samples)
     float w[S];           // bilateral weights (0 for padding / excluded)
     float wr[S];          // w * (I_ref - weighted mean)
-    float inv_wsum;       // 1 / sum w over the group
-    float srr;            // sum w (I_ref - mean)^2 over the group
+    float inv_wsum;       // 1 / sum w
+    float srr;            // sum w (I_ref - mean)^2
     float wsum;
-    float cu, cv;         // this lane's corner of the included sample rectangle
+    float cu_lo, cu_hi, cv_lo, cv_hi;  // corners of the included sample rectangle
     float rx0, rx1, rx2;  // K^-1 (x, y, 1)
-    float rc0, rc1, rc2;  // K^-1 (x + cu, y + cv, 1)
     bool ok;              // pixel exists and its reference patch is not flat
 };
 
@@ -154,74 +158,146 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
     pw.inv_wsum = sw > 0.0f ? 1.0f / sw : 0.0f;
     pw.srr = srr;
     pw.ok = exists && sw > 0.0f && srr >= kTauVar * sw && ku_hi >= 0 && kv_hi >= 0;
-    const int c = lg & 3;
-    int ku = (c & 1) ? ku_hi : ku_lo, kv = (c & 2) ? kv_hi : kv_lo;
-    pw.cu = rc.step * ((float)ku - half);
-    pw.cv = rc.step * ((float)kv - half);
+    pw.cu_lo = rc.step * ((float)ku_lo - half);
+    pw.cu_hi = rc.step * ((float)ku_hi - half);
+    pw.cv_lo = rc.step * ((float)kv_lo - half);
+    pw.cv_hi = rc.step * ((float)kv_hi - half);
     const float* Ki = rc.Kinv;
     float x = (float)px, y = (float)py;
     pw.rx0 = fmaf(Ki[0], x, fmaf(Ki[1], y, Ki[2]));
     pw.rx1 = fmaf(Ki[3], x, fmaf(Ki[4], y, Ki[5]));
     pw.rx2 = fmaf(Ki[6], x, fmaf(Ki[7], y, Ki[8]));
-    float xc = x + pw.cu, yc = y + pw.cv;
-    pw.rc0 = fmaf(Ki[0], xc, fmaf(Ki[1], yc, Ki[2]));
-    pw.rc1 = fmaf(Ki[3], xc, fmaf(Ki[4], yc, Ki[5]));
-    pw.rc2 = fmaf(Ki[6], xc, fmaf(Ki[7], yc, Ki[8]));
 }
 
-// Cost C(x) (Eq. 5) of plane hypothesis (n, d) at the group's pixel.  Must be
-// called by all 32 lanes of the warp (warp-uniform control flow); lanes of
-// groups whose hypothesis is invalid take part with discarded results.
-// Reading of the paper's silent points: the hypothesis is invalid (cost
-// C_max) unless d > 0, n.r < -1e-3 |r| at the pixel and n.r < 0 at every
-// window sample (plane in front of the reference camera); a view is excluded
-// when a sample leaves the source image or falls behind it (Sec. III-C), or
-// when its weighted variance is below 1e-6 on the [0,1] scale.
-template <int G, int S, bool VIEWS>
-__device__ __forceinline__ float eval_hyp(const RefConst& rc, const PixWin<S>& pw, int px, int py, float n0,
-                                          float n1, float n2, float d, bool want, float* view_cost,
-                                          unsigned& n_evals) {
-    const int lane = threadIdx.x & 31;
-    const unsigned gm = group_mask<G>(lane);
+// Source-view constants copied to shared memory once per block (72 bytes:
+// conflict-free when the groups of a warp read different views).
+struct ViewSm {
+    float A[9];
+    float b[3];
+    float wm1, hm1;       // W - 1, H - 1
+    uint32_t pitch, n_tex;
+    const float4* tex;
+};
+
+__device__ __forceinline__ void load_views(const RefConst& rc, ViewSm* sv) {
+    for (int j = threadIdx.x; j < rc.n_src; j += blockDim.x) {
+        const PairConst& P = rc.pair[j];
+        for (int i = 0; i < 9; ++i) sv[j].A[i] = P.A[i];
+        for (int i = 0; i < 3; ++i) sv[j].b[i] = P.b[i];
+        sv[j].wm1 = (float)(P.W - 1);
+        sv[j].hm1 = (float)(P.H - 1);
+        sv[j].pitch = (uint32_t)P.pitch;
+        sv[j].n_tex = P.n_tex;
+        sv[j].tex = P.tex;
+    }
+    __syncthreads();
+}
+
+// A plane hypothesis held by one lane: (n, d), validity and the homography
+// factors m = K^-T n / rho, 1/d.
+struct Cand {
+    float n0, n1, n2, d;
+    float m0, m1, invd;
+    bool ok;
+};
+
+// Reading of the paper's silent points: a hypothesis is usable only if
+// d > 0, n.r < -1e-3 |r| at the pixel and n.r < 0 at every window sample (the
+// plane lies in front of the reference camera; n.r is affine in the sample
+// position, so the four corners decide).
+template <int S>
+__device__ __forceinline__ Cand make_cand(const RefConst& rc, const PixWin<S>& pw, float n0, float n1, float n2,
+                                          float d, bool want) {
+    Cand c;
+    c.n0 = n0; c.n1 = n1; c.n2 = n2; c.d = d;
     const float* Ki = rc.Kinv;
     float nr = n0 * pw.rx0 + n1 * pw.rx1 + n2 * pw.rx2;
     float rlen = sqrtf(pw.rx0 * pw.rx0 + pw.rx1 * pw.rx1 + pw.rx2 * pw.rx2);
-    float nrc = n0 * pw.rc0 + n1 * pw.rc1 + n2 * pw.rc2;
-    bool hv = want && pw.ok && d > 0.0f && d < 3.0e38f && nr < -kGraze * rlen && nrc < 0.0f;
-    hv = ((__ballot_sync(0xffffffffu, hv) & gm) == gm);
-    if (!__any_sync(0xffffffffu, hv)) {
-        if (VIEWS && hv == false && (lane & (G - 1)) == 0 && view_cost)
-            for (int j = 0; j < rc.n_src; ++j) view_cost[j] = kCmax;
-        return kCmax;
-    }
-    // m = K^-T n / rho, rho = d (n . r_x); p0 = A x + b / d
-    float inv_rho = hv ? 1.0f / (d * nr) : 0.0f;
-    float m0 = (Ki[0] * n0 + Ki[3] * n1 + Ki[6] * n2) * inv_rho;
-    float m1 = (Ki[1] * n0 + Ki[4] * n1 + Ki[7] * n2) * inv_rho;
-    float invd = hv ? 1.0f / d : 0.0f;
+    float k0 = Ki[0] * n0 + Ki[3] * n1 + Ki[6] * n2;
+    float k1 = Ki[1] * n0 + Ki[4] * n1 + Ki[7] * n2;
+    bool corners = fmaf(pw.cu_lo, k0, fmaf(pw.cv_lo, k1, nr)) < 0.0f && fmaf(pw.cu_hi, k0, fmaf(pw.cv_lo, k1, nr)) < 0.0f &&
+                   fmaf(pw.cu_lo, k0, fmaf(pw.cv_hi, k1, nr)) < 0.0f && fmaf(pw.cu_hi, k0, fmaf(pw.cv_hi, k1, nr)) < 0.0f;
+    c.ok = want && pw.ok && d > 0.0f && d < 3.0e38f && nr < -kGraze * rlen && corners;
+    float inv_rho = c.ok ? 1.0f / (d * nr) : 0.0f;
+    c.m0 = k0 * inv_rho;
+    c.m1 = k1 * inv_rho;
+    c.invd = c.ok ? 1.0f / d : 0.0f;
+    return c;
+}
+
+// Costs C(x) (Eq. 5) of up to 8 hypotheses of the warp's pixel: lane c < nc
+// holds hypothesis c on entry and its cost on return.
+//   1. the (hypothesis, view) pairs whose window maps inside the source
+//      image (exact corner test: the image of the window is convex, w > 0
+//      included) are listed in `list` (per-warp shared memory, nc * n_src
+//      entries), hypothesis-major;
+//   2. each group of G lanes takes the next pair: S bilinear gathers per
+//      lane, two-pass weighted moments with group reductions, ZNCC (Eq. 4),
+//      C(x,j) = 1 - Z; a view is excluded when its weighted variance is below
+//      1e-6 on the [0,1] scale (reading);
+//   3. the per-view results are folded into the owner lane of the
+//      hypothesis in view order (Eq. 5, weights 1/max(C, 1e-6)).
+// Must be called by all 32 lanes with the same nc (warp-uniform).
+template <int G, int S, bool VIEWS>
+__device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __restrict__ sv, const PixWin<S>& pw,
+                                            int px, int py, const Cand& my, int nc, uint16_t* list,
+                                            float* view_cost, unsigned& n_evals) {
+    constexpr int NG = 32 / G;
+    const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
+    const int V = rc.n_src;
+    const int P = nc * V;
     const float x = (float)px, y = (float)py;
+    // ---- 1. list the pairs that map inside the source images
+    int count = 0;
+    for (int base = 0; base < P; base += 32) {
+        int i = base + lane;
+        bool act = i < P;
+        int c = act ? i / V : 0;
+        int j = act ? i - c * V : 0;
+        float m0 = __shfl_sync(0xffffffffu, my.m0, c);
+        float m1 = __shfl_sync(0xffffffffu, my.m1, c);
+        float invd = __shfl_sync(0xffffffffu, my.invd, c);
+        bool cok = __shfl_sync(0xffffffffu, (int)my.ok, c) != 0;
+        const ViewSm& v = sv[j];
+        float h0x = fmaf(v.b[0], m0, v.A[0]), h0y = fmaf(v.b[1], m0, v.A[3]), h0z = fmaf(v.b[2], m0, v.A[6]);
+        float h1x = fmaf(v.b[0], m1, v.A[1]), h1y = fmaf(v.b[1], m1, v.A[4]), h1z = fmaf(v.b[2], m1, v.A[7]);
+        float p0x = fmaf(v.b[0], invd, fmaf(v.A[0], x, fmaf(v.A[1], y, v.A[2])));
+        float p0y = fmaf(v.b[1], invd, fmaf(v.A[3], x, fmaf(v.A[4], y, v.A[5])));
+        float p0z = fmaf(v.b[2], invd, fmaf(v.A[6], x, fmaf(v.A[7], y, v.A[8])));
+        bool ok = act && cok;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float cu = (k & 1) ? pw.cu_hi : pw.cu_lo, cv = (k & 2) ? pw.cv_hi : pw.cv_lo;
+            float cx = fmaf(cu, h0x, fmaf(cv, h1x, p0x));
+            float cy = fmaf(cu, h0y, fmaf(cv, h1y, p0y));
+            float cz = fmaf(cu, h0z, fmaf(cv, h1z, p0z));
+            float icz = 1.0f / cz;
+            float xs = cx * icz, ys = cy * icz;
+            ok = ok && cz > 0.0f && xs >= 0.0f && xs <= v.wm1 && ys >= 0.0f && ys <= v.hm1;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok) list[count + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((c << 8) | j);
+        count += __popc(m);
+    }
+    if (VIEWS && view_cost && lane < V) view_cost[lane] = kCmax;
+    __syncwarp();
+    // ---- 2./3. evaluate the listed pairs, NG at a time
     int cnt = 0;
     float inv_sum = 0.0f;
-    for (int j = 0; j < rc.n_src; ++j) {
-        const PairConst& P = rc.pair[j];
-        float h0x = fmaf(P.b[0], m0, P.A[0]), h0y = fmaf(P.b[1], m0, P.A[3]), h0z = fmaf(P.b[2], m0, P.A[6]);
-        float h1x = fmaf(P.b[0], m1, P.A[1]), h1y = fmaf(P.b[1], m1, P.A[4]), h1z = fmaf(P.b[2], m1, P.A[7]);
-        float p0x = fmaf(P.b[0], invd, fmaf(P.A[0], x, fmaf(P.A[1], y, P.A[2])));
-        float p0y = fmaf(P.b[1], invd, fmaf(P.A[3], x, fmaf(P.A[4], y, P.A[5])));
-        float p0z = fmaf(P.b[2], invd, fmaf(P.A[6], x, fmaf(P.A[7], y, P.A[8])));
-        // this lane's corner of the window (exact convexity test: the window
-        // maps into the source image iff its four corners do, w > 0 included)
-        float cx = fmaf(pw.cu, h0x, fmaf(pw.cv, h1x, p0x));
-        float cy = fmaf(pw.cu, h0y, fmaf(pw.cv, h1y, p0y));
-        float cz = fmaf(pw.cu, h0z, fmaf(pw.cv, h1z, p0z));
-        float icz = 1.0f / cz;
-        float xs = cx * icz, ys = cy * icz;
-        bool cok = hv && cz > 0.0f && xs >= 0.0f && xs <= (float)(P.W - 1) && ys >= 0.0f && ys <= (float)(P.H - 1);
-        bool vok = ((__ballot_sync(0xffffffffu, cok) & gm) == gm);
-        if (!__any_sync(0xffffffffu, vok)) {
-            if (VIEWS && (lane & (G - 1)) == 0 && view_cost) view_cost[j] = kCmax;
-            continue;
-        }
+    for (int r = 0; r < count; r += NG) {
+        int it = r + grp;
+        bool has = it < count;
+        int e = list[has ? it : 0];
+        int c = e >> 8, j = e & 255;
+        float m0 = __shfl_sync(0xffffffffu, my.m0, c);
+        float m1 = __shfl_sync(0xffffffffu, my.m1, c);
+        float invd = __shfl_sync(0xffffffffu, my.invd, c);
+        const ViewSm& v = sv[j];
+        float h0x = fmaf(v.b[0], m0, v.A[0]), h0y = fmaf(v.b[1], m0, v.A[3]), h0z = fmaf(v.b[2], m0, v.A[6]);
+        float h1x = fmaf(v.b[0], m1, v.A[1]), h1y = fmaf(v.b[1], m1, v.A[4]), h1z = fmaf(v.b[2], m1, v.A[7]);
+        float p0x = fmaf(v.b[0], invd, fmaf(v.A[0], x, fmaf(v.A[1], y, v.A[2])));
+        float p0y = fmaf(v.b[1], invd, fmaf(v.A[3], x, fmaf(v.A[4], y, v.A[5])));
+        float p0z = fmaf(v.b[2], invd, fmaf(v.A[6], x, fmaf(v.A[7], y, v.A[8])));
         // sample coordinates shifted by -1/2 for tex_sample
         h0x = fmaf(-0.5f, h0z, h0x);
         h0y = fmaf(-0.5f, h0z, h0y);
@@ -229,7 +305,9 @@ __device__ __forceinline__ float eval_hyp(const RefConst& rc, const PixWin<S>& p
         h1y = fmaf(-0.5f, h1z, h1y);
         p0x = fmaf(-0.5f, p0z, p0x);
         p0y = fmaf(-0.5f, p0z, p0y);
-        float sv[S];
+        const float4* tex = v.tex;
+        const uint32_t pitch = v.pitch, n_tex = v.n_tex;
+        float sval[S];
         float s1 = 0.0f;
 #pragma unroll
         for (int k = 0; k < S; ++k) {
@@ -237,16 +315,16 @@ __device__ __forceinline__ float eval_hyp(const RefConst& rc, const PixWin<S>& p
             float Y = fmaf(pw.ou[k], h0y, fmaf(pw.ov[k], h1y, p0y));
             float Z = fmaf(pw.ou[k], h0z, fmaf(pw.ov[k], h1z, p0z));
             float iz = rcp_approx(Z);
-            float v = tex_sample(P.tex, P.pitch, P.n_tex, __fmul_rn(X, iz), __fmul_rn(Y, iz));
-            sv[k] = v;
-            s1 = fmaf(pw.w[k], v, s1);
+            float val = tex_sample(tex, (int)pitch, n_tex, __fmul_rn(X, iz), __fmul_rn(Y, iz));
+            sval[k] = val;
+            s1 = fmaf(pw.w[k], val, s1);
         }
         s1 = gsum<G>(s1);
         float mu = s1 * pw.inv_wsum;
         float sdd = 0.0f, srd = 0.0f;
 #pragma unroll
         for (int k = 0; k < S; ++k) {
-            float dv = sv[k] - mu;
+            float dv = sval[k] - mu;
             float t = pw.w[k] * dv;
             sdd = fmaf(t, dv, sdd);
             srd = fmaf(pw.wr[k], dv, srd);
@@ -254,27 +332,53 @@ __device__ __forceinline__ float eval_hyp(const RefConst& rc, const PixWin<S>& p
         sdd = gsum<G>(sdd);
         srd = gsum<G>(srd);
         float cj = kCmax;
-        n_evals += (vok && (lane & (G - 1)) == 0) ? 1u : 0u;
-        if (vok && sdd >= kTauVar * pw.wsum) {
+        bool okj = false;
+        if (has && sdd >= kTauVar * pw.wsum) {
             float z = srd * rsqrtf(pw.srr * sdd);
             z = fminf(1.0f, fmaxf(-1.0f, z));
             cj = 1.0f - z;
-            if (cj < kCmax) {
+            okj = cj < kCmax;
+            if (!okj) cj = kCmax;
+        }
+        if (has && lg == 0) {
+            n_evals++;
+            if (VIEWS && view_cost) view_cost[j] = cj;
+        }
+        // fold the NG results into the owner lanes, in list (= view) order
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            int cg = __shfl_sync(0xffffffffu, okj ? c : -1, g * G);
+            float cjg = __shfl_sync(0xffffffffu, cj, g * G);
+            if (lane == cg) {
                 cnt++;
-                inv_sum += 1.0f / fmaxf(cj, kEpsC);
-            } else {
-                cj = kCmax;
+                inv_sum += 1.0f / fmaxf(cjg, kEpsC);
             }
         }
-        if (VIEWS && (lane & (G - 1)) == 0 && view_cost) view_cost[j] = cj;
     }
-    return (hv && cnt > 0) ? (float)cnt / inv_sum : kCmax;
+    __syncwarp();
+    return (lane < nc && my.ok && cnt > 0) ? (float)cnt / inv_sum : kCmax;
 }
 
 // adds the warp's evaluated (pixel, hypothesis, view) count to the counter
 __device__ __forceinline__ void flush_evals(unsigned long long* counter, unsigned n) {
     unsigned t = __reduce_add_sync(0xffffffffu, n);
     if (counter && (threadIdx.x & 31) == 0 && t) atomicAdd(counter, (unsigned long long)t);
+}
+
+// index of the lowest cost among lanes 0..nc-1 (lowest lane on a tie); costs
+// of the other lanes are ignored
+__device__ __forceinline__ int warp_argmin(float cost, int nc, float& best) {
+    const int lane = threadIdx.x & 31;
+    float c = lane < nc ? cost : 3.0e38f;
+    int i = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float oc = __shfl_xor_sync(0xffffffffu, c, o);
+        int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (oc < c || (oc == c && oi < i)) { c = oc; i = oi; }
+    }
+    best = c;
+    return i;
 }
 
 // Sec. III-B: n = (cos t sin p, sin t sin p, cos p), turned to face the camera.

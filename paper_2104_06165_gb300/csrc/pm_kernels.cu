@@ -3,6 +3,10 @@
 //   Sec. III-B  random initialisation
 //   Sec. III-C  Eq. 4 weighted ZNCC, Eq. 5 aggregation, refinement
 //   Sec. III    red-black checkerboard updating
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
+
 #include "pm_device.cuh"
 
 using namespace mvsdev;
@@ -32,54 +36,76 @@ __global__ void k_build_texture(const uint8_t* __restrict__ img, int W, int H, f
     }
 }
 
+// Per-block shared memory: the source-view table and one pair list per warp.
+constexpr int kWarps = kBlock / 32;
+struct BlockSm {
+    ViewSm views[MVS_MAX_SRC];
+    uint16_t list[kWarps][8 * MVS_MAX_SRC];
+};
+
 // ---------------------------------------------------------------------------
-// Sec. III-B: random initialisation, then the cost of the initial plane
+// Sec. III-B: random initialisation, then the cost of the initial plane.
+// One warp per pixel, grid-stride over the pixels.
 // ---------------------------------------------------------------------------
 template <int G, int S>
 __global__ void __launch_bounds__(kBlock) k_init(const __grid_constant__ RefConst rc, float* view_cost) {
-    const int lane = threadIdx.x & 31;
+    __shared__ BlockSm sm;
+    load_views(rc, sm.views);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long npix = (long long)rc.W * rc.H;
-    const long long a = ((long long)blockIdx.x * kBlock + threadIdx.x) / G;
-    if (((long long)blockIdx.x * kBlock + (threadIdx.x & ~31)) / G >= npix) return;  // whole warp past the end
-    const bool exists = a < npix;
-    const int px = exists ? (int)(a % rc.W) : 0, py = exists ? (int)(a / rc.W) : 0;
-    PixWin<S> pw;
-    build_window<G, S>(rc, px, py, exists, pw);
-    float u[3];
-    draws3(rc, exists ? a : 0, -1, u);
-    float d = rc.d_lo + (rc.d_hi - rc.d_lo) * u[0];
-    float th = 2.0f * kPi * u[1];
-    float ph = kPi * (u[2] - 0.5f);
-    float n0, n1, n2;
-    normal_from_angles(th, ph, pw.rx0, pw.rx1, pw.rx2, n0, n1, n2);
-    float* vc = (view_cost && exists) ? view_cost + a * rc.n_src : nullptr;
     unsigned nev = 0;
-    float c = eval_hyp<G, S, true>(rc, pw, px, py, n0, n1, n2, d, exists, vc, nev);
-    flush_evals(rc.eval_counter, nev);
-    if (exists && (lane & (G - 1)) == 0) {
-        rc.plane[a] = make_float4(n0, n1, n2, d);
-        rc.cost[a] = c;
+    for (long long a = (long long)blockIdx.x * kWarps + warp; a < npix; a += (long long)gridDim.x * kWarps) {
+        const int px = (int)(a % rc.W), py = (int)(a / rc.W);
+        PixWin<S> pw;
+        build_window<G, S>(rc, px, py, true, pw);
+        float u[3];
+        draws3(rc, a, -1, u);
+        float d = rc.d_lo + (rc.d_hi - rc.d_lo) * u[0];
+        float th = 2.0f * kPi * u[1];
+        float ph = kPi * (u[2] - 0.5f);
+        float n0, n1, n2;
+        normal_from_angles(th, ph, pw.rx0, pw.rx1, pw.rx2, n0, n1, n2);
+        float* vc = view_cost ? view_cost + a * rc.n_src : nullptr;
+        float c = kCmax;
+        if (pw.ok) {
+            Cand my = make_cand(rc, pw, n0, n1, n2, d, lane == 0);
+            c = eval_batch<G, S, true>(rc, sm.views, pw, px, py, my, 1, sm.list[warp], vc, nev);
+        } else if (vc && lane < rc.n_src) {
+            vc[lane] = kCmax;
+        }
+        if (lane == 0) {
+            rc.plane[a] = make_float4(n0, n1, n2, d);
+            rc.cost[a] = c;
+        }
     }
+    flush_evals(rc.eval_counter, nev);
 }
 
 // cost of a given plane map
 template <int G, int S>
 __global__ void __launch_bounds__(kBlock) k_cost(const __grid_constant__ RefConst rc, const float4* __restrict__ plane,
                                                   float* __restrict__ cost, float* view_cost) {
-    const int lane = threadIdx.x & 31;
+    __shared__ BlockSm sm;
+    load_views(rc, sm.views);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long npix = (long long)rc.W * rc.H;
-    const long long a = ((long long)blockIdx.x * kBlock + threadIdx.x) / G;
-    if (((long long)blockIdx.x * kBlock + (threadIdx.x & ~31)) / G >= npix) return;
-    const bool exists = a < npix;
-    const int px = exists ? (int)(a % rc.W) : 0, py = exists ? (int)(a / rc.W) : 0;
-    PixWin<S> pw;
-    build_window<G, S>(rc, px, py, exists, pw);
-    float4 pl = exists ? plane[a] : make_float4(0.f, 0.f, -1.f, 1.f);
-    float* vc = (view_cost && exists) ? view_cost + a * rc.n_src : nullptr;
     unsigned nev = 0;
-    float c = eval_hyp<G, S, true>(rc, pw, px, py, pl.x, pl.y, pl.z, pl.w, exists, vc, nev);
+    for (long long a = (long long)blockIdx.x * kWarps + warp; a < npix; a += (long long)gridDim.x * kWarps) {
+        const int px = (int)(a % rc.W), py = (int)(a / rc.W);
+        PixWin<S> pw;
+        build_window<G, S>(rc, px, py, true, pw);
+        float4 pl = plane[a];
+        float* vc = view_cost ? view_cost + a * rc.n_src : nullptr;
+        float c = kCmax;
+        if (pw.ok) {
+            Cand my = make_cand(rc, pw, pl.x, pl.y, pl.z, pl.w, lane == 0);
+            c = eval_batch<G, S, true>(rc, sm.views, pw, px, py, my, 1, sm.list[warp], vc, nev);
+        } else if (vc && lane < rc.n_src) {
+            vc[lane] = kCmax;
+        }
+        if (lane == 0) cost[a] = c;
+    }
     flush_evals(rc.eval_counter, nev);
-    if (exists && (lane & (G - 1)) == 0) cost[a] = c;
 }
 
 // ---------------------------------------------------------------------------
@@ -103,35 +129,31 @@ __device__ __forceinline__ void near_member(int g, int k, int& dx, int& dy) {
 }
 
 template <int G, int S>
-__global__ void __launch_bounds__(kBlock) k_phase(const __grid_constant__ RefConst rc, int phase) {
-    const int lane = threadIdx.x & 31, lg = lane & (G - 1), gbase = lane & ~(G - 1);
+__global__ void __launch_bounds__(kBlock, 3) k_phase(const __grid_constant__ RefConst rc, int phase) {
+    __shared__ BlockSm sm;
+    load_views(rc, sm.views);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int color = phase & 1;
     const int Wa = (rc.W + 1) >> 1;
     const long long nact = (long long)Wa * rc.H;
-    const long long a = ((long long)blockIdx.x * kBlock + threadIdx.x) / G;
-    if (((long long)blockIdx.x * kBlock + (threadIdx.x & ~31)) / G >= nact) return;
-    const int py = (int)(a / Wa);
-    const int px = 2 * (int)(a % Wa) + ((py + color) & 1);
-    const bool exists = a < nact && px < rc.W;
-    const int qx = exists ? px : 0, qy = exists ? py : 0;
-    const long long pix = (long long)qy * rc.W + qx;
-    PixWin<S> pw;
-    build_window<G, S>(rc, qx, qy, exists, pw);
-
-    float4 cur = exists ? rc.plane[pix] : make_float4(0.f, 0.f, -1.f, 1.f);
-    float cur_c = exists ? rc.cost[pix] : kCmax;
     unsigned nev = 0;
+    for (long long a = (long long)blockIdx.x * kWarps + warp; a < nact; a += (long long)gridDim.x * kWarps) {
+        const int py = (int)(a / Wa);
+        const int px = 2 * (int)(a % Wa) + ((py + color) & 1);
+        if (px >= rc.W) continue;                       // warp-uniform
+        const long long pix = (long long)py * rc.W + px;
+        PixWin<S> pw;
+        build_window<G, S>(rc, px, py, true, pw);
+        if (!pw.ok) continue;                           // flat patch: every hypothesis costs C_max
+        float4 cur = rc.plane[pix];
+        float cur_c = rc.cost[pix];
 
-    // ---- candidate search: lane lg scans groups lg, lg + G, ...
-    constexpr int kSlots = (8 + G - 1) / G;
-    int cand[kSlots];
-#pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-        int g = s * G + lg;
-        int best = -1;
-        float bc = 0.0f;
-        if (g < 8 && exists) {
-            int cnt = g < 4 ? 6 : 11;
+        // ---- propagation: lane g < 8 scans group g and carries its plane over
+        int q = -1;
+        if (lane < 8) {
+            const int g = lane;
+            float bc = 0.0f;
+            const int cnt = g < 4 ? 6 : 11;
             for (int k = 0; k < cnt; ++k) {
                 int dx, dy;
                 if (g < 4) near_member(g, k, dx, dy);
@@ -140,28 +162,19 @@ __global__ void __launch_bounds__(kBlock) k_phase(const __grid_constant__ RefCon
                     dx = g == 6 ? -dist : (g == 7 ? dist : 0);
                     dy = g == 4 ? -dist : (g == 5 ? dist : 0);
                 }
-                int x2 = qx + dx, y2 = qy + dy;
+                int x2 = px + dx, y2 = py + dy;
                 if (x2 < 0 || x2 >= rc.W || y2 < 0 || y2 >= rc.H) continue;
-                int q = y2 * rc.W + x2;
-                float c = rc.cost[q];
-                if (best < 0 || c < bc) { best = q; bc = c; }
+                int qq = y2 * rc.W + x2;
+                float c = rc.cost[qq];
+                if (q < 0 || c < bc) { q = qq; bc = c; }
             }
         }
-        cand[s] = best;
-    }
-
-    // ---- propagation: evaluate the transferred candidate planes
-    float best_c = cur_c;
-    float4 best = cur;
-    bool changed = false;
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-        int q = __shfl_sync(0xffffffffu, cand[g / G], gbase + (g % G));
-        bool ok = exists && q >= 0;
-        float4 np = ok ? rc.plane[q] : make_float4(0.f, 0.f, -1.f, 1.f);
+        float4 np = make_float4(0.f, 0.f, -1.f, 1.f);
         float d = 0.0f;
+        bool ok = q >= 0;
         if (ok) {
             // the neighbour's plane carried over as a plane (reading)
+            np = rc.plane[q];
             int x2 = q % rc.W, y2 = q / rc.W;
             const float* Ki = rc.Kinv;
             float r0 = fmaf(Ki[0], (float)x2, fmaf(Ki[1], (float)y2, Ki[2]));
@@ -173,65 +186,82 @@ __global__ void __launch_bounds__(kBlock) k_phase(const __grid_constant__ RefCon
             d = ok ? rho / den : 0.0f;
             ok = ok && d >= rc.d_lo && d <= rc.d_hi;
         }
-        float c = eval_hyp<G, S, false>(rc, pw, qx, qy, np.x, np.y, np.z, d, ok, nullptr, nev);
-        if (ok && c < best_c) {
-            best_c = c;
-            best = make_float4(np.x, np.y, np.z, d);
-            changed = true;
+        // stage 0: the eight propagated planes; stage 1: the three refinement
+        // candidates built from the state after stage 0.  One call site keeps
+        // a single copy of the evaluation in the instruction cache.
+        float4 hyp4 = make_float4(np.x, np.y, np.z, d);
+        bool want = ok;
+#pragma unroll 1
+        for (int stage = 0; stage < 2; ++stage) {
+            if (stage == 1) {
+                // refinement (Sec. III-C): delta_d in [-d_hi/4, d_hi/4],
+                // delta_theta in [-pi/2, pi/2], delta_phi in [-pi/12, pi/12]
+                float u[3];
+                draws3(rc, pix, phase, u);
+                float dd = (2.0f * u[0] - 1.0f) * (rc.d_hi * 0.25f);
+                float dth = (2.0f * u[1] - 1.0f) * (kPi * 0.5f);
+                float dph = (2.0f * u[2] - 1.0f) * (kPi / 12.0f);
+                float d_new = fminf(fmaxf(cur.w + dd, rc.d_lo), rc.d_hi);
+                float m0 = cur.x, m1 = cur.y, m2 = cur.z;
+                if (m2 < 0.0f) { m0 = -m0; m1 = -m1; m2 = -m2; }
+                float th = atan2f(m1, m0);
+                float ph = acosf(fminf(1.0f, fmaxf(-1.0f, m2)));
+                float nn0, nn1, nn2;
+                normal_from_angles(th + dth, ph + dph, pw.rx0, pw.rx1, pw.rx2, nn0, nn1, nn2);
+                // candidates (d_new, n_old), (d_old, n_new), (d_new, n_new) in lanes 0..2
+                hyp4 = lane == 0 ? make_float4(cur.x, cur.y, cur.z, d_new)
+                     : (lane == 1 ? make_float4(nn0, nn1, nn2, cur.w) : make_float4(nn0, nn1, nn2, d_new));
+                want = lane < 3;
+            }
+            const int nc = stage == 0 ? 8 : 3;
+            Cand my = make_cand(rc, pw, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
+            float c = eval_batch<G, S, false>(rc, sm.views, pw, px, py, my, nc, sm.list[warp], nullptr, nev);
+            float bc;
+            int bi = warp_argmin(my.ok ? c : 3.0e38f, nc, bc);
+            if (bc < cur_c) {
+                cur = make_float4(__shfl_sync(0xffffffffu, hyp4.x, bi), __shfl_sync(0xffffffffu, hyp4.y, bi),
+                                  __shfl_sync(0xffffffffu, hyp4.z, bi), __shfl_sync(0xffffffffu, hyp4.w, bi));
+                cur_c = bc;
+            }
         }
-    }
-    if (changed) {
-        cur = best;
-        cur_c = best_c;
-    }
-
-    // ---- refinement (Sec. III-C): delta_d in [-d_hi/4, d_hi/4],
-    // delta_theta in [-pi/2, pi/2], delta_phi in [-pi/12, pi/12]
-    float u[3];
-    draws3(rc, pix, phase, u);
-    float dd = (2.0f * u[0] - 1.0f) * (rc.d_hi * 0.25f);
-    float dth = (2.0f * u[1] - 1.0f) * (kPi * 0.5f);
-    float dph = (2.0f * u[2] - 1.0f) * (kPi / 12.0f);
-    float d_new = fminf(fmaxf(cur.w + dd, rc.d_lo), rc.d_hi);
-    float m0 = cur.x, m1 = cur.y, m2 = cur.z;
-    if (m2 < 0.0f) { m0 = -m0; m1 = -m1; m2 = -m2; }
-    float th = atan2f(m1, m0);
-    float ph = acosf(fminf(1.0f, fmaxf(-1.0f, m2)));
-    float nn0, nn1, nn2;
-    normal_from_angles(th + dth, ph + dph, pw.rx0, pw.rx1, pw.rx2, nn0, nn1, nn2);
-    float4 rcand[3] = {make_float4(cur.x, cur.y, cur.z, d_new), make_float4(nn0, nn1, nn2, cur.w),
-                       make_float4(nn0, nn1, nn2, d_new)};
-    best_c = cur_c;
-    best = cur;
-    changed = false;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        float c = eval_hyp<G, S, false>(rc, pw, qx, qy, rcand[k].x, rcand[k].y, rcand[k].z, rcand[k].w, exists,
-                                         nullptr, nev);
-        if (exists && c < best_c) {
-            best_c = c;
-            best = rcand[k];
-            changed = true;
+        if (lane == 0) {
+            rc.plane[pix] = cur;
+            rc.cost[pix] = cur_c;
         }
-    }
-    if (changed) {
-        cur = best;
-        cur_c = best_c;
-    }
-    if (exists && lg == 0) {
-        rc.plane[pix] = cur;
-        rc.cost[pix] = cur_c;
     }
     flush_evals(rc.eval_counter, nev);
 }
 
-template <int G, int S>
-unsigned grid_for(long long units) {
-    long long threads = units * G;
-    return (unsigned)((threads + kBlock - 1) / kBlock);
+// grid of the grid-stride kernels: as many blocks as fit on the device at
+// once (occupancy query, cached per kernel), at most one warp per unit
+}  // namespace
+
+unsigned pm_grid_for(const void* kernel, long long units) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> per_sm_cache;
+    static int sms = 0;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        }
+        auto it = per_sm_cache.find(kernel);
+        if (it == per_sm_cache.end()) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+            per_sm = std::max(per_sm, 1);
+            per_sm_cache[kernel] = per_sm;
+        } else {
+            per_sm = it->second;
+        }
+    }
+    long long need = (units + kWarps - 1) / kWarps;
+    long long full = (long long)sms * per_sm;
+    return (unsigned)std::max<long long>(1, std::min(need, full));
 }
 
-}  // namespace
 
 // lanes per pixel and slots per lane for a window of n x n samples
 int pm_group_lanes(int n) {
@@ -242,15 +272,20 @@ int pm_group_lanes(int n) {
     return 32;
 }
 
-#define MVS_DISPATCH(n, CALL)                       \
-    do {                                            \
-        int _s = (n) * (n);                         \
-        if (_s <= 16) { CALL(4, 4); }               \
-        else if (_s <= 36) { CALL(4, 9); }          \
-        else if (_s <= 64) { CALL(8, 8); }          \
-        else if (_s <= 128) { CALL(8, 16); }        \
-        else if (_s <= 256) { CALL(16, 16); }       \
-        else { CALL(32, 16); }                      \
+// Lanes per pixel group (G) and slots per lane (S) for an n x n window:
+// G * S >= n * n.  lanes_hint 0 picks the default; 4, 8, 16 or 32 picks G.
+#define MVS_DISPATCH(n, hint, CALL)                                                       \
+    do {                                                                                  \
+        int _s = (n) * (n), _h = (hint);                                                  \
+        if (_s <= 16) { CALL(4, 4); }                                                     \
+        else if (_s <= 36) { if (_h == 8) { CALL(8, 5); } else { CALL(4, 9); } }          \
+        else if (_s <= 64) { if (_h == 16) { CALL(16, 4); } else { CALL(8, 8); } }        \
+        else if (_s <= 128) {                                                             \
+            if (_h == 16) { CALL(16, 8); } else if (_h == 32) { CALL(32, 4); }            \
+            else { CALL(8, 16); }                                                         \
+        }                                                                                 \
+        else if (_s <= 256) { if (_h == 32) { CALL(32, 8); } else { CALL(16, 16); } }     \
+        else { CALL(32, 16); }                                                            \
     } while (0)
 
 cudaError_t launch_build_texture(const uint8_t* img, int W, int H, float4* tex, cudaStream_t s) {
@@ -263,8 +298,8 @@ cudaError_t launch_build_texture(const uint8_t* img, int W, int H, float4* tex, 
 
 cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s) {
     long long npix = (long long)rc.W * rc.H;
-#define CALL(G, S) k_init<G, S><<<grid_for<G, S>(npix), kBlock, 0, s>>>(rc, view_cost)
-    MVS_DISPATCH(rc.n, CALL);
+#define CALL(G, S) k_init<G, S><<<pm_grid_for((const void*)k_init<G, S>, npix), kBlock, 0, s>>>(rc, view_cost)
+    MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
 #undef CALL
     count_launch();
     return cudaGetLastError();
@@ -272,8 +307,8 @@ cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s) {
 
 cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, float* view_cost, cudaStream_t s) {
     long long npix = (long long)rc.W * rc.H;
-#define CALL(G, S) k_cost<G, S><<<grid_for<G, S>(npix), kBlock, 0, s>>>(rc, plane, cost, view_cost)
-    MVS_DISPATCH(rc.n, CALL);
+#define CALL(G, S) k_cost<G, S><<<pm_grid_for((const void*)k_cost<G, S>, npix), kBlock, 0, s>>>(rc, plane, cost, view_cost)
+    MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
 #undef CALL
     count_launch();
     return cudaGetLastError();
@@ -281,8 +316,8 @@ cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, fl
 
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s) {
     long long nact = (long long)((rc.W + 1) / 2) * rc.H;
-#define CALL(G, S) k_phase<G, S><<<grid_for<G, S>(nact), kBlock, 0, s>>>(rc, phase)
-    MVS_DISPATCH(rc.n, CALL);
+#define CALL(G, S) k_phase<G, S><<<pm_grid_for((const void*)k_phase<G, S>, nact), kBlock, 0, s>>>(rc, phase)
+    MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
 #undef CALL
     count_launch();
     return cudaGetLastError();

@@ -39,7 +39,8 @@ class mvs_pm_params(C.Structure):
     _fields_ = [("win_radius", C.c_float), ("win_samples", C.c_int32), ("sigma_s", C.c_float),
                 ("sigma_c", C.c_float), ("d_lo", C.c_float), ("d_hi", C.c_float), ("iters", C.c_int32),
                 ("phase_begin", C.c_int32), ("phase_end", C.c_int32), ("init_mode", C.c_int32),
-                ("seed", C.c_uint64), ("precision", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("seed", C.c_uint64), ("precision", C.c_int32), ("lanes_per_pixel", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class mvs_depth_map(C.Structure):
@@ -72,11 +73,12 @@ class PMParams:
     init_mode: int = MVS_INIT_RANDOM
     seed: int = 0
     precision: int = 0
+    lanes_per_pixel: int = 0
 
     def c(self):
         return mvs_pm_params(self.win_radius, self.win_samples, self.sigma_s, self.sigma_c, self.d_lo, self.d_hi,
                              self.iters, self.phase_begin, self.phase_end, self.init_mode,
-                             int(self.seed) & 0xFFFFFFFFFFFFFFFF, self.precision)
+                             int(self.seed) & 0xFFFFFFFFFFFFFFFF, self.precision, self.lanes_per_pixel)
 
 
 @dataclass

@@ -1,0 +1,65 @@
+"""World-size-2 gloo test of the multi-rank host logic (view sharding and the
+plane-map exchange before the geometric filter)."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_2104_06165_gb300.dist import assign_views, exchange_plane_maps, owner_of
+
+
+def test_assignment_balances_pixels():
+    counts = [3072 * 2048] * 8 + [2048 * 1365] * 8 + [1536 * 1024] * 8
+    parts = assign_views(counts, 4)
+    assert sorted(v for p in parts for v in p) == list(range(24))
+    loads = [sum(counts[v] for v in p) for p in parts]
+    assert max(loads) - min(loads) <= 1536 * 1024
+    assert assign_views([5, 5], 1) == [[0, 1]]
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, shapes, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        parts = assign_views([h * w for h, w in shapes], world)
+        mine = {}
+        for v in parts[rank]:
+            H, W = shapes[v]
+            mine[v] = torch.full((H, W, 4), float(v)) + torch.arange(H * W * 4, dtype=torch.float32).reshape(H, W, 4)
+        allm = exchange_plane_maps(mine, shapes, parts)
+        ok = all(torch.equal(allm[v], torch.full(shapes[v] + (4,), float(v)) +
+                             torch.arange(shapes[v][0] * shapes[v][1] * 4, dtype=torch.float32).reshape(
+                                 shapes[v] + (4,))) for v in range(len(shapes)))
+        q.put((rank, ok, sorted(allm)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_world2_exchange():
+    shapes = [(6, 8), (5, 7), (6, 8), (3, 4), (4, 4)]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, shapes, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ok, views in res:
+        assert ok and views == list(range(len(shapes)))
+    assert set(owner_of(assign_views([48, 35, 48, 12, 16], 2)).values()) == {0, 1}

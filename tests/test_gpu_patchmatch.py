@@ -67,7 +67,10 @@ def test_gt_planes_score_low_on_texture(small, mvs_lib):
     inner[8:-8, 8:-8] = True
     tex = sc.gt_textured & inner
     assert np.median(cost[tex]) < 0.05
-    assert (cost[~sc.gt_textured] == 2.0).mean() > 0.9   # flat patches: C_max
+    # pixels whose whole window lies on a texture-less quad: flat patch, C_max
+    from scipy.ndimage import binary_erosion
+    flat = binary_erosion(~sc.gt_textured, structure=np.ones((13, 13), bool))
+    assert flat.sum() > 100 and (cost[flat] == 2.0).all()
 
 
 def test_init_parity(small, mvs_lib, oracle_lib):

@@ -1,0 +1,175 @@
+"""GPU-vs-oracle parity of the geometric filter (Sec. III-D) and of the plane
+hypothesis inference stages (Sec. III-E), each stage fed the same inputs on
+both sides (lockstep)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+COST_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def multi(mvs_lib, oracle_lib):
+    """Four views of one scene with the rendered (exact) plane maps of every
+    view stored in the context, plus noisy copies."""
+    import torch
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_scene(W=128, H=96, n_src=3, seed=21, baseline_frac=0.1)
+    ctx = mvs_lib.Context(sc.K, sc.R, sc.t, sc.images, stream=torch.cuda.current_stream())
+    osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
+    gt = {}
+    for v in range(4):
+        out = scenes.render(sc.quads, sc.K[v], sc.R[v], sc.t[v], 128, 96, want_gt=True, threads=1)
+        gt[v] = np.concatenate([out["normal"], out["depth"][..., None]], -1)
+    yield sc, ctx, osc, gt
+    ctx.close()
+
+
+def _store(mvs, ctx, v, plane, others):
+    """Put a given plane map of view v into the context (no phases run)."""
+    p = mvs.PMParams(win_radius=5.0, win_samples=6, iters=0, phase_begin=0, phase_end=0,
+                     init_mode=mvs.MVS_INIT_GIVEN)
+    pl = np.ascontiguousarray(plane, np.float32)
+    co = np.zeros(pl.shape[:2], np.float32)
+    mvs.mvs_patchmatch(ctx.h, v, others, p, pl, co)
+
+
+def test_geo_filter_parity(multi, mvs_lib, oracle_lib):
+    sc, ctx, osc, gt = multi
+    rng = np.random.default_rng(3)
+    noisy = {}
+    for v in range(4):
+        pl = gt[v].copy()
+        pl[..., 3] += rng.normal(0, 0.012, pl.shape[:2]) * (pl[..., 3] > 0)
+        noisy[v] = pl.astype(np.float32)
+        _store(mvs_lib, ctx, v, noisy[v], [u for u in range(4) if u != v])
+    keep = np.zeros((96, 128), np.uint8)
+    cnt = np.zeros((96, 128), np.int32)
+    mvs_lib.mvs_geo_filter(ctx.h, 0, [1, 2, 3], mvs_lib.FilterParams(), keep, cnt)
+    okeep, ocnt = oracle_lib.geo_filter(osc, 0, [1, 2, 3], {v: noisy[v].astype(np.float64) for v in range(4)})
+    assert 0.05 < keep.mean() < 0.98                 # a real mix of kept and dropped pixels
+    assert (cnt != ocnt).mean() <= 5e-4
+    assert (keep != okeep).mean() <= 5e-4
+
+
+def test_geo_filter_needs_source_maps(mvs_lib):
+    import torch
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_plane_scene(W=32, H=24, n_src=2, seed=1)
+    ctx = mvs_lib.Context(sc.K, sc.R, sc.t, sc.images, stream=torch.cuda.current_stream())
+    try:
+        with pytest.raises(mvs_lib.MvsError) as e:
+            mvs_lib.mvs_geo_filter(ctx.h, 0, [1, 2], mvs_lib.FilterParams(), np.zeros((24, 32), np.uint8))
+        assert e.value.status == mvs_lib.MVS_ESTATE
+    finally:
+        ctx.close()
+
+
+def _holes(gt_depth, rng):
+    known = (gt_depth > 0).astype(np.uint8)
+    known[20:60, 30:90] = 0                                   # a large hole
+    known[rng.uniform(size=known.shape) < 0.15] = 0           # scattered holes
+    return known
+
+
+def test_phi_hypotheses_parity(multi, mvs_lib, oracle_lib):
+    sc, ctx, osc, gt = multi
+    rng = np.random.default_rng(5)
+    known = _holes(gt[0][..., 3], rng)
+    depth = (gt[0][..., 3] * known).astype(np.float32)
+    hyp = np.zeros((96, 128, 4), np.float32)
+    valid = np.zeros((96, 128, 4), np.uint8)
+    phi = mvs_lib.PhiParams()
+    mvs_lib.mvs_phi_hypotheses(ctx.h, depth, known, phi, 2.0, 8.0, hyp, valid)
+    ohyp, ovalid = oracle_lib.phi_hypotheses(depth.astype(np.float64), known, d_lo=2.0, d_hi=8.0)
+    near_bound = (np.abs(ohyp - 2.0) < 1e-3) | (np.abs(ohyp - 8.0) < 1e-3)
+    assert ((valid != ovalid) & ~near_bound).sum() == 0
+    both = (valid == 1) & (ovalid == 1)
+    assert both.sum() > 1000
+    err = np.abs(hyp - ohyp)[both] / ohyp[both]
+    assert np.quantile(err, 0.999) < 1e-4 and err.max() < 1e-3
+
+
+def test_phi_cost_parity(multi, mvs_lib, oracle_lib):
+    sc, ctx, osc, gt = multi
+    rng = np.random.default_rng(6)
+    known = _holes(gt[0][..., 3], rng)
+    ohyp, ovalid = oracle_lib.phi_hypotheses(gt[0][..., 3] * known, known, d_lo=2.0, d_hi=8.0)
+    hyp = ohyp.astype(np.float32)
+    p = mvs_lib.PMParams(win_radius=5.0, win_samples=6)
+    hcost = np.zeros((96, 128, 4), np.float32)
+    mvs_lib.mvs_phi_cost(ctx.h, 0, [1, 2, 3], p, hyp, ovalid, hcost)
+    ocost, mg = oracle_lib.phi_cost(osc, 0, [1, 2, 3], p, hyp.astype(np.float64), ovalid, with_margin=True)
+    firm = mg > 1e-3
+    assert np.abs(hcost - ocost)[firm].max() <= COST_TOL
+    assert (hcost[ovalid == 0] == 2.0).all()
+
+
+def test_phi_mrf_parity(multi, mvs_lib, oracle_lib):
+    sc, ctx, osc, gt = multi
+    rng = np.random.default_rng(7)
+    known = _holes(gt[0][..., 3], rng)
+    depth = gt[0][..., 3] * known
+    ohyp, ovalid = oracle_lib.phi_hypotheses(depth, known, d_lo=2.0, d_hi=8.0)
+    p = mvs_lib.PMParams(win_radius=5.0, win_samples=6)
+    ocost = oracle_lib.phi_cost(osc, 0, [1, 2, 3], p, ohyp, ovalid)
+    f32 = lambda a: np.ascontiguousarray(a, np.float32)
+    for iters in (1, 3):
+        phi = mvs_lib.PhiParams(trw_iters=iters)
+        label = np.zeros((48, 64), np.int32)
+        mvs_lib.mvs_phi_mrf(ctx.h, known, f32(depth), f32(ohyp), ovalid, f32(ocost), phi, label)
+        # the oracle takes the same single-precision inputs
+        olabel, gap = oracle_lib.phi_mrf(known, f32(depth).astype(np.float64), f32(ohyp).astype(np.float64),
+                                         ovalid, f32(ocost).astype(np.float64), iters=iters)
+        assert np.array_equal(label < 0, olabel < 0) and np.array_equal(label == -2, olabel == -2)
+        clear = gap > 1e-3
+        assert (label[clear] == olabel[clear]).all()
+        assert (label != olabel).mean() < 0.01
+
+
+def test_phi_select_parity(multi, mvs_lib, oracle_lib):
+    sc, ctx, osc, gt = multi
+    rng = np.random.default_rng(8)
+    known = _holes(gt[0][..., 3], rng)
+    plane = gt[0] * known[..., None]
+    ohyp, ovalid = oracle_lib.phi_hypotheses(plane[..., 3], known, d_lo=2.0, d_hi=8.0)
+    p = mvs_lib.PMParams(win_radius=5.0, win_samples=6)
+    ocost = oracle_lib.phi_cost(osc, 0, [1, 2, 3], p, ohyp, ovalid)
+    olabel, _ = oracle_lib.phi_mrf(known, plane[..., 3], ohyp, ovalid, ocost)
+    opl, ofilled = oracle_lib.phi_select(osc, 0, known, ohyp, ovalid, olabel, plane)
+    gpl = np.ascontiguousarray(plane, np.float32)
+    mvs_lib.mvs_phi_select(ctx.h, 0, known, np.ascontiguousarray(ohyp, np.float32), ovalid, olabel, gpl)
+    gfilled = (gpl[..., 3] > 0) & (known == 0)
+    assert np.array_equal(gfilled, ofilled.astype(bool))
+    f = ofilled.astype(bool)
+    assert f.sum() > 500
+    assert np.abs(gpl[..., 3] - opl[..., 3])[f].max() <= 1e-6 * 8
+    assert np.abs(gpl[..., :3] - opl[..., :3])[f].max() <= 1e-3
+    assert np.array_equal(gpl[known == 1], plane[known == 1].astype(np.float32))
+
+
+def test_plane_infer_recovers_texture_less_planes(mvs_lib):
+    """End to end on a scene with texture-less quads: PatchMatch leaves the
+    flat regions at C_max; plane inference fills them close to the truth."""
+    import torch
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_scene(W=256, H=192, n_src=4, seed=31, baseline_frac=0.1, n_textured=2, n_flat=2,
+                           flat_frac=0.25)
+    p = mvs_lib.PMParams(win_radius=5.0, win_samples=6, iters=4, seed=9)
+    ctx = mvs_lib.Context(sc.K, sc.R, sc.t, sc.images, stream=torch.cuda.current_stream())
+    try:
+        pl = np.zeros((192, 256, 4), np.float32)
+        co = np.zeros((192, 256), np.float32)
+        mvs_lib.mvs_patchmatch(ctx.h, 0, [1, 2, 3, 4], p, pl, co)
+        gt = sc.gt_depth
+        before = (np.abs(pl[..., 3] - gt) / gt < 0.01) & (co < 0.5)
+        mvs_lib.mvs_plane_infer(ctx.h, 0, [1, 2, 3, 4], p, mvs_lib.PhiParams(), None, pl, co)
+        after = np.abs(pl[..., 3] - gt) / gt < 0.01
+        flat = ~sc.gt_textured
+        print(f"completeness @1%: before {before.mean():.3f} after {after.mean():.3f}; "
+              f"texture-less before {before[flat].mean():.3f} after {after[flat].mean():.3f}")
+        assert after[flat].mean() > before[flat].mean() + 0.3
+        assert after.mean() > before.mean()
+    finally:
+        ctx.close()
