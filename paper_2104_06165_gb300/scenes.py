@@ -36,6 +36,7 @@ class Quad:
     freqs: np.ndarray = None  # (K, 2) cycles per world unit
     phases: np.ndarray = None
     amps: np.ndarray = None
+    blanks: list = field(default_factory=list)   # texture-less patches: (c1, c2, h1, h2, value) in plane coords
 
 
 @dataclass
@@ -137,7 +138,10 @@ def _render_rows(quads, K, R, t, W, H, y0, y1, want_gt):
         acc = np.zeros(s1.shape)
         for k in range(len(q.amps)):
             acc += q.amps[k] * np.sin(2 * np.pi * (q.freqs[k, 0] * s1 + q.freqs[k, 1] * s2) + q.phases[k])
-        img[m] = 128.0 + acc
+        val = 128.0 + acc
+        for (c1, c2, h1, h2, bv) in q.blanks:
+            val = np.where((np.abs(s1 - c1) <= h1) & (np.abs(s2 - c2) <= h2), bv, val)
+        img[m] = val
     out = {"img": img}
     if want_gt:
         P = C + np.where(np.isfinite(best), best, 0.0)[..., None] * dirs
@@ -150,6 +154,14 @@ def _render_rows(quads, K, R, t, W, H, y0, y1, want_gt):
             nc = R @ q.normal
             nrm[m] = nc
             tex[m] = q.textured
+            if q.textured and q.blanks and m.any():
+                P = C + best[m][:, None] * dirs[m]
+                rel = P - q.center
+                s1, s2 = rel @ q.e1, rel @ q.e2
+                t_ = np.ones(s1.shape, bool)
+                for (c1, c2, h1, h2, bv) in q.blanks:
+                    t_ &= ~((np.abs(s1 - c1) <= h1) & (np.abs(s2 - c2) <= h2))
+                tex[m] = t_
         ray_c = np.stack(np.meshgrid(np.arange(W, dtype=float), np.arange(y0, y1, dtype=float)), -1)
         ray_c = np.concatenate([ray_c, np.ones(ray_c.shape[:2] + (1,))], -1) @ np.linalg.inv(K).T
         flip = np.sum(nrm * ray_c, -1) > 0
@@ -209,14 +221,16 @@ def _sources_ring(n_src, z_c, angles_deg, rng):
 
 def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_angles=None,
                n_textured=3, n_flat=1, flat_frac=None, d_lo=2.0, d_hi=8.0, quantise=True, threads=None):
-    """Scene of planar quads in front of a textured background plane.
+    """Scene of textured planar quads in front of a textured background plane,
+    with n_flat texture-less (constant-intensity) patches painted on those
+    planes.
 
     Default shape: W x H reference, focal f = 300 * W / 320 px (same field of
     view at every resolution), n_src source views.  With view_angles=None the
     sources sit on a ring of radius baseline_frac * 5 around the reference
     optical axis; otherwise at the given viewing angles (degrees) to the
-    scene centre.  flat_frac sizes the texture-less quads so that roughly that
-    fraction of the reference image is texture-less."""
+    scene centre.  flat_frac sizes the patches so that roughly that fraction
+    of the reference image is texture-less (default 8 %)."""
     rng = np.random.default_rng(seed)
     f = f if f is not None else 300.0 * W / 320.0
     K = intrinsics(W, H, f)
@@ -230,11 +244,7 @@ def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_an
     bg.freqs, bg.phases, bg.amps = _texture(rng, bg_depth, f)
     quads.append(bg)
     placed = []
-    flat_size = None
-    if flat_frac:
-        flat_size = math.sqrt(flat_frac * W * H / max(n_flat, 1)) * 1.1
-    for k in range(n_textured + n_flat):
-        textured = k < n_textured
+    for k in range(n_textured):
         for _ in range(50):
             u = rng.uniform(0.15 * W, 0.85 * W)
             v = rng.uniform(0.15 * H, 0.85 * H)
@@ -242,9 +252,21 @@ def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_an
                 break
         placed.append((u, v))
         depth = rng.uniform(3.0, 5.8)
-        size = rng.uniform(0.3, 0.45) * W if (textured or flat_size is None) else flat_size
-        quads.append(_quad_facing(rng, K, W, H, depth, u, v, size, textured, f,
-                                  tilt=50.0 if textured else 35.0))
+        size = rng.uniform(0.3, 0.45) * W
+        quads.append(_quad_facing(rng, K, W, H, depth, u, v, size, True, f, tilt=50.0))
+    # texture-less regions: blank patches painted on the textured quads, each
+    # centred on its quad and sized for flat_frac of the reference image in
+    # total (at most 80 % of the quad's side), so that a blank region is
+    # surrounded by texture of its own plane
+    target = (flat_frac if flat_frac is not None else 0.08) * W * H / max(n_flat, 1)
+    for k in range(n_flat):
+        q = quads[1 + k % max(n_textured, 1)] if n_textured else quads[0]
+        pc = K @ q.center
+        depth_c = pc[2]
+        quad_px = (2 * q.half[0] * f / depth_c) * (2 * q.half[1] * f / depth_c)
+        side = float(np.clip(math.sqrt(target / quad_px), 0.2, 0.8))
+        c1, c2 = rng.uniform(-0.1, 0.1) * q.half[0], rng.uniform(-0.1, 0.1) * q.half[1]
+        q.blanks.append((c1, c2, side * q.half[0], side * q.half[1], float(rng.uniform(70, 190))))
     Ks, Rs, ts = [K], [np.eye(3)], [np.zeros(3)]
     if view_angles is None:
         b = baseline_frac * z_c
@@ -300,14 +322,14 @@ def make_plane_scene(W=64, H=48, f=None, n_src=2, seed=0, depth=4.0, normal=(0.0
 # Workload shapes (stand-ins for the paper's ETH3D high-resolution inputs)
 # ---------------------------------------------------------------------------
 def scene_small(seed=0, **kw):
-    """320 x 240, 4 sources at baseline 0.1 x scene depth, 3 textured quads
-    + 1 texture-less quad in front of a textured background, depth [2, 8]."""
+    """320 x 240, 4 sources at baseline 0.1 x scene depth, 3 textured quads in
+    front of a textured background, one texture-less patch, depth [2, 8]."""
     return make_scene(W=320, H=240, n_src=4, seed=seed, baseline_frac=0.1, n_textured=3, n_flat=1, **kw)
 
 
 def scene_highres(seed=0, W=3072, H=2048, n_src=10, **kw):
     """3072 x 2048 reference + 10 sources at 15..40 degree viewing angles,
-    about 30 % of the reference covered by texture-less quads."""
+    texture-less patches sized for about 30 % of the reference."""
     angles = list(np.linspace(15.0, 40.0, n_src))
-    return make_scene(W=W, H=H, n_src=n_src, seed=seed, view_angles=angles, n_textured=4, n_flat=2,
+    return make_scene(W=W, H=H, n_src=n_src, seed=seed, view_angles=angles, n_textured=4, n_flat=4,
                       flat_frac=0.30, **kw)
