@@ -311,6 +311,10 @@ static int view_cost(const or_scene* s, int ref, int j, const or_pm* p, int x, i
             if (z > 1) z = 1;
             if (z < -1) z = -1;
             *cj = 1.0 - z;
+            /* decision margin of the delta(C, C_max) exclusion of Eq. 5: a view
+             * within 1e-4 of C_max is a fragile decision (contributes < 1e-3) */
+            double fc = (OR_CMAX - *cj) * 10.0;
+            if (fc < mg) mg = fc;
         }
     }
     free(sv);

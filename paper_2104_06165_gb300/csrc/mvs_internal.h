@@ -72,7 +72,7 @@ cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, fl
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s);
 int pm_group_lanes(int n_samples);
 // blocks of 128 threads for a grid-stride kernel over `units` warps of work
-unsigned pm_grid_for(const void* kernel, long long units);
+unsigned pm_grid_for(const void* kernel, long long units, size_t smem_bytes);
 
 struct FilterConst {
     int W, H;

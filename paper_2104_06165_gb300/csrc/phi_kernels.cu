@@ -195,17 +195,19 @@ __global__ void k_line_fit(int W, int H, const float* __restrict__ depth, const 
 // ---------------------------------------------------------------------------
 constexpr int kBlock = 128;
 constexpr int kWarps = kBlock / 32;
-struct BlockSm {
-    ViewSm views[MVS_MAX_SRC];
-    uint16_t list[kWarps][8 * MVS_MAX_SRC];
-};
+// Dynamic shared memory of a block: the view table, then one pair list per
+// warp (smem_block_bytes(n_src, kWarps) bytes).
+__device__ __forceinline__ PairSm* warp_pairs(unsigned char* smem, int n_src, int warp) {
+    return reinterpret_cast<PairSm*>(smem + smem_views_bytes(n_src)) + (size_t)warp * 8 * n_src;
+}
 
 // one warp per pixel, the four hypotheses of a pixel in lanes 0..3
 template <int G, int S>
 __global__ void __launch_bounds__(kBlock, 3) k_phi_cost(const __grid_constant__ RefConst rc, const float* __restrict__ hyp,
                                                       const uint8_t* __restrict__ valid, float* __restrict__ hcost) {
-    __shared__ BlockSm sm;
-    load_views(rc, sm.views);
+    extern __shared__ __align__(16) unsigned char smem[];
+    ViewSm* views = reinterpret_cast<ViewSm*>(smem);
+    load_views(rc, views);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long npix = (long long)rc.W * rc.H;
     unsigned nev = 0;
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_phi_cost(const __grid_constant__ 
         float c = kCmax;
         if (pw.ok) {
             Cand my = make_cand(rc, pw, 0.0f, 0.0f, -1.0f, h, v);
-            c = eval_batch<G, S, false>(rc, sm.views, pw, px, py, my, 4, sm.list[warp], nullptr, nev);
+            c = eval_batch<G, S, false>(rc, views, pw, px, py, my, 4, warp_pairs(smem, rc.n_src, warp), nullptr, nev);
         }
         if (lane < 4) hcost[4 * a + lane] = v ? c : kCmax;
     }
@@ -474,7 +476,7 @@ cudaError_t launch_phi_hypotheses(int W, int H, const float* depth, const uint8_
         if (_s <= 16) { CALL(4, 4); }               \
         else if (_s <= 36) { CALL(4, 9); }          \
         else if (_s <= 64) { CALL(8, 8); }          \
-        else if (_s <= 128) { CALL(8, 16); }        \
+        else if (_s <= 128) { CALL(16, 8); }        \
         else if (_s <= 256) { CALL(16, 16); }       \
         else { CALL(32, 16); }                      \
     } while (0)
@@ -482,7 +484,8 @@ cudaError_t launch_phi_hypotheses(int W, int H, const float* depth, const uint8_
 cudaError_t launch_phi_cost(const RefConst& rc, const float* hyp, const uint8_t* valid, float* hcost,
                             cudaStream_t s) {
     long long npix = (long long)rc.W * rc.H;
-#define CALL(G, S) k_phi_cost<G, S><<<pm_grid_for((const void*)k_phi_cost<G, S>, npix), kBlock, 0, s>>>(rc, hyp, valid, hcost)
+    const size_t smem = smem_block_bytes(rc.n_src, kWarps);
+#define CALL(G, S) k_phi_cost<G, S><<<pm_grid_for((const void*)k_phi_cost<G, S>, npix, smem), kBlock, smem, s>>>(rc, hyp, valid, hcost)
     MVS_DISPATCH(rc.n, CALL);
 #undef CALL
     count_launch();

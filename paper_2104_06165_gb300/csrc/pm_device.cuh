@@ -225,22 +225,41 @@ __device__ __forceinline__ Cand make_cand(const RefConst& rc, const PixWin<S>& p
     return c;
 }
 
+// One listed (hypothesis, view) pair in shared memory: the homography
+// columns H e1, H e2 and H x (shifted by -1/2 for tex_sample), the view,
+// and after evaluation its per-view cost (C_max when excluded).
+struct PairSm {
+    float h0x, h0y, h0z, h1x;
+    float h1y, h1z, p0x, p0y;
+    float p0z, res;
+    int j, c;
+};
+
+// Shared-memory bytes of a 128-thread block: the view table and, per warp,
+// room for 8 hypotheses x n_src pairs.
+__host__ __device__ constexpr size_t smem_views_bytes(int n_src) {
+    return ((size_t)n_src * sizeof(ViewSm) + 15) & ~(size_t)15;
+}
+__host__ __device__ constexpr size_t smem_block_bytes(int n_src, int warps) {
+    return smem_views_bytes(n_src) + (size_t)warps * 8 * n_src * sizeof(PairSm);
+}
+
 // Costs C(x) (Eq. 5) of up to 8 hypotheses of the warp's pixel: lane c < nc
 // holds hypothesis c on entry and its cost on return.
 //   1. the (hypothesis, view) pairs whose window maps inside the source
 //      image (exact corner test: the image of the window is convex, w > 0
-//      included) are listed in `list` (per-warp shared memory, nc * n_src
-//      entries), hypothesis-major;
+//      included) are listed in `pairs` (per-warp shared memory, nc * n_src
+//      entries) in hypothesis-major, view-minor order, with their homography;
 //   2. each group of G lanes takes the next pair: S bilinear gathers per
 //      lane, two-pass weighted moments with group reductions, ZNCC (Eq. 4),
 //      C(x,j) = 1 - Z; a view is excluded when its weighted variance is below
 //      1e-6 on the [0,1] scale (reading);
-//   3. the per-view results are folded into the owner lane of the
-//      hypothesis in view order (Eq. 5, weights 1/max(C, 1e-6)).
+//   3. lane c folds the per-view results of hypothesis c in view order
+//      (Eq. 5, weights 1/max(C, 1e-6)).
 // Must be called by all 32 lanes with the same nc (warp-uniform).
 template <int G, int S, bool VIEWS>
 __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __restrict__ sv, const PixWin<S>& pw,
-                                            int px, int py, const Cand& my, int nc, uint16_t* list,
+                                            int px, int py, const Cand& my, int nc, PairSm* pairs,
                                             float* view_cost, unsigned& n_evals) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
@@ -248,7 +267,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
     const int P = nc * V;
     const float x = (float)px, y = (float)py;
     // ---- 1. list the pairs that map inside the source images
-    int count = 0;
+    int count = 0, my_cnt = 0;
     for (int base = 0; base < P; base += 32) {
         int i = base + lane;
         bool act = i < P;
@@ -259,11 +278,15 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         float invd = __shfl_sync(0xffffffffu, my.invd, c);
         bool cok = __shfl_sync(0xffffffffu, (int)my.ok, c) != 0;
         const ViewSm& v = sv[j];
-        float h0x = fmaf(v.b[0], m0, v.A[0]), h0y = fmaf(v.b[1], m0, v.A[3]), h0z = fmaf(v.b[2], m0, v.A[6]);
-        float h1x = fmaf(v.b[0], m1, v.A[1]), h1y = fmaf(v.b[1], m1, v.A[4]), h1z = fmaf(v.b[2], m1, v.A[7]);
-        float p0x = fmaf(v.b[0], invd, fmaf(v.A[0], x, fmaf(v.A[1], y, v.A[2])));
-        float p0y = fmaf(v.b[1], invd, fmaf(v.A[3], x, fmaf(v.A[4], y, v.A[5])));
+        float h0z = fmaf(v.b[2], m0, v.A[6]), h1z = fmaf(v.b[2], m1, v.A[7]);
         float p0z = fmaf(v.b[2], invd, fmaf(v.A[6], x, fmaf(v.A[7], y, v.A[8])));
+        // coordinates shifted by -1/2 (tex_sample's convention)
+        float h0x = fmaf(-0.5f, h0z, fmaf(v.b[0], m0, v.A[0]));
+        float h0y = fmaf(-0.5f, h0z, fmaf(v.b[1], m0, v.A[3]));
+        float h1x = fmaf(-0.5f, h1z, fmaf(v.b[0], m1, v.A[1]));
+        float h1y = fmaf(-0.5f, h1z, fmaf(v.b[1], m1, v.A[4]));
+        float p0x = fmaf(-0.5f, p0z, fmaf(v.b[0], invd, fmaf(v.A[0], x, fmaf(v.A[1], y, v.A[2]))));
+        float p0y = fmaf(-0.5f, p0z, fmaf(v.b[1], invd, fmaf(v.A[3], x, fmaf(v.A[4], y, v.A[5]))));
         bool ok = act && cok;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -271,40 +294,43 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             float cx = fmaf(cu, h0x, fmaf(cv, h1x, p0x));
             float cy = fmaf(cu, h0y, fmaf(cv, h1y, p0y));
             float cz = fmaf(cu, h0z, fmaf(cv, h1z, p0z));
-            float icz = 1.0f / cz;
+            float icz = rcp_approx(cz);
             float xs = cx * icz, ys = cy * icz;
-            ok = ok && cz > 0.0f && xs >= 0.0f && xs <= v.wm1 && ys >= 0.0f && ys <= v.hm1;
+            ok = ok && cz > 0.0f && xs >= -0.5f && xs <= v.wm1 - 0.5f && ys >= -0.5f && ys <= v.hm1 - 0.5f;
         }
         unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (ok) list[count + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((c << 8) | j);
+        if (ok) {
+            PairSm& q = pairs[count + __popc(m & ((1u << lane) - 1u))];
+            q.h0x = h0x; q.h0y = h0y; q.h0z = h0z; q.h1x = h1x;
+            q.h1y = h1y; q.h1z = h1z; q.p0x = p0x; q.p0y = p0y;
+            q.p0z = p0z; q.j = j; q.c = c;
+        }
         count += __popc(m);
+        if (lane < nc) {   // pairs of hypothesis `lane` in this chunk
+            int lo = max(0, lane * V - base), hi = min(32, lane * V + V - base);
+            if (hi > lo) {
+                unsigned rm = (hi == 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+                my_cnt += __popc(m & rm);
+            }
+        }
     }
-    if (VIEWS && view_cost && lane < V) view_cost[lane] = kCmax;
+    // first list position of hypothesis `lane`: exclusive prefix sum
+    int start = my_cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, start, o);
+        if (lane >= o) start += t;
+    }
+    start -= my_cnt;
     __syncwarp();
-    // ---- 2./3. evaluate the listed pairs, NG at a time
-    int cnt = 0;
-    float inv_sum = 0.0f;
+    // ---- 2. evaluate the listed pairs, NG at a time
     for (int r = 0; r < count; r += NG) {
         int it = r + grp;
         bool has = it < count;
-        int e = list[has ? it : 0];
-        int c = e >> 8, j = e & 255;
-        float m0 = __shfl_sync(0xffffffffu, my.m0, c);
-        float m1 = __shfl_sync(0xffffffffu, my.m1, c);
-        float invd = __shfl_sync(0xffffffffu, my.invd, c);
-        const ViewSm& v = sv[j];
-        float h0x = fmaf(v.b[0], m0, v.A[0]), h0y = fmaf(v.b[1], m0, v.A[3]), h0z = fmaf(v.b[2], m0, v.A[6]);
-        float h1x = fmaf(v.b[0], m1, v.A[1]), h1y = fmaf(v.b[1], m1, v.A[4]), h1z = fmaf(v.b[2], m1, v.A[7]);
-        float p0x = fmaf(v.b[0], invd, fmaf(v.A[0], x, fmaf(v.A[1], y, v.A[2])));
-        float p0y = fmaf(v.b[1], invd, fmaf(v.A[3], x, fmaf(v.A[4], y, v.A[5])));
-        float p0z = fmaf(v.b[2], invd, fmaf(v.A[6], x, fmaf(v.A[7], y, v.A[8])));
-        // sample coordinates shifted by -1/2 for tex_sample
-        h0x = fmaf(-0.5f, h0z, h0x);
-        h0y = fmaf(-0.5f, h0z, h0y);
-        h1x = fmaf(-0.5f, h1z, h1x);
-        h1y = fmaf(-0.5f, h1z, h1y);
-        p0x = fmaf(-0.5f, p0z, p0x);
-        p0y = fmaf(-0.5f, p0z, p0y);
+        const PairSm& q = pairs[has ? it : 0];
+        const float h0x = q.h0x, h0y = q.h0y, h0z = q.h0z, h1x = q.h1x;
+        const float h1y = q.h1y, h1z = q.h1z, p0x = q.p0x, p0y = q.p0y, p0z = q.p0z;
+        const ViewSm& v = sv[q.j];
         const float4* tex = v.tex;
         const uint32_t pitch = v.pitch, n_tex = v.n_tex;
         float sval[S];
@@ -331,29 +357,33 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         }
         sdd = gsum<G>(sdd);
         srd = gsum<G>(srd);
-        float cj = kCmax;
-        bool okj = false;
-        if (has && sdd >= kTauVar * pw.wsum) {
-            float z = srd * rsqrtf(pw.srr * sdd);
-            z = fminf(1.0f, fmaxf(-1.0f, z));
-            cj = 1.0f - z;
-            okj = cj < kCmax;
-            if (!okj) cj = kCmax;
-        }
         if (has && lg == 0) {
+            float cj = kCmax;
+            if (sdd >= kTauVar * pw.wsum) {
+                float z = srd * rsqrtf(pw.srr * sdd);
+                z = fminf(1.0f, fmaxf(-1.0f, z));
+                cj = fminf(1.0f - z, kCmax);
+            }
+            pairs[it].res = cj;
             n_evals++;
-            if (VIEWS && view_cost) view_cost[j] = cj;
         }
-        // fold the NG results into the owner lanes, in list (= view) order
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            int cg = __shfl_sync(0xffffffffu, okj ? c : -1, g * G);
-            float cjg = __shfl_sync(0xffffffffu, cj, g * G);
-            if (lane == cg) {
+    }
+    __syncwarp();
+    // ---- 3. fold hypothesis `lane`'s views in view order
+    int cnt = 0;
+    float inv_sum = 0.0f;
+    if (lane < nc)
+        for (int p = start; p < start + my_cnt; ++p) {
+            float cj = pairs[p].res;
+            if (cj < kCmax) {
                 cnt++;
-                inv_sum += 1.0f / fmaxf(cjg, kEpsC);
+                inv_sum += 1.0f / fmaxf(cj, kEpsC);
             }
         }
+    if (VIEWS && view_cost) {
+        if (lane < V) view_cost[lane] = kCmax;
+        __syncwarp();
+        for (int p = lane; p < count; p += 32) view_cost[pairs[p].j] = pairs[p].res;
     }
     __syncwarp();
     return (lane < nc && my.ok && cnt > 0) ? (float)cnt / inv_sum : kCmax;

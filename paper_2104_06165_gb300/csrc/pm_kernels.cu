@@ -38,10 +38,11 @@ __global__ void k_build_texture(const uint8_t* __restrict__ img, int W, int H, f
 
 // Per-block shared memory: the source-view table and one pair list per warp.
 constexpr int kWarps = kBlock / 32;
-struct BlockSm {
-    ViewSm views[MVS_MAX_SRC];
-    uint16_t list[kWarps][8 * MVS_MAX_SRC];
-};
+// Dynamic shared memory of a block: the view table, then one pair list per
+// warp (smem_block_bytes(n_src, kWarps) bytes).
+__device__ __forceinline__ PairSm* warp_pairs(unsigned char* smem, int n_src, int warp) {
+    return reinterpret_cast<PairSm*>(smem + smem_views_bytes(n_src)) + (size_t)warp * 8 * n_src;
+}
 
 // ---------------------------------------------------------------------------
 // Sec. III-B: random initialisation, then the cost of the initial plane.
@@ -49,8 +50,9 @@ struct BlockSm {
 // ---------------------------------------------------------------------------
 template <int G, int S>
 __global__ void __launch_bounds__(kBlock) k_init(const __grid_constant__ RefConst rc, float* view_cost) {
-    __shared__ BlockSm sm;
-    load_views(rc, sm.views);
+    extern __shared__ __align__(16) unsigned char smem[];
+    ViewSm* views = reinterpret_cast<ViewSm*>(smem);
+    load_views(rc, views);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long npix = (long long)rc.W * rc.H;
     unsigned nev = 0;
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const __grid_constant__ RefCons
         float c = kCmax;
         if (pw.ok) {
             Cand my = make_cand(rc, pw, n0, n1, n2, d, lane == 0);
-            c = eval_batch<G, S, true>(rc, sm.views, pw, px, py, my, 1, sm.list[warp], vc, nev);
+            c = eval_batch<G, S, true>(rc, views, pw, px, py, my, 1, warp_pairs(smem, rc.n_src, warp), vc, nev);
         } else if (vc && lane < rc.n_src) {
             vc[lane] = kCmax;
         }
@@ -85,8 +87,9 @@ __global__ void __launch_bounds__(kBlock) k_init(const __grid_constant__ RefCons
 template <int G, int S>
 __global__ void __launch_bounds__(kBlock) k_cost(const __grid_constant__ RefConst rc, const float4* __restrict__ plane,
                                                   float* __restrict__ cost, float* view_cost) {
-    __shared__ BlockSm sm;
-    load_views(rc, sm.views);
+    extern __shared__ __align__(16) unsigned char smem[];
+    ViewSm* views = reinterpret_cast<ViewSm*>(smem);
+    load_views(rc, views);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long npix = (long long)rc.W * rc.H;
     unsigned nev = 0;
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__(kBlock) k_cost(const __grid_constant__ RefCons
         float c = kCmax;
         if (pw.ok) {
             Cand my = make_cand(rc, pw, pl.x, pl.y, pl.z, pl.w, lane == 0);
-            c = eval_batch<G, S, true>(rc, sm.views, pw, px, py, my, 1, sm.list[warp], vc, nev);
+            c = eval_batch<G, S, true>(rc, views, pw, px, py, my, 1, warp_pairs(smem, rc.n_src, warp), vc, nev);
         } else if (vc && lane < rc.n_src) {
             vc[lane] = kCmax;
         }
@@ -129,9 +132,10 @@ __device__ __forceinline__ void near_member(int g, int k, int& dx, int& dy) {
 }
 
 template <int G, int S>
-__global__ void __launch_bounds__(kBlock, 3) k_phase(const __grid_constant__ RefConst rc, int phase) {
-    __shared__ BlockSm sm;
-    load_views(rc, sm.views);
+__global__ void __launch_bounds__(kBlock, (S >= 16 ? 3 : 4)) k_phase(const __grid_constant__ RefConst rc, int phase) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ViewSm* views = reinterpret_cast<ViewSm*>(smem);
+    load_views(rc, views);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int color = phase & 1;
     const int Wa = (rc.W + 1) >> 1;
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_phase(const __grid_constant__ Ref
             }
             const int nc = stage == 0 ? 8 : 3;
             Cand my = make_cand(rc, pw, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
-            float c = eval_batch<G, S, false>(rc, sm.views, pw, px, py, my, nc, sm.list[warp], nullptr, nev);
+            float c = eval_batch<G, S, false>(rc, views, pw, px, py, my, nc, warp_pairs(smem, rc.n_src, warp), nullptr, nev);
             float bc;
             int bi = warp_argmin(my.ok ? c : 3.0e38f, nc, bc);
             if (bc < cur_c) {
@@ -236,9 +240,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_phase(const __grid_constant__ Ref
 // once (occupancy query, cached per kernel), at most one warp per unit
 }  // namespace
 
-unsigned pm_grid_for(const void* kernel, long long units) {
+unsigned pm_grid_for(const void* kernel, long long units, size_t smem) {
     static std::mutex mu;
-    static std::unordered_map<const void*, int> per_sm_cache;
+    static std::unordered_map<const void*, std::pair<size_t, int>> cache;   // kernel -> (smem, blocks per SM)
     static int sms = 0;
     int per_sm = 0;
     {
@@ -248,28 +252,19 @@ unsigned pm_grid_for(const void* kernel, long long units) {
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         }
-        auto it = per_sm_cache.find(kernel);
-        if (it == per_sm_cache.end()) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
-            per_sm = std::max(per_sm, 1);
-            per_sm_cache[kernel] = per_sm;
+        auto it = cache.find(kernel);
+        if (it != cache.end() && it->second.first == smem) {
+            per_sm = it->second.second;
         } else {
-            per_sm = it->second;
+            if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, smem);
+            per_sm = std::max(per_sm, 1);
+            cache[kernel] = {smem, per_sm};
         }
     }
     long long need = (units + kWarps - 1) / kWarps;
     long long full = (long long)sms * per_sm;
     return (unsigned)std::max<long long>(1, std::min(need, full));
-}
-
-
-// lanes per pixel and slots per lane for a window of n x n samples
-int pm_group_lanes(int n) {
-    int s = n * n;
-    if (s <= 36) return 4;
-    if (s <= 128) return 8;
-    if (s <= 256) return 16;
-    return 32;
 }
 
 // Lanes per pixel group (G) and slots per lane (S) for an n x n window:
@@ -281,8 +276,8 @@ int pm_group_lanes(int n) {
         else if (_s <= 36) { if (_h == 8) { CALL(8, 5); } else { CALL(4, 9); } }          \
         else if (_s <= 64) { if (_h == 16) { CALL(16, 4); } else { CALL(8, 8); } }        \
         else if (_s <= 128) {                                                             \
-            if (_h == 16) { CALL(16, 8); } else if (_h == 32) { CALL(32, 4); }            \
-            else { CALL(8, 16); }                                                         \
+            if (_h == 8) { CALL(8, 16); } else if (_h == 32) { CALL(32, 4); }             \
+            else { CALL(16, 8); }                                                         \
         }                                                                                 \
         else if (_s <= 256) { if (_h == 32) { CALL(32, 8); } else { CALL(16, 16); } }     \
         else { CALL(32, 16); }                                                            \
@@ -298,7 +293,8 @@ cudaError_t launch_build_texture(const uint8_t* img, int W, int H, float4* tex, 
 
 cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s) {
     long long npix = (long long)rc.W * rc.H;
-#define CALL(G, S) k_init<G, S><<<pm_grid_for((const void*)k_init<G, S>, npix), kBlock, 0, s>>>(rc, view_cost)
+    const size_t smem = smem_block_bytes(rc.n_src, kWarps);
+#define CALL(G, S) k_init<G, S><<<pm_grid_for((const void*)k_init<G, S>, npix, smem), kBlock, smem, s>>>(rc, view_cost)
     MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
 #undef CALL
     count_launch();
@@ -307,7 +303,8 @@ cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s) {
 
 cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, float* view_cost, cudaStream_t s) {
     long long npix = (long long)rc.W * rc.H;
-#define CALL(G, S) k_cost<G, S><<<pm_grid_for((const void*)k_cost<G, S>, npix), kBlock, 0, s>>>(rc, plane, cost, view_cost)
+    const size_t smem = smem_block_bytes(rc.n_src, kWarps);
+#define CALL(G, S) k_cost<G, S><<<pm_grid_for((const void*)k_cost<G, S>, npix, smem), kBlock, smem, s>>>(rc, plane, cost, view_cost)
     MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
 #undef CALL
     count_launch();
@@ -316,7 +313,8 @@ cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, fl
 
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s) {
     long long nact = (long long)((rc.W + 1) / 2) * rc.H;
-#define CALL(G, S) k_phase<G, S><<<pm_grid_for((const void*)k_phase<G, S>, nact), kBlock, 0, s>>>(rc, phase)
+    const size_t smem = smem_block_bytes(rc.n_src, kWarps);
+#define CALL(G, S) k_phase<G, S><<<pm_grid_for((const void*)k_phase<G, S>, nact, smem), kBlock, smem, s>>>(rc, phase)
     MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
 #undef CALL
     count_launch();
