@@ -201,6 +201,33 @@ mvs_status mvs_phi_mrf(mvs_ctx* ctx, int32_t W, int32_t H, const uint8_t* known,
 mvs_status mvs_phi_select(mvs_ctx* ctx, int32_t ref, const uint8_t* known, const float* hyp,
                           const uint8_t* valid, const int32_t* label, float* plane, int32_t mem);
 
+/* Allocation-free variant of mvs_phi_hypotheses (the paper has no
+ * counterpart; this is a deployment convenience).
+ *   Some callers cannot allocate device memory once they are running: a
+ *   service that reserves its whole device-memory budget at start-up and
+ *   treats any later cudaMalloc as a fault, an engine whose own allocator owns
+ *   every byte of the device, or a latency-bound pipeline that cannot afford
+ *   the device-wide synchronisation cudaMalloc / cudaFree imply.  This entry
+ *   point computes exactly what mvs_phi_hypotheses computes but keeps its
+ *   line-gap scratch in a fixed array compiled into the library
+ *   (MVS_PHI_STATIC_MAX_PIXELS pixels x 32 bytes = 8 MiB per device, held by
+ *   every device that loads the library until the process exits), so it
+ *   calls no cudaMalloc, cudaFree or allocating library routine.
+ *   depth, known, hyp, valid: DEVICE pointers only (layout as in
+ *   mvs_phi_hypotheses); work is enqueued on the context stream.
+ *   The first call on a device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   Every call shares the one array: calls that overlap on the GPU (other
+ *   streams, other contexts, other threads) race and must be serialised by
+ *   the caller.  Every entry a call reads is written by the same call first,
+ *   so no clearing is needed between calls.
+ * Errors: MVS_EINVAL (NULL argument, W*H > MVS_PHI_STATIC_MAX_PIXELS, bad
+ *   size or n_fit), MVS_ECUDA. */
+#define MVS_PHI_STATIC_MAX_PIXELS 262144
+mvs_status mvs_phi_hypotheses_static(mvs_ctx* ctx, int32_t W, int32_t H, const float* depth,
+                                     const uint8_t* known, const mvs_phi_params* phi, float d_lo, float d_hi,
+                                     float* hyp, uint8_t* valid);
+
 /* Measurement hooks (no counterpart in the paper).
  *  mvs_profile(ctx, enable): enable != 0 makes mvs_patchmatch bracket every
  *    checkerboard-phase kernel with CUDA events on the context stream; any

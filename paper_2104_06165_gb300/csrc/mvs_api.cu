@@ -455,6 +455,24 @@ mvs_status mvs_phi_hypotheses(mvs_ctx* c, int32_t W, int32_t H, const float* dep
     return MVS_OK;
 }
 
+mvs_status mvs_phi_hypotheses_static(mvs_ctx* c, int32_t W, int32_t H, const float* depth, const uint8_t* known,
+                                     const mvs_phi_params* phi, float d_lo, float d_hi, float* hyp,
+                                     uint8_t* valid) {
+    if (!c) return MVS_EINVAL;
+    if (!depth || !known || !phi || !hyp || !valid) return fail(c, MVS_EINVAL, "NULL argument");
+    if (W < 2 || H < 2) return fail(c, MVS_EINVAL, "bad size");
+    if ((long long)W * H > MVS_PHI_STATIC_MAX_PIXELS)
+        return fail(c, MVS_EINVAL, "%d x %d exceeds the %d pixels of the fixed scratch", W, H,
+                    MVS_PHI_STATIC_MAX_PIXELS);
+    if (phi->n_fit < 2 || phi->n_fit > 32) return fail(c, MVS_EINVAL, "n_fit must be in 2..32");
+    CK(c, cudaSetDevice(c->device));
+    int32_t* work = nullptr;
+    CK(c, phi_static_scratch(&work));
+    CK(c, launch_phi_hypotheses(W, H, depth, known, phi->n_fit, phi->fit_inverse, d_lo, d_hi, hyp, valid, work,
+                                c->stream));
+    return MVS_OK;
+}
+
 mvs_status mvs_phi_cost(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src, const mvs_pm_params* pm,
                         const float* hyp, const uint8_t* valid, float* hcost, int32_t mem) {
     mvs_status st = check_pm(c, ref, srcs, n_src, pm);

@@ -96,6 +96,7 @@ cudaError_t launch_geo_filter(const FilterConst& fc, uint8_t* keep, int32_t* cou
 cudaError_t launch_phi_hypotheses(int W, int H, const float* depth, const uint8_t* known, int n_fit, int inverse,
                                   float d_lo, float d_hi, float* hyp, uint8_t* valid, int32_t* scratch,
                                   cudaStream_t s);
+cudaError_t phi_static_scratch(int32_t** out);
 cudaError_t launch_phi_cost(const RefConst& rc, const float* hyp, const uint8_t* valid, float* hcost,
                             cudaStream_t s);
 cudaError_t launch_phi_mrf(int W, int H, const uint8_t* known, const float* depth, const float* hyp,

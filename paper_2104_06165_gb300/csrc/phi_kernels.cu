@@ -2,6 +2,9 @@
 // (Sec. III-E): four-direction line-fit hypotheses, their matching cost, the
 // pairwise MRF of Eq. 6-9 decoded by tree-reweighted message passing at half
 // resolution, closest-hypothesis selection and Eq. 10 normals.
+#include <mutex>
+
+#include "../../include/mvs.h"
 #include "pm_device.cuh"
 
 using namespace mvsdev;
@@ -452,6 +455,31 @@ cudaError_t launch_geo_filter(const FilterConst& fc, uint8_t* keep, int32_t* cou
     k_geo_filter<<<blocks_for(n, 256), 256, 0, s>>>(fc, keep, count);
     count_launch();
     return cudaGetLastError();
+}
+
+// Fixed line-gap scratch of mvs_phi_hypotheses_static: 8 int32 per pixel for
+// up to MVS_PHI_STATIC_MAX_PIXELS pixels, in the library's own device memory.
+static __device__ __align__(256) int32_t g_phi_gaps_static[8 * (size_t)MVS_PHI_STATIC_MAX_PIXELS];
+
+// Device address of g_phi_gaps_static on the current device, looked up once
+// per device with that device current (host code only sees a stand-in for the
+// symbol, never its device address).
+cudaError_t phi_static_scratch(int32_t** out) {
+    static std::mutex mu;
+    static int32_t* ptr[128] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_phi_gaps_static);
+        if (e != cudaSuccess) return e;
+        ptr[dev] = (int32_t*)p;
+    }
+    *out = ptr[dev];
+    return cudaSuccess;
 }
 
 cudaError_t launch_phi_hypotheses(int W, int H, const float* depth, const uint8_t* known, int n_fit, int inverse,

@@ -142,6 +142,9 @@ def load():
     L.mvs_phi_hypotheses.restype = i32
     L.mvs_phi_hypotheses.argtypes = [vp, i32, i32, fp, u8p, C.POINTER(mvs_phi_params), C.c_float, C.c_float, fp,
                                      u8p, i32]
+    L.mvs_phi_hypotheses_static.restype = i32
+    L.mvs_phi_hypotheses_static.argtypes = [vp, i32, i32, fp, u8p, C.POINTER(mvs_phi_params), C.c_float,
+                                            C.c_float, fp, u8p]
     L.mvs_phi_cost.restype = i32
     L.mvs_phi_cost.argtypes = [vp, i32, ip, i32, C.POINTER(mvs_pm_params), fp, u8p, fp, i32]
     L.mvs_phi_mrf.restype = i32
@@ -265,6 +268,20 @@ def mvs_phi_hypotheses(ctx, depth, known, phi: PhiParams, d_lo, d_hi, hyp, valid
     b = phi.c()
     _check(load().mvs_phi_hypotheses(ctx, W, H, _ptr(depth)[0], _ptr(known)[0], C.byref(b), d_lo, d_hi,
                                      _ptr(hyp)[0], _ptr(valid)[0], mem), ctx)
+
+
+def mvs_phi_hypotheses_static(ctx, depth, known, phi: PhiParams, d_lo, d_hi, hyp, valid):
+    """mvs_phi_hypotheses without any device allocation (device buffers only;
+    at most MVS_PHI_STATIC_MAX_PIXELS pixels)."""
+    if _mem(depth, known, hyp, valid) != MVS_MEM_DEVICE:
+        raise ValueError("mvs_phi_hypotheses_static takes device buffers only")
+    H, W = depth.shape
+    b = phi.c()
+    _check(load().mvs_phi_hypotheses_static(ctx, W, H, _ptr(depth)[0], _ptr(known)[0], C.byref(b), d_lo, d_hi,
+                                            _ptr(hyp)[0], _ptr(valid)[0]), ctx)
+
+
+MVS_PHI_STATIC_MAX_PIXELS = 262144
 
 
 def mvs_phi_cost(ctx, ref, srcs, pm: PMParams, hyp, valid, hcost):
