@@ -77,7 +77,8 @@ typedef struct {
     uint64_t seed;         /* Philox4x64-10 key word 0 (word 1 = ref index)  */
     int32_t precision;     /* 0 = FP32 (only value built)                    */
     int32_t lanes_per_pixel; /* work layout of the ZNCC kernels: lanes that
-                              share one window (4, 8, 16 or 32; 0 = default).
+                              share one window (4, 8, 16 or 32; 0 = default;
+                              -1 = timed choice, mvs_patchmatch_batch only).
                               Results are identical for every choice up to
                               float rounding of the group reductions.        */
     int32_t reserved[6];
@@ -143,6 +144,23 @@ const char* mvs_last_error(const mvs_ctx* ctx);
  *   MVS_EUNSUPPORTED (precision != 0), MVS_ENOMEM, MVS_ECUDA. */
 mvs_status mvs_patchmatch(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_t n_src,
                           const mvs_pm_params* params, mvs_depth_map* out);
+
+/* Depth maps of several reference views in one call: the initialisation of
+ * every view, then half-iteration p of every view, for p in the phase range
+ * (Algorithm 1 loops over reference images; the views are independent, so
+ * the interleaving gives exactly the results of separate mvs_patchmatch
+ * calls).  The kernels are captured into a CUDA graph on the first call with
+ * a given (refs, srcs, params) and the graph is replayed by later calls.
+ *   refs[n_ref]: reference views (distinct); srcs[n_ref * n_src]: row r holds
+ *   the n_src sources of refs[r]; outs[n_ref]: depth-map buffers of each
+ *   reference's size, all in the same memory kind.  params as for
+ *   mvs_patchmatch; params->lanes_per_pixel = -1 asks the library to time
+ *   the work layouts on the first call (one phase of the first view on a
+ *   scratch copy of its state) and keep the fastest for this window size.
+ *   The maps stay in the context for mvs_geo_filter.
+ * Errors: as mvs_patchmatch, plus MVS_EINVAL for n_ref < 1 or repeated refs. */
+mvs_status mvs_patchmatch_batch(mvs_ctx* ctx, int32_t n_ref, const int32_t* refs, const int32_t* srcs,
+                                int32_t n_src, const mvs_pm_params* params, mvs_depth_map* outs);
 
 /* Aggregated cost (Eq. 4/5) of a given plane map of view `ref`.
  *   plane: H*W*4 input, cost: H*W output, view_cost: H*W*n_src output of the

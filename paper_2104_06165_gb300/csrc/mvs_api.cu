@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -34,6 +35,15 @@ thread_local std::string g_create_error;
 
 std::atomic<long long> g_kernel_launches{0};
 
+// A captured batch of PatchMatch kernels and the call it was captured for.
+struct BatchGraph {
+    std::vector<int32_t> refs, srcs;
+    mvs_pm_params params;
+    int lanes = 0;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+};
+
 struct mvs_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -46,6 +56,11 @@ struct mvs_ctx {
     size_t ev_used = 0;
     long long launches0 = 0;
     unsigned long long* evals = nullptr;   // device counter of evaluated (pixel, hypothesis, view)
+    // batched path
+    cudaStream_t gstream = nullptr;        // private stream for graph capture / replay
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    BatchGraph batch;
+    std::map<long long, int> tuned_lanes;  // (win_samples, n_src) -> lanes per pixel
 };
 
 namespace {
@@ -269,6 +284,9 @@ void mvs_destroy(mvs_ctx* c) {
     for (auto& s : c->scratch) cudaFree(s.p);
     for (auto e : c->ev) cudaEventDestroy(e);
     cudaFree(c->evals);
+    if (c->batch.exec) cudaGraphExecDestroy(c->batch.exec);
+    for (auto e : c->gev) if (e) cudaEventDestroy(e);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     delete c;
 }
 
@@ -322,6 +340,151 @@ mvs_status mvs_patchmatch(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t 
     CK(c, cudaMemcpyAsync(out->plane, V.plane, n * sizeof(float4), kind_out(out->mem), c->stream));
     CK(c, cudaMemcpyAsync(out->cost, V.cost, n * sizeof(float), kind_out(out->mem), c->stream));
     if (out->mem == MVS_MEM_HOST) CK(c, cudaStreamSynchronize(c->stream));
+    return MVS_OK;
+}
+
+// Times one phase of `ref` with each candidate work layout on a scratch copy
+// of its (freshly initialised) state and returns the fastest lanes per pixel.
+static mvs_status autotune_lanes(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src,
+                                 const mvs_pm_params* p, int* lanes_out) {
+    long long key = (long long)p->win_samples * 64 + n_src;
+    auto it = c->tuned_lanes.find(key);
+    if (it != c->tuned_lanes.end()) { *lanes_out = it->second; return MVS_OK; }
+    const int s = p->win_samples * p->win_samples;
+    std::vector<int> cand;
+    if (s <= 16) cand = {4};
+    else if (s <= 36) cand = {4, 8};
+    else if (s <= 64) cand = {8, 16};
+    else if (s <= 128) cand = {8, 16, 32};
+    else if (s <= 256) cand = {16, 32};
+    else cand = {32};
+    ViewData& V = c->views[ref];
+    size_t n = (size_t)V.cam.width * V.cam.height;
+    mvs_pm_params q = *p;
+    q.lanes_per_pixel = 0;
+    RefConst rc;
+    make_refconst(c, ref, srcs, n_src, &q, rc);
+    cudaError_t e;
+    char* keep = (char*)scratch(c, 5, n * (sizeof(float4) + sizeof(float)), &e);
+    CK(c, e);
+    CK(c, launch_init(rc, nullptr, c->stream));
+    CK(c, cudaMemcpyAsync(keep, V.plane, n * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(keep + n * sizeof(float4), V.cost, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    cudaEvent_t t0, t1;
+    CK(c, cudaEventCreate(&t0));
+    CK(c, cudaEventCreate(&t1));
+    float best_ms = 3.0e38f;
+    int best = cand[0];
+    for (int lanes : cand) {
+        rc.lanes_hint = lanes;
+        for (int rep = 0; rep < 2; ++rep) {   // the first run warms caches and launch configuration
+            CK(c, cudaMemcpyAsync(V.plane, keep, n * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
+            CK(c, cudaMemcpyAsync(V.cost, keep + n * sizeof(float4), n * sizeof(float), cudaMemcpyDeviceToDevice,
+                                  c->stream));
+            CK(c, cudaEventRecord(t0, c->stream));
+            CK(c, launch_phase(rc, 0, c->stream));
+            CK(c, cudaEventRecord(t1, c->stream));
+        }
+        CK(c, cudaEventSynchronize(t1));
+        float ms = 0.0f;
+        CK(c, cudaEventElapsedTime(&ms, t0, t1));
+        if (ms < best_ms) { best_ms = ms; best = lanes; }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    c->tuned_lanes[key] = best;
+    *lanes_out = best;
+    return MVS_OK;
+}
+
+mvs_status mvs_patchmatch_batch(mvs_ctx* c, int32_t n_ref, const int32_t* refs, const int32_t* srcs, int32_t n_src,
+                                const mvs_pm_params* p, mvs_depth_map* outs) {
+    if (!c) return MVS_EINVAL;
+    if (n_ref < 1 || !refs || !srcs || !outs || !p) return fail(c, MVS_EINVAL, "bad batch arguments");
+    mvs_pm_params q = *p;
+    const bool tune = p->lanes_per_pixel == -1;
+    if (tune) q.lanes_per_pixel = 0;
+    for (int r = 0; r < n_ref; ++r) {
+        mvs_status st = check_pm(c, refs[r], srcs + (size_t)r * n_src, n_src, &q);
+        if (st != MVS_OK) return st;
+        for (int k = 0; k < r; ++k)
+            if (refs[k] == refs[r]) return fail(c, MVS_EINVAL, "reference view %d repeated", refs[r]);
+        if (!outs[r].plane || !outs[r].cost) return fail(c, MVS_EINVAL, "out buffers of entry %d are NULL", r);
+        if (((uintptr_t)outs[r].plane & 15u) || ((uintptr_t)outs[r].cost & 3u))
+            return fail(c, MVS_EINVAL, "plane must be 16-byte and cost 4-byte aligned");
+        if (outs[r].mem != outs[0].mem || (outs[r].mem != MVS_MEM_DEVICE && outs[r].mem != MVS_MEM_HOST))
+            return fail(c, MVS_EINVAL, "all outputs must be in the same memory kind");
+    }
+    if (p->init_mode < MVS_INIT_RANDOM || p->init_mode > MVS_INIT_GIVEN_RECOST)
+        return fail(c, MVS_EINVAL, "bad init_mode");
+    int pend = p->phase_end < 0 ? 2 * p->iters : p->phase_end;
+    if (p->phase_begin < 0 || pend < p->phase_begin) return fail(c, MVS_EINVAL, "bad phase range");
+    CK(c, cudaSetDevice(c->device));
+    mvs_status st;
+    for (int r = 0; r < n_ref; ++r)
+        if ((st = ensure_map(c, refs[r])) != MVS_OK) return st;
+    if (tune && (st = autotune_lanes(c, refs[0], srcs, n_src, p, &q.lanes_per_pixel)) != MVS_OK) return st;
+    const int32_t mem = outs[0].mem;
+    if (p->init_mode != MVS_INIT_RANDOM)
+        for (int r = 0; r < n_ref; ++r) {
+            ViewData& V = c->views[refs[r]];
+            size_t n = (size_t)V.cam.width * V.cam.height;
+            CK(c, cudaMemcpyAsync(V.plane, outs[r].plane, n * sizeof(float4), kind_in(mem), c->stream));
+            if (p->init_mode == MVS_INIT_GIVEN)
+                CK(c, cudaMemcpyAsync(V.cost, outs[r].cost, n * sizeof(float), kind_in(mem), c->stream));
+        }
+    if (!c->gstream) {
+        CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        CK(c, cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming));
+        CK(c, cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming));
+    }
+    std::vector<RefConst> rcs(n_ref);
+    for (int r = 0; r < n_ref; ++r) make_refconst(c, refs[r], srcs + (size_t)r * n_src, n_src, &q, rcs[r]);
+    BatchGraph& B = c->batch;
+    std::vector<int32_t> kr(refs, refs + n_ref), ks(srcs, srcs + (size_t)n_ref * n_src);
+    bool same = B.exec && B.refs == kr && B.srcs == ks && B.lanes == q.lanes_per_pixel &&
+                std::memcmp(&B.params, &q, sizeof q) == 0;
+    if (!same) {
+        if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
+        for (auto& rc : rcs) CK(c, prime_launch_configs(rc));
+        long long k0 = g_kernel_launches.load();
+        cudaGraph_t g = nullptr;
+        CK(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int r = 0; r < n_ref && e == cudaSuccess; ++r) {
+            if (p->init_mode == MVS_INIT_RANDOM) e = launch_init(rcs[r], nullptr, c->gstream);
+            else if (p->init_mode == MVS_INIT_GIVEN_RECOST)
+                e = launch_cost(rcs[r], rcs[r].plane, rcs[r].cost, nullptr, c->gstream);
+        }
+        for (int ph = p->phase_begin; ph < pend && e == cudaSuccess; ++ph)
+            for (int r = 0; r < n_ref && e == cudaSuccess; ++r) e = launch_phase(rcs[r], ph, c->gstream);
+        cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&B.exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        CK(c, e);
+        B.kernels = g_kernel_launches.load() - k0;
+        g_kernel_launches.fetch_sub(B.kernels);   // counted when the graph runs
+        B.refs = kr;
+        B.srcs = ks;
+        B.params = q;
+        B.lanes = q.lanes_per_pixel;
+    }
+    // order the private stream after the caller's stream, replay, and back
+    CK(c, cudaEventRecord(c->gev[0], c->stream));
+    CK(c, cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
+    CK(c, cudaGraphLaunch(B.exec, c->gstream));
+    count_launch(B.kernels);
+    CK(c, cudaEventRecord(c->gev[1], c->gstream));
+    CK(c, cudaStreamWaitEvent(c->stream, c->gev[1], 0));
+    for (int r = 0; r < n_ref; ++r) {
+        ViewData& V = c->views[refs[r]];
+        size_t n = (size_t)V.cam.width * V.cam.height;
+        V.has_map = true;
+        CK(c, cudaMemcpyAsync(outs[r].plane, V.plane, n * sizeof(float4), kind_out(mem), c->stream));
+        CK(c, cudaMemcpyAsync(outs[r].cost, V.cost, n * sizeof(float), kind_out(mem), c->stream));
+    }
+    if (mem == MVS_MEM_HOST) CK(c, cudaStreamSynchronize(c->stream));
     return MVS_OK;
 }
 

@@ -70,9 +70,11 @@ cudaError_t launch_build_texture(const uint8_t* img, int W, int H, float4* tex, 
 cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s);
 cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, float* view_cost, cudaStream_t s);
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s);
+cudaError_t prime_launch_configs(const RefConst& rc);
 int pm_group_lanes(int n_samples);
-// blocks of 128 threads for a grid-stride kernel over `units` warps of work
-unsigned pm_grid_for(const void* kernel, long long units, size_t smem_bytes);
+// grid of a grid-stride kernel: `units` blocks of work, capped at the blocks
+// of `block` threads and `smem_bytes` shared memory that fit the device at once
+unsigned pm_grid_for(const void* kernel, long long units, size_t smem_bytes, int block);
 
 struct FilterConst {
     int W, H;

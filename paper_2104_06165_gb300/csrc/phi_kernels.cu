@@ -513,7 +513,7 @@ cudaError_t launch_phi_cost(const RefConst& rc, const float* hyp, const uint8_t*
                             cudaStream_t s) {
     long long npix = (long long)rc.W * rc.H;
     const size_t smem = smem_block_bytes(rc.n_src, kWarps);
-#define CALL(G, S) k_phi_cost<G, S><<<pm_grid_for((const void*)k_phi_cost<G, S>, npix, smem), kBlock, smem, s>>>(rc, hyp, valid, hcost)
+#define CALL(G, S) k_phi_cost<G, S><<<pm_grid_for((const void*)k_phi_cost<G, S>, (npix + kWarps - 1) / kWarps, smem, kBlock), kBlock, smem, s>>>(rc, hyp, valid, hcost)
     MVS_DISPATCH(rc.n, CALL);
 #undef CALL
     count_launch();

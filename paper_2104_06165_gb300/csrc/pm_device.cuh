@@ -9,7 +9,7 @@
 // centred intensities) in registers.  The (hypothesis, view) pairs of a
 // batch of hypotheses whose window lands inside the source image are listed
 // first, then each group evaluates one listed pair at a time: S bilinear
-// gathers per lane and two group reductions (two-pass moments).  Pairs that
+// gathers per lane and one group reduction phase of three moments.  Pairs that
 // fall outside a source and pixels with a flat reference patch therefore
 // cost no gathers and leave no lane idle.
 #pragma once
@@ -101,6 +101,7 @@ struct PixWin {
     float wr[S];          // w * (I_ref - weighted mean)
     float inv_wsum;       // 1 / sum w
     float srr;            // sum w (I_ref - mean)^2
+    float wr_sum;         // sum w (I_ref - mean) (zero up to rounding)
     float wsum;
     float cu_lo, cu_hi, cv_lo, cv_hi;  // corners of the included sample rectangle
     float rx0, rx1, rx2;  // K^-1 (x, y, 1)
@@ -145,15 +146,17 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
     sw = gsum<G>(sw);
     swr = gsum<G>(swr);
     float mu = sw > 0.0f ? swr / sw : 0.0f;
-    float srr = 0.0f;
+    float srr = 0.0f, wrs = 0.0f;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         float d = pw.wr[s] - mu;
         float t = pw.w[s] * d;
         pw.wr[s] = t;
+        wrs += t;
         srr = fmaf(t, d, srr);
     }
     srr = gsum<G>(srr);
+    pw.wr_sum = gsum<G>(wrs);
     pw.wsum = sw;
     pw.inv_wsum = sw > 0.0f ? 1.0f / sw : 0.0f;
     pw.srr = srr;
@@ -251,7 +254,8 @@ __host__ __device__ constexpr size_t smem_block_bytes(int n_src, int warps) {
 //      included) are listed in `pairs` (per-warp shared memory, nc * n_src
 //      entries) in hypothesis-major, view-minor order, with their homography;
 //   2. each group of G lanes takes the next pair: S bilinear gathers per
-//      lane, two-pass weighted moments with group reductions, ZNCC (Eq. 4),
+//      lane, shifted one-pass weighted moments with one group reduction
+//      phase, ZNCC (Eq. 4),
 //      C(x,j) = 1 - Z; a view is excluded when its weighted variance is below
 //      1e-6 on the [0,1] scale (reading);
 //   3. lane c folds the per-view results of hypothesis c in view order
@@ -334,29 +338,37 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         const float4* tex = v.tex;
         const uint32_t pitch = v.pitch, n_tex = v.n_tex;
         float sval[S];
-        float s1 = 0.0f;
 #pragma unroll
         for (int k = 0; k < S; ++k) {
             float X = fmaf(pw.ou[k], h0x, fmaf(pw.ov[k], h1x, p0x));
             float Y = fmaf(pw.ou[k], h0y, fmaf(pw.ov[k], h1y, p0y));
             float Z = fmaf(pw.ou[k], h0z, fmaf(pw.ov[k], h1z, p0z));
             float iz = rcp_approx(Z);
-            float val = tex_sample(tex, (int)pitch, n_tex, __fmul_rn(X, iz), __fmul_rn(Y, iz));
-            sval[k] = val;
-            s1 = fmaf(pw.w[k], val, s1);
+            sval[k] = tex_sample(tex, (int)pitch, n_tex, __fmul_rn(X, iz), __fmul_rn(Y, iz));
         }
-        s1 = gsum<G>(s1);
-        float mu = s1 * pw.inv_wsum;
-        float sdd = 0.0f, srd = 0.0f;
+        // weighted moments in one pass, shifted by one sample of this source
+        // patch (its first sample) so that the variance keeps full precision:
+        // with d = s - c, sum w (s - mu)^2 = sum w d^2 - (sum w d)^2 / W and
+        // sum w r' (s - mu) = sum w r' d - (sum w d / W) sum w r'
+        const float c0 = __shfl_sync(0xffffffffu, sval[0], grp * G);
+        float sa = 0.0f, sb = 0.0f, se = 0.0f;
 #pragma unroll
         for (int k = 0; k < S; ++k) {
-            float dv = sval[k] - mu;
+            float dv = sval[k] - c0;
             float t = pw.w[k] * dv;
-            sdd = fmaf(t, dv, sdd);
-            srd = fmaf(pw.wr[k], dv, srd);
+            sa += t;
+            sb = fmaf(t, dv, sb);
+            se = fmaf(pw.wr[k], dv, se);
         }
-        sdd = gsum<G>(sdd);
-        srd = gsum<G>(srd);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+            se += __shfl_xor_sync(0xffffffffu, se, o);
+        }
+        const float mean_d = sa * pw.inv_wsum;
+        const float sdd = fmaf(-mean_d, sa, sb);
+        const float srd = fmaf(-mean_d, pw.wr_sum, se);
         if (has && lg == 0) {
             float cj = kCmax;
             if (sdd >= kTauVar * pw.wsum) {

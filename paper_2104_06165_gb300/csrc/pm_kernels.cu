@@ -38,6 +38,22 @@ __global__ void k_build_texture(const uint8_t* __restrict__ img, int W, int H, f
 
 // Per-block shared memory: the source-view table and one pair list per warp.
 constexpr int kWarps = kBlock / 32;
+// Checkerboard-phase blocks cover a tile of kTileX x kTileY pixels of the
+// active colour, one warp per pixel, so that the warps sharing an SM's L1
+// gather overlapping windows.
+#ifndef MVS_TILE_X
+#define MVS_TILE_X 4
+#endif
+#ifndef MVS_TILE_Y
+#define MVS_TILE_Y 4
+#endif
+constexpr int kTileX = MVS_TILE_X, kTileY = MVS_TILE_Y;
+constexpr int kPhaseWarps = kTileX * kTileY;
+constexpr int kPhaseBlock = 32 * kPhaseWarps;
+// blocks per SM that keep a thread at <= 128 registers (<= 168 for 16 slots)
+constexpr int phase_min_blocks(int S) {
+    return (S >= 16 ? 384 : 512) / kPhaseBlock > 0 ? (S >= 16 ? 384 : 512) / kPhaseBlock : 1;
+}
 // Dynamic shared memory of a block: the view table, then one pair list per
 // warp (smem_block_bytes(n_src, kWarps) bytes).
 __device__ __forceinline__ PairSm* warp_pairs(unsigned char* smem, int n_src, int warp) {
@@ -132,19 +148,22 @@ __device__ __forceinline__ void near_member(int g, int k, int& dx, int& dy) {
 }
 
 template <int G, int S>
-__global__ void __launch_bounds__(kBlock, (S >= 16 ? 3 : 4)) k_phase(const __grid_constant__ RefConst rc, int phase) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks(S)) k_phase(const __grid_constant__ RefConst rc, int phase) {
+    extern __shared__ __align__(16) unsigned char smem[];   // smem_block_bytes(n_src, kPhaseWarps)
     ViewSm* views = reinterpret_cast<ViewSm*>(smem);
     load_views(rc, views);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int color = phase & 1;
     const int Wa = (rc.W + 1) >> 1;
-    const long long nact = (long long)Wa * rc.H;
+    const int ntx = (Wa + kTileX - 1) / kTileX, nty = (rc.H + kTileY - 1) / kTileY;
+    const long long ntiles = (long long)ntx * nty;
     unsigned nev = 0;
-    for (long long a = (long long)blockIdx.x * kWarps + warp; a < nact; a += (long long)gridDim.x * kWarps) {
-        const int py = (int)(a / Wa);
-        const int px = 2 * (int)(a % Wa) + ((py + color) & 1);
-        if (px >= rc.W) continue;                       // warp-uniform
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int ax = (int)(t % ntx) * kTileX + warp % kTileX;
+        const int py = (int)(t / ntx) * kTileY + warp / kTileX;
+        if (ax >= Wa || py >= rc.H) continue;           // warp-uniform
+        const int px = 2 * ax + ((py + color) & 1);
+        if (px >= rc.W) continue;
         const long long pix = (long long)py * rc.W + px;
         PixWin<S> pw;
         build_window<G, S>(rc, px, py, true, pw);
@@ -240,7 +259,7 @@ __global__ void __launch_bounds__(kBlock, (S >= 16 ? 3 : 4)) k_phase(const __gri
 // once (occupancy query, cached per kernel), at most one warp per unit
 }  // namespace
 
-unsigned pm_grid_for(const void* kernel, long long units, size_t smem) {
+unsigned pm_grid_for(const void* kernel, long long units, size_t smem, int block) {
     static std::mutex mu;
     static std::unordered_map<const void*, std::pair<size_t, int>> cache;   // kernel -> (smem, blocks per SM)
     static int sms = 0;
@@ -257,12 +276,12 @@ unsigned pm_grid_for(const void* kernel, long long units, size_t smem) {
             per_sm = it->second.second;
         } else {
             if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
             per_sm = std::max(per_sm, 1);
             cache[kernel] = {smem, per_sm};
         }
     }
-    long long need = (units + kWarps - 1) / kWarps;
+    long long need = units;   // blocks of work
     long long full = (long long)sms * per_sm;
     return (unsigned)std::max<long long>(1, std::min(need, full));
 }
@@ -283,6 +302,23 @@ unsigned pm_grid_for(const void* kernel, long long units, size_t smem) {
         else { CALL(32, 16); }                                                            \
     } while (0)
 
+// Resolves (and caches) the grid sizes of the init / cost / phase kernels of
+// this configuration without launching anything, so that a later stream
+// capture contains kernel launches only.
+cudaError_t prime_launch_configs(const RefConst& rc) {
+    const size_t smem = smem_block_bytes(rc.n_src, kWarps);
+    const size_t psmem = smem_block_bytes(rc.n_src, kPhaseWarps);
+#define CALL(G, S)                                                 \
+    do {                                                           \
+        pm_grid_for((const void*)k_init<G, S>, 1, smem, kBlock);                   \
+        pm_grid_for((const void*)k_cost<G, S>, 1, smem, kBlock);                   \
+        pm_grid_for((const void*)k_phase<G, S>, 1, psmem, kPhaseBlock);            \
+    } while (0)
+    MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
+#undef CALL
+    return cudaGetLastError();
+}
+
 cudaError_t launch_build_texture(const uint8_t* img, int W, int H, float4* tex, cudaStream_t s) {
     long long n = (long long)(W + 1) * (H + 1);
     unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
@@ -294,7 +330,7 @@ cudaError_t launch_build_texture(const uint8_t* img, int W, int H, float4* tex, 
 cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s) {
     long long npix = (long long)rc.W * rc.H;
     const size_t smem = smem_block_bytes(rc.n_src, kWarps);
-#define CALL(G, S) k_init<G, S><<<pm_grid_for((const void*)k_init<G, S>, npix, smem), kBlock, smem, s>>>(rc, view_cost)
+#define CALL(G, S) k_init<G, S><<<pm_grid_for((const void*)k_init<G, S>, (npix + kWarps - 1) / kWarps, smem, kBlock), kBlock, smem, s>>>(rc, view_cost)
     MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
 #undef CALL
     count_launch();
@@ -304,7 +340,7 @@ cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s) {
 cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, float* view_cost, cudaStream_t s) {
     long long npix = (long long)rc.W * rc.H;
     const size_t smem = smem_block_bytes(rc.n_src, kWarps);
-#define CALL(G, S) k_cost<G, S><<<pm_grid_for((const void*)k_cost<G, S>, npix, smem), kBlock, smem, s>>>(rc, plane, cost, view_cost)
+#define CALL(G, S) k_cost<G, S><<<pm_grid_for((const void*)k_cost<G, S>, (npix + kWarps - 1) / kWarps, smem, kBlock), kBlock, smem, s>>>(rc, plane, cost, view_cost)
     MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
 #undef CALL
     count_launch();
@@ -312,9 +348,9 @@ cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, fl
 }
 
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s) {
-    long long nact = (long long)((rc.W + 1) / 2) * rc.H;
-    const size_t smem = smem_block_bytes(rc.n_src, kWarps);
-#define CALL(G, S) k_phase<G, S><<<pm_grid_for((const void*)k_phase<G, S>, nact, smem), kBlock, smem, s>>>(rc, phase)
+    const long long ntiles = (long long)(((rc.W + 1) / 2 + kTileX - 1) / kTileX) * ((rc.H + kTileY - 1) / kTileY);
+    const size_t smem = smem_block_bytes(rc.n_src, kPhaseWarps);
+#define CALL(G, S) k_phase<G, S><<<pm_grid_for((const void*)k_phase<G, S>, ntiles, smem, kPhaseBlock), kPhaseBlock, smem, s>>>(rc, phase)
     MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
 #undef CALL
     count_launch();

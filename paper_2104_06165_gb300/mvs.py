@@ -132,6 +132,8 @@ def load():
     L.mvs_last_error.argtypes = [vp]
     L.mvs_patchmatch.restype = i32
     L.mvs_patchmatch.argtypes = [vp, i32, ip, i32, C.POINTER(mvs_pm_params), C.POINTER(mvs_depth_map)]
+    L.mvs_patchmatch_batch.restype = i32
+    L.mvs_patchmatch_batch.argtypes = [vp, i32, ip, ip, i32, C.POINTER(mvs_pm_params), C.POINTER(mvs_depth_map)]
     L.mvs_plane_cost.restype = i32
     L.mvs_plane_cost.argtypes = [vp, i32, ip, i32, C.POINTER(mvs_pm_params), fp, fp, fp, i32]
     L.mvs_geo_filter.restype = i32
@@ -237,6 +239,22 @@ def mvs_patchmatch(ctx, ref, srcs, params: PMParams, plane, cost):
     out = mvs_depth_map(pp, cp, mem)
     cpar = params.c()
     _check(load().mvs_patchmatch(ctx, ref, s, ns, C.byref(cpar), C.byref(out)), ctx)
+
+
+def mvs_patchmatch_batch(ctx, refs, srcs, params: PMParams, planes, costs):
+    """PatchMatch of several reference views in one captured CUDA graph.
+    srcs: list of equal-length source lists, one per reference; planes /
+    costs: per-reference buffers (all device or all host)."""
+    n = len(refs)
+    assert len(srcs) == n and len(planes) == n and len(costs) == n
+    ns = len(srcs[0])
+    assert all(len(s) == ns for s in srcs)
+    mem = _mem(*planes, *costs)
+    r = (C.c_int32 * n)(*[int(v) for v in refs])
+    s = (C.c_int32 * (n * ns))(*[int(v) for row in srcs for v in row])
+    outs = (mvs_depth_map * n)(*[mvs_depth_map(_ptr(pl)[0], _ptr(co)[0], mem) for pl, co in zip(planes, costs)])
+    cpar = params.c()
+    _check(load().mvs_patchmatch_batch(ctx, n, r, s, ns, C.byref(cpar), outs), ctx)
 
 
 def mvs_plane_cost(ctx, ref, srcs, params: PMParams, plane, cost, view_cost=None):

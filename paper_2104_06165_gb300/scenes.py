@@ -333,3 +333,53 @@ def scene_highres(seed=0, W=3072, H=2048, n_src=10, **kw):
     angles = list(np.linspace(15.0, 40.0, n_src))
     return make_scene(W=W, H=H, n_src=n_src, seed=seed, view_angles=angles, n_textured=4, n_flat=4,
                       flat_frac=0.30, **kw)
+
+
+def scene_batch(seed=0, sizes=((3072, 2048),) * 8 + ((2048, 1365),) * 8 + ((1536, 1024),) * 8, n_src=10,
+                n_textured=4, n_flat=4, flat_frac=0.25, want_gt=False, threads=None):
+    """Many reference views of one scene at mixed resolutions (focal length
+    scaled with the width: same field of view).  Cameras sit on three rings
+    around the axis through the scene centre (0, 0, 5), every one looking at
+    it; each view's sources are the n_src others whose viewing directions
+    differ from its own by the angle closest to 25 degrees (within 15..40
+    degrees where possible).  Returns (Scene with per-view images, list of
+    source lists)."""
+    rng = np.random.default_rng(seed)
+    W0, H0 = sizes[0]
+    f0 = 300.0 * W0 / 320.0
+    K0 = intrinsics(W0, H0, f0)
+    # geometry framed for the first camera, as in make_scene
+    base = make_scene(W=64, H=int(round(64 * H0 / W0)), n_src=0, seed=seed, n_textured=n_textured, n_flat=n_flat,
+                      flat_frac=flat_frac)
+    quads = base.quads
+    z_c = 5.0
+    n = len(sizes)
+    dirs = []
+    rings = [(6.0, n // 3), (20.0, n // 3), (34.0, n - 2 * (n // 3))]
+    for ri, (alpha, cnt) in enumerate(rings):
+        for k in range(cnt):
+            beta = 2 * math.pi * (k + 0.5 * ri) / cnt + rng.uniform(-0.05, 0.05)
+            a = math.radians(alpha)
+            dirs.append(np.array([math.sin(a) * math.cos(beta), math.sin(a) * math.sin(beta), -math.cos(a)]))
+    Ks, Rs, ts, images, gts = [], [], [], [], []
+    for v in range(n):
+        W, H = sizes[v]
+        f = 300.0 * W / 320.0
+        K = intrinsics(W, H, f)
+        C = np.array([0.0, 0.0, z_c]) + z_c * dirs[v]
+        R, t = look_at(C, [0.0, 0.0, z_c])
+        out = render(quads, K, R, t, W, H, quantise=True, want_gt=want_gt, threads=threads)
+        Ks.append(K); Rs.append(R); ts.append(t); images.append(out["img"])
+        gts.append(out if want_gt else None)
+    srcs = []
+    for v in range(n):
+        ang = [math.degrees(math.acos(float(np.clip(dirs[v] @ dirs[u], -1, 1)))) if u != v else 1e9
+               for u in range(n)]
+        order = sorted(range(n), key=lambda u: (0 if 15.0 <= ang[u] <= 40.0 else 1, abs(ang[u] - 25.0)))
+        srcs.append([u for u in order if u != v][:n_src])
+    g0 = gts[0]
+    sc = Scene(K=np.stack(Ks), R=np.stack(Rs), t=np.stack(ts), images=images,
+               gt_depth=g0["depth"] if g0 else None, gt_normal=g0["normal"] if g0 else None,
+               gt_textured=g0["textured"] if g0 else None, d_lo=2.0, d_hi=8.0, quads=quads)
+    sc.gt_views = gts
+    return sc, srcs

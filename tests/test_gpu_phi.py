@@ -177,7 +177,39 @@ def test_plane_infer_recovers_texture_less_planes(mvs_lib):
         flat = ~sc.gt_textured
         print(f"completeness @1%: before {before.mean():.3f} after {after.mean():.3f}; "
               f"texture-less before {before[flat].mean():.3f} after {after[flat].mean():.3f}")
-        assert after[flat].mean() > before[flat].mean() + 0.2
+        # the FP64 oracle gives 0.18 -> 0.37 on the texture-less pixels of this
+        # scene (depth line fits on tilted planes); the GPU must do as well
+        assert after[flat].mean() > before[flat].mean() + 0.15
         assert after.mean() > before.mean() + 0.02
+    finally:
+        ctx.close()
+
+
+def test_plane_infer_end_to_end_parity(mvs_lib, oracle_lib):
+    """The whole mvs_plane_infer against the oracle's, from the same input
+    depth map: filled depths agree except where the MRF meets a near tie."""
+    import torch
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_scene(W=160, H=120, n_src=3, seed=41, baseline_frac=0.1, n_textured=2, n_flat=2,
+                           flat_frac=0.2)
+    p = mvs_lib.PMParams(win_radius=5.0, win_samples=6, iters=3, seed=4)
+    ctx = mvs_lib.Context(sc.K, sc.R, sc.t, sc.images, stream=torch.cuda.current_stream())
+    osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
+    try:
+        pl = np.zeros((120, 160, 4), np.float32)
+        co = np.zeros((120, 160), np.float32)
+        mvs_lib.mvs_patchmatch(ctx.h, 0, [1, 2, 3], p, pl, co)
+        known = ((pl[..., 3] > 0) & (co < 0.5)).astype(np.uint8)
+        opl, aux = oracle_lib.plane_infer(osc, 0, [1, 2, 3], p, known, pl.astype(np.float64))
+        gpl, gco = pl.copy(), co.copy()
+        mvs_lib.mvs_plane_infer(ctx.h, 0, [1, 2, 3], p, mvs_lib.PhiParams(), None, gpl, gco)
+        filled_o = aux["filled"].astype(bool)
+        filled_g = (gpl[..., 3] > 0) & (known == 0)
+        assert filled_o.sum() > 500
+        assert (filled_o != filled_g).mean() < 0.01
+        both = filled_o & filled_g
+        agree = np.abs(gpl[..., 3] - opl[..., 3]) <= 1e-3 * opl[..., 3]
+        assert agree[both].mean() > 0.97
+        assert np.array_equal(gpl[known == 1], pl[known == 1])
     finally:
         ctx.close()
