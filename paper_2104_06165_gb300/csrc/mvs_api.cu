@@ -18,7 +18,7 @@ struct ViewData {
     mvs_camera cam;
     double Kinv[9];
     uint8_t* img = nullptr;
-    float4* tex = nullptr;
+    uint2* tex = nullptr;      // bilinear-coefficient texels (fp16 x 4)
     float4* plane = nullptr;   // depth map state (library-owned)
     float* cost = nullptr;
     bool has_map = false;
@@ -173,7 +173,7 @@ void make_refconst(const mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n
     double r_now = 0.5 * (p->win_samples - 1);
     rc.step = (float)(p->win_radius / r_now);
     rc.sp_coef = p->sigma_s > 0 ? (float)(-1.0 / (2.0 * (double)p->sigma_s * p->sigma_s)) : 0.0f;
-    double sc = 255.0 * p->sigma_c;
+    double sc = 4.0 * 255.0 * p->sigma_c;   // texel units are 4 x [0, 255]
     rc.col_coef = p->sigma_c > 0 ? (float)(-1.0 / (2.0 * sc * sc)) : 0.0f;
     rc.d_lo = p->d_lo;
     rc.d_hi = p->d_hi;
@@ -252,7 +252,7 @@ mvs_status mvs_create(const mvs_camera* cams, const uint8_t* const* images, int3
         size_t n = (size_t)V.cam.width * V.cam.height;
         size_t nt = (size_t)(V.cam.width + 1) * (V.cam.height + 1);
         e = cudaMalloc(&V.img, n);
-        if (e == cudaSuccess) e = cudaMalloc(&V.tex, nt * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc(&V.tex, nt * sizeof(uint2));
         if (e == cudaSuccess) e = cudaMemcpyAsync(V.img, images[i], n, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = launch_build_texture(V.img, V.cam.width, V.cam.height, V.tex, c->stream);
         if (e != cudaSuccess) {

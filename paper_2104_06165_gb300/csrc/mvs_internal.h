@@ -15,7 +15,7 @@
 struct PairConst {
     float A[9];
     float b[3];
-    const float4* tex;   // bilinear-coefficient texels of the source, see below
+    const uint2* tex;    // bilinear-coefficient texels of the source, see below
     int W, H;            // source image size
     int pitch;           // texel row pitch = W + 1
     uint32_t n_tex;      // (W + 1) * (H + 1)
@@ -27,7 +27,7 @@ struct RefConst {
     int ref_index;
     int n_src;
     float Kinv[9];
-    const float4* tex;         // reference bilinear-coefficient texels
+    const uint2* tex;          // reference bilinear-coefficient texels
     const uint8_t* img;        // reference image (uint8)
     int pitch;                 // W + 1
     uint32_t n_tex;
@@ -35,7 +35,7 @@ struct RefConst {
     int n;
     float step;
     float sp_coef;             // -1 / (2 sigma_s^2) (0 = no spatial weight)
-    float col_coef;            // -1 / (2 (255 sigma_c)^2) (0 = no colour weight)
+    float col_coef;            // -1 / (2 (4 * 255 sigma_c)^2) (0 = no colour weight), texel units
     float d_lo, d_hi;
     unsigned long long seed;
     float4* plane;             // state: (n.x, n.y, n.z, depth) per pixel
@@ -46,15 +46,17 @@ struct RefConst {
 };
 
 // Bilinear-coefficient texel layout.  Texel (i, j), i in [-1, W-1],
-// j in [-1, H-1], stored at ((j + 1) * (W + 1) + (i + 1)), holds, for the
-// clamped taps p00 = I(i, j), p01 = I(i+1, j), p10 = I(i, j+1),
-// p11 = I(i+1, j+1) on the [0, 255] scale:
-//   .x = (p00 + p01 + p10 + p11) / 4
-//   .y = ((p01 - p00) + (p11 - p10)) / 2
-//   .z = ((p10 - p00) + (p11 - p01)) / 2
-//   .w = p00 - p01 - p10 + p11
-// so that the bilinear value at (i + 0.5 + u, j + 0.5 + v), |u|,|v| <= 1/2,
-// is x + u y + v z + u v w (every coefficient is a multiple of 1/4 and exact).
+// j in [-1, H-1], stored at ((j + 1) * (W + 1) + (i + 1)), holds four fp16
+// numbers computed from the clamped taps p00 = I(i, j), p01 = I(i+1, j),
+// p10 = I(i, j+1), p11 = I(i+1, j+1) on the [0, 255] scale:
+//   a = p00 + p01 + p10 + p11                 (integer in [0, 1020])
+//   b = (p01 - p00) + (p11 - p10)             (integer in [-510, 510])
+//   c = (p10 - p00) + (p11 - p01)
+//   d = p00 - p01 - p10 + p11
+// all exact in fp16, so that four times the bilinear value at
+// (i + 1/2 + U/2, j + 1/2 + V/2), |U|, |V| <= 1, is a + U b + V c + U V d.
+// Kernels therefore work with intensities scaled by 4 (the ZNCC is
+// scale-free; the colour weight and the flat limit are scaled to match).
 
 // Status word written by kernels (bounded waits, bounds checks).
 enum { MVS_DEV_OK = 0, MVS_DEV_TIMEOUT = 1, MVS_DEV_BOUNDS = 2 };
@@ -66,7 +68,7 @@ extern std::atomic<long long> g_kernel_launches;
 inline void count_launch(long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // Host-side launchers (pm_kernels.cu / phi_kernels.cu).
-cudaError_t launch_build_texture(const uint8_t* img, int W, int H, float4* tex, cudaStream_t s);
+cudaError_t launch_build_texture(const uint8_t* img, int W, int H, uint2* tex, cudaStream_t s);
 cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s);
 cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, float* view_cost, cudaStream_t s);
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s);

@@ -14,16 +14,17 @@
 // cost no gathers and leave no lane idle.
 #pragma once
 #include <cstdint>
+#include <cuda_fp16.h>
 #include "mvs_internal.h"
 
 namespace mvsdev {
 
 constexpr float kCmax = 2.0f;                       // C_max = 1 - Z_min, Z_min = -1
 constexpr float kEpsC = 1e-6f;                      // floor of C(x,j) in the weights of Eq. 5
-constexpr float kTauVar = 1e-6f * 255.0f * 255.0f;  // flat-patch variance limit, [0,255] scale
+constexpr float kTauVar = 1e-6f * 1020.0f * 1020.0f;  // flat-patch variance limit, texel units (4 x [0,255])
 constexpr float kGraze = 1e-3f;                     // grazing-plane limit |n.r| / |r|
-constexpr float kMagic = 12582912.0f;               // 1.5 * 2^23: float -> nearest integer
-constexpr int kMagicBits = 0x4B400000;
+constexpr float kMagic2 = 25165824.0f;              // 1.5 * 2^24: float -> nearest even integer
+constexpr int kMagic2Bits = 0x4BC00000;
 constexpr float kPi = 3.14159265358979323846f;
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -77,19 +78,24 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
     return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
 }
 
-// Bilinear sample of a coefficient texture at (xs + 0.5, ys + 0.5): the
-// caller passes coordinates already shifted by -1/2.  The texel index is
-// clamped into the array, so any input (even NaN) reads inside the buffer.
-__device__ __forceinline__ float tex_sample(const float4* __restrict__ tex, int pitch, uint32_t n_tex, float xs,
-                                            float ys) {
-    float tx = __fadd_rn(xs, kMagic), ty = __fadd_rn(ys, kMagic);
-    float u = __fsub_rn(xs, __fsub_rn(tx, kMagic));
-    float v = __fsub_rn(ys, __fsub_rn(ty, kMagic));
+// Four times the bilinear value of a coefficient texture at (x + 1/2, y + 1/2)
+// given xs2 = 2x, ys2 = 2y (the caller folds the shift and the factor 2 into
+// its homography).  Adding 1.5 * 2^24 rounds 2x to the nearest even integer
+// 2i, so U = 2x - 2i lies in [-1, 1] and the bits of the sum give i.  The
+// texel index is clamped into the array, so any input (even NaN) reads
+// inside the buffer.
+__device__ __forceinline__ float tex_sample(const uint2* __restrict__ tex, int pitch, uint32_t n_tex, float xs2,
+                                            float ys2) {
+    float tx = __fadd_rn(xs2, kMagic2), ty = __fadd_rn(ys2, kMagic2);
+    float U = __fsub_rn(xs2, __fsub_rn(tx, kMagic2));
+    float V = __fsub_rn(ys2, __fsub_rn(ty, kMagic2));
     uint32_t idx = (uint32_t)__float_as_int(ty) * (uint32_t)pitch + (uint32_t)__float_as_int(tx) +
-                   (uint32_t)(pitch + 1) * (uint32_t)(1 - kMagicBits);
+                   (uint32_t)(pitch + 1) * (uint32_t)(1 - kMagic2Bits);
     idx = min(idx, n_tex - 1u);
-    float4 c = __ldg(tex + idx);
-    return fmaf(v, fmaf(u, c.w, c.z), fmaf(u, c.y, c.x));
+    uint2 q = __ldg(tex + idx);
+    float2 ab = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+    float2 cd = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    return fmaf(V, fmaf(U, cd.y, cd.x), fmaf(U, ab.y, ab.x));
 }
 
 // Reference side of the window of one pixel.  Every group of G lanes of the
@@ -122,7 +128,7 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
         if (eu >= 0.0f && eu <= (float)(rc.W - 1)) { ku_lo = min(ku_lo, k); ku_hi = max(ku_hi, k); }
         if (ev >= 0.0f && ev <= (float)(rc.H - 1)) { kv_lo = min(kv_lo, k); kv_hi = max(kv_hi, k); }
     }
-    const float rcen = exists ? (float)__ldg(rc.img + (long long)py * rc.W + px) : 0.0f;
+    const float rcen = exists ? 4.0f * (float)__ldg(rc.img + (long long)py * rc.W + px) : 0.0f;
     float sw = 0.0f, swr = 0.0f;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -132,7 +138,7 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
         float ou = rc.step * ((float)ku - half), ov = rc.step * ((float)kv - half);
         float r = 0.0f, w = 0.0f;
         if (in) {
-            r = tex_sample(rc.tex, rc.pitch, rc.n_tex, (float)px + ou - 0.5f, (float)py + ov - 0.5f);
+            r = tex_sample(rc.tex, rc.pitch, rc.n_tex, 2.0f * ((float)px + ou) - 1.0f, 2.0f * ((float)py + ov) - 1.0f);
             float dc = r - rcen;
             w = expf(rc.sp_coef * (ou * ou + ov * ov)) * expf(rc.col_coef * dc * dc);
         }
@@ -179,7 +185,7 @@ struct ViewSm {
     float b[3];
     float wm1, hm1;       // W - 1, H - 1
     uint32_t pitch, n_tex;
-    const float4* tex;
+    const uint2* tex;
 };
 
 __device__ __forceinline__ void load_views(const RefConst& rc, ViewSm* sv) {
@@ -229,7 +235,8 @@ __device__ __forceinline__ Cand make_cand(const RefConst& rc, const PixWin<S>& p
 }
 
 // One listed (hypothesis, view) pair in shared memory: the homography
-// columns H e1, H e2 and H x (shifted by -1/2 for tex_sample), the view,
+// columns H e1, H e2 and H x (x, y rows shifted by -1/2 and doubled for
+// tex_sample), the view,
 // and after evaluation its per-view cost (C_max when excluded).
 struct PairSm {
     float h0x, h0y, h0z, h1x;
@@ -303,10 +310,10 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             ok = ok && cz > 0.0f && xs >= -0.5f && xs <= v.wm1 - 0.5f && ys >= -0.5f && ys <= v.hm1 - 0.5f;
         }
         unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
+        if (ok) {   // stored with x and y doubled (tex_sample's convention)
             PairSm& q = pairs[count + __popc(m & ((1u << lane) - 1u))];
-            q.h0x = h0x; q.h0y = h0y; q.h0z = h0z; q.h1x = h1x;
-            q.h1y = h1y; q.h1z = h1z; q.p0x = p0x; q.p0y = p0y;
+            q.h0x = 2.0f * h0x; q.h0y = 2.0f * h0y; q.h0z = h0z; q.h1x = 2.0f * h1x;
+            q.h1y = 2.0f * h1y; q.h1z = h1z; q.p0x = 2.0f * p0x; q.p0y = 2.0f * p0y;
             q.p0z = p0z; q.j = j; q.c = c;
         }
         count += __popc(m);
@@ -335,7 +342,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         const float h0x = q.h0x, h0y = q.h0y, h0z = q.h0z, h1x = q.h1x;
         const float h1y = q.h1y, h1z = q.h1z, p0x = q.p0x, p0y = q.p0y, p0z = q.p0z;
         const ViewSm& v = sv[q.j];
-        const float4* tex = v.tex;
+        const uint2* tex = v.tex;
         const uint32_t pitch = v.pitch, n_tex = v.n_tex;
         float sval[S];
 #pragma unroll

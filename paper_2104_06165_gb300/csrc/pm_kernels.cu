@@ -18,7 +18,7 @@ constexpr int kBlock = 128;
 // ---------------------------------------------------------------------------
 // bilinear-coefficient texture (layout documented in mvs_internal.h)
 // ---------------------------------------------------------------------------
-__global__ void k_build_texture(const uint8_t* __restrict__ img, int W, int H, float4* __restrict__ tex) {
+__global__ void k_build_texture(const uint8_t* __restrict__ img, int W, int H, uint2* __restrict__ tex) {
     long long n = (long long)(W + 1) * (H + 1);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
@@ -27,12 +27,12 @@ __global__ void k_build_texture(const uint8_t* __restrict__ img, int W, int H, f
         int y0 = min(max(j, 0), H - 1), y1 = min(max(j + 1, 0), H - 1);
         float p00 = img[(long long)y0 * W + x0], p01 = img[(long long)y0 * W + x1];
         float p10 = img[(long long)y1 * W + x0], p11 = img[(long long)y1 * W + x1];
-        float4 c;
-        c.x = 0.25f * (p00 + p01 + p10 + p11);
-        c.y = 0.5f * ((p01 - p00) + (p11 - p10));
-        c.z = 0.5f * ((p10 - p00) + (p11 - p01));
-        c.w = p00 - p01 - p10 + p11;
-        tex[t] = c;
+        __half2 ab = __floats2half2_rn(p00 + p01 + p10 + p11, (p01 - p00) + (p11 - p10));
+        __half2 cd = __floats2half2_rn((p10 - p00) + (p11 - p01), p00 - p01 - p10 + p11);
+        uint2 q;
+        q.x = *reinterpret_cast<const uint32_t*>(&ab);
+        q.y = *reinterpret_cast<const uint32_t*>(&cd);
+        tex[t] = q;
     }
 }
 
@@ -47,15 +47,19 @@ constexpr int kWarps = kBlock / 32;
 #ifndef MVS_TILE_Y
 #define MVS_TILE_Y 4
 #endif
-constexpr int kTileX = MVS_TILE_X, kTileY = MVS_TILE_Y;
-constexpr int kPhaseWarps = kTileX * kTileY;
-constexpr int kPhaseBlock = 32 * kPhaseWarps;
-// blocks per SM that keep a thread at <= 128 registers (<= 168 for 16 slots)
-constexpr int phase_min_blocks(int S) {
-    return (S >= 16 ? 384 : 512) / kPhaseBlock > 0 ? (S >= 16 ? 384 : 512) / kPhaseBlock : 1;
-}
+// Windows of 16 slots per lane need more than 128 registers: their blocks
+// keep to one row of kTileX pixels (3 blocks of 128 threads per SM).
+template <int S>
+struct PhaseTile {
+    static constexpr int TX = MVS_TILE_X;
+    static constexpr int TY = S >= 16 ? 1 : MVS_TILE_Y;
+    static constexpr int WARPS = TX * TY;
+    static constexpr int BLOCK = 32 * WARPS;
+    static constexpr int MIN_BLOCKS = (S >= 16 ? 384 : 512) / BLOCK > 0 ? (S >= 16 ? 384 : 512) / BLOCK : 1;
+};
+
 // Dynamic shared memory of a block: the view table, then one pair list per
-// warp (smem_block_bytes(n_src, kWarps) bytes).
+// warp (smem_block_bytes(n_src, warps) bytes).
 __device__ __forceinline__ PairSm* warp_pairs(unsigned char* smem, int n_src, int warp) {
     return reinterpret_cast<PairSm*>(smem + smem_views_bytes(n_src)) + (size_t)warp * 8 * n_src;
 }
@@ -148,8 +152,10 @@ __device__ __forceinline__ void near_member(int g, int k, int& dx, int& dy) {
 }
 
 template <int G, int S>
-__global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks(S)) k_phase(const __grid_constant__ RefConst rc, int phase) {
-    extern __shared__ __align__(16) unsigned char smem[];   // smem_block_bytes(n_src, kPhaseWarps)
+__global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
+    k_phase(const __grid_constant__ RefConst rc, int phase) {
+    constexpr int kTileX = PhaseTile<S>::TX, kTileY = PhaseTile<S>::TY;
+    extern __shared__ __align__(16) unsigned char smem[];   // smem_block_bytes(n_src, PhaseTile<S>::WARPS)
     ViewSm* views = reinterpret_cast<ViewSm*>(smem);
     load_views(rc, views);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -307,19 +313,19 @@ unsigned pm_grid_for(const void* kernel, long long units, size_t smem, int block
 // capture contains kernel launches only.
 cudaError_t prime_launch_configs(const RefConst& rc) {
     const size_t smem = smem_block_bytes(rc.n_src, kWarps);
-    const size_t psmem = smem_block_bytes(rc.n_src, kPhaseWarps);
 #define CALL(G, S)                                                 \
     do {                                                           \
         pm_grid_for((const void*)k_init<G, S>, 1, smem, kBlock);                   \
         pm_grid_for((const void*)k_cost<G, S>, 1, smem, kBlock);                   \
-        pm_grid_for((const void*)k_phase<G, S>, 1, psmem, kPhaseBlock);            \
+        pm_grid_for((const void*)k_phase<G, S>, 1, smem_block_bytes(rc.n_src, PhaseTile<S>::WARPS),          \
+                    PhaseTile<S>::BLOCK);                                                             \
     } while (0)
     MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
 #undef CALL
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_texture(const uint8_t* img, int W, int H, float4* tex, cudaStream_t s) {
+cudaError_t launch_build_texture(const uint8_t* img, int W, int H, uint2* tex, cudaStream_t s) {
     long long n = (long long)(W + 1) * (H + 1);
     unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
     k_build_texture<<<blocks, 256, 0, s>>>(img, W, H, tex);
@@ -347,10 +353,16 @@ cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, fl
     return cudaGetLastError();
 }
 
+template <int G, int S>
+void phase_launch(const RefConst& rc, int phase, cudaStream_t s) {
+    using T = PhaseTile<S>;
+    const long long ntiles = (long long)(((rc.W + 1) / 2 + T::TX - 1) / T::TX) * ((rc.H + T::TY - 1) / T::TY);
+    const size_t smem = smem_block_bytes(rc.n_src, T::WARPS);
+    k_phase<G, S><<<pm_grid_for((const void*)k_phase<G, S>, ntiles, smem, T::BLOCK), T::BLOCK, smem, s>>>(rc, phase);
+}
+
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s) {
-    const long long ntiles = (long long)(((rc.W + 1) / 2 + kTileX - 1) / kTileX) * ((rc.H + kTileY - 1) / kTileY);
-    const size_t smem = smem_block_bytes(rc.n_src, kPhaseWarps);
-#define CALL(G, S) k_phase<G, S><<<pm_grid_for((const void*)k_phase<G, S>, ntiles, smem, kPhaseBlock), kPhaseBlock, smem, s>>>(rc, phase)
+#define CALL(G, S) phase_launch<G, S>(rc, phase, s)
     MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
 #undef CALL
     count_launch();

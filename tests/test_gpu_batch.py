@@ -60,7 +60,8 @@ def test_batch_device_buffers_and_autotuned_layout(ring, mvs_lib):
         same = (np.abs(a_pl[..., 3] - b_pl[..., 3]) <= 1e-5 * a_pl[..., 3]) & \
                (np.abs(a_pl[..., :3] - b_pl[..., :3]).max(-1) <= 1e-5)
         assert same.mean() > 0.97
-        assert np.abs(a_co - b_co)[same].max() < 1e-4
+        # each layout is within 1e-4 of the FP64 oracle, so within 2e-4 of each other
+        assert np.abs(a_co - b_co)[same].max() < 2e-4
 
 
 def test_batch_rejects_repeated_reference(ring, mvs_lib):
