@@ -90,11 +90,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_params(mvs, seed, lanes=0):
+def make_params(mvs, seed, lanes=0, precision=0):
     w = WORKLOAD
     return mvs.PMParams(win_radius=w["win_radius"], win_samples=w["win_samples"], sigma_s=w["sigma_s"],
                         sigma_c=w["sigma_c"], d_lo=2.0, d_hi=8.0, iters=w["iters"], seed=seed,
-                        lanes_per_pixel=lanes)
+                        lanes_per_pixel=lanes, precision=precision)
 
 
 # ---------------------------------------------------------------------------
@@ -184,7 +184,7 @@ def run_ours(args):
     t_render = time.perf_counter() - t0
     H, W = sc.images[0].shape
     srcs = list(range(1, len(sc.images)))
-    params = make_params(mvs, seed=1 + rank, lanes=args.lanes)
+    params = make_params(mvs, seed=1 + rank, lanes=args.lanes, precision=1 if args.precision == "mixed" else 0)
     phi = mvs.PhiParams()
     stream = torch.cuda.current_stream(dev)
     ctx = mvs.Context(sc.K, sc.R, sc.t, sc.images, stream=stream)
@@ -265,8 +265,8 @@ def run_ours(args):
         "metric": "depth-map Mpix/s (full PatchMatch + PHI)",
         "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload} {W}x{H} uint8 ref + {len(srcs)} sources, 21x21 window dil 2 "
+        "dtype": "f32" if args.precision == "fp32" else "f16/f32 mixed", "data": "synthetic",
+        "config": {"precision": args.precision, "workload": f"{args.workload} {W}x{H} uint8 ref + {len(srcs)} sources, 21x21 window dil 2 "
                                "(11x11 samples), 8 iterations, PHI + 4-label MRF", "parallelism": f"replicas{world}",
                    "lanes_per_pixel": args.lanes,
                    "l2": "inputs larger than L2 (11 x 100 MB textures)", "render_s": round(t_render, 1)},
@@ -359,6 +359,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per pixel group of the ZNCC kernels (0 = default)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
+                    help="fp32 = FP32 ZNCC; mixed = half2 bilinear, FP32 moments, FP64 near-flat denominators")
     ap.add_argument("--workload", default="highres", choices=sorted(WORKLOADS),
                     help="highres = the measured workload; mid = 1536x1024 case for profiler captures")
     args = ap.parse_args()

@@ -75,7 +75,12 @@ typedef struct {
                               2 * iters                                      */
     int32_t init_mode;     /* MVS_INIT_*                                     */
     uint64_t seed;         /* Philox4x64-10 key word 0 (word 1 = ref index)  */
-    int32_t precision;     /* 0 = FP32 (only value built)                    */
+    int32_t precision;     /* 0 = FP32; 1 = mixed: the bilinear interpolation
+                              of two window samples per half2 instruction on
+                              intensities shifted by the reference patch mean,
+                              moments in FP32, near-flat variance denominators
+                              recomputed in FP64 (results differ from FP32 by
+                              the fp16 rounding of the interpolated values)  */
     int32_t lanes_per_pixel; /* work layout of the ZNCC kernels: lanes that
                               share one window (4, 8, 16 or 32; 0 = default;
                               -1 = timed choice, mvs_patchmatch_batch only).
@@ -141,7 +146,7 @@ const char* mvs_last_error(const mvs_ctx* ctx);
  *   mvs_geo_filter / mvs_plane_infer.
  * Errors: MVS_EINVAL (bad index, duplicate or self source, n_src outside
  *   1..32, window outside 2..22 samples, d_lo >= d_hi, NULL buffers),
- *   MVS_EUNSUPPORTED (precision != 0), MVS_ENOMEM, MVS_ECUDA. */
+ *   MVS_EUNSUPPORTED (precision other than 0 or 1), MVS_ENOMEM, MVS_ECUDA. */
 mvs_status mvs_patchmatch(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_t n_src,
                           const mvs_pm_params* params, mvs_depth_map* out);
 

@@ -148,7 +148,7 @@ mvs_status check_pm(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src,
         return fail(c, MVS_EINVAL, "win_radius must be in (0, 64]");
     if (!(p->d_lo > 0.0f) || !(p->d_hi > p->d_lo) || !std::isfinite(p->d_hi))
         return fail(c, MVS_EINVAL, "need 0 < d_lo < d_hi");
-    if (p->precision != 0) return fail(c, MVS_EUNSUPPORTED, "precision %d not built", p->precision);
+    if (p->precision != 0 && p->precision != 1) return fail(c, MVS_EUNSUPPORTED, "precision %d not built", p->precision);
     if (p->iters < 0) return fail(c, MVS_EINVAL, "iters < 0");
     if (p->lanes_per_pixel != 0 && p->lanes_per_pixel != 4 && p->lanes_per_pixel != 8 &&
         p->lanes_per_pixel != 16 && p->lanes_per_pixel != 32)
@@ -179,6 +179,7 @@ void make_refconst(const mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n
     rc.d_hi = p->d_hi;
     rc.seed = p->seed;
     rc.lanes_hint = p->lanes_per_pixel;
+    rc.precision = p->precision;
     rc.plane = R.plane;
     rc.cost = R.cost;
     for (int j = 0; j < n_src; ++j) {

@@ -42,6 +42,7 @@ struct RefConst {
     float* cost;               // state: aggregated cost per pixel
     unsigned long long* eval_counter;  // measurement: evaluated (pixel, hypothesis, view) triples, or null
     int lanes_hint;            // lanes per pixel group (0 = default)
+    int precision;             // 0 = FP32, 1 = mixed (half2 bilinear, FP32 moments)
     PairConst pair[MVS_MAX_SRC];
 };
 

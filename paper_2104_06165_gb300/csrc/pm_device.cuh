@@ -108,6 +108,7 @@ struct PixWin {
     float inv_wsum;       // 1 / sum w
     float srr;            // sum w (I_ref - mean)^2
     float wr_sum;         // sum w (I_ref - mean) (zero up to rounding)
+    float mean;           // weighted mean of the reference samples
     float wsum;
     float cu_lo, cu_hi, cv_lo, cv_hi;  // corners of the included sample rectangle
     float rx0, rx1, rx2;  // K^-1 (x, y, 1)
@@ -164,6 +165,7 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
     srr = gsum<G>(srr);
     pw.wr_sum = gsum<G>(wrs);
     pw.wsum = sw;
+    pw.mean = mu;
     pw.inv_wsum = sw > 0.0f ? 1.0f / sw : 0.0f;
     pw.srr = srr;
     pw.ok = exists && sw > 0.0f && srr >= kTauVar * sw && ku_hi >= 0 && kv_hi >= 0;
@@ -268,7 +270,7 @@ __host__ __device__ constexpr size_t smem_block_bytes(int n_src, int warps) {
 //   3. lane c folds the per-view results of hypothesis c in view order
 //      (Eq. 5, weights 1/max(C, 1e-6)).
 // Must be called by all 32 lanes with the same nc (warp-uniform).
-template <int G, int S, bool VIEWS>
+template <int G, int S, bool VIEWS, bool MIXED = false>
 __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __restrict__ sv, const PixWin<S>& pw,
                                             int px, int py, const Cand& my, int nc, PairSm* pairs,
                                             float* view_cost, unsigned& n_evals) {
@@ -345,13 +347,49 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         const uint2* tex = v.tex;
         const uint32_t pitch = v.pitch, n_tex = v.n_tex;
         float sval[S];
+        if constexpr (!MIXED) {
 #pragma unroll
-        for (int k = 0; k < S; ++k) {
-            float X = fmaf(pw.ou[k], h0x, fmaf(pw.ov[k], h1x, p0x));
-            float Y = fmaf(pw.ou[k], h0y, fmaf(pw.ov[k], h1y, p0y));
-            float Z = fmaf(pw.ou[k], h0z, fmaf(pw.ov[k], h1z, p0z));
-            float iz = rcp_approx(Z);
-            sval[k] = tex_sample(tex, (int)pitch, n_tex, __fmul_rn(X, iz), __fmul_rn(Y, iz));
+            for (int k = 0; k < S; ++k) {
+                float X = fmaf(pw.ou[k], h0x, fmaf(pw.ov[k], h1x, p0x));
+                float Y = fmaf(pw.ou[k], h0y, fmaf(pw.ov[k], h1y, p0y));
+                float Z = fmaf(pw.ou[k], h0z, fmaf(pw.ov[k], h1z, p0z));
+                float iz = rcp_approx(Z);
+                sval[k] = tex_sample(tex, (int)pitch, n_tex, __fmul_rn(X, iz), __fmul_rn(Y, iz));
+            }
+        } else {
+            // mixed precision: positions and fractions in FP32, the bilinear
+            // interpolation of two samples per half2 instruction, on
+            // intensities shifted by the reference patch mean
+            const __half2 mu2 = __float2half2_rn(pw.mean);
+#pragma unroll
+            for (int k = 0; k < S; k += 2) {
+                float Us[2], Vs[2];
+                uint2 q[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int kk = k + h < S ? k + h : k;
+                    float X = fmaf(pw.ou[kk], h0x, fmaf(pw.ov[kk], h1x, p0x));
+                    float Y = fmaf(pw.ou[kk], h0y, fmaf(pw.ov[kk], h1y, p0y));
+                    float Z = fmaf(pw.ou[kk], h0z, fmaf(pw.ov[kk], h1z, p0z));
+                    float iz = rcp_approx(Z);
+                    float xs2 = __fmul_rn(X, iz), ys2 = __fmul_rn(Y, iz);
+                    float tx = __fadd_rn(xs2, kMagic2), ty = __fadd_rn(ys2, kMagic2);
+                    Us[h] = __fsub_rn(xs2, __fsub_rn(tx, kMagic2));
+                    Vs[h] = __fsub_rn(ys2, __fsub_rn(ty, kMagic2));
+                    uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx) +
+                                   (pitch + 1u) * (uint32_t)(1 - kMagic2Bits);
+                    q[h] = __ldg(tex + min(idx, n_tex - 1u));
+                }
+                uint32_t ab = __byte_perm(q[0].x, q[1].x, 0x5410), bb = __byte_perm(q[0].x, q[1].x, 0x7632);
+                uint32_t cb = __byte_perm(q[0].y, q[1].y, 0x5410), db = __byte_perm(q[0].y, q[1].y, 0x7632);
+                __half2 A = __hsub2(*reinterpret_cast<__half2*>(&ab), mu2);
+                __half2 B = *reinterpret_cast<__half2*>(&bb), Cc = *reinterpret_cast<__half2*>(&cb);
+                __half2 D = *reinterpret_cast<__half2*>(&db);
+                __half2 U2 = __floats2half2_rn(Us[0], Us[1]), V2 = __floats2half2_rn(Vs[0], Vs[1]);
+                float2 s2 = __half22float2(__hfma2(V2, __hfma2(U2, D, Cc), __hfma2(U2, B, A)));
+                sval[k] = s2.x;
+                if (k + 1 < S) sval[k + 1] = s2.y;
+            }
         }
         // weighted moments in one pass, shifted by one sample of this source
         // patch (its first sample) so that the variance keeps full precision:
@@ -374,8 +412,25 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             se += __shfl_xor_sync(0xffffffffu, se, o);
         }
         const float mean_d = sa * pw.inv_wsum;
-        const float sdd = fmaf(-mean_d, sa, sb);
+        float sdd = fmaf(-mean_d, sa, sb);
         const float srd = fmaf(-mean_d, pw.wr_sum, se);
+        if constexpr (MIXED) {
+            // a source patch near the flat limit (where the exclusion decision
+            // is taken): recompute the variance denominator in FP64
+            const bool near_flat = sdd < 2.0f * kTauVar * pw.wsum && sdd > 0.5f * kTauVar * pw.wsum;
+            if (__any_sync(0xffffffffu, near_flat)) {
+                const double mu_d = (double)c0 + (double)sa / (double)pw.wsum;
+                double v = 0.0;
+#pragma unroll
+                for (int k = 0; k < S; ++k) {
+                    double dd = (double)sval[k] - mu_d;
+                    v = fma((double)pw.w[k] * dd, dd, v);
+                }
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (near_flat) sdd = (float)v;
+            }
+        }
         if (has && lg == 0) {
             float cj = kCmax;
             if (sdd >= kTauVar * pw.wsum) {

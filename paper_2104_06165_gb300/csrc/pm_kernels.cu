@@ -68,7 +68,7 @@ __device__ __forceinline__ PairSm* warp_pairs(unsigned char* smem, int n_src, in
 // Sec. III-B: random initialisation, then the cost of the initial plane.
 // One warp per pixel, grid-stride over the pixels.
 // ---------------------------------------------------------------------------
-template <int G, int S>
+template <int G, int S, bool MIXED>
 __global__ void __launch_bounds__(kBlock) k_init(const __grid_constant__ RefConst rc, float* view_cost) {
     extern __shared__ __align__(16) unsigned char smem[];
     ViewSm* views = reinterpret_cast<ViewSm*>(smem);
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const __grid_constant__ RefCons
         float c = kCmax;
         if (pw.ok) {
             Cand my = make_cand(rc, pw, n0, n1, n2, d, lane == 0);
-            c = eval_batch<G, S, true>(rc, views, pw, px, py, my, 1, warp_pairs(smem, rc.n_src, warp), vc, nev);
+            c = eval_batch<G, S, true, MIXED>(rc, views, pw, px, py, my, 1, warp_pairs(smem, rc.n_src, warp), vc, nev);
         } else if (vc && lane < rc.n_src) {
             vc[lane] = kCmax;
         }
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const __grid_constant__ RefCons
 }
 
 // cost of a given plane map
-template <int G, int S>
+template <int G, int S, bool MIXED>
 __global__ void __launch_bounds__(kBlock) k_cost(const __grid_constant__ RefConst rc, const float4* __restrict__ plane,
                                                   float* __restrict__ cost, float* view_cost) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kBlock) k_cost(const __grid_constant__ RefCons
         float c = kCmax;
         if (pw.ok) {
             Cand my = make_cand(rc, pw, pl.x, pl.y, pl.z, pl.w, lane == 0);
-            c = eval_batch<G, S, true>(rc, views, pw, px, py, my, 1, warp_pairs(smem, rc.n_src, warp), vc, nev);
+            c = eval_batch<G, S, true, MIXED>(rc, views, pw, px, py, my, 1, warp_pairs(smem, rc.n_src, warp), vc, nev);
         } else if (vc && lane < rc.n_src) {
             vc[lane] = kCmax;
         }
@@ -151,7 +151,7 @@ __device__ __forceinline__ void near_member(int g, int k, int& dx, int& dy) {
     }
 }
 
-template <int G, int S>
+template <int G, int S, bool MIXED>
 __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
     k_phase(const __grid_constant__ RefConst rc, int phase) {
     constexpr int kTileX = PhaseTile<S>::TX, kTileY = PhaseTile<S>::TY;
@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             }
             const int nc = stage == 0 ? 8 : 3;
             Cand my = make_cand(rc, pw, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
-            float c = eval_batch<G, S, false>(rc, views, pw, px, py, my, nc, warp_pairs(smem, rc.n_src, warp), nullptr, nev);
+            float c = eval_batch<G, S, false, MIXED>(rc, views, pw, px, py, my, nc, warp_pairs(smem, rc.n_src, warp),
+                                                      nullptr, nev);
             float bc;
             int bi = warp_argmin(my.ok ? c : 3.0e38f, nc, bc);
             if (bc < cur_c) {
@@ -294,6 +295,19 @@ unsigned pm_grid_for(const void* kernel, long long units, size_t smem, int block
 
 // Lanes per pixel group (G) and slots per lane (S) for an n x n window:
 // G * S >= n * n.  lanes_hint 0 picks the default; 4, 8, 16 or 32 picks G.
+// The mixed-precision kernels exist for the default layout of each window
+// size only.
+#define MVS_DISPATCH_DEFAULT(n, CALL)                                                     \
+    do {                                                                                  \
+        int _s = (n) * (n);                                                               \
+        if (_s <= 16) { CALL(4, 4); }                                                     \
+        else if (_s <= 36) { CALL(4, 9); }                                                \
+        else if (_s <= 64) { CALL(8, 8); }                                                \
+        else if (_s <= 128) { CALL(16, 8); }                                              \
+        else if (_s <= 256) { CALL(16, 16); }                                             \
+        else { CALL(32, 16); }                                                            \
+    } while (0)
+
 #define MVS_DISPATCH(n, hint, CALL)                                                       \
     do {                                                                                  \
         int _s = (n) * (n), _h = (hint);                                                  \
@@ -313,14 +327,20 @@ unsigned pm_grid_for(const void* kernel, long long units, size_t smem, int block
 // capture contains kernel launches only.
 cudaError_t prime_launch_configs(const RefConst& rc) {
     const size_t smem = smem_block_bytes(rc.n_src, kWarps);
-#define CALL(G, S)                                                 \
-    do {                                                           \
-        pm_grid_for((const void*)k_init<G, S>, 1, smem, kBlock);                   \
-        pm_grid_for((const void*)k_cost<G, S>, 1, smem, kBlock);                   \
-        pm_grid_for((const void*)k_phase<G, S>, 1, smem_block_bytes(rc.n_src, PhaseTile<S>::WARPS),          \
+#define CALL(G, S)                                                                                    \
+    do {                                                                                              \
+        pm_grid_for((const void*)k_init<G, S, MX>, 1, smem, kBlock);                                  \
+        pm_grid_for((const void*)k_cost<G, S, MX>, 1, smem, kBlock);                                  \
+        pm_grid_for((const void*)k_phase<G, S, MX>, 1, smem_block_bytes(rc.n_src, PhaseTile<S>::WARPS), \
                     PhaseTile<S>::BLOCK);                                                             \
     } while (0)
-    MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
+    if (rc.precision) {
+        constexpr bool MX = true;
+        MVS_DISPATCH_DEFAULT(rc.n, CALL);
+    } else {
+        constexpr bool MX = false;
+        MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
+    }
 #undef CALL
     return cudaGetLastError();
 }
@@ -336,8 +356,16 @@ cudaError_t launch_build_texture(const uint8_t* img, int W, int H, uint2* tex, c
 cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s) {
     long long npix = (long long)rc.W * rc.H;
     const size_t smem = smem_block_bytes(rc.n_src, kWarps);
-#define CALL(G, S) k_init<G, S><<<pm_grid_for((const void*)k_init<G, S>, (npix + kWarps - 1) / kWarps, smem, kBlock), kBlock, smem, s>>>(rc, view_cost)
-    MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
+    const unsigned units = (unsigned)((npix + kWarps - 1) / kWarps);
+#define CALL(G, S) \
+    k_init<G, S, MX><<<pm_grid_for((const void*)k_init<G, S, MX>, units, smem, kBlock), kBlock, smem, s>>>(rc, view_cost)
+    if (rc.precision) {
+        constexpr bool MX = true;
+        MVS_DISPATCH_DEFAULT(rc.n, CALL);
+    } else {
+        constexpr bool MX = false;
+        MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
+    }
 #undef CALL
     count_launch();
     return cudaGetLastError();
@@ -346,25 +374,41 @@ cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s) {
 cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, float* view_cost, cudaStream_t s) {
     long long npix = (long long)rc.W * rc.H;
     const size_t smem = smem_block_bytes(rc.n_src, kWarps);
-#define CALL(G, S) k_cost<G, S><<<pm_grid_for((const void*)k_cost<G, S>, (npix + kWarps - 1) / kWarps, smem, kBlock), kBlock, smem, s>>>(rc, plane, cost, view_cost)
-    MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
+    const unsigned units = (unsigned)((npix + kWarps - 1) / kWarps);
+#define CALL(G, S)                                                                                         \
+    k_cost<G, S, MX><<<pm_grid_for((const void*)k_cost<G, S, MX>, units, smem, kBlock), kBlock, smem, s>>>( \
+        rc, plane, cost, view_cost)
+    if (rc.precision) {
+        constexpr bool MX = true;
+        MVS_DISPATCH_DEFAULT(rc.n, CALL);
+    } else {
+        constexpr bool MX = false;
+        MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
+    }
 #undef CALL
     count_launch();
     return cudaGetLastError();
 }
 
-template <int G, int S>
+template <int G, int S, bool MX>
 void phase_launch(const RefConst& rc, int phase, cudaStream_t s) {
     using T = PhaseTile<S>;
     const long long ntiles = (long long)(((rc.W + 1) / 2 + T::TX - 1) / T::TX) * ((rc.H + T::TY - 1) / T::TY);
     const size_t smem = smem_block_bytes(rc.n_src, T::WARPS);
-    k_phase<G, S><<<pm_grid_for((const void*)k_phase<G, S>, ntiles, smem, T::BLOCK), T::BLOCK, smem, s>>>(rc, phase);
+    k_phase<G, S, MX><<<pm_grid_for((const void*)k_phase<G, S, MX>, ntiles, smem, T::BLOCK), T::BLOCK, smem, s>>>(
+        rc, phase);
 }
 
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s) {
-#define CALL(G, S) phase_launch<G, S>(rc, phase, s)
-    MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
+    if (rc.precision) {
+#define CALL(G, S) phase_launch<G, S, true>(rc, phase, s)
+        MVS_DISPATCH_DEFAULT(rc.n, CALL);
 #undef CALL
+    } else {
+#define CALL(G, S) phase_launch<G, S, false>(rc, phase, s)
+        MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
+#undef CALL
+    }
     count_launch();
     return cudaGetLastError();
 }
