@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
 class _PM(C.Structure):
     _fields_ = [("win_radius", C.c_double), ("win_samples", C.c_int), ("sigma_s", C.c_double),
                 ("sigma_c", C.c_double), ("d_lo", C.c_double), ("d_hi", C.c_double),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("n_prop", C.c_int), ("props", C.POINTER(C.c_double))]
 
 
 class _Filter(C.Structure):
@@ -122,9 +122,13 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def _pm(p) -> _PM:
+def _pm(p, props=None) -> _PM:
+    """props: None or an FP64 array (H, W, K, 4) kept alive by the caller."""
+    if props is None:
+        return _PM(float(p.win_radius), int(p.win_samples), float(p.sigma_s), float(p.sigma_c),
+                   float(p.d_lo), float(p.d_hi), int(p.seed) & 0xFFFFFFFFFFFFFFFF, 0, None)
     return _PM(float(p.win_radius), int(p.win_samples), float(p.sigma_s), float(p.sigma_c),
-               float(p.d_lo), float(p.d_hi), int(p.seed) & 0xFFFFFFFFFFFFFFFF)
+               float(p.d_lo), float(p.d_hi), int(p.seed) & 0xFFFFFFFFFFFFFFFF, int(props.shape[2]), _d(props))
 
 
 class Scene:
@@ -235,12 +239,14 @@ def group_members(g):
     return out[: 2 * c].reshape(c, 2)
 
 
-def phase(scene, ref, srcs, p, ph, plane, cost):
-    """One checkerboard half-iteration (propagation + refinement) starting
-    from the given state.  Returns the new (plane, cost) and a dict of
-    decision diagnostics."""
+def phase(scene, ref, srcs, p, ph, plane, cost, proposals=None):
+    """One checkerboard half-iteration (propagation, learned proposals when
+    given as an (H, W, K, 4) plane array, refinement) starting from the given
+    state.  Returns the new (plane, cost) and a dict of decision diagnostics
+    (win_prop is 8 + k when proposal k won)."""
     H, W = scene.shape(ref)
     s = _srcs(srcs)
+    props = None if proposals is None else np.ascontiguousarray(proposals, dtype=np.float64)
     pl = _f64(plane).reshape(H, W, 4).copy()
     co = _f64(cost).reshape(H, W).copy()
     wp = np.zeros((H, W), np.int32)
@@ -248,7 +254,8 @@ def phase(scene, ref, srcs, p, ph, plane, cost):
     gp = np.zeros((H, W), np.float64)
     gr = np.zeros((H, W), np.float64)
     mg = np.full((H, W), np.inf, np.float64)
-    lib().or_phase(scene.h, ref, _i(s), len(s), C.byref(_pm(p)), int(ph), _d(pl), _d(co), _i(wp), _d(gp),
+    pm = _pm(p, props)
+    lib().or_phase(scene.h, ref, _i(s), len(s), C.byref(pm), int(ph), _d(pl), _d(co), _i(wp), _d(gp),
                    _i(wr), _d(gr), _d(mg))
     return pl, co, {"win_prop": wp, "gap_prop": gp, "win_ref": wr, "gap_ref": gr, "margin": mg}
 

@@ -66,6 +66,8 @@ typedef struct {
     double sigma_c;      /* bilateral colour sigma, [0,1] scale (<= 0: none)*/
     double d_lo, d_hi;   /* depth range                                     */
     uint64_t seed;
+    int n_prop;          /* learned proposals per pixel (0: none)           */
+    const double* props; /* H*W*n_prop*4 planes (nx, ny, nz, d) or NULL     */
 } or_pm;
 
 static void m3_mul(const double* A, const double* B, double* C) {
@@ -540,13 +542,39 @@ void or_phase(const or_scene* s, int ref, const int* srcs, int ns, const or_pm* 
                 if (v < lo1) { lo2 = lo1; lo1 = v; } else if (v < lo2) lo2 = v;
                 if (v < bestc) { bestc = v; bw = g; }
             }
-            if (win_prop) win_prop[i] = bw;
-            if (gap_prop) gap_prop[i] = lo2 - lo1;
+            double gap = lo2 - lo1;
             if (bw >= 0) {
                 memcpy(cur_n, cand_n[bw], sizeof cur_n);
                 cur_d = cand_d[bw];
                 cur_c = cand_c[bw];
             }
+
+            /* learned proposals (no counterpart in the paper): the pixel's
+             * n_prop given planes compete after the propagated ones, in
+             * slot order, and replace the state only if strictly cheaper; a
+             * slot whose depth lies outside [d_lo, d_hi] is skipped */
+            if (p->n_prop > 0 && p->props) {
+                int pw = -1;
+                double pbest = cur_c, pn[3] = {0, 0, 0}, pd = 0;
+                lo1 = cur_c; lo2 = 1e300;
+                for (int k = 0; k < p->n_prop; ++k) {
+                    const double* pr = p->props + 4 * ((long)i * p->n_prop + k);
+                    if (!(pr[3] >= p->d_lo && pr[3] <= p->d_hi)) continue;
+                    double v = pixel_cost(s, ref, srcs, ns, p, x, y, pr, pr[3], win, NULL, &mg);
+                    if (mg < mg_all) mg_all = mg;
+                    if (v < lo1) { lo2 = lo1; lo1 = v; } else if (v < lo2) lo2 = v;
+                    if (v < pbest) { pbest = v; pw = k; memcpy(pn, pr, sizeof pn); pd = pr[3]; }
+                }
+                if (lo2 - lo1 < gap) gap = lo2 - lo1;
+                if (pw >= 0) {
+                    bw = 8 + pw;
+                    memcpy(cur_n, pn, sizeof cur_n);
+                    cur_d = pd;
+                    cur_c = pbest;
+                }
+            }
+            if (win_prop) win_prop[i] = bw;
+            if (gap_prop) gap_prop[i] = gap;
 
             /* refinement (Sec. III-C): delta_d in [-d_max/4, d_max/4]
              * (reading: d_max = upper end of the depth range), delta_theta

@@ -257,6 +257,50 @@ def test_patchmatch_equals_init_plus_phases(oracle_lib, tiny):
     assert np.array_equal(a_pl, pl) and np.array_equal(a_co, co)
 
 
+def test_proposals_outside_the_depth_range_change_nothing(oracle_lib, tiny):
+    sc, osc = tiny
+    p = P(seed=4)
+    pl, co = oracle_lib.init(osc, 0, [1, 2], p)
+    props = np.zeros((30, 40, 3, 4))
+    props[..., 2] = -1.0
+    props[..., 0, 3] = 0.0          # unused slot
+    props[..., 1, 3] = 1.9          # below d_lo
+    props[..., 2, 3] = 8.5          # above d_hi
+    for ph in range(2):
+        a_pl, a_co, a_d = oracle_lib.phase(osc, 0, [1, 2], p, ph, pl, co)
+        b_pl, b_co, b_d = oracle_lib.phase(osc, 0, [1, 2], p, ph, pl, co, proposals=props)
+        assert np.array_equal(a_pl, b_pl) and np.array_equal(a_co, b_co)
+        assert np.array_equal(a_d["win_prop"], b_d["win_prop"])
+        pl, co = a_pl, a_co
+
+
+def test_ground_truth_proposals_are_taken(oracle_lib):
+    """On a single textured plane the true plane offered as a proposal wins
+    wherever it is cheaper than what propagation found; the phase's cost is
+    then at most the true plane's cost (refinement only lowers it)."""
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_plane_scene(W=32, H=24, n_src=2, seed=12, depth=4.0, normal=(0.2, -0.1, -1.0), f=60.0,
+                                 baseline=0.25)
+    osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
+    p = P(seed=6, win_radius=3.0, win_samples=4)
+    pl, co = oracle_lib.init(osc, 0, [1, 2], p)
+    gt = np.concatenate([sc.gt_normal, sc.gt_depth[..., None]], -1)
+    gt_cost = oracle_lib.plane_cost(osc, 0, [1, 2], p, gt)
+    rng = np.random.default_rng(0)
+    props = np.zeros((24, 32, 2, 4))
+    props[..., 0, :] = gt
+    props[..., 1, :3] = [0.0, 0.0, -1.0]
+    props[..., 1, 3] = rng.uniform(2.0, 8.0, (24, 32))
+    yy, xx = np.mgrid[0:24, 0:32]
+    mine = ((xx + yy) & 1) == 0
+    pl2, co2, d = oracle_lib.phase(osc, 0, [1, 2], p, 0, pl, co, proposals=props)
+    assert (co2[mine] <= gt_cost[mine] + 1e-12).all()
+    took_gt = d["win_prop"] == 8
+    assert took_gt[mine].mean() > 0.5
+    kept = took_gt & mine & (d["win_ref"] < 0)        # no refinement candidate replaced it
+    assert kept.any() and np.allclose(pl2[kept], gt[kept], atol=1e-12)
+
+
 def test_patchmatch_reaches_exhaustive_search_minimum(oracle_lib):
     """Tiny scene of one slanted plane: after 6 iterations PatchMatch's cost
     is within 1e-3 of (or below) the best of an exhaustive search over 48
