@@ -86,7 +86,19 @@ typedef struct {
                               -1 = timed choice, mvs_patchmatch_batch only).
                               Results are identical for every choice up to
                               float rounding of the group reductions.        */
-    int32_t reserved[6];
+    int32_t n_prop;        /* learned proposals per pixel, 0..8 (0: none)    */
+    int32_t reserved0;
+    const float* proposals;/* DEVICE, H*W*n_prop*4 (n.x, n.y, n.z, depth)
+                              planes per pixel, e.g. from mvs_propose; in
+                              every half-iteration each pixel of the phase's
+                              colour scores its n_prop proposals right after
+                              the propagated planes and takes the cheapest
+                              if it is strictly cheaper than its state (no
+                              counterpart in the paper: extra candidates of
+                              the propagation step, judged by Eq. 5).  Zero
+                              depth marks an unused slot.  NULL with
+                              n_prop = 0.                                    */
+    int32_t reserved[2];
 } mvs_pm_params;
 
 /* Depth-map buffers supplied by the caller. */
@@ -266,6 +278,85 @@ mvs_status mvs_phi_hypotheses_static(mvs_ctx* ctx, int32_t W, int32_t H, const f
 mvs_status mvs_profile(mvs_ctx* ctx, int32_t enable);
 mvs_status mvs_profile_read(mvs_ctx* ctx, double* phase_ms, int64_t* phase_launches, int64_t* kernel_launches,
                             int64_t* phase_evals);
+
+/* ------------------------------------------------------------------------
+ * Learned plane proposals (no counterpart in the paper).
+ *
+ * A small U-Net maps a PatchMatch state of a reference view (image, plane
+ * map, cost map after one or two iterations) to K = 4 planes per pixel that
+ * mvs_patchmatch then scores as extra propagation candidates
+ * (mvs_pm_params.n_prop / proposals); the Eq. 5 cost still decides, so a
+ * bad proposal is never taken over a better plane.
+ *
+ * Network: 16 input channels (image / 255, inverse depth normalised to
+ * [1/d_hi, 1/d_lo] -> [0, 1], normal (3), cost / 2, ten zero channels);
+ * encoder 3x3 conv + ReLU at 32, 48, 64, 96, 128 channels with 2x2 average
+ * pooling between levels; decoder nearest 2x up-sampling, concatenation
+ * with the encoder output of the level, 3x3 conv + ReLU at 96, 64, 48, 32
+ * channels; 1x1 head to 16 outputs = 4 x (a, m.x, m.y, m.z).  Proposal k
+ * has inverse depth 1/d_hi + (1/d_lo - 1/d_hi) sigmoid(a_k) and normal
+ * m_k / |m_k| turned to face the camera.  Weights and activations are
+ * bfloat16 with fp32 accumulation; master weights and Adam moments fp32.
+ * Parameters are ordered layer by layer (e0..e4, d3..d0, head), each as
+ * weights [c_out][tap][c_in] (tap = 3 dy + dx of the 3x3 stencil) then
+ * bias [c_out].
+ *
+ * Training loss over the pixels with mask != 0:
+ *   L = 1/(W H) sum_x min_k ( |rho_k - 1/d_t| / (1/d_lo - 1/d_hi)
+ *                             + lambda (1 - |n_k . n_t|) ),  lambda = 0.1
+ * (first k on ties), targets (n_t, d_t) a plane map.
+ *
+ * All image, map and output pointers below are DEVICE pointers on the
+ * network's device; W and H are multiples of 16 within the capacity given
+ * to mvs_cnn_create.  Work is ordered on the stream given there.
+ * ------------------------------------------------------------------------ */
+typedef struct mvs_cnn mvs_cnn;   /* opaque, owned by the library */
+
+/* Create a network for images up to max_width x max_height (multiples of 16,
+ * at most 8192) and depth range [d_lo, d_hi], with He-initialised weights
+ * drawn from `seed`; buffers for activations and gradients at the maximum
+ * size are allocated here (about 2.3 kB per pixel).
+ * Errors: MVS_EINVAL, MVS_ENOMEM, MVS_ECUDA. */
+mvs_status mvs_cnn_create(int32_t max_width, int32_t max_height, float d_lo, float d_hi, uint64_t seed,
+                          void* cuda_stream, mvs_cnn** out);
+void mvs_cnn_destroy(mvs_cnn* net);              /* NULL-safe */
+const char* mvs_cnn_last_error(const mvs_cnn* net);
+
+/* Number of parameters (weights and biases of all layers). */
+mvs_status mvs_cnn_n_params(const mvs_cnn* net, int64_t* count);
+/* Copy all parameters, or the gradients of the last mvs_cnn_backward, to a
+ * HOST array of mvs_cnn_n_params floats, or set the parameters from one
+ * (the bfloat16 copies are refreshed).  These synchronise the stream. */
+mvs_status mvs_cnn_get_params(mvs_cnn* net, float* host_out);
+mvs_status mvs_cnn_set_params(mvs_cnn* net, const float* host_in);
+mvs_status mvs_cnn_get_grads(mvs_cnn* net, float* host_out);
+
+/* Forward pass: img[H*W] uint8, plane[H*W*4], cost[H*W] -> out[H*W*16] raw
+ * head outputs (fp32). */
+mvs_status mvs_cnn_forward(mvs_cnn* net, const uint8_t* img, const float* plane, const float* cost, int32_t W,
+                           int32_t H, float* out);
+
+/* Forward pass, loss against target[H*W*4] (planes) on mask[H*W] != 0 and
+ * backward pass; the gradients replace those of the previous call.  W is at
+ * most 768 here.  loss_out: HOST float or NULL (non-NULL synchronises). */
+mvs_status mvs_cnn_backward(mvs_cnn* net, const uint8_t* img, const float* plane, const float* cost, int32_t W,
+                            int32_t H, const float* target, const uint8_t* mask, float* loss_out);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with
+ * learning rate lr on the gradients of the last mvs_cnn_backward. */
+mvs_status mvs_cnn_adam_step(mvs_cnn* net, float lr);
+
+/* Forward pass and decoding: proposals[H*W*4*4] = 4 planes per pixel
+ * (n.x, n.y, n.z, depth) for the reference camera with inverse intrinsics
+ * Kinv (host, row-major). */
+mvs_status mvs_cnn_propose(mvs_cnn* net, const uint8_t* img, const float* plane, const float* cost, int32_t W,
+                           int32_t H, const double Kinv[9], float* proposals);
+
+/* mvs_cnn_propose on the image and the current depth map of context view
+ * `ref` (the state left by the last mvs_patchmatch of that view); runs on
+ * the context stream, which must be the network's device.
+ * Errors: MVS_ESTATE if the view has no map, MVS_EINVAL, MVS_ECUDA. */
+mvs_status mvs_propose(mvs_ctx* ctx, int32_t ref, mvs_cnn* net, float* proposals);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,806 @@
+// Learned plane proposals: a small U-Net that maps the reference image and an
+// early PatchMatch state to K = 4 plane hypotheses per pixel, trained on the
+// depth maps the plain pipeline produces.  (No counterpart in the paper; the
+// proposals only add candidates to the propagation step, the ZNCC cost of
+// Eq. 4/5 still decides.)
+//
+// Tensors are channels-last bfloat16 (pixel-major, channels contiguous, a
+// multiple of 16 channels); convolutions are implicit GEMMs on the tensor
+// cores (mma.sync m16n8k16, bf16 inputs, fp32 accumulation): M = pixels,
+// N = output channels, K = taps x input channels.  The data gradient is the
+// same kernel run on the output gradient with flipped, transposed weights;
+// the weight gradient is a shared-memory-tiled reduction over pixels.
+// Master weights, gradients and Adam moments are fp32.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mvs.h"
+#include "mvs_internal.h"
+#include "pm_device.cuh"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+struct Mat3 {
+    float m[9];
+};
+
+// ---------------------------------------------------------------------------
+// convolution (3x3 or 1x1, stride 1, zero padding) as an implicit GEMM
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// One warp computes 16 consecutive pixels (row-major order, rows may wrap)
+// x NC output channels [n_off, n_off + NC) of a convolution with `taps`
+// taps (9 = 3x3, 1 = 1x1).  in: H*W*Cin; w: [n_total][taps][Cin];
+// out: H*W*out_ch, this call writing channels [out_off, out_off + NC).
+// Cin is a multiple of 16; pixels past W*H are neither read nor written.
+template <int NC, bool RELU, bool OUT_F32>
+__global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ in, int Cin, int W, int H,
+                                              const bf16* __restrict__ w, const float* __restrict__ bias, int taps,
+                                              int n_off, void* __restrict__ out, int out_ch, int out_off) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long npix = (long long)W * H;
+    const long long p0 = ((long long)blockIdx.x * 4 + warp) * 16;
+    if (p0 >= npix) return;
+    const int g = lane >> 2, t = lane & 3;
+    // the two pixels whose rows of A this lane supplies (fragment rows g, g + 8)
+    const long long pa_ = p0 + g, pb_ = p0 + g + 8;
+    const bool va = pa_ < npix, vb = pb_ < npix;
+    const int ya0 = (int)(pa_ / W), xa0 = (int)(pa_ % W);
+    const int yb0 = (int)(pb_ / W), xb0 = (int)(pb_ % W);
+    float acc[NC / 8][4];
+#pragma unroll
+    for (int i = 0; i < NC / 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
+    for (int tap = 0; tap < taps; ++tap) {
+        const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
+        const int ya = ya0 + dy, xa = xa0 + dx, yb = yb0 + dy, xb = xb0 + dx;
+        const bool oka = va && ya >= 0 && ya < H && xa >= 0 && xa < W;
+        const bool okb = vb && yb >= 0 && yb < H && xb >= 0 && xb < W;
+        const bf16* pa = in + (oka ? ((long long)ya * W + xa) * Cin : 0) + 2 * t;
+        const bf16* pb = in + (okb ? ((long long)yb * W + xb) * Cin : 0) + 2 * t;
+        for (int c0 = 0; c0 < Cin; c0 += 16) {
+            uint32_t a0 = oka ? ld32(pa + c0) : 0u, a1 = okb ? ld32(pb + c0) : 0u;
+            uint32_t a2 = oka ? ld32(pa + c0 + 8) : 0u, a3 = okb ? ld32(pb + c0 + 8) : 0u;
+#pragma unroll
+            for (int nt = 0; nt < NC / 8; ++nt) {
+                const bf16* wp = w + ((long long)(n_off + nt * 8 + g) * taps + tap) * Cin + c0 + 2 * t;
+                mma_bf16(acc[nt], a0, a1, a2, a3, ld32(wp), ld32(wp + 8));
+            }
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < NC / 8; ++nt) {
+        const int n = nt * 8 + 2 * t;
+        float b0 = bias ? bias[n_off + n] : 0.0f, b1 = bias ? bias[n_off + n + 1] : 0.0f;
+        float v0 = acc[nt][0] + b0, v1 = acc[nt][1] + b1, v2 = acc[nt][2] + b0, v3 = acc[nt][3] + b1;
+        if (RELU) {
+            v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); v2 = fmaxf(v2, 0.0f); v3 = fmaxf(v3, 0.0f);
+        }
+        if (OUT_F32) {
+            float* o = (float*)out;
+            if (va) { o[pa_ * out_ch + out_off + n] = v0; o[pa_ * out_ch + out_off + n + 1] = v1; }
+            if (vb) { o[pb_ * out_ch + out_off + n] = v2; o[pb_ * out_ch + out_off + n + 1] = v3; }
+        } else {
+            bf16* o = (bf16*)out;
+            if (va) *reinterpret_cast<__nv_bfloat162*>(o + pa_ * out_ch + out_off + n) = __floats2bfloat162_rn(v0, v1);
+            if (vb) *reinterpret_cast<__nv_bfloat162*>(o + pb_ * out_ch + out_off + n) = __floats2bfloat162_rn(v2, v3);
+        }
+    }
+}
+
+// Weight gradient: dw[co][tap][ci] += sum_p dy[p][co] * x[p + tap][ci],
+// db[co] += sum_p dy[p][co].  A block of 16 x 16 threads owns 16 output x 16
+// input channels and `rows` image rows; rows are staged in shared memory.
+__global__ void __launch_bounds__(256) k_conv_wgrad(const bf16* __restrict__ x, int Cin, const bf16* __restrict__ dy,
+                                                    int Cout, int W, int H, int taps, int rows, float* __restrict__ dw,
+                                                    float* __restrict__ db) {
+    extern __shared__ float sm[];
+    float* dys = sm;                    // [W][16]
+    float* xs = sm + W * 16;            // [3][W + 2][16]
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int co = blockIdx.x * 16 + ty, ci = blockIdx.y * 16 + tx;
+    float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    float bacc = 0.0f;
+    const int y0 = blockIdx.z * rows;
+    for (int y = y0; y < min(H, y0 + rows); ++y) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < W * 16; i += 256) {
+            int px = i >> 4, c = i & 15;
+            dys[i] = __bfloat162float(dy[((long long)y * W + px) * Cout + blockIdx.x * 16 + c]);
+        }
+        const int nr = taps == 9 ? 3 : 1;
+        for (int i = threadIdx.x; i < nr * (W + 2) * 16; i += 256) {
+            int c = i & 15, rest = i >> 4, px = rest % (W + 2) - 1, r = rest / (W + 2);
+            int yy = taps == 9 ? y + r - 1 : y;
+            float v = 0.0f;
+            if (yy >= 0 && yy < H && px >= 0 && px < W) v = __bfloat162float(x[((long long)yy * W + px) * Cin + blockIdx.y * 16 + c]);
+            xs[i] = v;
+        }
+        __syncthreads();
+        for (int px = 0; px < W; ++px) {
+            float d = dys[px * 16 + ty];
+            bacc += d;
+            if (taps == 9) {
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    int r = tap / 3, dx = tap % 3;   // x index px + dx - 1, stored at +1
+                    acc[tap] = fmaf(d, xs[(r * (W + 2) + px + dx) * 16 + tx], acc[tap]);
+                }
+            } else {
+                acc[0] = fmaf(d, xs[(px + 1) * 16 + tx], acc[0]);
+            }
+        }
+    }
+    for (int tap = 0; tap < taps; ++tap) atomicAdd(&dw[((long long)co * taps + tap) * Cin + ci], acc[tap]);
+    if (db && blockIdx.y == 0 && tx == 0) atomicAdd(&db[co], bacc);
+}
+
+// ---------------------------------------------------------------------------
+// elementwise pieces
+// ---------------------------------------------------------------------------
+__global__ void k_pool_fwd(const bf16* __restrict__ in, int W, int H, int C, bf16* __restrict__ out) {
+    long long n = (long long)(W / 2) * (H / 2) * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int c = (int)(i % C);
+        long long p = i / C;
+        int x = (int)(p % (W / 2)), y = (int)(p / (W / 2));
+        float s = 0.0f;
+        for (int j = 0; j < 2; ++j)
+            for (int k = 0; k < 2; ++k) s += __bfloat162float(in[((long long)(2 * y + j) * W + 2 * x + k) * C + c]);
+        out[i] = __float2bfloat16(0.25f * s);
+    }
+}
+
+// din (W x H, C) += 1/4 of dout at the parent pixel (accumulate when add != 0)
+__global__ void k_pool_bwd(const bf16* __restrict__ dout, int W, int H, int C, bf16* __restrict__ din, int add) {
+    long long n = (long long)W * H * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int c = (int)(i % C);
+        long long p = i / C;
+        int x = (int)(p % W), y = (int)(p / W);
+        float v = 0.25f * __bfloat162float(dout[((long long)(y / 2) * (W / 2) + x / 2) * C + c]);
+        if (add) v += __bfloat162float(din[i]);
+        din[i] = __float2bfloat16(v);
+    }
+}
+
+// nearest up-sampling of in (W/2 x H/2, C) into channels [0, C) of out
+// (W x H, out_ch)
+__global__ void k_up_fwd(const bf16* __restrict__ in, int W, int H, int C, bf16* __restrict__ out, int out_ch) {
+    long long n = (long long)W * H * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int c = (int)(i % C);
+        long long p = i / C;
+        int x = (int)(p % W), y = (int)(p / W);
+        out[p * out_ch + c] = in[((long long)(y / 2) * (W / 2) + x / 2) * C + c];
+    }
+}
+
+// gradient of the up-sampling: din (W/2 x H/2, C) = sum of the four children
+// of channels [0, C) of dout (W x H, dout_ch)
+__global__ void k_up_bwd(const bf16* __restrict__ dout, int W, int H, int C, int dout_ch, bf16* __restrict__ din) {
+    long long n = (long long)(W / 2) * (H / 2) * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int c = (int)(i % C);
+        long long p = i / C;
+        int x = (int)(p % (W / 2)), y = (int)(p / (W / 2));
+        float s = 0.0f;
+        for (int j = 0; j < 2; ++j)
+            for (int k = 0; k < 2; ++k) s += __bfloat162float(dout[((long long)(2 * y + j) * W + 2 * x + k) * dout_ch + c]);
+        din[i] = __float2bfloat16(s);
+    }
+}
+
+// copy channels: dst[p][d_off + c] = src[p][s_off + c], c < C; add != 0 adds
+__global__ void k_copy_ch(const bf16* __restrict__ src, int s_ch, int s_off, bf16* __restrict__ dst, int d_ch, int d_off,
+                          int C, long long npix, int add) {
+    long long n = npix * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int c = (int)(i % C);
+        long long p = i / C;
+        float v = __bfloat162float(src[p * s_ch + s_off + c]);
+        if (add) v += __bfloat162float(dst[p * d_ch + d_off + c]);
+        dst[p * d_ch + d_off + c] = __float2bfloat16(v);
+    }
+}
+
+// gradient through ReLU: g *= (y > 0)
+__global__ void k_relu_mask(bf16* __restrict__ g, const bf16* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(y[i]) > 0.0f)) g[i] = __float2bfloat16(0.0f);
+}
+
+__global__ void k_f32_to_bf16(const float* __restrict__ a, bf16* __restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = __float2bfloat16(a[i]);
+}
+
+// weights [co][tap][ci] (fp32) -> bf16 copy and the flipped transpose
+// [ci][8 - tap][co] used by the data gradient
+__global__ void k_weights_bf16(const float* __restrict__ w, int co_n, int taps, int ci_n, bf16* __restrict__ wb,
+                               bf16* __restrict__ wf) {
+    long long n = (long long)co_n * taps * ci_n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int ci = (int)(i % ci_n);
+        long long r = i / ci_n;
+        int tap = (int)(r % taps), co = (int)(r / taps);
+        bf16 v = __float2bfloat16(w[i]);
+        wb[i] = v;
+        wf[((long long)ci * taps + (taps - 1 - tap)) * co_n + co] = v;
+    }
+}
+
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float gi = g[i];
+        float mi = b1 * m[i] + (1.0f - b1) * gi, vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// proposal head: 16 outputs per pixel = 4 x (a, nx, ny, nz); inverse depth
+// rho = 1/d_hi + (1/d_lo - 1/d_hi) sigmoid(a), normal = (nx, ny, nz) / norm
+// ---------------------------------------------------------------------------
+struct HeadConst {
+    float rho_lo, rho_hi;   // 1/d_hi, 1/d_lo
+    float lambda_n;         // weight of the normal term
+};
+
+__device__ __forceinline__ void decode(const float* o, const HeadConst& hc, float& rho, float n[3], float& len,
+                                       float& sig) {
+    sig = 1.0f / (1.0f + expf(-o[0]));
+    rho = hc.rho_lo + (hc.rho_hi - hc.rho_lo) * sig;
+    len = sqrtf(o[1] * o[1] + o[2] * o[2] + o[3] * o[3]) + 1e-12f;
+    n[0] = o[1] / len; n[1] = o[2] / len; n[2] = o[3] / len;
+}
+
+// per pixel with a target: loss = min_k |rho_k - rho_t| / (rho_hi - rho_lo)
+// + lambda (1 - |n_k . n_t|), rho_t = 1 / target depth; the first k wins
+// ties.  L = scale * sum over target pixels; writes dL/d out and adds L to
+// *loss_sum.
+__global__ void k_proposal_loss(const float* __restrict__ out, const float4* __restrict__ target,
+                                const uint8_t* __restrict__ mask, long long npix, HeadConst hc, float scale,
+                                float* __restrict__ grad, float* __restrict__ loss_sum) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    float lsum = 0.0f;
+    if (i < npix) {
+        float* gp = grad + 16 * i;
+        for (int k = 0; k < 16; ++k) gp[k] = 0.0f;
+        if (mask[i]) {
+            const float4 t4 = target[i];
+            const float tp[4] = {1.0f / t4.w, t4.x, t4.y, t4.z};
+            const float span = hc.rho_hi - hc.rho_lo;
+            int best = 0;
+            float bl = 3.0e38f;
+            for (int k = 0; k < 4; ++k) {
+                float rho, n[3], len, sig;
+                decode(out + 16 * i + 4 * k, hc, rho, n, len, sig);
+                float l = fabsf(rho - tp[0]) / span + hc.lambda_n * (1.0f - fabsf(n[0] * tp[1] + n[1] * tp[2] + n[2] * tp[3]));
+                if (l < bl) { bl = l; best = k; }
+            }
+            float rho, n[3], len, sig;
+            const float* o = out + 16 * i + 4 * best;
+            decode(o, hc, rho, n, len, sig);
+            float sgn = rho > tp[0] ? 1.0f : (rho < tp[0] ? -1.0f : 0.0f);
+            gp[4 * best] = scale * sgn * sig * (1.0f - sig);
+            float dot = n[0] * tp[1] + n[1] * tp[2] + n[2] * tp[3];
+            float sd = dot > 0.0f ? 1.0f : (dot < 0.0f ? -1.0f : 0.0f);
+            for (int c = 0; c < 3; ++c)
+                gp[4 * best + 1 + c] = scale * hc.lambda_n * (-sd) * (tp[1 + c] - dot * n[c]) / len;
+            lsum = bl * scale;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if ((threadIdx.x & 31) == 0 && lsum != 0.0f) atomicAdd(loss_sum, lsum);
+}
+
+// decode the head into K = 4 planes per pixel (n facing the camera, depth)
+__global__ void k_decode_proposals(const float* __restrict__ out, long long npix, int W, HeadConst hc, Mat3 Kinv,
+                                   float4* __restrict__ props) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= npix) return;
+    int x = (int)(i % W), y = (int)(i / W);
+    float r0 = Kinv.m[0] * x + Kinv.m[1] * y + Kinv.m[2], r1 = Kinv.m[3] * x + Kinv.m[4] * y + Kinv.m[5];
+    float r2 = Kinv.m[6] * x + Kinv.m[7] * y + Kinv.m[8];
+    for (int k = 0; k < 4; ++k) {
+        float rho, n[3], len, sig;
+        decode(out + 16 * i + 4 * k, hc, rho, n, len, sig);
+        if (n[0] * r0 + n[1] * r1 + n[2] * r2 > 0.0f) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+        props[4 * i + k] = make_float4(n[0], n[1], n[2], 1.0f / rho);
+    }
+}
+
+// network input (16 channels, bf16): image / 255, normalised inverse depth,
+// normal (3), cost / 2, zeros
+__global__ void k_make_input(const uint8_t* __restrict__ img, const float4* __restrict__ plane,
+                             const float* __restrict__ cost, long long npix, HeadConst hc, bf16* __restrict__ in) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= npix) return;
+    float4 p = plane[i];
+    float rho = p.w > 0.0f ? 1.0f / p.w : hc.rho_lo;
+    float v[16] = {img[i] / 255.0f, (rho - hc.rho_lo) / (hc.rho_hi - hc.rho_lo), p.x, p.y, p.z, cost[i] * 0.5f,
+                   0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < 16; ++c) in[16 * i + c] = __float2bfloat16(v[c]);
+}
+
+unsigned blocks(long long n, int b = 256) {
+    long long g = (n + b - 1) / b;
+    return (unsigned)(g > 152LL * 32 ? 152LL * 32 : (g < 1 ? 1 : g));
+}
+
+}  // namespace
+
+// ===========================================================================
+// host side: the network, its buffers and the C ABI
+// ===========================================================================
+namespace {
+
+struct Layer {
+    int cin, cout, taps;
+    bool relu;
+    size_t nw;                     // cout * taps * cin
+    float *w, *b, *gw, *gb, *mw, *vw, *mb, *vb;
+    bf16 *wb, *wf;                 // bf16 weights and flipped transpose
+};
+
+// channel plan (level l has 1/2^l resolution)
+enum { E0, E1, E2, E3, E4, D3, D2, D1, D0, HEAD, NL };
+const int kLayerCin[NL] = {16, 32, 48, 64, 96, 224, 160, 112, 80, 32};
+const int kLayerCout[NL] = {32, 48, 64, 96, 128, 96, 64, 48, 32, 16};
+
+cudaError_t g_cnn_err = cudaSuccess;
+
+// widest level-0 image the weight-gradient kernel stages in shared memory
+// (256 B per column)
+constexpr int kMaxTrainWidth = 768;
+
+}  // namespace
+
+struct mvs_cnn {
+    int maxW = 0, maxH = 0;
+    cudaStream_t stream = nullptr;
+    HeadConst hc;
+    Layer L[NL];
+    // activations (bf16, channels last)
+    bf16 *x = nullptr, *e[5] = {}, *p[4] = {}, *c[4] = {}, *d[4] = {};
+    float* y = nullptr;            // head output, 16 channels fp32
+    // gradients
+    bf16 *gyb = nullptr, *gd[4] = {}, *gc[4] = {}, *ge[5] = {}, *gp[4] = {};
+    float* gy = nullptr;
+    float* loss = nullptr;
+    int steps = 0;
+    std::string err;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t cnn_alloc(mvs_cnn* n, T** p, size_t count) {
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T) + 256);
+    if (e == cudaSuccess) n->allocs.push_back((void*)*p);
+    return e;
+}
+
+// Outputs [n_off, n_off + nc) with nc in {64, 48, 32, 16}.
+cudaError_t conv_launch(const bf16* in, int Cin, int W, int H, const bf16* w, const float* bias, int taps, int Cout,
+                        bool relu, bool out_f32, void* out, int out_ch, int out_off, cudaStream_t s) {
+    long long tiles = ((long long)W * H + 15) / 16;
+    unsigned grid = (unsigned)((tiles + 3) / 4);
+    for (int n_off = 0; n_off < Cout;) {
+        int rem = Cout - n_off;
+        int nc = rem >= 64 ? 64 : (rem >= 48 ? 48 : (rem >= 32 ? 32 : 16));
+#define LAUNCH(NC)                                                                                          \
+    if (out_f32)                                                                                            \
+        k_conv<NC, false, true><<<grid, 128, 0, s>>>(in, Cin, W, H, w, bias, taps, n_off, out, out_ch, out_off + n_off); \
+    else if (relu)                                                                                          \
+        k_conv<NC, true, false><<<grid, 128, 0, s>>>(in, Cin, W, H, w, bias, taps, n_off, out, out_ch, out_off + n_off); \
+    else                                                                                                    \
+        k_conv<NC, false, false><<<grid, 128, 0, s>>>(in, Cin, W, H, w, bias, taps, n_off, out, out_ch, out_off + n_off)
+        if (nc == 64) { LAUNCH(64); } else if (nc == 48) { LAUNCH(48); } else if (nc == 32) { LAUNCH(32); } else { LAUNCH(16); }
+#undef LAUNCH
+        count_launch();
+        n_off += nc;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t wgrad_launch(const bf16* x, int Cin, const bf16* dy, int Cout, int W, int H, int taps, float* dw, float* db,
+                         cudaStream_t s) {
+    const int rows = 4;
+    dim3 grid(Cout / 16, Cin / 16, (H + rows - 1) / rows);
+    size_t smem = (size_t)(W * 16 + 3 * (W + 2) * 16) * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    k_conv_wgrad<<<grid, 256, smem, s>>>(x, Cin, dy, Cout, W, H, taps, rows, dw, db);
+    count_launch();
+    return cudaGetLastError();
+}
+
+#define CUK(call)                         \
+    do {                                  \
+        cudaError_t _e = (call);          \
+        if (_e != cudaSuccess) return _e; \
+    } while (0)
+
+cudaError_t refresh_bf16(mvs_cnn* n) {
+    for (int i = 0; i < NL; ++i) {
+        Layer& L = n->L[i];
+        k_weights_bf16<<<blocks((long long)L.nw), 256, 0, n->stream>>>(L.w, L.cout, L.taps, L.cin, L.wb, L.wf);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+// forward pass; x must hold the 16-channel input of a W x H image
+cudaError_t cnn_forward(mvs_cnn* n, int W, int H) {
+    cudaStream_t s = n->stream;
+    auto C = [&](int l) -> const Layer& { return n->L[l]; };
+    int Ws[5], Hs[5];
+    for (int l = 0; l < 5; ++l) { Ws[l] = W >> l; Hs[l] = H >> l; }
+    // encoder
+    const bf16* in = n->x;
+    for (int l = 0; l <= 4; ++l) {
+        const Layer& L = C(E0 + l);
+        if (l > 0) {
+            k_pool_fwd<<<blocks((long long)Ws[l] * Hs[l] * C(E0 + l - 1).cout), 256, 0, s>>>(
+                n->e[l - 1], Ws[l - 1], Hs[l - 1], C(E0 + l - 1).cout, n->p[l - 1]);
+            count_launch();
+            in = n->p[l - 1];
+        }
+        CUK(conv_launch(in, L.cin, Ws[l], Hs[l], L.wb, L.b, 9, L.cout, true, false, n->e[l], L.cout, 0, s));
+    }
+    // decoder: level l = 3..0, c[l] = [up(prev) | e[l]]
+    const bf16* prev = n->e[4];
+    int prev_ch = C(E4).cout;
+    for (int l = 3; l >= 0; --l) {
+        const Layer& L = C(D3 + (3 - l));
+        int ch = L.cin;
+        k_up_fwd<<<blocks((long long)Ws[l] * Hs[l] * prev_ch), 256, 0, s>>>(prev, Ws[l], Hs[l], prev_ch, n->c[l], ch);
+        count_launch();
+        k_copy_ch<<<blocks((long long)Ws[l] * Hs[l] * C(E0 + l).cout), 256, 0, s>>>(
+            n->e[l], C(E0 + l).cout, 0, n->c[l], ch, prev_ch, C(E0 + l).cout, (long long)Ws[l] * Hs[l], 0);
+        count_launch();
+        CUK(conv_launch(n->c[l], ch, Ws[l], Hs[l], L.wb, L.b, 9, L.cout, true, false, n->d[l], L.cout, 0, s));
+        prev = n->d[l];
+        prev_ch = L.cout;
+    }
+    const Layer& Hd = C(HEAD);
+    CUK(conv_launch(n->d[0], Hd.cin, W, H, Hd.wb, Hd.b, 1, Hd.cout, false, true, n->y, Hd.cout, 0, s));
+    return cudaGetLastError();
+}
+
+// backward pass from gy (fp32, 16 channels); fills every layer's gw / gb
+cudaError_t cnn_backward(mvs_cnn* n, int W, int H) {
+    cudaStream_t s = n->stream;
+    int Ws[5], Hs[5];
+    for (int l = 0; l < 5; ++l) { Ws[l] = W >> l; Hs[l] = H >> l; }
+    for (int i = 0; i < NL; ++i) {
+        CUK(cudaMemsetAsync(n->L[i].gw, 0, n->L[i].nw * sizeof(float), s));
+        CUK(cudaMemsetAsync(n->L[i].gb, 0, n->L[i].cout * sizeof(float), s));
+    }
+    const long long np0 = (long long)W * H;
+    k_f32_to_bf16<<<blocks(np0 * 16), 256, 0, s>>>(n->gy, n->gyb, np0 * 16);
+    count_launch();
+    Layer& Hd = n->L[HEAD];
+    CUK(wgrad_launch(n->d[0], Hd.cin, n->gyb, Hd.cout, W, H, 1, Hd.gw, Hd.gb, s));
+    CUK(conv_launch(n->gyb, Hd.cout, W, H, Hd.wf, nullptr, 1, Hd.cin, false, false, n->gd[0], Hd.cin, 0, s));
+    // decoder levels 0..3: gd[l] is the gradient of d[l]
+    for (int l = 0; l <= 3; ++l) {
+        Layer& L = n->L[D3 + (3 - l)];
+        long long np = (long long)Ws[l] * Hs[l];
+        k_relu_mask<<<blocks(np * L.cout), 256, 0, s>>>(n->gd[l], n->d[l], np * L.cout);
+        count_launch();
+        CUK(wgrad_launch(n->c[l], L.cin, n->gd[l], L.cout, Ws[l], Hs[l], 9, L.gw, L.gb, s));
+        CUK(conv_launch(n->gd[l], L.cout, Ws[l], Hs[l], L.wf, nullptr, 9, L.cin, false, false, n->gc[l], L.cin, 0, s));
+        // split gc[l] = [g up(prev) | g e[l] (skip)]
+        int up_ch = L.cin - n->L[E0 + l].cout;
+        k_copy_ch<<<blocks(np * n->L[E0 + l].cout), 256, 0, s>>>(n->gc[l], L.cin, up_ch, n->ge[l], n->L[E0 + l].cout,
+                                                                 0, n->L[E0 + l].cout, np, 0);
+        count_launch();
+        bf16* dst = l < 3 ? n->gd[l + 1] : n->ge[4];
+        long long npc = (long long)Ws[l + 1] * Hs[l + 1];
+        k_up_bwd<<<blocks(npc * up_ch), 256, 0, s>>>(n->gc[l], Ws[l], Hs[l], up_ch, L.cin, dst);
+        count_launch();
+    }
+    // encoder levels 4..0: ge[l] is the gradient of e[l]
+    for (int l = 4; l >= 0; --l) {
+        Layer& L = n->L[E0 + l];
+        long long np = (long long)Ws[l] * Hs[l];
+        k_relu_mask<<<blocks(np * L.cout), 256, 0, s>>>(n->ge[l], n->e[l], np * L.cout);
+        count_launch();
+        const bf16* in = l > 0 ? n->p[l - 1] : n->x;
+        CUK(wgrad_launch(in, L.cin, n->ge[l], L.cout, Ws[l], Hs[l], 9, L.gw, L.gb, s));
+        if (l > 0) {
+            CUK(conv_launch(n->ge[l], L.cout, Ws[l], Hs[l], L.wf, nullptr, 9, L.cin, false, false, n->gp[l - 1], L.cin,
+                            0, s));
+            long long npf = (long long)Ws[l - 1] * Hs[l - 1];
+            k_pool_bwd<<<blocks(npf * L.cin), 256, 0, s>>>(n->gp[l - 1], Ws[l - 1], Hs[l - 1], L.cin, n->ge[l - 1], 1);
+            count_launch();
+        }
+    }
+    return cudaGetLastError();
+}
+
+uint64_t splitmix(uint64_t& s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+mvs_status cnn_fail(mvs_cnn* n, mvs_status st, const char* msg, cudaError_t e = cudaSuccess) {
+    if (n) n->err = std::string(msg) + (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : "");
+    return st;
+}
+
+#define CNK(n, call)                                                                        \
+    do {                                                                                    \
+        cudaError_t _e = (call);                                                            \
+        if (_e != cudaSuccess)                                                              \
+            return cnn_fail((n), _e == cudaErrorMemoryAllocation ? MVS_ENOMEM : MVS_ECUDA, #call, _e); \
+    } while (0)
+
+bool shape_ok(const mvs_cnn* n, int W, int H) {
+    return W >= 16 && H >= 16 && W % 16 == 0 && H % 16 == 0 && W <= n->maxW && H <= n->maxH;
+}
+
+}  // namespace
+
+// network input from a PatchMatch state, forward pass, decode (the steps
+// mvs_propose in mvs_api.cu runs on a context's view)
+cudaError_t cnn_propose(mvs_cnn* n, const uint8_t* img, const float4* plane, const float* cost, int W, int H,
+                        const double Kinv[9], float4* props, cudaStream_t s) {
+    cudaStream_t keep = n->stream;
+    n->stream = s;
+    const long long np = (long long)W * H;
+    k_make_input<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(img, plane, cost, np, n->hc, n->x);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cnn_forward(n, W, H);
+    if (e == cudaSuccess) {
+        Mat3 K;
+        for (int i = 0; i < 9; ++i) K.m[i] = (float)Kinv[i];
+        k_decode_proposals<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(n->y, np, W, n->hc, K, props);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    n->stream = keep;
+    return e;
+}
+
+bool cnn_shape_ok(const mvs_cnn* n, int W, int H) { return shape_ok(n, W, H); }
+
+extern "C" {
+
+mvs_status mvs_cnn_create(int32_t max_width, int32_t max_height, float d_lo, float d_hi, uint64_t seed,
+                          void* cuda_stream, mvs_cnn** out) {
+    if (!out) return MVS_EINVAL;
+    *out = nullptr;
+    if (max_width < 16 || max_height < 16 || max_width % 16 || max_height % 16 || max_width > 8192 ||
+        max_height > 8192 || !(d_lo > 0) || !(d_hi > d_lo))
+        return MVS_EINVAL;
+    mvs_cnn* n = new (std::nothrow) mvs_cnn();
+    if (!n) return MVS_ENOMEM;
+    n->maxW = max_width;
+    n->maxH = max_height;
+    n->stream = (cudaStream_t)cuda_stream;
+    n->hc.rho_lo = 1.0f / d_hi;
+    n->hc.rho_hi = 1.0f / d_lo;
+    n->hc.lambda_n = 0.1f;
+    const long long np = (long long)max_width * max_height;
+    cudaError_t e = cudaSuccess;
+    uint64_t rs = seed ^ 0x6A09E667F3BCC909ULL;
+    for (int i = 0; i < NL && e == cudaSuccess; ++i) {
+        Layer& L = n->L[i];
+        L.cin = kLayerCin[i];
+        L.cout = kLayerCout[i];
+        L.taps = i == HEAD ? 1 : 9;
+        L.relu = i != HEAD;
+        L.nw = (size_t)L.cout * L.taps * L.cin;
+        e = cnn_alloc(n, &L.w, L.nw);
+        if (e == cudaSuccess) e = cnn_alloc(n, &L.gw, L.nw);
+        if (e == cudaSuccess) e = cnn_alloc(n, &L.mw, L.nw);
+        if (e == cudaSuccess) e = cnn_alloc(n, &L.vw, L.nw);
+        if (e == cudaSuccess) e = cnn_alloc(n, &L.b, L.cout);
+        if (e == cudaSuccess) e = cnn_alloc(n, &L.gb, L.cout);
+        if (e == cudaSuccess) e = cnn_alloc(n, &L.mb, L.cout);
+        if (e == cudaSuccess) e = cnn_alloc(n, &L.vb, L.cout);
+        if (e == cudaSuccess) e = cnn_alloc(n, &L.wb, L.nw);
+        if (e == cudaSuccess) e = cnn_alloc(n, &L.wf, L.nw);
+        if (e != cudaSuccess) break;
+        // He initialisation (Box-Muller on a splitmix64 stream); the first
+        // layer's padding channels (6..15) and the head start small
+        std::vector<float> hw(L.nw);
+        const int fan_in = L.taps * (i == E0 ? 6 : L.cin);
+        const float sd = (i == HEAD ? 0.1f : 1.0f) * sqrtf(2.0f / fan_in);
+        for (size_t k = 0; k < L.nw; ++k) {
+            double u1 = ((splitmix(rs) >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+            double u2 = (splitmix(rs) >> 11) * (1.0 / 9007199254740992.0);
+            float v = (float)(sqrt(-2.0 * log(u1)) * cos(2.0 * 3.14159265358979323846 * u2)) * sd;
+            if (i == E0 && (int)(k % L.cin) >= 6) v = 0.0f;
+            hw[k] = v;
+        }
+        e = cudaMemcpy(L.w, hw.data(), L.nw * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(L.b, 0, L.cout * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(L.mw, 0, L.nw * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(L.vw, 0, L.nw * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(L.mb, 0, L.cout * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(L.vb, 0, L.cout * sizeof(float));
+    }
+    // activations and gradients at the maximum size
+    for (int l = 0; l < 5 && e == cudaSuccess; ++l) {
+        long long npl = np >> (2 * l);
+        e = cnn_alloc(n, &n->e[l], npl * kLayerCout[E0 + l]);
+        if (e == cudaSuccess) e = cnn_alloc(n, &n->ge[l], npl * kLayerCout[E0 + l]);
+        if (e == cudaSuccess && l < 4) e = cnn_alloc(n, &n->p[l], (npl / 4) * kLayerCout[E0 + l]);
+        if (e == cudaSuccess && l < 4) e = cnn_alloc(n, &n->gp[l], (npl / 4) * kLayerCout[E0 + l]);
+        if (e == cudaSuccess && l < 4) e = cnn_alloc(n, &n->c[l], npl * kLayerCin[D3 + (3 - l)]);
+        if (e == cudaSuccess && l < 4) e = cnn_alloc(n, &n->gc[l], npl * kLayerCin[D3 + (3 - l)]);
+        if (e == cudaSuccess && l < 4) e = cnn_alloc(n, &n->d[l], npl * kLayerCout[D3 + (3 - l)]);
+        if (e == cudaSuccess && l < 4) e = cnn_alloc(n, &n->gd[l], npl * kLayerCout[D3 + (3 - l)]);
+    }
+    if (e == cudaSuccess) e = cnn_alloc(n, &n->x, np * 16);
+    if (e == cudaSuccess) e = cnn_alloc(n, &n->y, np * 16);
+    if (e == cudaSuccess) e = cnn_alloc(n, &n->gy, np * 16);
+    if (e == cudaSuccess) e = cnn_alloc(n, &n->gyb, np * 16);
+    if (e == cudaSuccess) e = cnn_alloc(n, &n->loss, 1);
+    if (e == cudaSuccess) e = refresh_bf16(n);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    if (e != cudaSuccess) {
+        g_cnn_err = e;
+        mvs_cnn_destroy(n);
+        return e == cudaErrorMemoryAllocation ? MVS_ENOMEM : MVS_ECUDA;
+    }
+    *out = n;
+    return MVS_OK;
+}
+
+void mvs_cnn_destroy(mvs_cnn* n) {
+    if (!n) return;
+    cudaStreamSynchronize(n->stream);
+    for (void* p : n->allocs) cudaFree(p);
+    delete n;
+}
+
+const char* mvs_cnn_last_error(const mvs_cnn* n) {
+    return n ? n->err.c_str() : (g_cnn_err != cudaSuccess ? cudaGetErrorString(g_cnn_err) : "");
+}
+
+mvs_status mvs_cnn_n_params(const mvs_cnn* n, int64_t* count) {
+    if (!n || !count) return MVS_EINVAL;
+    int64_t t = 0;
+    for (int i = 0; i < NL; ++i) t += (int64_t)n->L[i].nw + n->L[i].cout;
+    *count = t;
+    return MVS_OK;
+}
+
+static mvs_status copy_params(mvs_cnn* n, float* host, bool grads, bool set) {
+    size_t off = 0;
+    for (int i = 0; i < NL; ++i) {
+        Layer& L = n->L[i];
+        float* w = grads ? L.gw : L.w;
+        float* b = grads ? L.gb : L.b;
+        if (set) {
+            CNK(n, cudaMemcpyAsync(w, host + off, L.nw * sizeof(float), cudaMemcpyHostToDevice, n->stream));
+            CNK(n, cudaMemcpyAsync(b, host + off + L.nw, L.cout * sizeof(float), cudaMemcpyHostToDevice, n->stream));
+        } else {
+            CNK(n, cudaMemcpyAsync(host + off, w, L.nw * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+            CNK(n, cudaMemcpyAsync(host + off + L.nw, b, L.cout * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+        }
+        off += L.nw + L.cout;
+    }
+    if (set) CNK(n, refresh_bf16(n));
+    CNK(n, cudaStreamSynchronize(n->stream));
+    return MVS_OK;
+}
+
+mvs_status mvs_cnn_get_params(mvs_cnn* n, float* host_out) {
+    if (!n || !host_out) return MVS_EINVAL;
+    return copy_params(n, host_out, false, false);
+}
+
+mvs_status mvs_cnn_set_params(mvs_cnn* n, const float* host_in) {
+    if (!n || !host_in) return MVS_EINVAL;
+    return copy_params(n, const_cast<float*>(host_in), false, true);
+}
+
+mvs_status mvs_cnn_get_grads(mvs_cnn* n, float* host_out) {
+    if (!n || !host_out) return MVS_EINVAL;
+    return copy_params(n, host_out, true, false);
+}
+
+static mvs_status run_forward(mvs_cnn* n, const uint8_t* img, const float4* plane, const float* cost, int W, int H) {
+    if (!shape_ok(n, W, H))
+        return cnn_fail(n, MVS_EINVAL, "width and height must be multiples of 16 within the capacity");
+    if (((uintptr_t)plane & 15u) || ((uintptr_t)cost & 3u))
+        return cnn_fail(n, MVS_EINVAL, "plane must be 16-byte and cost 4-byte aligned");
+    const long long np = (long long)W * H;
+    k_make_input<<<(unsigned)((np + 255) / 256), 256, 0, n->stream>>>(img, plane, cost, np, n->hc, n->x);
+    count_launch();
+    CNK(n, cudaGetLastError());
+    CNK(n, cnn_forward(n, W, H));
+    return MVS_OK;
+}
+
+mvs_status mvs_cnn_forward(mvs_cnn* n, const uint8_t* img, const float* plane, const float* cost, int32_t W,
+                           int32_t H, float* out) {
+    if (!n || !img || !plane || !cost || !out) return MVS_EINVAL;
+    mvs_status st = run_forward(n, img, (const float4*)plane, cost, W, H);
+    if (st != MVS_OK) return st;
+    CNK(n, cudaMemcpyAsync(out, n->y, (size_t)W * H * 16 * sizeof(float), cudaMemcpyDeviceToDevice, n->stream));
+    return MVS_OK;
+}
+
+mvs_status mvs_cnn_backward(mvs_cnn* n, const uint8_t* img, const float* plane, const float* cost, int32_t W,
+                            int32_t H, const float* target, const uint8_t* mask, float* loss_out) {
+    if (!n || !img || !plane || !cost || !target || !mask) return MVS_EINVAL;
+    if (W > kMaxTrainWidth) return cnn_fail(n, MVS_EINVAL, "training width above the weight-gradient kernel's limit");
+    if ((uintptr_t)target & 15u) return cnn_fail(n, MVS_EINVAL, "target must be 16-byte aligned");
+    mvs_status st = run_forward(n, img, (const float4*)plane, cost, W, H);
+    if (st != MVS_OK) return st;
+    const long long np = (long long)W * H;
+    CNK(n, cudaMemsetAsync(n->loss, 0, sizeof(float), n->stream));
+    k_proposal_loss<<<(unsigned)((np + 255) / 256), 256, 0, n->stream>>>(n->y, (const float4*)target, mask, np, n->hc,
+                                                                         1.0f / (float)np, n->gy, n->loss);
+    count_launch();
+    CNK(n, cudaGetLastError());
+    CNK(n, cnn_backward(n, W, H));
+    if (loss_out) {
+        CNK(n, cudaMemcpyAsync(loss_out, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+        CNK(n, cudaStreamSynchronize(n->stream));
+    }
+    return MVS_OK;
+}
+
+mvs_status mvs_cnn_propose(mvs_cnn* n, const uint8_t* img, const float* plane, const float* cost, int32_t W,
+                           int32_t H, const double Kinv[9], float* proposals) {
+    if (!n || !img || !plane || !cost || !Kinv || !proposals) return MVS_EINVAL;
+    if (!shape_ok(n, W, H))
+        return cnn_fail(n, MVS_EINVAL, "width and height must be multiples of 16 within the capacity");
+    if (((uintptr_t)plane & 15u) || ((uintptr_t)cost & 3u) || ((uintptr_t)proposals & 15u))
+        return cnn_fail(n, MVS_EINVAL, "plane and proposals must be 16-byte, cost 4-byte aligned");
+    CNK(n, cnn_propose(n, img, (const float4*)plane, cost, W, H, Kinv, (float4*)proposals, n->stream));
+    return MVS_OK;
+}
+
+mvs_status mvs_cnn_adam_step(mvs_cnn* n, float lr) {
+    if (!n || !(lr > 0)) return MVS_EINVAL;
+    n->steps++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)n->steps), c2 = 1.0f - powf(b2, (float)n->steps);
+    for (int i = 0; i < NL; ++i) {
+        Layer& L = n->L[i];
+        k_adam<<<blocks((long long)L.nw), 256, 0, n->stream>>>(L.w, L.gw, L.mw, L.vw, (long long)L.nw, lr, b1, b2, 1e-8f,
+                                                               c1, c2);
+        k_adam<<<1, 256, 0, n->stream>>>(L.b, L.gb, L.mb, L.vb, L.cout, lr, b1, b2, 1e-8f, c1, c2);
+        count_launch(2);
+    }
+    CNK(n, cudaGetLastError());
+    CNK(n, refresh_bf16(n));
+    return MVS_OK;
+}
+
+}  // extern "C"

@@ -153,6 +153,10 @@ mvs_status check_pm(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src,
     if (p->lanes_per_pixel != 0 && p->lanes_per_pixel != 4 && p->lanes_per_pixel != 8 &&
         p->lanes_per_pixel != 16 && p->lanes_per_pixel != 32)
         return fail(c, MVS_EINVAL, "lanes_per_pixel must be 0, 4, 8, 16 or 32");
+    if (p->n_prop < 0 || p->n_prop > 8) return fail(c, MVS_EINVAL, "n_prop must be in 0..8");
+    if ((p->n_prop > 0) != (p->proposals != nullptr))
+        return fail(c, MVS_EINVAL, "proposals must be given exactly when n_prop > 0");
+    if ((uintptr_t)p->proposals & 15u) return fail(c, MVS_EINVAL, "proposals must be 16-byte aligned");
     return MVS_OK;
 }
 
@@ -180,6 +184,8 @@ void make_refconst(const mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n
     rc.seed = p->seed;
     rc.lanes_hint = p->lanes_per_pixel;
     rc.precision = p->precision;
+    rc.n_prop = p->n_prop;
+    rc.props = reinterpret_cast<const float4*>(p->proposals);
     rc.plane = R.plane;
     rc.cost = R.cost;
     for (int j = 0; j < n_src; ++j) {
@@ -402,6 +408,7 @@ mvs_status mvs_patchmatch_batch(mvs_ctx* c, int32_t n_ref, const int32_t* refs, 
                                 const mvs_pm_params* p, mvs_depth_map* outs) {
     if (!c) return MVS_EINVAL;
     if (n_ref < 1 || !refs || !srcs || !outs || !p) return fail(c, MVS_EINVAL, "bad batch arguments");
+    if (p->n_prop != 0) return fail(c, MVS_EUNSUPPORTED, "learned proposals are per view: use mvs_patchmatch");
     mvs_pm_params q = *p;
     const bool tune = p->lanes_per_pixel == -1;
     if (tune) q.lanes_per_pixel = 0;
@@ -821,6 +828,21 @@ mvs_status mvs_plane_infer(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t
     V.has_map = true;
     CK(c, cudaMemcpyAsync(inout->plane, V.plane, n * sizeof(float4), kind_out(mem), c->stream));
     if (mem == MVS_MEM_HOST) CK(c, cudaStreamSynchronize(c->stream));
+    return MVS_OK;
+}
+
+mvs_status mvs_propose(mvs_ctx* c, int32_t ref, mvs_cnn* net, float* proposals) {
+    mvs_status st = check_view(c, ref);
+    if (st != MVS_OK) return st;
+    if (!net || !proposals) return fail(c, MVS_EINVAL, "net and proposals must be given");
+    if ((uintptr_t)proposals & 15u) return fail(c, MVS_EINVAL, "proposals must be 16-byte aligned");
+    ViewData& V = c->views[ref];
+    if (!V.has_map) return fail(c, MVS_ESTATE, "view %d has no depth map", ref);
+    if (!cnn_shape_ok(net, V.cam.width, V.cam.height))
+        return fail(c, MVS_EINVAL, "view size %dx%d is not a multiple of 16 within the network's capacity",
+                    V.cam.width, V.cam.height);
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cnn_propose(net, V.img, V.plane, V.cost, V.cam.width, V.cam.height, V.Kinv, (float4*)proposals, c->stream));
     return MVS_OK;
 }
 

@@ -43,6 +43,8 @@ struct RefConst {
     unsigned long long* eval_counter;  // measurement: evaluated (pixel, hypothesis, view) triples, or null
     int lanes_hint;            // lanes per pixel group (0 = default)
     int precision;             // 0 = FP32, 1 = mixed (half2 bilinear, FP32 moments)
+    int n_prop;                // learned proposals per pixel (0 = none)
+    const float4* props;       // H*W*n_prop planes (n, depth), or null
     PairConst pair[MVS_MAX_SRC];
 };
 
@@ -113,3 +115,9 @@ cudaError_t launch_phi_select(const RefConst& rc, const uint8_t* known, const fl
 cudaError_t launch_known_from_cost(int W, int H, const float4* plane, const float* cost, float hole_cost,
                                    uint8_t* known, float* depth, cudaStream_t s);
 cudaError_t launch_depth_of(int W, int H, const float4* plane, const uint8_t* known, float* depth, cudaStream_t s);
+
+// learned proposals (cnn_kernels.cu)
+struct mvs_cnn;
+cudaError_t cnn_propose(mvs_cnn* n, const uint8_t* img, const float4* plane, const float* cost, int W, int H,
+                        const double Kinv[9], float4* props, cudaStream_t s);
+bool cnn_shape_ok(const mvs_cnn* n, int W, int H);

@@ -215,14 +215,20 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             d = ok ? rho / den : 0.0f;
             ok = ok && d >= rc.d_lo && d <= rc.d_hi;
         }
-        // stage 0: the eight propagated planes; stage 1: the three refinement
-        // candidates built from the state after stage 0.  One call site keeps
-        // a single copy of the evaluation in the instruction cache.
+        // stage 0: the eight propagated planes; stage 1: the learned
+        // proposals of this pixel (when given); stage 2: the three refinement
+        // candidates built from the state after stages 0 and 1.  One call
+        // site keeps a single copy of the evaluation in the instruction cache.
         float4 hyp4 = make_float4(np.x, np.y, np.z, d);
         bool want = ok;
 #pragma unroll 1
-        for (int stage = 0; stage < 2; ++stage) {
+        for (int stage = 0; stage < 3; ++stage) {
             if (stage == 1) {
+                if (rc.n_prop == 0) continue;
+                const bool has = lane < rc.n_prop;
+                hyp4 = has ? rc.props[pix * rc.n_prop + lane] : make_float4(0.f, 0.f, -1.f, 0.f);
+                want = has && hyp4.w >= rc.d_lo && hyp4.w <= rc.d_hi;
+            } else if (stage == 2) {
                 // refinement (Sec. III-C): delta_d in [-d_hi/4, d_hi/4],
                 // delta_theta in [-pi/2, pi/2], delta_phi in [-pi/12, pi/12]
                 float u[3];
@@ -242,7 +248,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
                      : (lane == 1 ? make_float4(nn0, nn1, nn2, cur.w) : make_float4(nn0, nn1, nn2, d_new));
                 want = lane < 3;
             }
-            const int nc = stage == 0 ? 8 : 3;
+            const int nc = stage == 0 ? 8 : (stage == 1 ? rc.n_prop : 3);
             Cand my = make_cand(rc, pw, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
             float c = eval_batch<G, S, false, MIXED>(rc, views, pw, px, py, my, nc, warp_pairs(smem, rc.n_src, warp),
                                                       nullptr, nev);

@@ -40,7 +40,8 @@ class mvs_pm_params(C.Structure):
                 ("sigma_c", C.c_float), ("d_lo", C.c_float), ("d_hi", C.c_float), ("iters", C.c_int32),
                 ("phase_begin", C.c_int32), ("phase_end", C.c_int32), ("init_mode", C.c_int32),
                 ("seed", C.c_uint64), ("precision", C.c_int32), ("lanes_per_pixel", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("n_prop", C.c_int32), ("reserved0", C.c_int32), ("proposals", C.c_void_p),
+                ("reserved", C.c_int32 * 2)]
 
 
 class mvs_depth_map(C.Structure):
@@ -74,11 +75,15 @@ class PMParams:
     seed: int = 0
     precision: int = 0
     lanes_per_pixel: int = 0
+    n_prop: int = 0
+    proposals: object = None        # device buffer (H, W, n_prop, 4) float32 or None
 
     def c(self):
+        pp = _ptr(self.proposals)[0] if self.proposals is not None else None
         return mvs_pm_params(self.win_radius, self.win_samples, self.sigma_s, self.sigma_c, self.d_lo, self.d_hi,
                              self.iters, self.phase_begin, self.phase_end, self.init_mode,
-                             int(self.seed) & 0xFFFFFFFFFFFFFFFF, self.precision, self.lanes_per_pixel)
+                             int(self.seed) & 0xFFFFFFFFFFFFFFFF, self.precision, self.lanes_per_pixel,
+                             self.n_prop, 0, pp)
 
 
 @dataclass
@@ -155,6 +160,27 @@ def load():
     L.mvs_phi_select.argtypes = [vp, i32, u8p, fp, u8p, vp, fp, i32]
     L.mvs_profile.restype = i32
     L.mvs_profile.argtypes = [vp, i32]
+    L.mvs_cnn_create.restype = i32
+    L.mvs_cnn_create.argtypes = [i32, i32, C.c_float, C.c_float, C.c_uint64, vp, C.POINTER(C.c_void_p)]
+    L.mvs_cnn_destroy.restype = None
+    L.mvs_cnn_destroy.argtypes = [vp]
+    L.mvs_cnn_last_error.restype = C.c_char_p
+    L.mvs_cnn_last_error.argtypes = [vp]
+    L.mvs_cnn_n_params.restype = i32
+    L.mvs_cnn_n_params.argtypes = [vp, C.POINTER(C.c_int64)]
+    for name in ("mvs_cnn_get_params", "mvs_cnn_set_params", "mvs_cnn_get_grads"):
+        getattr(L, name).restype = i32
+        getattr(L, name).argtypes = [vp, fp]
+    L.mvs_cnn_forward.restype = i32
+    L.mvs_cnn_forward.argtypes = [vp, u8p, fp, fp, i32, i32, fp]
+    L.mvs_cnn_backward.restype = i32
+    L.mvs_cnn_backward.argtypes = [vp, u8p, fp, fp, i32, i32, fp, u8p, C.POINTER(C.c_float)]
+    L.mvs_cnn_adam_step.restype = i32
+    L.mvs_cnn_adam_step.argtypes = [vp, C.c_float]
+    L.mvs_cnn_propose.restype = i32
+    L.mvs_cnn_propose.argtypes = [vp, u8p, fp, fp, i32, i32, C.POINTER(C.c_double), fp]
+    L.mvs_propose.restype = i32
+    L.mvs_propose.argtypes = [vp, i32, vp, fp]
     L.mvs_profile_read.restype = i32
     L.mvs_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_int64)]
@@ -334,6 +360,88 @@ def mvs_profile_read(ctx):
     a, b, e = C.c_int64(), C.c_int64(), C.c_int64()
     _check(load().mvs_profile_read(ctx, C.byref(ms), C.byref(a), C.byref(b), C.byref(e)), ctx)
     return ms.value, a.value, b.value, e.value
+
+
+def _check_cnn(status, net):
+    if status != MVS_OK:
+        msg = load().mvs_cnn_last_error(net)
+        raise MvsError(status, msg.decode() if msg else "")
+
+
+def _dev(*bufs):
+    for b in bufs:
+        if _ptr(b)[1] != MVS_MEM_DEVICE:
+            raise ValueError("the proposal network takes device buffers only")
+    return [_ptr(b)[0] for b in bufs]
+
+
+def mvs_cnn_create(max_width, max_height, d_lo, d_hi, seed=0, stream=None):
+    h = C.c_void_p()
+    _check_cnn(load().mvs_cnn_create(int(max_width), int(max_height), float(d_lo), float(d_hi),
+                                     int(seed) & 0xFFFFFFFFFFFFFFFF, _stream_handle(stream), C.byref(h)), None)
+    return h
+
+
+def mvs_cnn_destroy(net):
+    load().mvs_cnn_destroy(net)
+
+
+def mvs_cnn_n_params(net):
+    n = C.c_int64()
+    _check_cnn(load().mvs_cnn_n_params(net, C.byref(n)), net)
+    return n.value
+
+
+def mvs_cnn_get_params(net):
+    a = np.zeros(mvs_cnn_n_params(net), np.float32)
+    _check_cnn(load().mvs_cnn_get_params(net, a.ctypes.data), net)
+    return a
+
+
+def mvs_cnn_set_params(net, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != mvs_cnn_n_params(net):
+        raise ValueError("parameter count mismatch")
+    _check_cnn(load().mvs_cnn_set_params(net, a.ctypes.data), net)
+
+
+def mvs_cnn_get_grads(net):
+    a = np.zeros(mvs_cnn_n_params(net), np.float32)
+    _check_cnn(load().mvs_cnn_get_grads(net, a.ctypes.data), net)
+    return a
+
+
+def mvs_cnn_forward(net, img, plane, cost, out):
+    """img (H, W) uint8, plane (H, W, 4), cost (H, W) -> out (H, W, 16)."""
+    H, W = img.shape
+    pi, pp, pc, po = _dev(img, plane, cost, out)
+    _check_cnn(load().mvs_cnn_forward(net, pi, pp, pc, W, H, po), net)
+
+
+def mvs_cnn_backward(net, img, plane, cost, target, mask):
+    """Forward + loss against target planes on mask + backward; returns the loss."""
+    H, W = img.shape
+    pi, pp, pc, pt, pm = _dev(img, plane, cost, target, mask)
+    loss = C.c_float()
+    _check_cnn(load().mvs_cnn_backward(net, pi, pp, pc, W, H, pt, pm, C.byref(loss)), net)
+    return loss.value
+
+
+def mvs_cnn_adam_step(net, lr):
+    _check_cnn(load().mvs_cnn_adam_step(net, float(lr)), net)
+
+
+def mvs_cnn_propose(net, img, plane, cost, Kinv, proposals):
+    H, W = img.shape
+    pi, pp, pc, pr = _dev(img, plane, cost, proposals)
+    k = (C.c_double * 9)(*[float(v) for v in np.asarray(Kinv, float).ravel()])
+    _check_cnn(load().mvs_cnn_propose(net, pi, pp, pc, W, H, k, pr), net)
+
+
+def mvs_propose(ctx, ref, net, proposals):
+    """Proposals (H, W, 4, 4) float32 device buffer from the current map of `ref`."""
+    (pr,) = _dev(proposals)
+    _check(load().mvs_propose(ctx, int(ref), net, pr), ctx)
 
 
 class Context:

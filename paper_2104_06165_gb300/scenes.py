@@ -220,7 +220,8 @@ def _sources_ring(n_src, z_c, angles_deg, rng):
 
 
 def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_angles=None,
-               n_textured=3, n_flat=1, flat_frac=None, d_lo=2.0, d_hi=8.0, quantise=True, threads=None):
+               n_textured=3, n_flat=1, flat_frac=None, d_lo=2.0, d_hi=8.0, quantise=True, threads=None,
+               flat_bg=0.0):
     """Scene of textured planar quads in front of a textured background plane,
     with n_flat texture-less (constant-intensity) patches painted on those
     planes.
@@ -230,7 +231,9 @@ def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_an
     sources sit on a ring of radius baseline_frac * 5 around the reference
     optical axis; otherwise at the given viewing angles (degrees) to the
     scene centre.  flat_frac sizes the patches so that roughly that fraction
-    of the reference image is texture-less (default 8 %)."""
+    of the reference image is texture-less (default 8 %); flat_bg > 0 adds
+    three blank squares on the background plane at random image positions,
+    together about that fraction of the image before occlusion."""
     rng = np.random.default_rng(seed)
     f = f if f is not None else 300.0 * W / 320.0
     K = intrinsics(W, H, f)
@@ -267,6 +270,16 @@ def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_an
         side = float(np.clip(math.sqrt(target / quad_px), 0.2, 0.8))
         c1, c2 = rng.uniform(-0.1, 0.1) * q.half[0], rng.uniform(-0.1, 0.1) * q.half[1]
         q.blanks.append((c1, c2, side * q.half[0], side * q.half[1], float(rng.uniform(70, 190))))
+    if flat_bg > 0:
+        Kinv = np.linalg.inv(K)
+        side_px = math.sqrt(flat_bg * W * H / 3.0)
+        for k in range(3):
+            u, v = rng.uniform(0.1 * W, 0.9 * W), rng.uniform(0.1 * H, 0.9 * H)
+            r = Kinv @ np.array([u, v, 1.0])
+            X = r * (bg.normal @ bg.center) / (bg.normal @ r)
+            half = 0.5 * side_px * X[2] / f
+            bg.blanks.append((float(bg.e1 @ (X - bg.center)), float(bg.e2 @ (X - bg.center)), half, half,
+                              float(rng.uniform(70, 190))))
     Ks, Rs, ts = [K], [np.eye(3)], [np.zeros(3)]
     if view_angles is None:
         b = baseline_frac * z_c
