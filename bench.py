@@ -32,7 +32,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(W=3072, H=2048, n_src=10, win_radius=10.0, win_samples=11, iters=8, sigma_s=5.0, sigma_c=0.2)
 # smaller case of the same kernels for profiler captures (inputs still larger than L2)
-WORKLOADS = {"highres": WORKLOAD, "mid": dict(WORKLOAD, W=1536, H=1024), "batch24": dict(WORKLOAD)}
+WORKLOADS = {"highres": WORKLOAD, "mid": dict(WORKLOAD, W=1536, H=1024), "batch24": dict(WORKLOAD),
+             "learned": dict(WORKLOAD, W=1536, H=1024, iters=4)}
 BATCH_SIZES = ((3072, 2048),) * 8 + ((2048, 1365),) * 8 + ((1536, 1024),) * 8
 FLOP_PER_SAMPLE = 26          # algorithmic FP32 flops per window sample of one ZNCC (FMA = 2)
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
@@ -276,7 +277,9 @@ def run_ours(args):
         "ncc_evals_per_s": evals / (phase_ms / 1e3) if phase_ms > 0 else None,
         "phase_kernel_ms": phase_ms / max(1, phase_n),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": (tpp * H * W if (tpp := phase_traffic_per_pixel()) else None),
+                     "traffic_unit": "bytes per launch (ncu dram read+write, 1536x1024 capture scaled by pixels)",
                      "kernel": "k_phase (checkerboard propagation + refinement)",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
         "clocks": clk.summary(),
@@ -351,6 +354,126 @@ def run_batch(args):
     ctx.close()
 
 
+PHASE_SOURCES = ["paper_2104_06165_gb300/csrc/pm_kernels.cu", "paper_2104_06165_gb300/csrc/pm_device.cuh",
+                 "paper_2104_06165_gb300/csrc/mvs_internal.h"]
+
+
+def phase_traffic_per_pixel():
+    """DRAM bytes per reference pixel of one k_phase launch from the committed
+    ncu summary, or None when the kernel sources changed since the capture."""
+    import hashlib
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "k_phase_mid_full.md")).read()
+        vals = dict(l.split(": ", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes_per_pixel:",
+                                                                                "sources_sha256:")))
+        h = hashlib.sha256()
+        for f in PHASE_SOURCES:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() != vals["sources_sha256"].strip():
+            return None
+        return float(vals["traffic_bytes_per_pixel"])
+    except Exception:
+        return None
+
+
+def _peak_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def run_learned(args):
+    """Learned plane proposals on 1536 x 1024 scenes with about half of the
+    image texture-less: one step = initialisation, one plain iteration, the
+    proposal network on that state, three iterations with K = 4 proposals
+    per pixel.  The plain 8-iteration depth map of the same scene is timed
+    the same way; both are scored by completeness (depth within 1 % of the
+    ground truth)."""
+    import torch
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2104_06165_gb300 import mvs, proposals as P
+    mvs.load()
+    t0 = time.perf_counter()
+    sc = P.scene(2000 + rank)
+    t_render = time.perf_counter() - t0
+    H, W = sc.images[0].shape
+    srcs = list(range(1, len(sc.images)))
+    stream = torch.cuda.current_stream(dev)
+    ctx = mvs.Context(sc.K, sc.R, sc.t, sc.images, stream=stream)
+    net = mvs.mvs_cnn_create(W, H, 2.0, 8.0, 0, stream)
+    P.load_weights(net)
+    plane = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    cost = torch.empty((H, W), dtype=torch.float32, device=dev)
+    props = torch.empty((H, W, P.K_PROP, 4), dtype=torch.float32, device=dev)
+    learned = lambda: P.learned_patchmatch(ctx, 0, srcs, P.pm_params(1 + rank), net, plane, cost, props, iters=4)
+    plain8 = lambda: mvs.mvs_patchmatch(ctx.h, 0, srcs, P.pm_params(1 + rank, iters=8), plane, cost)
+
+    def timed(fn, clk=None):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        mvs.mvs_profile(ctx.h, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = mvs.mvs_profile_read(ctx.h)
+        mvs.mvs_profile(ctx.h, 0)
+        return e0.elapsed_time(e1) / args.steps, prof, P.completeness(plane.cpu().numpy(), sc.gt_depth)
+
+    with ClockSampler(local) as clk:
+        ms_l, prof_l, comp_l = timed(learned)
+        ms_p, prof_p, comp_p = timed(plain8)
+    # the proposal network alone (forward + decode) on the learned state
+    learned()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        mvs.mvs_propose(ctx.h, 0, net, props)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    cnn_ms = e0.elapsed_time(e1) / reps
+    from paper_2104_06165_gb300.proposals import cnn_flops
+    peak_bf16, peak_kind = _peak_bf16()
+    cnn_tf = cnn_flops(W, H) / (cnn_ms / 1e3) / 1e12
+    phase_ms, phase_n, launches, evals = prof_l
+    n2 = WORKLOAD["win_samples"] ** 2
+    achieved = evals * n2 * FLOP_PER_SAMPLE / (phase_ms / 1e3) / 1e12 if phase_ms > 0 else None
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    mpix = H * W / 1e6
+    line = {
+        "metric": "depth-map Mpix/s (learned proposals + 4-iteration PatchMatch)", "value": mpix / (ms_l / 1e3),
+        "unit": "Mpix/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_l,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
+        "data": "synthetic",
+        "config": {"workload": f"learned {W}x{H} uint8 ref + {len(srcs)} sources, ~50% texture-less, 21x21 window "
+                               "dil 2, 1 plain iteration + proposal network + 3 iterations with 4 proposals/pixel",
+                   "render_s": round(t_render, 1), "l2": "inputs larger than L2 (11 x 25 MB textures)"},
+        "completeness": comp_l,
+        "plain8": {"value": mpix / (ms_p / 1e3), "ms_per_step": ms_p, "completeness": comp_p},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "k_phase (propagation + proposals + refinement)",
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
+        "cnn": {"ms": cnn_ms, "achieved_tflops": cnn_tf, "peak_tflops": peak_bf16, "peak": peak_kind,
+                "frac": cnn_tf / peak_bf16, "bound": "tensor"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    mvs.mvs_cnn_destroy(net)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,13 +485,16 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
                     help="fp32 = FP32 ZNCC; mixed = half2 bilinear, FP32 moments, FP64 near-flat denominators")
     ap.add_argument("--workload", default="highres", choices=sorted(WORKLOADS),
-                    help="highres = the measured workload; mid = 1536x1024 case for profiler captures")
+                    help="highres = the measured workload; mid = 1536x1024 case for profiler captures; "
+                         "batch24 = 24 views in one graph; learned = learned proposals vs plain 8 iterations")
     args = ap.parse_args()
     WORKLOAD.update(WORKLOADS[args.workload])
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch24":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 
