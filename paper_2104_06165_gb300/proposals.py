@@ -48,6 +48,15 @@ def pm_params(seed, iters=8, **kw):
                         iters=iters, seed=seed, **kw)
 
 
+def cnn_flops(W, H):
+    """Algorithmic flops of one forward pass (2 per multiply-add of every
+    convolution) at a W x H input."""
+    levels = [0, 1, 2, 3, 4, 3, 2, 1, 0, 0]
+    layers = [(16, 32, 9), (32, 48, 9), (48, 64, 9), (64, 96, 9), (96, 128, 9),
+              (224, 96, 9), (160, 64, 9), (112, 48, 9), (80, 32, 9), (32, 16, 1)]
+    return sum(2 * (W >> l) * (H >> l) * co * t * ci for l, (ci, co, t) in zip(levels, layers))
+
+
 def load_weights(net, path=WEIGHTS):
     mvs.mvs_cnn_set_params(net, np.load(path))
 
