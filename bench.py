@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(W=3072, H=2048, n_src=10, win_radius=10.0, win_samples=11, iters=8, sigma_s=5.0, sigma_c=0.2)
 # smaller case of the same kernels for profiler captures (inputs still larger than L2)
 WORKLOADS = {"highres": WORKLOAD, "mid": dict(WORKLOAD, W=1536, H=1024), "batch24": dict(WORKLOAD),
-             "learned": dict(WORKLOAD, W=1536, H=1024, iters=4)}
+             "learned": dict(WORKLOAD, W=1536, H=1024, iters=4), "table3": dict(WORKLOAD)}
 BATCH_SIZES = ((3072, 2048),) * 8 + ((2048, 1365),) * 8 + ((1536, 1024),) * 8
 FLOP_PER_SAMPLE = 26          # algorithmic FP32 flops per window sample of one ZNCC (FMA = 2)
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
@@ -474,6 +474,67 @@ def run_learned(args):
     ctx.close()
 
 
+TABLE3 = [(5, 5), (5, 6), (6, 6), (5, 7), (7, 7), (5, 8), (8, 8), (5, 9), (9, 9), (5, 10), (10, 10)]
+TABLE3_PAPER_S = {(5, 5): 9.79, (5, 6): 10.02, (6, 6): 12.58, (5, 7): 9.57, (7, 7): 16.41, (5, 8): 10.04,
+                  (8, 8): 20.92, (5, 9): 10.51, (9, 9): 25.91, (5, 10): 10.86, (10, 10): 31.60}
+
+
+def run_table3(args):
+    """The paper's window-radius study (Sec. IV-B, Table III) on the
+    high-resolution synthetic workload: for each (r_now, r_orig) the 8-
+    iteration depth map (PatchMatch only, r_now samples per half side at
+    spacing r_orig / r_now), its time and its completeness against the
+    ground truth at 1 %, 2 % and 5 % relative depth error."""
+    import torch
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2104_06165_gb300 import mvs, scenes
+    mvs.load()
+    w = WORKLOAD
+    sc = scenes.scene_highres(seed=rank, W=w["W"], H=w["H"], n_src=w["n_src"])
+    H, W = sc.images[0].shape
+    srcs = list(range(1, len(sc.images)))
+    stream = torch.cuda.current_stream(dev)
+    ctx = mvs.Context(sc.K, sc.R, sc.t, sc.images, stream=stream)
+    plane = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    cost = torch.empty((H, W), dtype=torch.float32, device=dev)
+    gt = sc.gt_depth
+    rows = []
+    with ClockSampler(local) as clk:
+        for r_now, r_orig in TABLE3:
+            p = mvs.PMParams(win_radius=float(r_orig), win_samples=2 * r_now + 1, sigma_s=w["sigma_s"],
+                             sigma_c=w["sigma_c"], d_lo=2.0, d_hi=8.0, iters=w["iters"], seed=1 + rank)
+            for _ in range(args.warmup):
+                mvs.mvs_patchmatch(ctx.h, 0, srcs, p, plane, cost)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                mvs.mvs_patchmatch(ctx.h, 0, srcs, p, plane, cost)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            d = plane[..., 3].cpu().numpy()
+            err = np.abs(d - gt) / np.where(gt > 0, gt, 1.0)
+            rows.append({"r_now": r_now, "r_orig": r_orig, "ms": ms, "mpix_s": H * W / 1e3 / ms,
+                         "completeness": {f"{t}%": float((err <= t / 100).mean()) for t in (1, 2, 5)},
+                         "paper_time_s": TABLE3_PAPER_S[(r_now, r_orig)]})
+    base = rows[0]["ms"]
+    for r in rows:
+        r["time_vs_5_5"] = r["ms"] / base
+    line = {"metric": "depth-map Mpix/s per window configuration (Table III study)",
+            "value": rows[3]["mpix_s"], "unit": "Mpix/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rows[3]["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"table3 {W}x{H} uint8 ref + {len(srcs)} sources, 8 iterations, PatchMatch "
+                                   "only; value = the paper's 5/7 setting",
+                       "paper_hardware": "RTX 3070, ETH3D training scenes at 3024x2016 (context only)"},
+            "rows": rows, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -486,7 +547,8 @@ def main():
                     help="fp32 = FP32 ZNCC; mixed = half2 bilinear, FP32 moments, FP64 near-flat denominators")
     ap.add_argument("--workload", default="highres", choices=sorted(WORKLOADS),
                     help="highres = the measured workload; mid = 1536x1024 case for profiler captures; "
-                         "batch24 = 24 views in one graph; learned = learned proposals vs plain 8 iterations")
+                         "batch24 = 24 views in one graph; learned = learned proposals vs plain 8 iterations; "
+                         "table3 = the paper's window-radius study")
     args = ap.parse_args()
     WORKLOAD.update(WORKLOADS[args.workload])
     if args.impl == "reference":
@@ -495,6 +557,8 @@ def main():
         run_batch(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "table3":
+        run_table3(args)
     else:
         run_ours(args)
 

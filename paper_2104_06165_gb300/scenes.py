@@ -189,7 +189,7 @@ def render(quads, K, R, t, W, H, quantise=True, want_gt=False, threads=None):
     return out
 
 
-def _quad_facing(rng, K, W, H, depth, u, v, size_px, textured, f, tilt=50.0, flat_value=None):
+def _quad_facing(rng, K, W, H, depth, u, v, size_px, textured, f, tilt=50.0, flat_value=None, tex_std=38.0):
     """Quad whose centre projects to reference pixel (u, v) at the given
     depth, roughly size_px pixels across, tilted up to `tilt` degrees."""
     ray = np.linalg.inv(K) @ np.array([u, v, 1.0])
@@ -200,7 +200,7 @@ def _quad_facing(rng, K, W, H, depth, u, v, size_px, textured, f, tilt=50.0, fla
     q = Quad(center=center, normal=n, e1=e1, e2=e2, half=(half, half * rng.uniform(0.6, 1.0)),
              textured=textured)
     if textured:
-        q.freqs, q.phases, q.amps = _texture(rng, depth, f)
+        q.freqs, q.phases, q.amps = _texture(rng, depth, f, std=tex_std)
     else:
         q.flat_value = float(flat_value if flat_value is not None else rng.uniform(70, 190))
     return q
@@ -221,7 +221,7 @@ def _sources_ring(n_src, z_c, angles_deg, rng):
 
 def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_angles=None,
                n_textured=3, n_flat=1, flat_frac=None, d_lo=2.0, d_hi=8.0, quantise=True, threads=None,
-               flat_bg=0.0):
+               flat_bg=0.0, tex_std=38.0, noise_std=0.0):
     """Scene of textured planar quads in front of a textured background plane,
     with n_flat texture-less (constant-intensity) patches painted on those
     planes.
@@ -233,7 +233,9 @@ def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_an
     scene centre.  flat_frac sizes the patches so that roughly that fraction
     of the reference image is texture-less (default 8 %); flat_bg > 0 adds
     three blank squares on the background plane at random image positions,
-    together about that fraction of the image before occlusion."""
+    together about that fraction of the image before occlusion.  tex_std is
+    the texture contrast (grey levels); noise_std > 0 adds independent
+    Gaussian noise of that deviation to every view before rounding."""
     rng = np.random.default_rng(seed)
     f = f if f is not None else 300.0 * W / 320.0
     K = intrinsics(W, H, f)
@@ -244,7 +246,7 @@ def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_an
     n_bg = _random_normal(rng, 15.0)
     e1, e2 = _plane_axes(n_bg)
     bg = Quad(center=np.array([0.0, 0.0, bg_depth]), normal=n_bg, e1=e1, e2=e2, half=(40.0, 40.0), textured=True)
-    bg.freqs, bg.phases, bg.amps = _texture(rng, bg_depth, f)
+    bg.freqs, bg.phases, bg.amps = _texture(rng, bg_depth, f, std=tex_std)
     quads.append(bg)
     placed = []
     for k in range(n_textured):
@@ -256,7 +258,7 @@ def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_an
         placed.append((u, v))
         depth = rng.uniform(3.0, 5.8)
         size = rng.uniform(0.3, 0.45) * W
-        quads.append(_quad_facing(rng, K, W, H, depth, u, v, size, True, f, tilt=50.0))
+        quads.append(_quad_facing(rng, K, W, H, depth, u, v, size, True, f, tilt=50.0, tex_std=tex_std))
     # texture-less regions: blank patches painted on the textured quads, each
     # centred on its quad and sized for flat_frac of the reference image in
     # total (at most 80 % of the quad's side), so that a blank region is
@@ -293,8 +295,13 @@ def make_scene(W=320, H=240, f=None, n_src=4, seed=0, baseline_frac=0.1, view_an
     images = []
     gt = None
     for v in range(len(Ks)):
-        out = render(quads, Ks[v], Rs[v], ts[v], W, H, quantise=quantise, want_gt=(v == 0), threads=threads)
-        images.append(out["img"])
+        out = render(quads, Ks[v], Rs[v], ts[v], W, H, quantise=quantise and noise_std <= 0, want_gt=(v == 0),
+                     threads=threads)
+        img = out["img"]
+        if noise_std > 0:     # render gave [0, 1] floats: noise in grey levels
+            img = img * 255.0 + rng.normal(0.0, noise_std, img.shape)
+            img = np.clip(np.rint(img), 0, 255).astype(np.uint8) if quantise else np.clip(img, 0, 255) / 255.0
+        images.append(img)
         if v == 0:
             gt = out
     return Scene(K=np.stack(Ks), R=np.stack(Rs), t=np.stack(ts), images=images, gt_depth=gt["depth"],
