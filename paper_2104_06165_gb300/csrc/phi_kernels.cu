@@ -2,6 +2,9 @@
 // (Sec. III-E): four-direction line-fit hypotheses, their matching cost, the
 // pairwise MRF of Eq. 6-9 decoded by tree-reweighted message passing at half
 // resolution, closest-hypothesis selection and Eq. 10 normals.
+#include <cooperative_groups.h>
+
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/mvs.h"
@@ -242,10 +245,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_phi_cost(const __grid_constant__ 
 // tie).  The raster order is run as anti-diagonal wavefronts (a node only
 // depends on its up / left neighbours in the forward pass and on its down /
 // right neighbours in the backward pass), which gives the same result as the
-// sequential sweep: tiles of T x T nodes are processed one tile-diagonal per
-// launch and, inside a tile, one node-diagonal per __syncthreads step.
+// sequential sweep: one cooperative launch per pass walks the gw + gh - 1
+// node diagonals, the nodes of a diagonal in parallel, with a grid-wide
+// barrier between diagonals.
 // ---------------------------------------------------------------------------
-constexpr int kT = 32;
+constexpr int kWaveBlock = 256;
 
 struct MrfBufs {
     int gw, gh;
@@ -328,21 +332,15 @@ __device__ void trw_node(const MrfBufs& mb, int x, int y, bool forward, float k3
     }
 }
 
-__global__ void __launch_bounds__(kT) k_trw_diag(MrfBufs mb, int tile_diag, bool forward, float k3) {
-    int ntx = (mb.gw + kT - 1) / kT, nty = (mb.gh + kT - 1) / kT;
-    int D = forward ? tile_diag : (ntx + nty - 2 - tile_diag);
-    int ty_lo = max(0, D - (ntx - 1));
-    int ty = ty_lo + blockIdx.x;
-    int tx = D - ty;
-    if (ty >= nty || tx < 0) return;
-    for (int s = 0; s < 2 * kT - 1; ++s) {
-        int l = forward ? s : (2 * kT - 2 - s);
-        int lx = threadIdx.x, ly = l - lx;
-        if (ly >= 0 && ly < kT) {
-            int x = tx * kT + lx, y = ty * kT + ly;
-            if (x < mb.gw && y < mb.gh) trw_node(mb, x, y, forward, k3);
-        }
-        __syncthreads();
+__global__ void __launch_bounds__(kWaveBlock) k_trw_wave(MrfBufs mb, bool forward, float k3) {
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    const int nd = mb.gw + mb.gh - 1;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (int s = 0; s < nd; ++s) {
+        const int d = forward ? s : nd - 1 - s;
+        const int x_lo = max(0, d - (mb.gh - 1)), x_hi = min(d, mb.gw - 1);
+        for (int x = x_lo + tid; x <= x_hi; x += nth) trw_node(mb, x, d - x, forward, k3);
+        grid.sync();   // every block runs the same number of steps
     }
 }
 
@@ -542,17 +540,29 @@ cudaError_t launch_phi_mrf(int W, int H, const uint8_t* known, const float* dept
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int ntx = (mb.gw + kT - 1) / kT, nty = (mb.gh + kT - 1) / kT;
+    // enough co-resident blocks for the longest diagonal (min(gw, gh) nodes)
+    static int max_blocks = 0;
+    {
+        static std::mutex mu;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!max_blocks) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trw_wave, kWaveBlock, 0);
+            max_blocks = std::max(1, sms * per_sm);
+        }
+    }
+    const int want = (std::min(mb.gw, mb.gh) + kWaveBlock - 1) / kWaveBlock;
+    dim3 grid(std::max(1, std::min(want, max_blocks))), block(kWaveBlock);
     for (int it = 0; it < iters; ++it)
-        for (int pass = 0; pass < 2; ++pass)
-            for (int D = 0; D < ntx + nty - 1; ++D) {
-                int Dd = pass == 0 ? D : (ntx + nty - 2 - D);
-                int ty_lo = max(0, Dd - (ntx - 1)), ty_hi = min(nty - 1, Dd);
-                k_trw_diag<<<ty_hi - ty_lo + 1, kT, 0, s>>>(mb, D, pass == 0, k3);
-                count_launch();
-                e = cudaGetLastError();
-                if (e != cudaSuccess) return e;
-            }
+        for (int pass = 0; pass < 2; ++pass) {
+            bool forward = pass == 0;
+            void* args[] = {(void*)&mb, (void*)&forward, (void*)&k3};
+            e = cudaLaunchCooperativeKernel((const void*)k_trw_wave, grid, block, args, 0, s);
+            count_launch();
+            if (e != cudaSuccess) return e;
+        }
     k_trw_decode<<<blocks_for(g, 256), 256, 0, s>>>(mb, label);
     count_launch();
     return cudaGetLastError();
