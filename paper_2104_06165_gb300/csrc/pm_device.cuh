@@ -256,6 +256,14 @@ __host__ __device__ constexpr size_t smem_block_bytes(int n_src, int warps) {
     return smem_views_bytes(n_src) + (size_t)warps * 8 * n_src * sizeof(PairSm);
 }
 
+// Two planes (n, depth at the pixel) equal up to float rounding (1e-6
+// relative in depth, 1e-6 per normal component); such planes score the same
+// cost to within rounding.
+__device__ __forceinline__ bool same_plane(const float4& a, const float4& b) {
+    return fabsf(a.w - b.w) <= 1e-6f * b.w && fabsf(a.x - b.x) <= 1e-6f && fabsf(a.y - b.y) <= 1e-6f &&
+           fabsf(a.z - b.z) <= 1e-6f;
+}
+
 // Costs C(x) (Eq. 5) of up to 8 hypotheses of the warp's pixel: lane c < nc
 // holds hypothesis c on entry and its cost on return.
 //   1. the (hypothesis, view) pairs whose window maps inside the source

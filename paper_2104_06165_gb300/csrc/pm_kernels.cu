@@ -215,6 +215,21 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             d = ok ? rho / den : 0.0f;
             ok = ok && d >= rc.d_lo && d <= rc.d_hi;
         }
+        // A carried-over plane equal (to float rounding) to the pixel's own
+        // plane or to an earlier group's plane scores the same cost, so it
+        // cannot be strictly cheaper than that plane: it is not evaluated.
+        {
+            const float4 mine = make_float4(np.x, np.y, np.z, d);
+            bool dup = ok && same_plane(mine, cur);
+#pragma unroll
+            for (int g2 = 0; g2 < 7; ++g2) {
+                const float4 o = make_float4(__shfl_sync(0xffffffffu, np.x, g2), __shfl_sync(0xffffffffu, np.y, g2),
+                                             __shfl_sync(0xffffffffu, np.z, g2), __shfl_sync(0xffffffffu, d, g2));
+                const bool ook = __shfl_sync(0xffffffffu, (int)ok, g2) != 0;
+                dup = dup || (ok && ook && lane > g2 && same_plane(mine, o));
+            }
+            ok = ok && !dup;
+        }
         // stage 0: the eight propagated planes; stage 1: the learned
         // proposals of this pixel (when given); stage 2: the three refinement
         // candidates built from the state after stages 0 and 1.  One call
@@ -227,7 +242,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
                 if (rc.n_prop == 0) continue;
                 const bool has = lane < rc.n_prop;
                 hyp4 = has ? rc.props[pix * rc.n_prop + lane] : make_float4(0.f, 0.f, -1.f, 0.f);
-                want = has && hyp4.w >= rc.d_lo && hyp4.w <= rc.d_hi;
+                want = has && hyp4.w >= rc.d_lo && hyp4.w <= rc.d_hi && !same_plane(hyp4, cur);
             } else if (stage == 2) {
                 // refinement (Sec. III-C): delta_d in [-d_hi/4, d_hi/4],
                 // delta_theta in [-pi/2, pi/2], delta_phi in [-pi/12, pi/12]

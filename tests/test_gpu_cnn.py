@@ -294,10 +294,12 @@ def test_trained_proposals_gain(mvs_lib):
     a held-out 1536 x 1024 scene of the training distribution, scored by
     completeness (depth within 1 % of the ground truth).
 
-    Measured on GB300: learned-4 reaches plain-8's completeness with about
-    60 % of its ZNCC evaluations, and equals plain-4 (these scenes converge
-    in two plain iterations, so the proposals find nothing plain PatchMatch
-    misses).  The test pins both facts."""
+    Measured on GB300: learned-4 reaches plain-8's completeness with 78 % of
+    its ZNCC evaluations (the phase kernel skips candidates that repeat the
+    pixel's plane, which thins plain-8's converged iterations), and equals
+    plain-4, which needs fewer evaluations still (these scenes converge in
+    two plain iterations, so the proposals find nothing plain PatchMatch
+    misses).  The test pins these facts."""
     import torch
     from paper_2104_06165_gb300 import proposals as P
     sc = P.scene(1500)
@@ -327,8 +329,9 @@ def test_trained_proposals_gain(mvs_lib):
         mvs_lib.mvs_cnn_destroy(net)
     (c4, e4), (c8, e8), (cl, el) = res["plain4"], res["plain8"], res["learned4"]
     assert cl >= c8 - 0.002, res            # equal completeness to plain-8 ...
-    assert el <= 0.7 * e8, res              # ... with far fewer ZNCC evaluations
-    assert abs(cl - c4) <= 0.002, res       # and no gain over plain-4
+    assert el < e8, res                     # ... with fewer ZNCC evaluations
+    assert abs(cl - c4) <= 0.002, res       # no gain over plain-4 ...
+    assert el > e4, res                     # ... which evaluates fewer
     # the proposals are planes of the scene: on textured pixels one of the
     # four lies within 1 % of the true depth far more often than chance
     tex = sc.gt_textured
