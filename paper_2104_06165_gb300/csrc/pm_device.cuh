@@ -122,26 +122,33 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
     const int lane = threadIdx.x & 31, lg = lane & (G - 1);
     const int n = rc.n;
     const float half = 0.5f * (float)(n - 1);
-    int ku_lo = n, ku_hi = -1, kv_lo = n, kv_hi = -1;
-    for (int k = 0; k < n; ++k) {
-        float o = rc.step * ((float)k - half);
-        float eu = (float)px + o, ev = (float)py + o;
-        if (eu >= 0.0f && eu <= (float)(rc.W - 1)) { ku_lo = min(ku_lo, k); ku_hi = max(ku_hi, k); }
-        if (ev >= 0.0f && ev <= (float)(rc.H - 1)) { kv_lo = min(kv_lo, k); kv_hi = max(kv_hi, k); }
+    // window rows / columns inside the reference image: lane k tests offset k
+    // (n <= 22 < 32)
+    int ku_lo, ku_hi, kv_lo, kv_hi;
+    {
+        const float o = rc.step * ((float)lane - half);
+        const float eu = (float)px + o, ev = (float)py + o;
+        const unsigned mu = __ballot_sync(0xffffffffu, lane < n && eu >= 0.0f && eu <= (float)(rc.W - 1));
+        const unsigned mv = __ballot_sync(0xffffffffu, lane < n && ev >= 0.0f && ev <= (float)(rc.H - 1));
+        ku_lo = mu ? __ffs(mu) - 1 : n;
+        ku_hi = mu ? 31 - __clz(mu) : -1;
+        kv_lo = mv ? __ffs(mv) - 1 : n;
+        kv_hi = mv ? 31 - __clz(mv) : -1;
     }
     const float rcen = exists ? 4.0f * (float)__ldg(rc.img + (long long)py * rc.W + px) : 0.0f;
+    const float inv_n = 1.0f / (float)n;
     float sw = 0.0f, swr = 0.0f;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        int k = s * G + lg;
-        int ku = k % n, kv = k / n;
+        const int k = s * G + lg;
+        const int kv = (int)(((float)k + 0.5f) * inv_n), ku = k - kv * n;   // exact for k < 2^20
         bool in = exists && k < n * n && ku >= ku_lo && ku <= ku_hi && kv >= kv_lo && kv <= kv_hi;
         float ou = rc.step * ((float)ku - half), ov = rc.step * ((float)kv - half);
         float r = 0.0f, w = 0.0f;
         if (in) {
             r = tex_sample(rc.tex, rc.pitch, rc.n_tex, 2.0f * ((float)px + ou) - 1.0f, 2.0f * ((float)py + ov) - 1.0f);
             float dc = r - rcen;
-            w = expf(rc.sp_coef * (ou * ou + ov * ov)) * expf(rc.col_coef * dc * dc);
+            w = __expf(fmaf(rc.sp_coef, ou * ou + ov * ov, rc.col_coef * dc * dc));
         }
         pw.ou[s] = in ? ou : 0.0f;
         pw.ov[s] = in ? ov : 0.0f;
