@@ -211,6 +211,20 @@ def plane_cost(scene, ref, srcs, p, plane, with_views=False):
     return (cost, vc, mg) if with_views else cost
 
 
+def cost_at(scene, ref, srcs, p, xs, ys, planes):
+    """Eq. 4/5 cost (and decision margin) of planes (n, 4) at the reference
+    pixels (xs[k], ys[k]) only."""
+    s = _srcs(srcs)
+    xs = np.ascontiguousarray(xs, np.int32)
+    ys = np.ascontiguousarray(ys, np.int32)
+    pl = np.ascontiguousarray(_f64(planes).reshape(-1, 4))
+    n = len(xs)
+    cost = np.zeros(n, np.float64)
+    mg = np.zeros(n, np.float64)
+    lib().or_cost_at(scene.h, ref, _i(s), len(s), C.byref(_pm(p)), n, _i(xs), _i(ys), _d(pl), _d(cost), _d(mg))
+    return cost, mg
+
+
 def wzncc(w, a, b):
     w, a, b = _f64(w), _f64(a), _f64(b)
     return lib().or_wzncc(len(w), _d(w), _d(a), _d(b))

@@ -364,6 +364,21 @@ static double pixel_cost(const or_scene* s, int ref, const int* srcs, int ns, co
     return aggregate(ns, cj, ok);
 }
 
+/* Eq. 4/5 cost of n given planes (nx, ny, nz, d) at the pixels (xs[k], ys[k])
+ * of the reference: the same as or_plane_cost at those pixels, without
+ * touching the others (for sampled checks on large images) */
+void or_cost_at(const or_scene* s, int ref, const int* srcs, int ns, const or_pm* p, int n, const int* xs,
+                const int* ys, const double* planes, double* cost, double* margin_out) {
+    or_window* win = (or_window*)malloc(sizeof(or_window));
+    for (int k = 0; k < n; ++k) {
+        double mg;
+        ref_window(s, ref, p, xs[k], ys[k], win);
+        cost[k] = pixel_cost(s, ref, srcs, ns, p, xs[k], ys[k], planes + 4 * k, planes[4 * k + 3], win, NULL, &mg);
+        if (margin_out) margin_out[k] = mg;
+    }
+    free(win);
+}
+
 /* cost map of a given plane map; plane = H*W*4 (nx, ny, nz, d) */
 void or_plane_cost(const or_scene* s, int ref, const int* srcs, int ns, const or_pm* p, const double* plane,
                    double* cost, double* view_cost_out, double* margin_out) {

@@ -1,0 +1,99 @@
+"""Edge cases of the PatchMatch path against the oracle: tiny and one-row
+images, a single source view, sources that see none of the reference,
+texture-less images."""
+import copy
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _params(mvs, **kw):
+    base = dict(win_radius=5.0, win_samples=6, sigma_s=5.0, sigma_c=0.2, iters=2, seed=99)
+    base.update(kw)
+    return mvs.PMParams(**base)
+
+
+def _run(mvs, sc, srcs, p):
+    import torch
+    ctx = mvs.Context(sc.K, sc.R, sc.t, sc.images, stream=torch.cuda.current_stream())
+    try:
+        H, W = sc.images[0].shape
+        pl = np.zeros((H, W, 4), np.float32)
+        co = np.zeros((H, W), np.float32)
+        mvs.mvs_patchmatch(ctx.h, 0, srcs, p, pl, co)
+    finally:
+        ctx.close()
+    return pl, co
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (7, 1), (1, 9), (5, 3)])
+def test_tiny_images_match_the_oracle(mvs_lib, oracle_lib, W, H):
+    """Images smaller than the window: every reference patch is flat or
+    clipped; results equal the oracle's (init draws, C_max costs)."""
+    from paper_2104_06165_gb300 import scenes
+    big = scenes.make_scene(W=64, H=48, n_src=2, seed=5, baseline_frac=0.1)
+    K = big.K.copy()
+    imgs = [np.ascontiguousarray(im[20:20 + H, 30:30 + W]) for im in big.images]
+    K[:, 0, 2] -= 30
+    K[:, 1, 2] -= 20
+    sc = copy.copy(big)
+    sc.K, sc.images = K, imgs
+    p = _params(mvs_lib)
+    pl, co = _run(mvs_lib, sc, [1, 2], p)
+    osc = oracle_lib.Scene(K, big.R, big.t, imgs)
+    opl, oco = oracle_lib.patchmatch(osc, 0, [1, 2], p, p.iters)
+    assert np.abs(pl[..., 3] - opl[..., 3]).max() <= 1e-4 * 8
+    assert np.abs(co - oco).max() <= 1e-4
+
+
+def test_single_source_view_phase_parity(mvs_lib, oracle_lib):
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_scene(W=80, H=60, n_src=1, seed=21, baseline_frac=0.1)
+    p = _params(mvs_lib, iters=2)
+    pl, co = _run(mvs_lib, sc, [1], p)
+    osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
+    opl, oco = oracle_lib.patchmatch(osc, 0, [1], p, p.iters)
+    rel = np.abs(pl[..., 3] - opl[..., 3]) / opl[..., 3]
+    assert (rel <= 0.005).mean() >= 0.99
+
+
+def test_sources_that_see_nothing_give_cmax(mvs_lib, oracle_lib):
+    """Source cameras turned away from the scene: every view is excluded, so
+    every cost is C_max and no hypothesis ever replaces the initial one."""
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_scene(W=48, H=40, n_src=2, seed=3, baseline_frac=0.1)
+    R = sc.R.copy()
+    t = sc.t.copy()
+    flip = np.diag([-1.0, 1.0, -1.0])          # rotate the sources by 180 degrees about y
+    for j in (1, 2):
+        R[j] = flip @ R[j]
+        t[j] = flip @ t[j]
+    sc2 = copy.copy(sc)
+    sc2.R, sc2.t = R, t
+    p = _params(mvs_lib, iters=2)
+    pl, co = _run(mvs_lib, sc2, [1, 2], p)
+    assert (co == 2.0).all()
+    p0 = _params(mvs_lib, iters=0)
+    pl0, _ = _run(mvs_lib, sc2, [1, 2], p0)
+    assert np.array_equal(pl, pl0)
+    osc = oracle_lib.Scene(sc.K, R, t, sc.images)
+    opl, oco = oracle_lib.patchmatch(osc, 0, [1, 2], p, p.iters)
+    assert (oco == 2.0).all()
+    assert np.abs(pl[..., 3] - opl[..., 3]).max() <= 1e-6 * 8
+
+
+def test_texture_less_images_keep_their_initial_planes(mvs_lib, oracle_lib):
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_scene(W=40, H=32, n_src=2, seed=4, baseline_frac=0.1)
+    flat = [np.full_like(im, 120) for im in sc.images]
+    sc2 = copy.copy(sc)
+    sc2.images = flat
+    p = _params(mvs_lib)
+    pl, co = _run(mvs_lib, sc2, [1, 2], p)
+    pl0, _ = _run(mvs_lib, sc2, [1, 2], _params(mvs_lib, iters=0))
+    assert (co == 2.0).all() and np.array_equal(pl, pl0)
+    osc = oracle_lib.Scene(sc.K, sc.R, sc.t, flat)
+    opl, oco = oracle_lib.patchmatch(osc, 0, [1, 2], p, p.iters)
+    assert (oco == 2.0).all()

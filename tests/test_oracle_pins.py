@@ -530,3 +530,14 @@ def test_paper_constants_fixture():
     assert p.iters == g["iterations"] and q.trw_iters == g["trw_iterations"] and q.n_fit == g["n_fit"]
     assert (f_.depth_tol, f_.max_angle_deg, f_.max_reproj_px) == (g["filter_depth"], g["filter_angle_deg"],
                                                                   g["filter_reproj_px"])
+
+
+def test_cost_at_equals_the_cost_map(oracle_lib, tiny):
+    sc, osc = tiny
+    p = P(seed=2)
+    pl, _ = oracle_lib.init(osc, 0, [1, 2], p)
+    full = oracle_lib.plane_cost(osc, 0, [1, 2], p, pl)
+    xs = np.array([0, 5, 39, 20, 11])
+    ys = np.array([0, 7, 29, 15, 3])
+    c, _ = oracle_lib.cost_at(osc, 0, [1, 2], p, xs, ys, pl[ys, xs])
+    assert np.array_equal(c, full[ys, xs])
