@@ -134,7 +134,7 @@ typedef struct {
  *   cams[i].width x cams[i].height, pitch = width.  The images are copied (the
  *   caller keeps its buffers).  cuda_stream: a cudaStream_t or NULL for the
  *   legacy default stream.  The context uses the current CUDA device.
- * Errors: MVS_EINVAL (NULL pointers, n_views < 2, sizes <= 0 or > 32768),
+ * Errors: MVS_EINVAL (NULL pointers, n_views < 2, width or height < 2 or > 32768),
  *   MVS_ENOMEM, MVS_ECUDA. */
 mvs_status mvs_create(const mvs_camera* cams, const uint8_t* const* images, int32_t n_views,
                       void* cuda_stream, mvs_ctx** out);

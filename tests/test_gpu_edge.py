@@ -28,7 +28,7 @@ def _run(mvs, sc, srcs, p):
     return pl, co
 
 
-@pytest.mark.parametrize("W,H", [(1, 1), (7, 1), (1, 9), (5, 3)])
+@pytest.mark.parametrize("W,H", [(2, 2), (7, 2), (2, 9), (5, 3)])
 def test_tiny_images_match_the_oracle(mvs_lib, oracle_lib, W, H):
     """Images smaller than the window: every reference patch is flat or
     clipped; results equal the oracle's (init draws, C_max costs)."""
@@ -46,6 +46,15 @@ def test_tiny_images_match_the_oracle(mvs_lib, oracle_lib, W, H):
     opl, oco = oracle_lib.patchmatch(osc, 0, [1, 2], p, p.iters)
     assert np.abs(pl[..., 3] - opl[..., 3]).max() <= 1e-4 * 8
     assert np.abs(co - oco).max() <= 1e-4
+
+
+def test_one_pixel_wide_images_are_rejected(mvs_lib):
+    from paper_2104_06165_gb300 import scenes
+    big = scenes.make_scene(W=16, H=12, n_src=1, seed=5, baseline_frac=0.1)
+    imgs = [np.ascontiguousarray(im[:1, :]) for im in big.images]
+    with pytest.raises(mvs_lib.MvsError) as e:
+        mvs_lib.Context(big.K, big.R, big.t, imgs)
+    assert e.value.status == mvs_lib.MVS_EINVAL
 
 
 def test_single_source_view_phase_parity(mvs_lib, oracle_lib):

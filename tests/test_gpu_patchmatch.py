@@ -157,4 +157,4 @@ def test_free_running_depth(small, mvs_lib, oracle_lib):
     rel = np.abs(pl[..., 3] - opl[..., 3]) / opl[..., 3]
     frac = (rel <= 0.005).mean()
     print(f"free-running: depth within 0.5% on {frac:.5f} of pixels")
-    assert frac >= 0.98
+    assert frac >= 0.999        # measured 0.99943 on GB300
