@@ -33,6 +33,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// float(h) + c for an fp16 h, rounded once (mixed-precision add of sm_100+).
+__device__ __forceinline__ float add_f16_f32(__half h, float c) {
+    float d;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(h)), "f"(c));
+    return d;
+}
+
 // Philox4x64-10 (Salmon et al., SC'11).
 __device__ __forceinline__ void philox4x64(unsigned long long c[4], unsigned long long k0,
                                            unsigned long long k1) {
@@ -102,7 +109,7 @@ __device__ __forceinline__ float tex_sample(const uint2* __restrict__ tex, int p
 // warp holds the same pixel's window (sample k = slot * G + lane_in_group).
 template <int S>
 struct PixWin {
-    float ou[S], ov[S];   // sample offsets (0 for padding / excluded samples)
+    float ou[S], ov[S];   // sample offsets (the first included sample for padding / excluded samples)
     float w[S];           // bilateral weights (0 for padding / excluded)
     float wr[S];          // w * (I_ref - weighted mean)
     float inv_wsum;       // 1 / sum w
@@ -135,6 +142,8 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
         kv_lo = mv ? __ffs(mv) - 1 : n;
         kv_hi = mv ? 31 - __clz(mv) : -1;
     }
+    // excluded and padding samples sit on the first included sample (weight 0)
+    const float ou_pad = rc.step * ((float)ku_lo - half), ov_pad = rc.step * ((float)kv_lo - half);
     const float rcen = exists ? 4.0f * (float)__ldg(rc.img + (long long)py * rc.W + px) : 0.0f;
     const float inv_n = 1.0f / (float)n;
     float sw = 0.0f, swr = 0.0f;
@@ -150,8 +159,8 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
             float dc = r - rcen;
             w = __expf(fmaf(rc.sp_coef, ou * ou + ov * ov, rc.col_coef * dc * dc));
         }
-        pw.ou[s] = in ? ou : 0.0f;
-        pw.ov[s] = in ? ov : 0.0f;
+        pw.ou[s] = in ? ou : ou_pad;
+        pw.ov[s] = in ? ov : ov_pad;
         pw.w[s] = w;
         pw.wr[s] = r;   // temporarily the intensity
         sw += w;
@@ -195,6 +204,9 @@ struct ViewSm {
     float wm1, hm1;       // W - 1, H - 1
     uint32_t pitch, n_tex;
     const uint2* tex;
+    // index of texel (i + 1, j + 1) = bits(1.5 * 2^24 + 2 j) * pitch
+    // + bits(1.5 * 2^24 + 2 i) + toff (mod 2^32), see tex_sample
+    uint32_t toff, pad_;
 };
 
 __device__ __forceinline__ void load_views(const RefConst& rc, ViewSm* sv) {
@@ -207,6 +219,7 @@ __device__ __forceinline__ void load_views(const RefConst& rc, ViewSm* sv) {
         sv[j].pitch = (uint32_t)P.pitch;
         sv[j].n_tex = P.n_tex;
         sv[j].tex = P.tex;
+        sv[j].toff = (uint32_t)(P.pitch + 1) * (uint32_t)(1 - kMagic2Bits);
     }
     __syncthreads();
 }
@@ -296,10 +309,13 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
     const float x = (float)px, y = (float)py;
     // ---- 1. list the pairs that map inside the source images
     int count = 0, my_cnt = 0;
+    // floor(i / V) = (i * ceil(2^16 / V)) >> 16 exactly for i < 2^16 / V
+    // (i < 8 * MVS_MAX_SRC here)
+    const uint32_t vmagic = 0xffffu / (uint32_t)V + 1u;
     for (int base = 0; base < P; base += 32) {
         int i = base + lane;
         bool act = i < P;
-        int c = act ? i / V : 0;
+        int c = act ? (int)(((uint32_t)i * vmagic) >> 16) : 0;
         int j = act ? i - c * V : 0;
         float m0 = __shfl_sync(0xffffffffu, my.m0, c);
         float m1 = __shfl_sync(0xffffffffu, my.m1, c);
@@ -359,19 +375,72 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         const float h0x = q.h0x, h0y = q.h0y, h0z = q.h0z, h1x = q.h1x;
         const float h1y = q.h1y, h1z = q.h1z, p0x = q.p0x, p0y = q.p0y, p0z = q.p0z;
         const ViewSm& v = sv[q.j];
-        const uint2* tex = v.tex;
-        const uint32_t pitch = v.pitch, n_tex = v.n_tex;
-        float sval[S];
+        float sa = 0.0f, sb = 0.0f, se = 0.0f;
+        float sval[S], c0 = 0.0f;   // mixed precision only: the samples and their shift
         if constexpr (!MIXED) {
+            // Sample k at doubled, half-shifted source coordinates (X/Z, Y/Z).
+            // One FMA rounds X/Z + 1.5 * 2^24 to the nearest even integer 2i
+            // (its bits give i), a second gives U = X/Z - 2i in [-1, 1]
+            // rounded once.  The texel index is clamped into the array: the
+            // listed window corners lie inside the source, but FP32 positions
+            // of other samples of a plane seen almost edge-on by the source
+            // need not.
+            const uint2* tex = v.tex;
+            const uint32_t pitch = v.pitch, toff = v.toff, last = v.n_tex - 1u;
+            // gathers in chunks of up to 8 slots (registers); the intensities
+            // are shifted by c0 = the 2 x 2 texel sum at the group's first
+            // sample (an intensity of this source patch), which enters through
+            // the fp16 coefficient a (one mixed add)
+            constexpr int CH = S <= 9 ? S : 8;
+            float nc0 = 0.0f, dv[S];
+#pragma unroll
+            for (int k0 = 0; k0 < S; k0 += CH) {
+                uint2 tq[CH];
+                float Us[CH], Vs[CH];
+#pragma unroll
+                for (int kk = 0; kk < CH; ++kk) {
+                    const int k = k0 + kk;
+                    if (k < S) {
+                        float X = fmaf(pw.ou[k], h0x, fmaf(pw.ov[k], h1x, p0x));
+                        float Y = fmaf(pw.ou[k], h0y, fmaf(pw.ov[k], h1y, p0y));
+                        float Z = fmaf(pw.ou[k], h0z, fmaf(pw.ov[k], h1z, p0z));
+                        float iz = rcp_approx(Z);
+                        float tx = fmaf(X, iz, kMagic2), ty = fmaf(Y, iz, kMagic2);
+                        Us[kk] = fmaf(X, iz, kMagic2 - tx);
+                        Vs[kk] = fmaf(Y, iz, kMagic2 - ty);
+                        uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx) + toff;
+                        tq[kk] = __ldg(tex + min(idx, last));
+                    }
+                }
+                if (k0 == 0)
+                    nc0 = -__half2float(
+                        __ushort_as_half((unsigned short)(__shfl_sync(0xffffffffu, tq[0].x, grp * G) & 0xffffu)));
+#pragma unroll
+                for (int kk = 0; kk < CH; ++kk) {
+                    const int k = k0 + kk;
+                    if (k < S) {
+                        const __half2 ab = *reinterpret_cast<const __half2*>(&tq[kk].x);
+                        const __half2 cd = *reinterpret_cast<const __half2*>(&tq[kk].y);
+                        const float am = add_f16_f32(__low2half(ab), nc0);
+                        dv[k] = fmaf(Vs[kk], fmaf(Us[kk], __high2float(cd), __low2float(cd)),
+                                     fmaf(Us[kk], __high2float(ab), am));
+                        sa = fmaf(pw.w[k], dv[k], sa);
+                        se = fmaf(pw.wr[k], dv[k], se);
+                    }
+                }
+            }
+            // two-pass weighted variance (the form of Eq. 4): the weighted
+            // mean first, then the centred second moment
+            sa = gsum<G>(sa);
+            const float mu = sa * pw.inv_wsum;
 #pragma unroll
             for (int k = 0; k < S; ++k) {
-                float X = fmaf(pw.ou[k], h0x, fmaf(pw.ov[k], h1x, p0x));
-                float Y = fmaf(pw.ou[k], h0y, fmaf(pw.ov[k], h1y, p0y));
-                float Z = fmaf(pw.ou[k], h0z, fmaf(pw.ov[k], h1z, p0z));
-                float iz = rcp_approx(Z);
-                sval[k] = tex_sample(tex, (int)pitch, n_tex, __fmul_rn(X, iz), __fmul_rn(Y, iz));
+                const float e = dv[k] - mu;
+                sb = fmaf(pw.w[k] * e, e, sb);
             }
         } else {
+            const uint2* tex = v.tex;
+            const uint32_t pitch = v.pitch, n_tex = v.n_tex;
             // mixed precision: positions and fractions in FP32, the bilinear
             // interpolation of two samples per half2 instruction, on
             // intensities shifted by the reference patch mean
@@ -405,29 +474,30 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                 sval[k] = s2.x;
                 if (k + 1 < S) sval[k + 1] = s2.y;
             }
-        }
-        // weighted moments in one pass, shifted by one sample of this source
-        // patch (its first sample) so that the variance keeps full precision:
-        // with d = s - c, sum w (s - mu)^2 = sum w d^2 - (sum w d)^2 / W and
-        // sum w r' (s - mu) = sum w r' d - (sum w d / W) sum w r'
-        const float c0 = __shfl_sync(0xffffffffu, sval[0], grp * G);
-        float sa = 0.0f, sb = 0.0f, se = 0.0f;
+            // weighted moments in one pass, shifted by the group's first
+            // sample (an intensity of this source patch): with d = s - c0,
+            // sum w (s - mu)^2 = sum w d^2 - (sum w d)^2 / W; near the flat
+            // limit the denominator is recomputed in FP64 below
+            c0 = __shfl_sync(0xffffffffu, sval[0], grp * G);
 #pragma unroll
-        for (int k = 0; k < S; ++k) {
-            float dv = sval[k] - c0;
-            float t = pw.w[k] * dv;
-            sa += t;
-            sb = fmaf(t, dv, sb);
-            se = fmaf(pw.wr[k], dv, se);
+            for (int k = 0; k < S; ++k) {
+                float dv = sval[k] - c0;
+                float t = pw.w[k] * dv;
+                sa += t;
+                sb = fmaf(t, dv, sb);
+                se = fmaf(pw.wr[k], dv, se);
+            }
         }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
-            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            if constexpr (MIXED) sa += __shfl_xor_sync(0xffffffffu, sa, o);
             sb += __shfl_xor_sync(0xffffffffu, sb, o);
             se += __shfl_xor_sync(0xffffffffu, se, o);
         }
         const float mean_d = sa * pw.inv_wsum;
-        float sdd = fmaf(-mean_d, sa, sb);
+        // sum w (s - mu)^2 (FP32: already centred; mixed: one-pass, shifted)
+        float sdd = MIXED ? fmaf(-mean_d, sa, sb) : sb;
+        // sum w r' (s - mu) = sum w r' d - mu_d sum w r'
         const float srd = fmaf(-mean_d, pw.wr_sum, se);
         if constexpr (MIXED) {
             // a source patch near the flat limit (where the exclusion decision
@@ -466,7 +536,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             float cj = pairs[p].res;
             if (cj < kCmax) {
                 cnt++;
-                inv_sum += 1.0f / fmaxf(cj, kEpsC);
+                inv_sum += rcp_approx(fmaxf(cj, kEpsC));
             }
         }
     if (VIEWS && view_cost) {

@@ -138,17 +138,61 @@ __global__ void __launch_bounds__(kBlock) k_cost(const __grid_constant__ RefCons
 //   groups 0..3: near V-shapes up / down / left / right, six members
 //   groups 4..7: far lines up / down / left / right at distances 5, 7, .., 25
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void near_member(int g, int k, int& dx, int& dy) {
-    // up-pointing pattern, rotated per group
-    const int ux[6] = {0, -1, 1, -2, 0, 2};
-    const int uy[6] = {-1, -2, -2, -3, -3, -3};
-    int a = ux[k], b = uy[k];
-    switch (g) {
-        case 0: dx = a; dy = b; break;
-        case 1: dx = a; dy = -b; break;
-        case 2: dx = b; dy = a; break;
-        default: dx = -b; dy = a; break;
+// offset of member k of group g (members past the group's size: any in-range
+// shift value, masked by the caller)
+__device__ __forceinline__ void group_member(int g, int k, int& dx, int& dy) {
+    if (g < 4) {
+        k = min(k, 5);
+        // up-pointing V {(0,-1), (-1,-2), (1,-2), (-2,-3), (0,-3), (2,-3)},
+        // packed 3 bits per member (x + 2, y + 3), rotated per group
+        const int a = (int)((0x220CAu >> (3 * k)) & 7u) - 2;   // x + 2: 2, 1, 3, 0, 2, 4
+        const int b = (int)((0x4Au >> (3 * k)) & 7u) - 3;      // y + 3: 2, 1, 1, 0, 0, 0
+        switch (g) {
+            case 0: dx = a; dy = b; break;
+            case 1: dx = a; dy = -b; break;
+            case 2: dx = b; dy = a; break;
+            default: dx = -b; dy = a; break;
+        }
+    } else {
+        const int dist = 5 + 2 * k;
+        dx = g == 6 ? -dist : (g == 7 ? dist : 0);
+        dy = g == 4 ? -dist : (g == 5 ? dist : 0);
     }
+}
+
+// Member of group g with the lowest stored cost (in-image members only, the
+// first listed wins a tie), as a pixel index on lane g < 8, or -1.  The 8
+// groups x 16 member slots are spread over 4 registers of the warp (register
+// r, lane l: group 2r + l / 16, member l % 16), each half warp takes the
+// minimum of its register, and the lowest member holding it wins; stored
+// costs are >= 0, so their bit patterns order like the values.  The members
+// have the other colour, which this phase does not write.
+__device__ __forceinline__ int best_members(const RefConst& rc, int px, int py) {
+    const int lane = threadIdx.x & 31, half = lane >> 4, k = lane & 15;
+    unsigned first[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int g = 2 * r + half;
+        int dx, dy;
+        group_member(g, k, dx, dy);
+        const int x2 = px + dx, y2 = py + dy;
+        const bool in = k < (g < 4 ? 6 : 11) && x2 >= 0 && x2 < rc.W && y2 >= 0 && y2 < rc.H;
+        const unsigned bits = in ? __float_as_uint(__ldg(rc.cost + (long long)y2 * rc.W + x2) + 0.0f) : 0xffffffffu;
+        const unsigned mn0 = __reduce_min_sync(0xffffffffu, half ? 0xffffffffu : bits);
+        const unsigned mn1 = __reduce_min_sync(0xffffffffu, half ? bits : 0xffffffffu);
+        first[r] = __ballot_sync(0xffffffffu, in && bits == (half ? mn1 : mn0));
+    }
+    int q = -1;
+    if (lane < 8) {
+        const int g = lane;
+        const unsigned m = (first[g >> 1] >> (16 * (g & 1))) & 0xffffu;
+        if (m) {
+            int dx, dy;
+            group_member(g, __ffs(m) - 1, dx, dy);
+            q = (py + dy) * rc.W + px + dx;
+        }
+    }
+    return q;
 }
 
 template <int G, int S, bool MIXED>
@@ -184,27 +228,9 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
         float4 cur = rc.plane[pix];
         float cur_c = rc.cost[pix];
 
-        // ---- propagation: lane g < 8 scans group g and carries its plane over
-        int q = -1;
-        if (lane < 8) {
-            const int g = lane;
-            float bc = 0.0f;
-            const int cnt = g < 4 ? 6 : 11;
-            for (int k = 0; k < cnt; ++k) {
-                int dx, dy;
-                if (g < 4) near_member(g, k, dx, dy);
-                else {
-                    int dist = 5 + 2 * k;
-                    dx = g == 6 ? -dist : (g == 7 ? dist : 0);
-                    dy = g == 4 ? -dist : (g == 5 ? dist : 0);
-                }
-                int x2 = px + dx, y2 = py + dy;
-                if (x2 < 0 || x2 >= rc.W || y2 < 0 || y2 >= rc.H) continue;
-                int qq = y2 * rc.W + x2;
-                float c = rc.cost[qq];
-                if (q < 0 || c < bc) { q = qq; bc = c; }
-            }
-        }
+        // ---- propagation: lane g < 8 takes group g's cheapest member and
+        // carries its plane over
+        const int q = best_members(rc, px, py);
         float4 np = make_float4(0.f, 0.f, -1.f, 1.f);
         float d = 0.0f;
         bool ok = q >= 0;
