@@ -119,6 +119,7 @@ struct PixWin {
     float wsum;
     float cu_lo, cu_hi, cv_lo, cv_hi;  // corners of the included sample rectangle
     float rx0, rx1, rx2;  // K^-1 (x, y, 1)
+    float rlen;           // |K^-1 (x, y, 1)|
     bool ok;              // pixel exists and its reference patch is not flat
 };
 
@@ -145,7 +146,7 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
     // excluded and padding samples sit on the first included sample (weight 0)
     const float ou_pad = rc.step * ((float)ku_lo - half), ov_pad = rc.step * ((float)kv_lo - half);
     const float rcen = exists ? 4.0f * (float)__ldg(rc.img + (long long)py * rc.W + px) : 0.0f;
-    const float inv_n = 1.0f / (float)n;
+    const float inv_n = rcp_approx((float)n);   // (k + 1/2) / n stays 1/(2n) away from integers
     float sw = 0.0f, swr = 0.0f;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -168,7 +169,8 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
     }
     sw = gsum<G>(sw);
     swr = gsum<G>(swr);
-    float mu = sw > 0.0f ? swr / sw : 0.0f;
+    const float inv_sw = sw > 0.0f ? rcp_approx(sw) : 0.0f;
+    float mu = swr * inv_sw;
     float srr = 0.0f, wrs = 0.0f;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -182,7 +184,7 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
     pw.wr_sum = gsum<G>(wrs);
     pw.wsum = sw;
     pw.mean = mu;
-    pw.inv_wsum = sw > 0.0f ? 1.0f / sw : 0.0f;
+    pw.inv_wsum = inv_sw;
     pw.srr = srr;
     pw.ok = exists && sw > 0.0f && srr >= kTauVar * sw && ku_hi >= 0 && kv_hi >= 0;
     pw.cu_lo = rc.step * ((float)ku_lo - half);
@@ -194,19 +196,20 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
     pw.rx0 = fmaf(Ki[0], x, fmaf(Ki[1], y, Ki[2]));
     pw.rx1 = fmaf(Ki[3], x, fmaf(Ki[4], y, Ki[5]));
     pw.rx2 = fmaf(Ki[6], x, fmaf(Ki[7], y, Ki[8]));
+    pw.rlen = sqrtf(pw.rx0 * pw.rx0 + pw.rx1 * pw.rx1 + pw.rx2 * pw.rx2);
 }
 
-// Source-view constants copied to shared memory once per block (72 bytes:
-// conflict-free when the groups of a warp read different views).
-struct ViewSm {
-    float A[9];
-    float b[3];
-    float wm1, hm1;       // W - 1, H - 1
-    uint32_t pitch, n_tex;
+// Source-view constants copied to shared memory once per block (80 bytes,
+// read as 16-byte words).
+struct __align__(16) ViewSm {
     const uint2* tex;
     // index of texel (i + 1, j + 1) = bits(1.5 * 2^24 + 2 j) * pitch
     // + bits(1.5 * 2^24 + 2 i) + toff (mod 2^32), see tex_sample
-    uint32_t toff, pad_;
+    uint32_t pitch, toff;
+    uint32_t last, pad_;  // last texel index (W + 1) (H + 1) - 1
+    float wm1, hm1;       // W - 1, H - 1
+    float A[9];
+    float b[3];
 };
 
 __device__ __forceinline__ void load_views(const RefConst& rc, ViewSm* sv) {
@@ -217,7 +220,7 @@ __device__ __forceinline__ void load_views(const RefConst& rc, ViewSm* sv) {
         sv[j].wm1 = (float)(P.W - 1);
         sv[j].hm1 = (float)(P.H - 1);
         sv[j].pitch = (uint32_t)P.pitch;
-        sv[j].n_tex = P.n_tex;
+        sv[j].last = P.n_tex - 1u;
         sv[j].tex = P.tex;
         sv[j].toff = (uint32_t)(P.pitch + 1) * (uint32_t)(1 - kMagic2Bits);
     }
@@ -243,28 +246,28 @@ __device__ __forceinline__ Cand make_cand(const RefConst& rc, const PixWin<S>& p
     c.n0 = n0; c.n1 = n1; c.n2 = n2; c.d = d;
     const float* Ki = rc.Kinv;
     float nr = n0 * pw.rx0 + n1 * pw.rx1 + n2 * pw.rx2;
-    float rlen = sqrtf(pw.rx0 * pw.rx0 + pw.rx1 * pw.rx1 + pw.rx2 * pw.rx2);
     float k0 = Ki[0] * n0 + Ki[3] * n1 + Ki[6] * n2;
     float k1 = Ki[1] * n0 + Ki[4] * n1 + Ki[7] * n2;
     bool corners = fmaf(pw.cu_lo, k0, fmaf(pw.cv_lo, k1, nr)) < 0.0f && fmaf(pw.cu_hi, k0, fmaf(pw.cv_lo, k1, nr)) < 0.0f &&
                    fmaf(pw.cu_lo, k0, fmaf(pw.cv_hi, k1, nr)) < 0.0f && fmaf(pw.cu_hi, k0, fmaf(pw.cv_hi, k1, nr)) < 0.0f;
-    c.ok = want && pw.ok && d > 0.0f && d < 3.0e38f && nr < -kGraze * rlen && corners;
-    float inv_rho = c.ok ? 1.0f / (d * nr) : 0.0f;
+    c.ok = want && pw.ok && d > 0.0f && d < 3.0e38f && nr < -kGraze * pw.rlen && corners;
+    float inv_rho = c.ok ? rcp_approx(d * nr) : 0.0f;
     c.m0 = k0 * inv_rho;
     c.m1 = k1 * inv_rho;
-    c.invd = c.ok ? 1.0f / d : 0.0f;
+    c.invd = c.ok ? rcp_approx(d) : 0.0f;
     return c;
 }
 
-// One listed (hypothesis, view) pair in shared memory: the homography
-// columns H e1, H e2 and H x (x, y rows shifted by -1/2 and doubled for
-// tex_sample), the view,
-// and after evaluation its per-view cost (C_max when excluded).
-struct PairSm {
+// One listed (hypothesis, view) pair in shared memory (three 16-byte
+// words): the homography columns H e1, H e2 and H x (x, y rows shifted by
+// -1/2 and doubled for tex_sample), the view, and after evaluation its
+// per-view cost C(x, j) (C_max when excluded) and Eq. 5 weight
+// 1 / max(C(x, j), 1e-6) (0 when excluded).
+struct __align__(16) PairSm {
     float h0x, h0y, h0z, h1x;
     float h1y, h1z, p0x, p0y;
-    float p0z, res;
-    int j, c;
+    float p0z, res, inv;
+    int j;
 };
 
 // Shared-memory bytes of a 128-thread block: the view table and, per warp,
@@ -286,13 +289,14 @@ __device__ __forceinline__ bool same_plane(const float4& a, const float4& b) {
 
 // Costs C(x) (Eq. 5) of up to 8 hypotheses of the warp's pixel: lane c < nc
 // holds hypothesis c on entry and its cost on return.
-//   1. the (hypothesis, view) pairs whose window maps inside the source
-//      image (exact corner test: the image of the window is convex, w > 0
-//      included) are listed in `pairs` (per-warp shared memory, nc * n_src
-//      entries) in hypothesis-major, view-minor order, with their homography;
+//   1. the (hypothesis, view) pairs of the usable hypotheses whose window
+//      maps inside the source image (corner test: the image of the window is
+//      convex, w > 0 included) are listed in `pairs` (per-warp shared memory,
+//      nc * n_src entries) in hypothesis-major, view-minor order, with their
+//      homography;
 //   2. each group of G lanes takes the next pair: S bilinear gathers per
-//      lane, shifted one-pass weighted moments with one group reduction
-//      phase, ZNCC (Eq. 4),
+//      lane, the weighted mean, then the centred moments (group reductions),
+//      ZNCC (Eq. 4),
 //      C(x,j) = 1 - Z; a view is excluded when its weighted variance is below
 //      1e-6 on the [0,1] scale (reading);
 //   3. lane c folds the per-view results of hypothesis c in view order
@@ -305,9 +309,20 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
     const int V = rc.n_src;
-    const int P = nc * V;
     const float x = (float)px, y = (float)py;
-    // ---- 1. list the pairs that map inside the source images
+    // ---- 1. list the pairs that map inside the source images, over the
+    // usable hypotheses only: lane r < nok holds the lane of the r-th one
+    const unsigned okm = __ballot_sync(0xffffffffu, lane < nc && my.ok);
+    const int nok = __popc(okm), rank = __popc(okm & ((1u << lane) - 1u));
+    int hyp_of;
+    {
+        unsigned m = okm;   // drop the lowest set bit `lane` times (nc <= 8)
+#pragma unroll
+        for (int t = 0; t < 7; ++t)
+            if (t < lane) m &= m - 1u;
+        hyp_of = m ? __ffs(m) - 1 : 0;
+    }
+    const int P = nok * V;
     int count = 0, my_cnt = 0;
     // floor(i / V) = (i * ceil(2^16 / V)) >> 16 exactly for i < 2^16 / V
     // (i < 8 * MVS_MAX_SRC here)
@@ -315,12 +330,12 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
     for (int base = 0; base < P; base += 32) {
         int i = base + lane;
         bool act = i < P;
-        int c = act ? (int)(((uint32_t)i * vmagic) >> 16) : 0;
-        int j = act ? i - c * V : 0;
+        int cr = act ? (int)(((uint32_t)i * vmagic) >> 16) : 0;
+        int j = act ? i - cr * V : 0;
+        int c = __shfl_sync(0xffffffffu, hyp_of, cr);
         float m0 = __shfl_sync(0xffffffffu, my.m0, c);
         float m1 = __shfl_sync(0xffffffffu, my.m1, c);
         float invd = __shfl_sync(0xffffffffu, my.invd, c);
-        bool cok = __shfl_sync(0xffffffffu, (int)my.ok, c) != 0;
         const ViewSm& v = sv[j];
         float h0z = fmaf(v.b[2], m0, v.A[6]), h1z = fmaf(v.b[2], m1, v.A[7]);
         float p0z = fmaf(v.b[2], invd, fmaf(v.A[6], x, fmaf(v.A[7], y, v.A[8])));
@@ -331,7 +346,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         float h1y = fmaf(-0.5f, h1z, fmaf(v.b[1], m1, v.A[4]));
         float p0x = fmaf(-0.5f, p0z, fmaf(v.b[0], invd, fmaf(v.A[0], x, fmaf(v.A[1], y, v.A[2]))));
         float p0y = fmaf(-0.5f, p0z, fmaf(v.b[1], invd, fmaf(v.A[3], x, fmaf(v.A[4], y, v.A[5]))));
-        bool ok = act && cok;
+        bool ok = act;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float cu = (k & 1) ? pw.cu_hi : pw.cu_lo, cv = (k & 2) ? pw.cv_hi : pw.cv_lo;
@@ -347,11 +362,11 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             PairSm& q = pairs[count + __popc(m & ((1u << lane) - 1u))];
             q.h0x = 2.0f * h0x; q.h0y = 2.0f * h0y; q.h0z = h0z; q.h1x = 2.0f * h1x;
             q.h1y = 2.0f * h1y; q.h1z = h1z; q.p0x = 2.0f * p0x; q.p0y = 2.0f * p0y;
-            q.p0z = p0z; q.j = j; q.c = c;
+            q.p0z = p0z; q.j = j;
         }
         count += __popc(m);
-        if (lane < nc) {   // pairs of hypothesis `lane` in this chunk
-            int lo = max(0, lane * V - base), hi = min(32, lane * V + V - base);
+        if ((okm >> lane) & 1u) {   // pairs of hypothesis `lane` in this chunk
+            int lo = max(0, rank * V - base), hi = min(32, rank * V + V - base);
             if (hi > lo) {
                 unsigned rm = (hi == 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
                 my_cnt += __popc(m & rm);
@@ -386,7 +401,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             // of other samples of a plane seen almost edge-on by the source
             // need not.
             const uint2* tex = v.tex;
-            const uint32_t pitch = v.pitch, toff = v.toff, last = v.n_tex - 1u;
+            const uint32_t pitch = v.pitch, toff = v.toff, last = v.last;
             // gathers in chunks of up to 8 slots (registers); the intensities
             // are shifted by c0 = the 2 x 2 texel sum at the group's first
             // sample (an intensity of this source patch), which enters through
@@ -440,7 +455,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             }
         } else {
             const uint2* tex = v.tex;
-            const uint32_t pitch = v.pitch, n_tex = v.n_tex;
+            const uint32_t pitch = v.pitch, last = v.last;
             // mixed precision: positions and fractions in FP32, the bilinear
             // interpolation of two samples per half2 instruction, on
             // intensities shifted by the reference patch mean
@@ -462,7 +477,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                     Vs[h] = __fsub_rn(ys2, __fsub_rn(ty, kMagic2));
                     uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx) +
                                    (pitch + 1u) * (uint32_t)(1 - kMagic2Bits);
-                    q[h] = __ldg(tex + min(idx, n_tex - 1u));
+                    q[h] = __ldg(tex + min(idx, last));
                 }
                 uint32_t ab = __byte_perm(q[0].x, q[1].x, 0x5410), bb = __byte_perm(q[0].x, q[1].x, 0x7632);
                 uint32_t cb = __byte_perm(q[0].y, q[1].y, 0x5410), db = __byte_perm(q[0].y, q[1].y, 0x7632);
@@ -516,14 +531,14 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                 if (near_flat) sdd = (float)v;
             }
         }
+        // ZNCC, C(x, j) = 1 - Z, and its Eq. 5 weight (all lanes compute,
+        // the group's first lane stores)
+        const bool flat = !(sdd >= kTauVar * pw.wsum);
+        const float z = fminf(1.0f, fmaxf(-1.0f, srd * rsqrtf(pw.srr * sdd)));
+        const float cj = flat ? kCmax : fminf(1.0f - z, kCmax);
         if (has && lg == 0) {
-            float cj = kCmax;
-            if (sdd >= kTauVar * pw.wsum) {
-                float z = srd * rsqrtf(pw.srr * sdd);
-                z = fminf(1.0f, fmaxf(-1.0f, z));
-                cj = fminf(1.0f - z, kCmax);
-            }
             pairs[it].res = cj;
+            pairs[it].inv = cj < kCmax ? rcp_approx(fmaxf(cj, kEpsC)) : 0.0f;
             n_evals++;
         }
     }
@@ -531,13 +546,12 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
     // ---- 3. fold hypothesis `lane`'s views in view order
     int cnt = 0;
     float inv_sum = 0.0f;
-    if (lane < nc)
-        for (int p = start; p < start + my_cnt; ++p) {
-            float cj = pairs[p].res;
-            if (cj < kCmax) {
-                cnt++;
-                inv_sum += rcp_approx(fmaxf(cj, kEpsC));
-            }
+    const int max_cnt = __reduce_max_sync(0xffffffffu, (unsigned)my_cnt);   // warp-uniform trip count
+    for (int t = 0; t < max_cnt; ++t)
+        if (t < my_cnt) {
+            const float wv = pairs[start + t].inv;
+            cnt += wv > 0.0f;
+            inv_sum += wv;
         }
     if (VIEWS && view_cost) {
         if (lane < V) view_cost[lane] = kCmax;
@@ -545,7 +559,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         for (int p = lane; p < count; p += 32) view_cost[pairs[p].j] = pairs[p].res;
     }
     __syncwarp();
-    return (lane < nc && my.ok && cnt > 0) ? (float)cnt / inv_sum : kCmax;
+    return (lane < nc && my.ok && cnt > 0) ? (float)cnt * rcp_approx(inv_sum) : kCmax;
 }
 
 // adds the warp's evaluated (pixel, hypothesis, view) count to the counter

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             float rho = np.w * (np.x * r0 + np.y * r1 + np.z * r2);
             float den = np.x * pw.rx0 + np.y * pw.rx1 + np.z * pw.rx2;
             ok = den < 0.0f;
-            d = ok ? rho / den : 0.0f;
+            d = ok ? rho * rcp_approx(den) : 0.0f;
             ok = ok && d >= rc.d_lo && d <= rc.d_hi;
         }
         // A carried-over plane equal (to float rounding) to the pixel's own
