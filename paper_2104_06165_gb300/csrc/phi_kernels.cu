@@ -244,12 +244,20 @@ __global__ void __launch_bounds__(kBlock, 3) k_phi_cost(const __grid_constant__ 
 // backward pass; decode = per-node argmin of the belief (lowest label on a
 // tie).  The raster order is run as anti-diagonal wavefronts (a node only
 // depends on its up / left neighbours in the forward pass and on its down /
-// right neighbours in the backward pass), which gives the same result as the
-// sequential sweep: one cooperative launch per pass walks the gw + gh - 1
-// node diagonals, the nodes of a diagonal in parallel, with a grid-wide
-// barrier between diagonals.
+// right neighbours in the backward pass), which gives the same messages as
+// the sequential sweep.  One cooperative launch per pass pipelines strips of
+// kTrwRows node rows: a block owns strips b, b + gridDim.x, ... and walks each
+// in tiles of kTrwCols columns; at stage k strip s takes tile k - s, whose
+// upper neighbour tile (strip s - 1) was finished at stage k - 1 and whose
+// left neighbour tile by the same block at stage k - 1.  Stages are separated
+// by a grid barrier (ns + nb - 1 of them instead of gw + gh - 1), and the
+// anti-diagonals of a tile by a block barrier.  Inside a tile one warp takes
+// one node: lane (d, lq, l) evaluates the min-sum term of own label l towards
+// label lq of the d-th outgoing neighbour.  Messages are written by other
+// multiprocessors, so they are read and written at L2 (ld/st .cg).  The
+// backward pass runs the same schedule on the mirrored grid.
 // ---------------------------------------------------------------------------
-constexpr int kWaveBlock = 256;
+constexpr int kTrwRows = 32, kTrwCols = 32, kTrwBlock = 32 * kTrwRows;
 
 struct MrfBufs {
     int gw, gh;
@@ -292,55 +300,61 @@ __device__ __forceinline__ float pair_energy(float h1, float h2, float k3) {
     return -2.0f * logf(k3 - fminf(1.0f, rel));
 }
 
-__device__ void trw_node(const MrfBufs& mb, int x, int y, bool forward, float k3) {
-    long long i = (long long)y * mb.gw + x;
-    int L = mb.nlab[i];
-    if (!L) return;
+// Messages of node (x, y) to its later (forward) or earlier (backward)
+// neighbours; called by a whole warp.
+__device__ __forceinline__ void trw_node_warp(const MrfBufs& mb, int x, int y, bool forward, float k3) {
+    const int lane = threadIdx.x & 31;
+    const long long i = (long long)y * mb.gw + x;
+    const int L = mb.nlab[i];
+    if (!L) return;                                       // warp-uniform
     const int nbx[4] = {0, 0, -1, 1}, nby[4] = {-1, 1, 0, 0};
-    float bel[4];
-    for (int l = 0; l < 4; ++l) {
-        float b = mb.un[4 * i + l];
-        for (int d = 0; d < 4; ++d) b += mb.msg[16 * i + 4 * d + l];
-        bel[l] = b;
-    }
-    int before = 0, after = 0;
-    bool pres[4];
+    int before = 0, after = 0, Lq = 0;
+    const int dsel = lane >> 4, lq = (lane >> 2) & 3, l = lane & 3;
+    const int dir = forward ? (dsel ? 3 : 1) : (dsel ? 2 : 0);
+    long long q = 0;
+#pragma unroll
     for (int d = 0; d < 4; ++d) {
-        int qx = x + nbx[d], qy = y + nby[d];
-        pres[d] = qx >= 0 && qx < mb.gw && qy >= 0 && qy < mb.gh && mb.nlab[(long long)qy * mb.gw + qx] > 0;
-        if (pres[d]) { if (d == 0 || d == 2) before++; else after++; }
+        const int qx = x + nbx[d], qy = y + nby[d];
+        const bool in = qx >= 0 && qx < mb.gw && qy >= 0 && qy < mb.gh;
+        const long long qi = (long long)qy * mb.gw + qx;
+        const int nq = in ? mb.nlab[qi] : 0;
+        if (nq > 0) { if (d == 0 || d == 2) before++; else after++; }
+        if (d == dir) { Lq = nq; q = qi; }
     }
-    int mx = max(before, after);
-    float gamma = mx > 0 ? 1.0f / (float)mx : 1.0f;
-    for (int d = 0; d < 4; ++d) {
-        bool later = (d == 1 || d == 3);
-        if (later != forward || !pres[d]) continue;
-        long long q = (long long)(y + nby[d]) * mb.gw + (x + nbx[d]);
-        int Lq = mb.nlab[q];
-        float out[4], mn = 3.0e38f;
-        for (int lq = 0; lq < Lq; ++lq) {
-            float best = 3.0e38f;
-            for (int l = 0; l < L; ++l) {
-                float e = gamma * bel[l] - mb.msg[16 * i + 4 * d + l] + pair_energy(mb.lab[4 * i + l], mb.lab[4 * q + lq], k3);
-                best = fminf(best, e);
-            }
-            out[lq] = best;
-            mn = fminf(mn, best);
-        }
-        int od = d ^ 1;
-        for (int lq = 0; lq < Lq; ++lq) mb.msg[16 * q + 4 * od + lq] = out[lq] - mn;
-    }
+    const int mx = max(before, after);
+    const float gamma = mx > 0 ? 1.0f / (float)mx : 1.0f;
+    // belief of own label l: unary + the four incoming messages
+    float bel = mb.un[4 * i + l];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) bel += __ldcg(mb.msg + 16 * i + 4 * d + l);
+    float e = 3.0e38f;
+    if (l < L && lq < Lq)
+        e = gamma * bel - __ldcg(mb.msg + 16 * i + 4 * dir + l) + pair_energy(mb.lab[4 * i + l], mb.lab[4 * q + lq], k3);
+    // minimum over own labels, then over the target's labels (normalisation)
+    e = fminf(e, __shfl_xor_sync(0xffffffffu, e, 1));
+    e = fminf(e, __shfl_xor_sync(0xffffffffu, e, 2));
+    float mn = fminf(e, __shfl_xor_sync(0xffffffffu, e, 4));
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 8));
+    if (l == 0 && lq < Lq) __stcg(mb.msg + 16 * q + 4 * (dir ^ 1) + lq, e - mn);
 }
 
-__global__ void __launch_bounds__(kWaveBlock) k_trw_wave(MrfBufs mb, bool forward, float k3) {
+__global__ void __launch_bounds__(kTrwBlock, 1) k_trw_strips(MrfBufs mb, bool forward, float k3) {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
-    const int nd = mb.gw + mb.gh - 1;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    for (int s = 0; s < nd; ++s) {
-        const int d = forward ? s : nd - 1 - s;
-        const int x_lo = max(0, d - (mb.gh - 1)), x_hi = min(d, mb.gw - 1);
-        for (int x = x_lo + tid; x <= x_hi; x += nth) trw_node(mb, x, d - x, forward, k3);
-        grid.sync();   // every block runs the same number of steps
+    const int warp = threadIdx.x >> 5;
+    const int ns = (mb.gh + kTrwRows - 1) / kTrwRows, nb = (mb.gw + kTrwCols - 1) / kTrwCols;
+    for (int k = 0; k < ns + nb - 1; ++k) {
+        for (int st = blockIdx.x; st < ns; st += gridDim.x) {
+            const int c = k - st;
+            if (c < 0 || c >= nb) continue;              // block-uniform
+            for (int t = 0; t < kTrwRows + kTrwCols - 1; ++t) {
+                const int u = t - warp;                   // tile column of this warp's node
+                const int xf = c * kTrwCols + u, yf = st * kTrwRows + warp;   // pass-local coordinates
+                if (u >= 0 && u < kTrwCols && xf < mb.gw && yf < mb.gh)
+                    trw_node_warp(mb, forward ? xf : mb.gw - 1 - xf, forward ? yf : mb.gh - 1 - yf, forward, k3);
+                __syncthreads();
+            }
+        }
+        grid.sync();                                      // every block runs the same number of stages
     }
 }
 
@@ -540,7 +554,7 @@ cudaError_t launch_phi_mrf(int W, int H, const uint8_t* known, const float* dept
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // enough co-resident blocks for the longest diagonal (min(gw, gh) nodes)
+    // one block per strip, at most as many as are co-resident
     static int max_blocks = 0;
     {
         static std::mutex mu;
@@ -549,17 +563,17 @@ cudaError_t launch_phi_mrf(int W, int H, const uint8_t* known, const float* dept
             int dev = 0, sms = 0, per_sm = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trw_wave, kWaveBlock, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trw_strips, kTrwBlock, 0);
             max_blocks = std::max(1, sms * per_sm);
         }
     }
-    const int want = (std::min(mb.gw, mb.gh) + kWaveBlock - 1) / kWaveBlock;
-    dim3 grid(std::max(1, std::min(want, max_blocks))), block(kWaveBlock);
+    const int want = (mb.gh + kTrwRows - 1) / kTrwRows;
+    dim3 grid(std::max(1, std::min(want, max_blocks))), block(kTrwBlock);
     for (int it = 0; it < iters; ++it)
         for (int pass = 0; pass < 2; ++pass) {
             bool forward = pass == 0;
             void* args[] = {(void*)&mb, (void*)&forward, (void*)&k3};
-            e = cudaLaunchCooperativeKernel((const void*)k_trw_wave, grid, block, args, 0, s);
+            e = cudaLaunchCooperativeKernel((const void*)k_trw_strips, grid, block, args, 0, s);
             count_launch();
             if (e != cudaSuccess) return e;
         }
