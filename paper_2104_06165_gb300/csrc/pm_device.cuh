@@ -13,6 +13,7 @@
 // fall outside a source and pixels with a flat reference patch therefore
 // cost no gathers and leave no lane idle.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_fp16.h>
 #include "mvs_internal.h"
@@ -212,6 +213,11 @@ struct __align__(16) ViewSm {
     float b[3];
 };
 
+static_assert(sizeof(ViewSm) == 80 && offsetof(ViewSm, pitch) == 8 && offsetof(ViewSm, toff) == 12 &&
+                  offsetof(ViewSm, last) == 16 && offsetof(ViewSm, wm1) == 24 && offsetof(ViewSm, A) == 32 &&
+                  offsetof(ViewSm, b) == 68,
+              "eval_batch reads ViewSm as 128-bit words");
+
 __device__ __forceinline__ void load_views(const RefConst& rc, ViewSm* sv) {
     for (int j = threadIdx.x; j < rc.n_src; j += blockDim.x) {
         const PairConst& P = rc.pair[j];
@@ -269,6 +275,10 @@ struct __align__(16) PairSm {
     float p0z, res, inv;
     int j;
 };
+
+static_assert(sizeof(PairSm) == 48 && offsetof(PairSm, h1y) == 16 && offsetof(PairSm, p0z) == 32 &&
+                  offsetof(PairSm, res) == 36 && offsetof(PairSm, inv) == 40 && offsetof(PairSm, j) == 44,
+              "eval_batch reads and writes PairSm as 128-bit words");
 
 // Shared-memory bytes of a 128-thread block: the view table and, per warp,
 // room for 8 hypotheses x n_src pairs.
@@ -336,16 +346,20 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         float m0 = __shfl_sync(0xffffffffu, my.m0, c);
         float m1 = __shfl_sync(0xffffffffu, my.m1, c);
         float invd = __shfl_sync(0xffffffffu, my.invd, c);
-        const ViewSm& v = sv[j];
-        float h0z = fmaf(v.b[2], m0, v.A[6]), h1z = fmaf(v.b[2], m1, v.A[7]);
-        float p0z = fmaf(v.b[2], invd, fmaf(v.A[6], x, fmaf(v.A[7], y, v.A[8])));
+        // the view record as 128-bit words: (wm1, hm1) in word 1, A and b in 2..4
+        const float4* vw = reinterpret_cast<const float4*>(sv + j);
+        const float4 w1 = vw[1], w2 = vw[2], w3 = vw[3], w4 = vw[4];
+        const float A0 = w2.x, A1 = w2.y, A2 = w2.z, A3 = w2.w, A4 = w3.x, A5 = w3.y, A6 = w3.z, A7 = w3.w;
+        const float A8 = w4.x, b0 = w4.y, b1 = w4.z, b2 = w4.w;
+        float h0z = fmaf(b2, m0, A6), h1z = fmaf(b2, m1, A7);
+        float p0z = fmaf(b2, invd, fmaf(A6, x, fmaf(A7, y, A8)));
         // coordinates shifted by -1/2 (tex_sample's convention)
-        float h0x = fmaf(-0.5f, h0z, fmaf(v.b[0], m0, v.A[0]));
-        float h0y = fmaf(-0.5f, h0z, fmaf(v.b[1], m0, v.A[3]));
-        float h1x = fmaf(-0.5f, h1z, fmaf(v.b[0], m1, v.A[1]));
-        float h1y = fmaf(-0.5f, h1z, fmaf(v.b[1], m1, v.A[4]));
-        float p0x = fmaf(-0.5f, p0z, fmaf(v.b[0], invd, fmaf(v.A[0], x, fmaf(v.A[1], y, v.A[2]))));
-        float p0y = fmaf(-0.5f, p0z, fmaf(v.b[1], invd, fmaf(v.A[3], x, fmaf(v.A[4], y, v.A[5]))));
+        float h0x = fmaf(-0.5f, h0z, fmaf(b0, m0, A0));
+        float h0y = fmaf(-0.5f, h0z, fmaf(b1, m0, A3));
+        float h1x = fmaf(-0.5f, h1z, fmaf(b0, m1, A1));
+        float h1y = fmaf(-0.5f, h1z, fmaf(b1, m1, A4));
+        float p0x = fmaf(-0.5f, p0z, fmaf(b0, invd, fmaf(A0, x, fmaf(A1, y, A2))));
+        float p0y = fmaf(-0.5f, p0z, fmaf(b1, invd, fmaf(A3, x, fmaf(A4, y, A5))));
         bool ok = act;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -355,14 +369,14 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             float cz = fmaf(cu, h0z, fmaf(cv, h1z, p0z));
             float icz = rcp_approx(cz);
             float xs = cx * icz, ys = cy * icz;
-            ok = ok && cz > 0.0f && xs >= -0.5f && xs <= v.wm1 - 0.5f && ys >= -0.5f && ys <= v.hm1 - 0.5f;
+            ok = ok && cz > 0.0f && xs >= -0.5f && xs <= w1.z - 0.5f && ys >= -0.5f && ys <= w1.w - 0.5f;
         }
         unsigned m = __ballot_sync(0xffffffffu, ok);
         if (ok) {   // stored with x and y doubled (tex_sample's convention)
-            PairSm& q = pairs[count + __popc(m & ((1u << lane) - 1u))];
-            q.h0x = 2.0f * h0x; q.h0y = 2.0f * h0y; q.h0z = h0z; q.h1x = 2.0f * h1x;
-            q.h1y = 2.0f * h1y; q.h1z = h1z; q.p0x = 2.0f * p0x; q.p0y = 2.0f * p0y;
-            q.p0z = p0z; q.j = j;
+            float4* qw = reinterpret_cast<float4*>(pairs + count + __popc(m & ((1u << lane) - 1u)));
+            qw[0] = make_float4(2.0f * h0x, 2.0f * h0y, h0z, 2.0f * h1x);
+            qw[1] = make_float4(2.0f * h1y, h1z, 2.0f * p0x, 2.0f * p0y);
+            qw[2] = make_float4(p0z, 0.0f, 0.0f, __int_as_float(j));
         }
         count += __popc(m);
         if ((okm >> lane) & 1u) {   // pairs of hypothesis `lane` in this chunk
@@ -386,10 +400,14 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
     for (int r = 0; r < count; r += NG) {
         int it = r + grp;
         bool has = it < count;
-        const PairSm& q = pairs[has ? it : 0];
-        const float h0x = q.h0x, h0y = q.h0y, h0z = q.h0z, h1x = q.h1x;
-        const float h1y = q.h1y, h1z = q.h1z, p0x = q.p0x, p0y = q.p0y, p0z = q.p0z;
-        const ViewSm& v = sv[q.j];
+        const float4* qw = reinterpret_cast<const float4*>(pairs + (has ? it : 0));
+        const float4 qa = qw[0], qb = qw[1], qc = qw[2];
+        const float h0x = qa.x, h0y = qa.y, h0z = qa.z, h1x = qa.w;
+        const float h1y = qb.x, h1z = qb.y, p0x = qb.z, p0y = qb.w, p0z = qc.x;
+        // view words 0 (texels, pitch, toff) and 1 (last texel)
+        const uint4 v0 = reinterpret_cast<const uint4*>(sv + __float_as_int(qc.w))[0];
+        const uint32_t v_last = reinterpret_cast<const uint4*>(sv + __float_as_int(qc.w))[1].x;
+        const uint2* v_tex = reinterpret_cast<const uint2*>(((unsigned long long)v0.y << 32) | v0.x);
         float sa = 0.0f, sb = 0.0f, se = 0.0f;
         float sval[S], c0 = 0.0f;   // mixed precision only: the samples and their shift
         if constexpr (!MIXED) {
@@ -400,8 +418,8 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             // listed window corners lie inside the source, but FP32 positions
             // of other samples of a plane seen almost edge-on by the source
             // need not.
-            const uint2* tex = v.tex;
-            const uint32_t pitch = v.pitch, toff = v.toff, last = v.last;
+            const uint2* tex = v_tex;
+            const uint32_t pitch = v0.z, toff = v0.w, last = v_last;
             // gathers in chunks of up to 8 slots (registers); the intensities
             // are shifted by c0 = the 2 x 2 texel sum at the group's first
             // sample (an intensity of this source patch), which enters through
@@ -454,8 +472,8 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                 sb = fmaf(pw.w[k] * e, e, sb);
             }
         } else {
-            const uint2* tex = v.tex;
-            const uint32_t pitch = v.pitch, last = v.last;
+            const uint2* tex = v_tex;
+            const uint32_t pitch = v0.z, last = v_last;
             // mixed precision: positions and fractions in FP32, the bilinear
             // interpolation of two samples per half2 instruction, on
             // intensities shifted by the reference patch mean

@@ -195,33 +195,71 @@ __device__ __forceinline__ int best_members(const RefConst& rc, int px, int py) 
     return q;
 }
 
+// Refinement perturbations of one pixel, drawn ahead for the next 32 pixels
+// of a warp (one lane each): delta_d, and cos / sin of delta_theta and of
+// delta_phi.  20 bytes per pixel, after the pair lists.
+__host__ __device__ constexpr size_t phase_smem_bytes(int n_src, int warps) {
+    return smem_block_bytes(n_src, warps) + (size_t)warps * 32 * (sizeof(float4) + sizeof(float));
+}
+
+// Tiles are visited in super-tiles of 8 x 16 tiles so that the pixels in
+// flight at once form a compact region (a smaller source footprint in L2;
+// within a phase the order of the pixels does not change the result).
+// Pixel of the active colour that warp `warp` takes in tile t, or -1.
+template <int TX, int TY>
+__device__ __forceinline__ long long phase_pixel(const RefConst& rc, long long t, int warp, int color, int& px,
+                                                 int& py) {
+    constexpr int kSTX = 8, kSTY = 16;
+    const int Wa = (rc.W + 1) >> 1;
+    const int ntx = (Wa + TX - 1) / TX, nty = (rc.H + TY - 1) / TY;
+    const int nstx = (ntx + kSTX - 1) / kSTX;
+    const int sti = (int)(t / (kSTX * kSTY)), r = (int)(t % (kSTX * kSTY));
+    const int tx = (sti % nstx) * kSTX + r % kSTX, ty = (sti / nstx) * kSTY + r / kSTX;
+    const int ax = tx * TX + warp % TX;
+    py = ty * TY + warp / TX;
+    px = 2 * ax + ((py + color) & 1);
+    if (tx >= ntx || ty >= nty || ax >= Wa || py >= rc.H || px >= rc.W) return -1;
+    return (long long)py * rc.W + px;
+}
+
 template <int G, int S, bool MIXED>
 __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
     k_phase(const __grid_constant__ RefConst rc, int phase) {
     constexpr int kTileX = PhaseTile<S>::TX, kTileY = PhaseTile<S>::TY;
-    extern __shared__ __align__(16) unsigned char smem[];   // smem_block_bytes(n_src, PhaseTile<S>::WARPS)
+    constexpr int kWarpsB = PhaseTile<S>::WARPS;
+    extern __shared__ __align__(16) unsigned char smem[];   // phase_smem_bytes(n_src, PhaseTile<S>::WARPS)
     ViewSm* views = reinterpret_cast<ViewSm*>(smem);
     load_views(rc, views);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int color = phase & 1;
+    float4* draw4 = reinterpret_cast<float4*>(smem + smem_block_bytes(rc.n_src, kWarpsB)) + warp * 32;
+    float* draw1 = reinterpret_cast<float*>(reinterpret_cast<float4*>(smem + smem_block_bytes(rc.n_src, kWarpsB)) +
+                                            kWarpsB * 32) + warp * 32;
     const int Wa = (rc.W + 1) >> 1;
     const int ntx = (Wa + kTileX - 1) / kTileX, nty = (rc.H + kTileY - 1) / kTileY;
-    // tiles are visited in super-tiles of 8 x 16 tiles so that the pixels in
-    // flight at once form a compact region (a smaller source footprint in L2;
-    // within a phase the order of the pixels does not change the result)
-    constexpr int kSTX = 8, kSTY = 16;
-    const int nstx = (ntx + kSTX - 1) / kSTX, nsty = (nty + kSTY - 1) / kSTY;
-    const long long ntiles = (long long)nstx * nsty * (kSTX * kSTY);
-    unsigned nev = 0;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int sti = (int)(t / (kSTX * kSTY)), r = (int)(t % (kSTX * kSTY));
-        const int tx = (sti % nstx) * kSTX + r % kSTX, ty = (sti / nstx) * kSTY + r / kSTX;
-        const int ax = tx * kTileX + warp % kTileX;
-        const int py = ty * kTileY + warp / kTileX;
-        if (tx >= ntx || ty >= nty || ax >= Wa || py >= rc.H) continue;   // warp-uniform
-        const int px = 2 * ax + ((py + color) & 1);
-        if (px >= rc.W) continue;
-        const long long pix = (long long)py * rc.W + px;
+    const int nstx = (ntx + 7) / 8, nsty = (nty + 15) / 16;
+    const long long ntiles = (long long)nstx * nsty * (8 * 16);
+    unsigned nev = 0, it = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        if ((it & 31u) == 0) {
+            // refinement perturbations (Sec. III-C) of this warp's next 32
+            // pixels, one per lane: delta_d in [-d_hi/4, d_hi/4],
+            // delta_theta in [-pi/2, pi/2], delta_phi in [-pi/12, pi/12]
+            int qx, qy;
+            const long long q = phase_pixel<kTileX, kTileY>(rc, t + (long long)lane * gridDim.x, warp, color, qx, qy);
+            float u[3];
+            draws3(rc, q < 0 ? 0 : q, phase, u);
+            float sdt, cdt, sdp, cdp;
+            sincosf((2.0f * u[1] - 1.0f) * (kPi * 0.5f), &sdt, &cdt);
+            sincosf((2.0f * u[2] - 1.0f) * (kPi / 12.0f), &sdp, &cdp);
+            __syncwarp();
+            draw4[lane] = make_float4((2.0f * u[0] - 1.0f) * (rc.d_hi * 0.25f), cdt, sdt, cdp);
+            draw1[lane] = sdp;
+            __syncwarp();
+        }
+        int px, py;
+        const long long pix = phase_pixel<kTileX, kTileY>(rc, t, warp, color, px, py);
+        if (pix < 0) continue;   // warp-uniform
         PixWin<S> pw;
         build_window<G, S>(rc, px, py, true, pw);
         if (!pw.ok) continue;                           // flat patch: every hypothesis costs C_max
@@ -277,20 +315,28 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
                 hyp4 = has ? rc.props[pix * rc.n_prop + lane] : make_float4(0.f, 0.f, -1.f, 0.f);
                 want = has && hyp4.w >= rc.d_lo && hyp4.w <= rc.d_hi && !same_plane(hyp4, cur);
             } else if (stage == 2) {
-                // refinement (Sec. III-C): delta_d in [-d_hi/4, d_hi/4],
-                // delta_theta in [-pi/2, pi/2], delta_phi in [-pi/12, pi/12]
-                float u[3];
-                draws3(rc, pix, phase, u);
-                float dd = (2.0f * u[0] - 1.0f) * (rc.d_hi * 0.25f);
-                float dth = (2.0f * u[1] - 1.0f) * (kPi * 0.5f);
-                float dph = (2.0f * u[2] - 1.0f) * (kPi / 12.0f);
-                float d_new = fminf(fmaxf(cur.w + dd, rc.d_lo), rc.d_hi);
+                // refinement (Sec. III-C): d + delta_d clamped to the range;
+                // the normal's angles theta = atan2(m1, m0), phi = acos(m2)
+                // (after flipping to m2 >= 0) move by delta_theta, delta_phi,
+                // taken through the angle-addition formulas
+                const float4 r4 = draw4[it & 31u];
+                const float sdp = draw1[it & 31u];
+                float d_new = fminf(fmaxf(cur.w + r4.x, rc.d_lo), rc.d_hi);
                 float m0 = cur.x, m1 = cur.y, m2 = cur.z;
                 if (m2 < 0.0f) { m0 = -m0; m1 = -m1; m2 = -m2; }
-                float th = atan2f(m1, m0);
-                float ph = acosf(fminf(1.0f, fmaxf(-1.0f, m2)));
-                float nn0, nn1, nn2;
-                normal_from_angles(th + dth, ph + dph, pw.rx0, pw.rx1, pw.rx2, nn0, nn1, nn2);
+                const float rr = sqrtf(m0 * m0 + m1 * m1);
+                // cos / sin of atan2(m1, m0); atan2(+-0, x) is 0 for x = +0 and pi for x = -0
+                const float irr = rr > 0.0f ? 1.0f / rr : 0.0f;
+                const float ct = rr > 0.0f ? m0 * irr : (signbit(m0) ? -1.0f : 1.0f), st = m1 * irr;
+                const float cp = fminf(1.0f, fmaxf(-1.0f, m2)), sp = sqrtf(fmaxf(0.0f, 1.0f - cp * cp));
+                const float ct2 = ct * r4.y - st * r4.z, st2 = st * r4.y + ct * r4.z;
+                const float cp2 = cp * r4.w - sp * sdp, sp2 = sp * r4.w + cp * sdp;
+                float nn0 = ct2 * sp2, nn1 = st2 * sp2, nn2 = cp2;
+                if (nn0 * pw.rx0 + nn1 * pw.rx1 + nn2 * pw.rx2 > 0.0f) {   // face the camera
+                    nn0 = -nn0;
+                    nn1 = -nn1;
+                    nn2 = -nn2;
+                }
                 // candidates (d_new, n_old), (d_old, n_new), (d_new, n_new) in lanes 0..2
                 hyp4 = lane == 0 ? make_float4(cur.x, cur.y, cur.z, d_new)
                      : (lane == 1 ? make_float4(nn0, nn1, nn2, cur.w) : make_float4(nn0, nn1, nn2, d_new));
@@ -385,7 +431,7 @@ cudaError_t prime_launch_configs(const RefConst& rc) {
     do {                                                                                              \
         pm_grid_for((const void*)k_init<G, S, MX>, 1, smem, kBlock);                                  \
         pm_grid_for((const void*)k_cost<G, S, MX>, 1, smem, kBlock);                                  \
-        pm_grid_for((const void*)k_phase<G, S, MX>, 1, smem_block_bytes(rc.n_src, PhaseTile<S>::WARPS), \
+        pm_grid_for((const void*)k_phase<G, S, MX>, 1, phase_smem_bytes(rc.n_src, PhaseTile<S>::WARPS), \
                     PhaseTile<S>::BLOCK);                                                             \
     } while (0)
     if (rc.precision) {
@@ -448,7 +494,7 @@ template <int G, int S, bool MX>
 void phase_launch(const RefConst& rc, int phase, cudaStream_t s) {
     using T = PhaseTile<S>;
     const long long ntiles = (long long)(((rc.W + 1) / 2 + T::TX - 1) / T::TX) * ((rc.H + T::TY - 1) / T::TY);
-    const size_t smem = smem_block_bytes(rc.n_src, T::WARPS);
+    const size_t smem = phase_smem_bytes(rc.n_src, T::WARPS);
     k_phase<G, S, MX><<<pm_grid_for((const void*)k_phase<G, S, MX>, ntiles, smem, T::BLOCK), T::BLOCK, smem, s>>>(
         rc, phase);
 }
