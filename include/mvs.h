@@ -162,18 +162,19 @@ const char* mvs_last_error(const mvs_ctx* ctx);
 mvs_status mvs_patchmatch(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_t n_src,
                           const mvs_pm_params* params, mvs_depth_map* out);
 
-/* Depth maps of several reference views in one call: the initialisation of
- * every view, then half-iteration p of every view, for p in the phase range
+/* Depth maps of several reference views in one call: for each view in
+ * turn, its initialisation and its half-iterations in the phase range
  * (Algorithm 1 loops over reference images; the views are independent, so
- * the interleaving gives exactly the results of separate mvs_patchmatch
- * calls).  The kernels are captured into a CUDA graph on the first call with
- * a given (refs, srcs, params) and the graph is replayed by later calls.
+ * the results equal those of separate mvs_patchmatch calls).  The kernels
+ * are captured into a CUDA graph on the first call with a given
+ * (refs, srcs, params) and the graph is replayed by later calls.
  *   refs[n_ref]: reference views (distinct); srcs[n_ref * n_src]: row r holds
  *   the n_src sources of refs[r]; outs[n_ref]: depth-map buffers of each
  *   reference's size, all in the same memory kind.  params as for
  *   mvs_patchmatch; params->lanes_per_pixel = -1 asks the library to time
- *   the work layouts on the first call (one phase of the first view on a
- *   scratch copy of its state) and keep the fastest for this window size.
+ *   the work layouts on the first call (two iterations of the first view,
+ *   each from the same initial state, in the view's own buffers before its
+ *   real run) and keep the fastest for this window size.
  *   The maps stay in the context for mvs_geo_filter.
  * Errors: as mvs_patchmatch, plus MVS_EINVAL for n_ref < 1 or repeated refs. */
 mvs_status mvs_patchmatch_batch(mvs_ctx* ctx, int32_t n_ref, const int32_t* refs, const int32_t* srcs,

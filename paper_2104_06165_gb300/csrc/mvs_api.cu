@@ -350,8 +350,9 @@ mvs_status mvs_patchmatch(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t 
     return MVS_OK;
 }
 
-// Times one phase of `ref` with each candidate work layout on a scratch copy
-// of its (freshly initialised) state and returns the fastest lanes per pixel.
+// Times two iterations (four phases) of `ref` with each candidate work
+// layout, each from the same freshly initialised state, and returns the
+// fastest lanes per pixel.
 static mvs_status autotune_lanes(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src,
                                  const mvs_pm_params* p, int* lanes_out) {
     long long key = (long long)p->win_samples * 64 + n_src;
@@ -389,7 +390,7 @@ static mvs_status autotune_lanes(mvs_ctx* c, int32_t ref, const int32_t* srcs, i
             CK(c, cudaMemcpyAsync(V.cost, keep + n * sizeof(float4), n * sizeof(float), cudaMemcpyDeviceToDevice,
                                   c->stream));
             CK(c, cudaEventRecord(t0, c->stream));
-            CK(c, launch_phase(rc, 0, c->stream));
+            for (int ph = 0; ph < 4; ++ph) CK(c, launch_phase(rc, ph, c->stream));
             CK(c, cudaEventRecord(t1, c->stream));
         }
         CK(c, cudaEventSynchronize(t1));
@@ -459,13 +460,13 @@ mvs_status mvs_patchmatch_batch(mvs_ctx* c, int32_t n_ref, const int32_t* refs, 
         cudaGraph_t g = nullptr;
         CK(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
+        // view after view: consecutive launches share their source textures in L2
         for (int r = 0; r < n_ref && e == cudaSuccess; ++r) {
             if (p->init_mode == MVS_INIT_RANDOM) e = launch_init(rcs[r], nullptr, c->gstream);
             else if (p->init_mode == MVS_INIT_GIVEN_RECOST)
                 e = launch_cost(rcs[r], rcs[r].plane, rcs[r].cost, nullptr, c->gstream);
+            for (int ph = p->phase_begin; ph < pend && e == cudaSuccess; ++ph) e = launch_phase(rcs[r], ph, c->gstream);
         }
-        for (int ph = p->phase_begin; ph < pend && e == cudaSuccess; ++ph)
-            for (int r = 0; r < n_ref && e == cudaSuccess; ++r) e = launch_phase(rcs[r], ph, c->gstream);
         cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&B.exec, g, 0);

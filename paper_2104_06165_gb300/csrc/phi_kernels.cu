@@ -201,11 +201,6 @@ __global__ void k_line_fit(int W, int H, const float* __restrict__ depth, const 
 // ---------------------------------------------------------------------------
 constexpr int kBlock = 128;
 constexpr int kWarps = kBlock / 32;
-// Dynamic shared memory of a block: the view table, then one pair list per
-// warp (smem_block_bytes(n_src, kWarps) bytes).
-__device__ __forceinline__ PairSm* warp_pairs(unsigned char* smem, int n_src, int warp) {
-    return reinterpret_cast<PairSm*>(smem + smem_views_bytes(n_src)) + (size_t)warp * 8 * n_src;
-}
 
 // one warp per pixel, the four hypotheses of a pixel in lanes 0..3
 template <int G, int S>

@@ -267,26 +267,32 @@ __device__ __forceinline__ Cand make_cand(const RefConst& rc, const PixWin<S>& p
 // One listed (hypothesis, view) pair in shared memory (three 16-byte
 // words): the homography columns H e1, H e2 and H x (x, y rows shifted by
 // -1/2 and doubled for tex_sample), the view, and after evaluation its
-// per-view cost C(x, j) (C_max when excluded) and Eq. 5 weight
-// 1 / max(C(x, j), 1e-6) (0 when excluded).
+// per-view cost C(x, j) (C_max when excluded), the hypothesis and the view.
 struct __align__(16) PairSm {
     float h0x, h0y, h0z, h1x;
     float h1y, h1z, p0x, p0y;
-    float p0z, res, inv;
-    int j;
+    float p0z, res;
+    int c, j;
 };
 
 static_assert(sizeof(PairSm) == 48 && offsetof(PairSm, h1y) == 16 && offsetof(PairSm, p0z) == 32 &&
-                  offsetof(PairSm, res) == 36 && offsetof(PairSm, inv) == 40 && offsetof(PairSm, j) == 44,
+                  offsetof(PairSm, res) == 36 && offsetof(PairSm, c) == 40 && offsetof(PairSm, j) == 44,
               "eval_batch reads and writes PairSm as 128-bit words");
 
-// Shared-memory bytes of a 128-thread block: the view table and, per warp,
-// room for 8 hypotheses x n_src pairs.
+// Shared-memory bytes of a block: the view table and, per warp, room for
+// 8 hypotheses x n_src pairs followed by their 8 x n_src Eq. 5 weights.
 __host__ __device__ constexpr size_t smem_views_bytes(int n_src) {
     return ((size_t)n_src * sizeof(ViewSm) + 15) & ~(size_t)15;
 }
+__host__ __device__ constexpr size_t smem_warp_bytes(int n_src) {
+    return (size_t)8 * n_src * (sizeof(PairSm) + sizeof(float));   // 416 n_src: a multiple of 16
+}
 __host__ __device__ constexpr size_t smem_block_bytes(int n_src, int warps) {
-    return smem_views_bytes(n_src) + (size_t)warps * 8 * n_src * sizeof(PairSm);
+    return smem_views_bytes(n_src) + (size_t)warps * smem_warp_bytes(n_src);
+}
+// pair list of warp `warp` in a block's dynamic shared memory
+__device__ __forceinline__ PairSm* warp_pairs(unsigned char* smem, int n_src, int warp) {
+    return reinterpret_cast<PairSm*>(smem + smem_views_bytes(n_src) + (size_t)warp * smem_warp_bytes(n_src));
 }
 
 // Two planes (n, depth at the pixel) equal up to float rounding (1e-6
@@ -323,7 +329,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
     // ---- 1. list the pairs that map inside the source images, over the
     // usable hypotheses only: lane r < nok holds the lane of the r-th one
     const unsigned okm = __ballot_sync(0xffffffffu, lane < nc && my.ok);
-    const int nok = __popc(okm), rank = __popc(okm & ((1u << lane) - 1u));
+    const int nok = __popc(okm);
     int hyp_of;
     {
         unsigned m = okm;   // drop the lowest set bit `lane` times (nc <= 8)
@@ -332,16 +338,22 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             if (t < lane) m &= m - 1u;
         hyp_of = m ? __ffs(m) - 1 : 0;
     }
+    // Pairs are listed view-major (all usable hypotheses of view 0, then of
+    // view 1, ...): the groups of a round then gather from the same source,
+    // usually around the same place (neighbouring planes).  Their Eq. 5
+    // weights go to tab[hypothesis][view], so that each hypothesis still
+    // folds its views in view order.
+    float* tab = reinterpret_cast<float*>(pairs + 8 * V);
     const int P = nok * V;
-    int count = 0, my_cnt = 0;
-    // floor(i / V) = (i * ceil(2^16 / V)) >> 16 exactly for i < 2^16 / V
+    int count = 0;
+    // floor(i / nok) = (i * ceil(2^16 / nok)) >> 16 exactly for i < 2^16 / nok
     // (i < 8 * MVS_MAX_SRC here)
-    const uint32_t vmagic = 0xffffu / (uint32_t)V + 1u;
+    const uint32_t kmagic = nok ? 0xffffu / (uint32_t)nok + 1u : 0u;
     for (int base = 0; base < P; base += 32) {
         int i = base + lane;
         bool act = i < P;
-        int cr = act ? (int)(((uint32_t)i * vmagic) >> 16) : 0;
-        int j = act ? i - cr * V : 0;
+        int j = act ? (int)(((uint32_t)i * kmagic) >> 16) : 0;
+        int cr = act ? i - j * nok : 0;
         int c = __shfl_sync(0xffffffffu, hyp_of, cr);
         float m0 = __shfl_sync(0xffffffffu, my.m0, c);
         float m1 = __shfl_sync(0xffffffffu, my.m1, c);
@@ -376,25 +388,12 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             float4* qw = reinterpret_cast<float4*>(pairs + count + __popc(m & ((1u << lane) - 1u)));
             qw[0] = make_float4(2.0f * h0x, 2.0f * h0y, h0z, 2.0f * h1x);
             qw[1] = make_float4(2.0f * h1y, h1z, 2.0f * p0x, 2.0f * p0y);
-            qw[2] = make_float4(p0z, 0.0f, 0.0f, __int_as_float(j));
+            qw[2] = make_float4(p0z, 0.0f, __int_as_float(c), __int_as_float(j));
+        } else if (act) {
+            tab[c * V + j] = 0.0f;   // view excluded for this hypothesis
         }
         count += __popc(m);
-        if ((okm >> lane) & 1u) {   // pairs of hypothesis `lane` in this chunk
-            int lo = max(0, rank * V - base), hi = min(32, rank * V + V - base);
-            if (hi > lo) {
-                unsigned rm = (hi == 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-                my_cnt += __popc(m & rm);
-            }
-        }
     }
-    // first list position of hypothesis `lane`: exclusive prefix sum
-    int start = my_cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, start, o);
-        if (lane >= o) start += t;
-    }
-    start -= my_cnt;
     __syncwarp();
     // ---- 2. evaluate the listed pairs, NG at a time
     for (int r = 0; r < count; r += NG) {
@@ -473,9 +472,9 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             }
         } else {
             const uint2* tex = v_tex;
-            const uint32_t pitch = v0.z, last = v_last;
-            // mixed precision: positions and fractions in FP32, the bilinear
-            // interpolation of two samples per half2 instruction, on
+            const uint32_t pitch = v0.z, toff = v0.w, last = v_last;
+            // mixed precision: positions and fractions in FP32 (as above), the
+            // bilinear interpolation of two samples per half2 instruction, on
             // intensities shifted by the reference patch mean
             const __half2 mu2 = __float2half2_rn(pw.mean);
 #pragma unroll
@@ -489,12 +488,10 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                     float Y = fmaf(pw.ou[kk], h0y, fmaf(pw.ov[kk], h1y, p0y));
                     float Z = fmaf(pw.ou[kk], h0z, fmaf(pw.ov[kk], h1z, p0z));
                     float iz = rcp_approx(Z);
-                    float xs2 = __fmul_rn(X, iz), ys2 = __fmul_rn(Y, iz);
-                    float tx = __fadd_rn(xs2, kMagic2), ty = __fadd_rn(ys2, kMagic2);
-                    Us[h] = __fsub_rn(xs2, __fsub_rn(tx, kMagic2));
-                    Vs[h] = __fsub_rn(ys2, __fsub_rn(ty, kMagic2));
-                    uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx) +
-                                   (pitch + 1u) * (uint32_t)(1 - kMagic2Bits);
+                    float tx = fmaf(X, iz, kMagic2), ty = fmaf(Y, iz, kMagic2);
+                    Us[h] = fmaf(X, iz, kMagic2 - tx);
+                    Vs[h] = fmaf(Y, iz, kMagic2 - ty);
+                    uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx) + toff;
                     q[h] = __ldg(tex + min(idx, last));
                 }
                 uint32_t ab = __byte_perm(q[0].x, q[1].x, 0x5410), bb = __byte_perm(q[0].x, q[1].x, 0x7632);
@@ -555,8 +552,8 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         const float z = fminf(1.0f, fmaxf(-1.0f, srd * rsqrtf(pw.srr * sdd)));
         const float cj = flat ? kCmax : fminf(1.0f - z, kCmax);
         if (has && lg == 0) {
-            pairs[it].res = cj;
-            pairs[it].inv = cj < kCmax ? rcp_approx(fmaxf(cj, kEpsC)) : 0.0f;
+            if (VIEWS) pairs[it].res = cj;
+            tab[__float_as_int(qc.z) * V + __float_as_int(qc.w)] = cj < kCmax ? rcp_approx(fmaxf(cj, kEpsC)) : 0.0f;
             n_evals++;
         }
     }
@@ -564,10 +561,9 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
     // ---- 3. fold hypothesis `lane`'s views in view order
     int cnt = 0;
     float inv_sum = 0.0f;
-    const int max_cnt = __reduce_max_sync(0xffffffffu, (unsigned)my_cnt);   // warp-uniform trip count
-    for (int t = 0; t < max_cnt; ++t)
-        if (t < my_cnt) {
-            const float wv = pairs[start + t].inv;
+    if ((okm >> lane) & 1u)
+        for (int j = 0; j < V; ++j) {
+            const float wv = tab[lane * V + j];
             cnt += wv > 0.0f;
             inv_sum += wv;
         }

@@ -58,12 +58,6 @@ struct PhaseTile {
     static constexpr int MIN_BLOCKS = (S >= 16 ? 384 : 512) / BLOCK > 0 ? (S >= 16 ? 384 : 512) / BLOCK : 1;
 };
 
-// Dynamic shared memory of a block: the view table, then one pair list per
-// warp (smem_block_bytes(n_src, warps) bytes).
-__device__ __forceinline__ PairSm* warp_pairs(unsigned char* smem, int n_src, int warp) {
-    return reinterpret_cast<PairSm*>(smem + smem_views_bytes(n_src)) + (size_t)warp * 8 * n_src;
-}
-
 // ---------------------------------------------------------------------------
 // Sec. III-B: random initialisation, then the cost of the initial plane.
 // One warp per pixel, grid-stride over the pixels.
