@@ -102,6 +102,9 @@ def lib():
             L.or_eq10_normal.argtypes = [vp, C.c_int, dp, C.c_int, C.c_int, dp]
             L.or_plane_infer.argtypes = [vp, C.c_int, ip, C.c_int, C.POINTER(_PM), C.POINTER(_Phi), up, dp,
                                          dp, up, dp, ip, dp, up]
+            L.or_fuse.restype = C.c_long
+            L.or_fuse.argtypes = [vp, C.c_int, ip, C.POINTER(dp), C.POINTER(up), C.c_double,
+                                  C.POINTER(C.c_float), ip, C.POINTER(C.c_long), C.c_long]
             _lib = L
     return _lib
 
@@ -417,3 +420,24 @@ def plane_infer(scene, ref, srcs, p, known, plane, k1=4.0, k2=0.5, k3=2.0, n_fit
                          _d(hyp), _u8(valid), _d(hcost), _i(label), _d(refd), _u8(filled))
     return pl, {"hyp": hyp, "valid": valid, "hcost": hcost, "label": label, "refdepth": refd,
                 "filled": filled}
+
+
+def fuse(scene, order, planes, keep=None, rel_tol=0.01):
+    """Sec. III-F depth-map fusion of the views in ``order`` (decisions in
+    single precision, see or_fuse).  ``planes`` maps view index to its
+    (H, W, 4) plane map, ``keep`` optionally to a uint8 mask.  Returns
+    (points (n, 4) float32 = x, y, z, merged count; source view (n,);
+    source pixel (n,))."""
+    order = [int(v) for v in order]
+    n = len(order)
+    arrs = [_f64(planes[v]) for v in order]
+    kps = [None if keep is None or keep.get(v) is None else np.ascontiguousarray(keep[v], np.uint8) for v in order]
+    dps = (C.POINTER(C.c_double) * n)(*[_d(a) for a in arrs])
+    ups = (C.POINTER(C.c_ubyte) * n)(*[(_u8(k) if k is not None else C.POINTER(C.c_ubyte)()) for k in kps])
+    cap = int(sum(scene.shape(v)[0] * scene.shape(v)[1] for v in order))
+    pts = np.zeros((max(cap, 1), 4), np.float32)
+    sv = np.zeros(max(cap, 1), np.int32)
+    sp = np.zeros(max(cap, 1), np.int64)
+    m = lib().or_fuse(scene.h, n, _i(np.asarray(order, np.int32)), dps, ups, float(rel_tol),
+                      pts.ctypes.data_as(C.POINTER(C.c_float)), _i(sv), sp.ctypes.data_as(C.POINTER(C.c_long)), cap)
+    return pts[:m], sv[:m], sp[:m]

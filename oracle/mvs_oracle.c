@@ -20,6 +20,8 @@
  *                reconstructed pixels, Eq. 6 unary, Eq. 7 pairwise, Eq. 8/9
  *                MAP via tree-reweighted message passing at half resolution,
  *                closest-hypothesis selection, Eq. 10 normals
+ *   Sec. III-F   depth-map fusion: greedy merging of back-projected pixels
+ *                whose relative difference is below 0.01, image by image
  *   Sec. IV      parameters {r_now, r_orig, k1, k2, k3} = {5, 7, 4, 0.5, 2},
  *                one TRW iteration
  *
@@ -1089,4 +1091,119 @@ void or_plane_infer(const or_scene* s, int ref, const int* srcs, int ns, const o
     if (hcost_out) memcpy(hcost_out, hcost, sizeof(double) * 4 * N);
     if (label_out) memcpy(label_out, label, sizeof(int) * G);
     free(depth); free(hyp); free(valid); free(hcost); free(label);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. III-F: depth-map fusion                                         */
+/* ------------------------------------------------------------------ */
+/* The paper fixes no precision for fusion, and its decisions (which pixel
+ * of image j a point lands on, whether two points agree) are integers, so
+ * the oracle takes them in single precision, operation by operation, with
+ * no fused multiply-add (this file is built with -ffp-contract=off):
+ *   back-projection of pixel (x, y) of view v with z-depth d (reading: a
+ *   pinhole K = [fx s cx; 0 fy cy; 0 0 1], x_cam = R X + t):
+ *     yc = (y - cy) / fy, xc = ((x - cx) - s yc) / fx, Xc = (d xc, d yc, d),
+ *     X = R^T (Xc - t), each component ((R0k e0 + R1k e1) + R2k e2);
+ *   projection into view j: c = R X + t, each component
+ *     ((Rk0 X0 + Rk1 X1) + Rk2 X2) + tk, u = ((fx c0 + s c1) + cx c2) / c2,
+ *     v = (fy c1 + cy c2) / c2, pixel [x'_j] = (floor(u + 1/2), floor(v + 1/2))
+ *     when c2 > 0 and the pixel lies in the image;
+ *   relative difference (reading: distance over the z-depth of X_i in view
+ *     i): ((e0 e0 + e1 e1) + e2 e2) < (tol d_i)^2;
+ *   merged point: (X_i + X'_j1 + X'_j2 + ...) / count, summed in view order.
+ * Camera values are the doubles of the scene rounded to float. */
+typedef struct { float fx, sk, cx, fy, cy, R[9], t[3]; } or_fcam;
+
+static or_fcam fcam(const or_view* v) {
+    or_fcam c;
+    c.fx = (float)v->K[0]; c.sk = (float)v->K[1]; c.cx = (float)v->K[2];
+    c.fy = (float)v->K[4]; c.cy = (float)v->K[5];
+    for (int k = 0; k < 9; ++k) c.R[k] = (float)v->R[k];
+    for (int k = 0; k < 3; ++k) c.t[k] = (float)v->t[k];
+    return c;
+}
+
+static void fuse_backproject(const or_fcam* c, int x, int y, float d, float X[3]) {
+    float yc = ((float)y - c->cy) / c->fy;
+    float xc = (((float)x - c->cx) - c->sk * yc) / c->fx;
+    float e[3] = {d * xc - c->t[0], d * yc - c->t[1], d - c->t[2]};
+    for (int k = 0; k < 3; ++k) X[k] = (c->R[k] * e[0] + c->R[3 + k] * e[1]) + c->R[6 + k] * e[2];
+}
+
+/* pixel index of [x'_j], or -1 */
+static long fuse_project(const or_fcam* c, int W, int H, const float X[3]) {
+    float q[3];
+    for (int k = 0; k < 3; ++k) q[k] = ((c->R[3 * k] * X[0] + c->R[3 * k + 1] * X[1]) + c->R[3 * k + 2] * X[2]) + c->t[k];
+    if (!(q[2] > 0.0f)) return -1;
+    float u = ((c->fx * q[0] + c->sk * q[1]) + c->cx * q[2]) / q[2];
+    float v = (c->fy * q[1] + c->cy * q[2]) / q[2];
+    float fu = floorf(u + 0.5f), fv = floorf(v + 0.5f);
+    if (!(fu >= 0.0f && fu <= (float)(W - 1) && fv >= 0.0f && fv <= (float)(H - 1))) return -1;
+    return (long)fv * W + (long)fu;
+}
+
+/* Fusion of the depth maps of views order[0..n-1], in that order (Sec. III-F):
+ * every remaining pixel x of image i (depth > 0, kept by keep[v] when given,
+ * not merged before) is back-projected to X_i; for every remaining image j
+ * the pixel [x'_j] that X_i projects to is back-projected to X'_j, and when
+ * the relative difference is below rel_tol that pixel is merged (removed
+ * from image j) and X'_j joins the average; after its pixels, image i is
+ * removed.  planes[a] and keep[a] belong to view order[a] (keep NULL or
+ * keep[a] NULL: every pixel with depth).  Points are emitted in view order,
+ * then raster order:
+ * pts[4k..4k+3] = (x, y, z, number of merged pixels), src_view[k],
+ * src_pix[k] = the emitting pixel.  Writes at most cap points and returns
+ * the number of points. */
+long or_fuse(const or_scene* s, int n, const int* order, const double* const* planes,
+             const unsigned char* const* keep, double rel_tol, float* pts, int* src_view, long* src_pix, long cap) {
+    unsigned char** alive = (unsigned char**)calloc((size_t)n, sizeof(unsigned char*));
+    or_fcam* cam = (or_fcam*)calloc((size_t)n, sizeof(or_fcam));
+    for (int a = 0; a < n; ++a) {
+        const or_view* V = &s->v[order[a]];
+        long N = (long)V->W * V->H;
+        alive[a] = (unsigned char*)malloc((size_t)N);
+        for (long i = 0; i < N; ++i)
+            alive[a][i] = (unsigned char)((float)planes[a][4 * i + 3] > 0.0f && (!keep || !keep[a] || keep[a][i]));
+        cam[a] = fcam(V);
+    }
+    const float tol = (float)rel_tol;
+    long np = 0;
+    for (int a = 0; a < n; ++a) {
+        const or_view* V = &s->v[order[a]];
+        for (int y = 0; y < V->H; ++y)
+            for (int x = 0; x < V->W; ++x) {
+                long i = (long)y * V->W + x;
+                if (!alive[a][i]) continue;
+                float d = (float)planes[a][4 * i + 3];
+                float X[3], sum[3];
+                fuse_backproject(&cam[a], x, y, d, X);
+                for (int k = 0; k < 3; ++k) sum[k] = X[k];
+                int cnt = 1;
+                float thr = tol * d;
+                for (int b = a + 1; b < n; ++b) {
+                    const or_view* S = &s->v[order[b]];
+                    long t = fuse_project(&cam[b], S->W, S->H, X);
+                    if (t < 0 || !alive[b][t]) continue;
+                    float Y[3];
+                    fuse_backproject(&cam[b], (int)(t % S->W), (int)(t / S->W), (float)planes[b][4 * t + 3], Y);
+                    float e0 = X[0] - Y[0], e1 = X[1] - Y[1], e2 = X[2] - Y[2];
+                    if (!(((e0 * e0 + e1 * e1) + e2 * e2) < thr * thr)) continue;
+                    alive[b][t] = 0;
+                    for (int k = 0; k < 3; ++k) sum[k] = sum[k] + Y[k];
+                    cnt++;
+                }
+                alive[a][i] = 0;
+                if (np < cap) {
+                    for (int k = 0; k < 3; ++k) pts[4 * np + k] = sum[k] / (float)cnt;
+                    pts[4 * np + 3] = (float)cnt;
+                    if (src_view) src_view[np] = order[a];
+                    if (src_pix) src_pix[np] = i;
+                }
+                np++;
+            }
+    }
+    for (int a = 0; a < n; ++a) free(alive[a]);
+    free(alive);
+    free(cam);
+    return np;
 }
