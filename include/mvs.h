@@ -198,6 +198,35 @@ mvs_status mvs_plane_cost(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_
 mvs_status mvs_geo_filter(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_t n_src,
                           const mvs_filter_params* fp, uint8_t* keep_mask, int32_t* count, int32_t mem);
 
+/* Depth-map fusion into one point cloud (Sec. III-F, the last step of
+ * Algorithm 1).  The views are taken in the order given; every remaining
+ * pixel x of image i (depth > 0, kept by its mask, not merged before) is
+ * back-projected to X_i, and for every later image j the pixel [x'_j] that
+ * X_i projects to (nearest pixel) is back-projected to X'_j; when
+ * |X_i - X'_j| < rel_tol * (z-depth of X_i in image i) that pixel is merged:
+ * removed from image j, X'_j joins the average.  The paper fixes no
+ * precision; the decisions are taken in single precision, every operation
+ * rounded on its own, in the order stated in fuse_kernels.cu (readings:
+ * pinhole K, the distance relative to the z-depth, nearest pixel by
+ * floor(u + 1/2)).
+ *   views[n_views]: processing order, distinct views whose depth maps are in
+ *   the context (mvs_patchmatch / mvs_plane_infer results).
+ *   keep_masks: NULL, or n_views pointers to H*W uint8 masks (1 = kept) or
+ *   NULL (every pixel with depth); masks live in `mem`.
+ *   rel_tol: the paper's 0.01.
+ *   points: capacity x 4 floats (x, y, z, merged pixel count) in world
+ *   coordinates, written in processing order of the views, then raster order
+ *   of the emitting pixel; src: capacity x 2 int32 (view, pixel index) or
+ *   NULL; both in `mem` (device or host).  The call synchronises and sets
+ *   *n_points to the number of points of the cloud.
+ * Errors: MVS_EINVAL (bad or repeated view, rel_tol <= 0, bad buffers, or
+ *   more points than capacity: then the first `capacity` points are written
+ *   and *n_points holds the full count), MVS_ESTATE (a view without depth
+ *   map), MVS_EUNSUPPORTED (a view whose K is not pinhole), MVS_ENOMEM,
+ *   MVS_ECUDA. */
+mvs_status mvs_fuse(mvs_ctx* ctx, int32_t n_views, const int32_t* views, const uint8_t* const* keep_masks,
+                    float rel_tol, float* points, int32_t* src, int64_t capacity, int64_t* n_points, int32_t mem);
+
 /* Plane hypothesis inference (Sec. III-E) on view `ref`: four line-fit
  * hypotheses per hole, their matching cost through the sources, a pairwise
  * MRF (Eq. 6-9) decoded by TRW at half resolution, closest-hypothesis

@@ -19,7 +19,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
          "-Xptxas", "-warn-spills"]
-SOURCES = ["mvs_api.cu", "pm_kernels.cu", "phi_kernels.cu", "cnn_kernels.cu"]
+SOURCES = ["mvs_api.cu", "pm_kernels.cu", "phi_kernels.cu", "cnn_kernels.cu", "fuse_kernels.cu"]
 
 
 def _deps():

@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/mvs.h): context management,
 // argument checking, per-view constants in double precision, and the
 // stream-ordered sequencing of the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -49,7 +50,7 @@ struct mvs_ctx {
     cudaStream_t stream = nullptr;
     std::vector<ViewData> views;
     std::string err;
-    Scratch scratch[6];
+    Scratch scratch[8];
     // measurement hooks
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -586,6 +587,101 @@ mvs_status mvs_geo_filter(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t 
         if (count) CK(c, cudaMemcpyAsync(count, cnt_d, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
     }
+    return MVS_OK;
+}
+
+mvs_status mvs_fuse(mvs_ctx* c, int32_t n_views, const int32_t* views, const uint8_t* const* keep_masks, float rel_tol,
+                    float* points, int32_t* src, int64_t capacity, int64_t* n_points, int32_t mem) {
+    if (!c) return MVS_EINVAL;
+    if (!views || n_views < 1 || n_views > (int32_t)c->views.size())
+        return fail(c, MVS_EINVAL, "need 1..%d views", (int)c->views.size());
+    if (!n_points || capacity < 0 || (capacity > 0 && !points)) return fail(c, MVS_EINVAL, "bad output arguments");
+    if (!(rel_tol > 0.0f)) return fail(c, MVS_EINVAL, "rel_tol must be > 0");
+    if (mem != MVS_MEM_DEVICE && mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    std::vector<char> seen(c->views.size(), 0);
+    for (int a = 0; a < n_views; ++a) {
+        const int v = views[a];
+        if (v < 0 || v >= (int32_t)c->views.size() || seen[v]) return fail(c, MVS_EINVAL, "bad or repeated view %d", v);
+        seen[v] = 1;
+        if (!c->views[v].has_map) return fail(c, MVS_ESTATE, "view %d has no depth map", v);
+        const double* K = c->views[v].cam.K;
+        if (K[3] != 0.0 || K[6] != 0.0 || K[7] != 0.0 || K[8] != 1.0)
+            return fail(c, MVS_EUNSUPPORTED, "view %d: fusion needs a pinhole K = [fx s cx; 0 fy cy; 0 0 1]", v);
+    }
+    CK(c, cudaSetDevice(c->device));
+    // scratch slot 6, every region starting on a 16-byte boundary: per view
+    // the claim and alive arrays (and a device copy of a host keep mask),
+    // then block counts, block offsets, the running total and the views
+    auto a16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    const bool copy_keep = mem == MVS_MEM_HOST && keep_masks;
+    size_t bytes = 0, max_blocks = 1;
+    for (int a = 0; a < n_views; ++a) {
+        const size_t np = (size_t)c->views[views[a]].cam.width * c->views[views[a]].cam.height;
+        bytes += a16(np * sizeof(int)) + a16(np) * (copy_keep ? 2 : 1);
+        max_blocks = std::max(max_blocks, (np + 255) / 256);
+    }
+    bytes += a16(max_blocks * sizeof(int)) + a16(max_blocks * sizeof(long long)) + 16 +
+             a16((size_t)n_views * sizeof(FuseView));
+    cudaError_t e;
+    char* buf = (char*)scratch(c, 6, bytes, &e);
+    CK(c, e);
+    std::vector<FuseView> fv(n_views);
+    std::vector<const uint8_t*> keep_d(n_views, nullptr);
+    char* q = buf;
+    for (int a = 0; a < n_views; ++a) {
+        const ViewData& V = c->views[views[a]];
+        const size_t np = (size_t)V.cam.width * V.cam.height;
+        FuseView& f = fv[a];
+        f.fx = (float)V.cam.K[0]; f.sk = (float)V.cam.K[1]; f.cx = (float)V.cam.K[2];
+        f.fy = (float)V.cam.K[4]; f.cy = (float)V.cam.K[5];
+        for (int i = 0; i < 9; ++i) f.R[i] = (float)V.cam.R[i];
+        for (int i = 0; i < 3; ++i) f.t[i] = (float)V.cam.t[i];
+        f.W = V.cam.width;
+        f.H = V.cam.height;
+        f.index = views[a];
+        f.plane = V.plane;
+        f.claim = (int*)q;
+        q += a16(np * sizeof(int));
+        f.alive = (uint8_t*)q;
+        q += a16(np);
+        if (copy_keep) {
+            if (keep_masks[a]) {
+                CK(c, cudaMemcpyAsync(q, keep_masks[a], np, cudaMemcpyHostToDevice, c->stream));
+                keep_d[a] = (const uint8_t*)q;
+            }
+            q += a16(np);
+        } else if (keep_masks) {
+            keep_d[a] = keep_masks[a];
+        }
+    }
+    int* block_count = (int*)q;
+    q += a16(max_blocks * sizeof(int));
+    long long* block_off = (long long*)q;
+    q += a16(max_blocks * sizeof(long long));
+    long long* total = (long long*)q;
+    q += 16;
+    FuseView* dev_views = (FuseView*)q;
+    float4* pts_d = (float4*)points;
+    int2* src_d = (int2*)src;
+    if (mem == MVS_MEM_HOST && capacity > 0) {
+        char* ob = (char*)scratch(c, 7, (size_t)capacity * (sizeof(float4) + (src ? sizeof(int2) : 0)), &e);
+        CK(c, e);
+        pts_d = (float4*)ob;
+        src_d = src ? (int2*)(ob + (size_t)capacity * sizeof(float4)) : nullptr;
+    }
+    CK(c, launch_fuse(fv.data(), dev_views, n_views, keep_masks ? keep_d.data() : nullptr, rel_tol, block_count,
+                      block_off, total, pts_d, src_d, capacity, c->stream));
+    long long tot = 0;
+    CK(c, cudaMemcpyAsync(&tot, total, sizeof tot, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *n_points = tot;
+    const long long nw = std::min<long long>(tot, capacity);
+    if (mem == MVS_MEM_HOST && nw > 0) {
+        CK(c, cudaMemcpyAsync(points, pts_d, (size_t)nw * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+        if (src) CK(c, cudaMemcpyAsync(src, src_d, (size_t)nw * sizeof(int2), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    if (tot > capacity) return fail(c, MVS_EINVAL, "%lld points do not fit the capacity of %lld", tot, (long long)capacity);
     return MVS_OK;
 }
 

@@ -116,6 +116,20 @@ cudaError_t launch_known_from_cost(int W, int H, const float4* plane, const floa
                                    uint8_t* known, float* depth, cudaStream_t s);
 cudaError_t launch_depth_of(int W, int H, const float4* plane, const uint8_t* known, float* depth, cudaStream_t s);
 
+// depth-map fusion (fuse_kernels.cu): one view as seen by the fusion kernels
+struct FuseView {
+    float fx, sk, cx, fy, cy;    // pinhole K = [fx sk cx; 0 fy cy; 0 0 1]
+    float R[9], t[3];            // x_cam = R X + t
+    int W, H;
+    int index;                   // context view index (reported with each point)
+    const float4* plane;         // depth map (depth in .w, 0 = none)
+    uint8_t* alive;              // W*H: 1 = still present
+    int* claim;                  // W*H: lowest claiming pixel of the view being fused
+};
+cudaError_t launch_fuse(const FuseView* host_views, FuseView* dev_views, int n, const uint8_t* const* keep, float tol,
+                        int* block_count, long long* block_off, long long* total, float4* points, int2* src,
+                        long long cap, cudaStream_t s);
+
 // learned proposals (cnn_kernels.cu)
 struct mvs_cnn;
 cudaError_t cnn_propose(mvs_cnn* n, const uint8_t* img, const float4* plane, const float* cost, int W, int H,

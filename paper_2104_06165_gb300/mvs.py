@@ -181,6 +181,8 @@ def load():
     L.mvs_cnn_propose.argtypes = [vp, u8p, fp, fp, i32, i32, C.POINTER(C.c_double), fp]
     L.mvs_propose.restype = i32
     L.mvs_propose.argtypes = [vp, i32, vp, fp]
+    L.mvs_fuse.restype = i32
+    L.mvs_fuse.argtypes = [vp, i32, ip, C.c_void_p, C.c_float, fp, vp, C.c_int64, C.POINTER(C.c_int64), i32]
     L.mvs_profile_read.restype = i32
     L.mvs_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_int64)]
@@ -296,6 +298,27 @@ def mvs_geo_filter(ctx, ref, srcs, fparams: FilterParams, keep, count=None):
     s, ns = _srcs(srcs)
     cpar = fparams.c()
     _check(load().mvs_geo_filter(ctx, ref, s, ns, C.byref(cpar), _ptr(keep)[0], _ptr(count)[0], mem), ctx)
+
+
+def mvs_fuse(ctx, views, points, src=None, keep_masks=None, rel_tol=0.01):
+    """Depth-map fusion of the context's maps of ``views`` (in that order)
+    into ``points`` (capacity x 4 float32: x, y, z, merged count) and
+    optionally ``src`` (capacity x 2 int32: view, pixel); ``keep_masks`` is
+    None or one uint8 (H, W) mask or None per view.  Returns the number of
+    points."""
+    kms = list(keep_masks) if keep_masks is not None else []
+    mem = _mem(points, src, *[k for k in kms if k is not None])
+    v, nv = _srcs(views)
+    km = None
+    if keep_masks is not None:
+        if len(kms) != nv:
+            raise ValueError("one keep mask (or None) per view")
+        km = (C.c_void_p * nv)(*[_ptr(k)[0] for k in kms])
+    cap = points.shape[0]
+    n = C.c_int64(0)
+    _check(load().mvs_fuse(ctx, nv, v, km, C.c_float(rel_tol), _ptr(points)[0], _ptr(src)[0], cap, C.byref(n), mem),
+           ctx)
+    return n.value
 
 
 def mvs_plane_infer(ctx, ref, srcs, pm: PMParams, phi: PhiParams, keep_mask, plane, cost):

@@ -1,0 +1,117 @@
+"""Depth-map fusion (Sec. III-F) on the GPU against the oracle.  Both sides
+take the fusion decisions in single precision with the same operations,
+each rounded on its own, so the number of points, the emitting pixels and
+the points themselves agree bit for bit."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+F, CX, CY = 100.0, 11.5, 3.5
+W, H, D, B = 24, 8, 4.0, 0.2          # cameras shifted by whole pixels (s = 5)
+S = int(round(F * B / D))
+
+
+def _load_maps(mvs, ctx, maps, n_views):
+    """Put given plane maps into the context (initial state, no phases)."""
+    for v, pl in maps.items():
+        hh, ww = pl.shape[:2]
+        p = mvs.PMParams(win_radius=5.0, win_samples=6, iters=0, phase_begin=0, phase_end=0,
+                         init_mode=mvs.MVS_INIT_GIVEN)
+        srcs = [u for u in range(n_views) if u != v][:4]
+        mvs.mvs_patchmatch(ctx.h, v, srcs, p, np.ascontiguousarray(pl, np.float32), np.zeros((hh, ww), np.float32))
+
+
+def _gpu_fuse(mvs, ctx, order, keep=None):
+    n_pix = len(order) * H * W
+    pts = np.zeros((n_pix, 4), np.float32)
+    src = np.zeros((n_pix, 2), np.int32)
+    n = mvs.mvs_fuse(ctx.h, order, pts, src, keep_masks=keep)
+    return pts[:n], src[:n]
+
+
+def test_closed_form_plane_equals_oracle(mvs_lib, oracle_lib):
+    import torch
+    n = 3
+    K = np.tile(np.array([[F, 0, CX], [0, F, CY], [0, 0, 1]], np.float64), (n, 1, 1))
+    R = np.tile(np.eye(3), (n, 1, 1))
+    t = np.array([[-k * B, 0.0, 0.0] for k in range(n)])
+    imgs = [np.full((H, W), 128, np.uint8) for _ in range(n)]
+    pl = np.zeros((H, W, 4))
+    pl[..., 2], pl[..., 3] = -1.0, D
+    maps = {v: pl for v in range(n)}
+    ctx = mvs_lib.Context(K, R, t, imgs, stream=torch.cuda.current_stream())
+    try:
+        _load_maps(mvs_lib, ctx, maps, n)
+        pts, src = _gpu_fuse(mvs_lib, ctx, [0, 1, 2])
+    finally:
+        ctx.close()
+    assert len(pts) == H * (W + 2 * S) and pts[:, 3].sum() == 3 * H * W
+    opts, osv, osp = oracle_lib.fuse(oracle_lib.Scene(K, R, t, imgs), [0, 1, 2], maps)
+    assert np.array_equal(src[:, 0], osv) and np.array_equal(src[:, 1], osp)
+    assert np.array_equal(pts, opts)
+
+
+@pytest.fixture(scope="module")
+def fused_scene(mvs_lib):
+    """Five views of the small synthetic scene: PatchMatch maps and
+    geometric-filter masks computed by the library."""
+    import torch
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_scene(W=128, H=96, n_src=4, seed=13, baseline_frac=0.1)
+    n = len(sc.images)
+    ctx = mvs_lib.Context(sc.K, sc.R, sc.t, sc.images, stream=torch.cuda.current_stream())
+    p = mvs_lib.PMParams(win_radius=5.0, win_samples=6, iters=3, seed=9)
+    hh, ww = sc.images[0].shape
+    maps = {}
+    for v in range(n):
+        pl = np.zeros((hh, ww, 4), np.float32)
+        co = np.zeros((hh, ww), np.float32)
+        mvs_lib.mvs_patchmatch(ctx.h, v, [u for u in range(n) if u != v], p, pl, co)
+        maps[v] = pl
+    keep = {}
+    for v in range(n):
+        k = np.zeros((hh, ww), np.uint8)
+        mvs_lib.mvs_geo_filter(ctx.h, v, [u for u in range(n) if u != v], mvs_lib.FilterParams(), k)
+        keep[v] = k
+    yield sc, ctx, maps, keep
+    ctx.close()
+
+
+@pytest.mark.parametrize("order", [[0, 1, 2, 3, 4], [4, 2, 0, 3, 1]])
+def test_patchmatch_maps_equal_oracle(fused_scene, mvs_lib, oracle_lib, order):
+    sc, ctx, maps, keep = fused_scene
+    hh, ww = sc.images[0].shape
+    cap = len(order) * hh * ww
+    pts = np.zeros((cap, 4), np.float32)
+    src = np.zeros((cap, 2), np.int32)
+    n = mvs_lib.mvs_fuse(ctx.h, order, pts, src, keep_masks=[keep[v] for v in order])
+    osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
+    opts, osv, osp = oracle_lib.fuse(osc, order, {v: maps[v].astype(np.float64) for v in order}, keep=keep)
+    assert n == len(opts)
+    assert np.array_equal(src[:n, 0], osv) and np.array_equal(src[:n, 1], osp)
+    assert np.array_equal(pts[:n], opts)
+    # merging happened, and every kept pixel ends in exactly one point
+    assert (opts[:, 3] > 1).mean() > 0.3
+    assert opts[:, 3].sum() == sum(int(((maps[v][..., 3] > 0) & (keep[v] > 0)).sum()) for v in order)
+
+
+def test_device_buffers_and_capacity(fused_scene, mvs_lib):
+    import torch
+    sc, ctx, maps, keep = fused_scene
+    hh, ww = sc.images[0].shape
+    order = [0, 1, 2, 3, 4]
+    cap = 5 * hh * ww
+    h_pts = np.zeros((cap, 4), np.float32)
+    n = mvs_lib.mvs_fuse(ctx.h, order, h_pts, None, keep_masks=[keep[v] for v in order])
+    d_pts = torch.zeros((cap, 4), dtype=torch.float32, device="cuda")
+    d_src = torch.zeros((cap, 2), dtype=torch.int32, device="cuda")
+    d_keep = [torch.from_numpy(keep[v]).cuda() for v in order]
+    n2 = mvs_lib.mvs_fuse(ctx.h, order, d_pts, d_src, keep_masks=d_keep)
+    torch.cuda.synchronize()
+    assert n2 == n and np.array_equal(d_pts.cpu().numpy()[:n], h_pts[:n])
+    # too small a buffer: the call fails and writes the first points only
+    small = np.zeros((n - 7, 4), np.float32)
+    with pytest.raises(mvs_lib.MvsError):
+        mvs_lib.mvs_fuse(ctx.h, order, small, None, keep_masks=[keep[v] for v in order])
+    assert np.array_equal(small, h_pts[: n - 7])
