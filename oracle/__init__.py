@@ -105,6 +105,7 @@ def lib():
             L.or_fuse.restype = C.c_long
             L.or_fuse.argtypes = [vp, C.c_int, ip, C.POINTER(dp), C.POINTER(up), C.c_double,
                                   C.POINTER(C.c_float), ip, C.POINTER(C.c_long), C.c_long]
+            L.or_select_neighbors.argtypes = [vp, C.c_long, dp, up, C.c_double, C.c_double, C.c_int, ip, dp, ip, dp]
             _lib = L
     return _lib
 
@@ -441,3 +442,19 @@ def fuse(scene, order, planes, keep=None, rel_tol=0.01):
     m = lib().or_fuse(scene.h, n, _i(np.asarray(order, np.int32)), dps, ups, float(rel_tol),
                       pts.ctypes.data_as(C.POINTER(C.c_float)), _i(sv), sp.ctypes.data_as(C.POINTER(C.c_long)), cap)
     return pts[:m], sv[:m], sp[:m]
+
+
+def select_neighbors(scene, X, vis, eps=0.05, t_tau=1.0, k=8):
+    """Sec. III-A neighbouring-image selection (Eqs. 1-3) from sparse points
+    X (n, 3) and their visibility vis (n, n_views) bool.  Returns (neighbours
+    (n_views, k) int, -1 padded; tau, n_shared, zeta (n_views, n_views))."""
+    X = _f64(np.asarray(X).reshape(-1, 3))
+    vis = np.ascontiguousarray(vis, np.uint8)
+    n = scene.n
+    nbr = np.zeros((n, k), np.int32)
+    tau = np.zeros((n, n))
+    na = np.zeros((n, n), np.int32)
+    zeta = np.zeros((n, n))
+    lib().or_select_neighbors(scene.h, len(X), _d(X), _u8(vis), float(eps), float(t_tau), int(k), _i(nbr), _d(tau),
+                              _i(na), _d(zeta))
+    return nbr, tau, na, zeta

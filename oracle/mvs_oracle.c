@@ -20,6 +20,8 @@
  *                reconstructed pixels, Eq. 6 unary, Eq. 7 pairwise, Eq. 8/9
  *                MAP via tree-reweighted message passing at half resolution,
  *                closest-hypothesis selection, Eq. 10 normals
+ *   Sec. III-A   neighbouring-image selection: Eq. 1 disturbance, Eq. 2 tau,
+ *                Eq. 3 zeta over the sparse points two images share
  *   Sec. III-F   depth-map fusion: greedy merging of back-projected pixels
  *                whose relative difference is below 0.01, image by image
  *   Sec. IV      parameters {r_now, r_orig, k1, k2, k3} = {5, 7, 4, 0.5, 2},
@@ -1206,4 +1208,84 @@ long or_fuse(const or_scene* s, int n, const int* order, const double* const* pl
     free(alive);
     free(cam);
     return np;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. III-A: neighbouring-image selection (Eqs. 1-3)                  */
+/* ------------------------------------------------------------------ */
+/* For reference image i and every other image j, A = the sparse points
+ * visible in both; Eq. 1 disturbs each X in A along the ray from the
+ * centre C_i, X^ = (1 + eps) X - eps C_i; Eq. 2 averages the displacement
+ * of its projection into j, tau = mean |x^'_j - x'_j|; Eq. 3 scores
+ * zeta = (1 / N_A) min(b_ij, 0.1) min(theta_ij, 0.05) with b_ij the
+ * baseline and theta_ij the angle between the principal axes (reading:
+ * radians).  Images with tau < t_tau or no shared point are removed (zeta
+ * reported as +inf); the rest are sorted by zeta from small to large (tie:
+ * lower index) and the first k kept.  X: 3 doubles per point; vis[p * n + v]
+ * = 1 when point p is visible in view v.  Outputs: nbr[i * k + r] (-1 past
+ * the kept ones), tau / zeta / n_shared [i * n + j] (NULL: not written). */
+void or_select_neighbors(const or_scene* s, long n_pts, const double* X, const unsigned char* vis, double eps,
+                         double t_tau, int k, int* nbr, double* tau_out, int* na_out, double* zeta_out) {
+    const int n = s->n;
+    double* C = (double*)malloc(sizeof(double) * 3 * n);
+    for (int v = 0; v < n; ++v) {
+        const double* R = s->v[v].R;
+        const double* t = s->v[v].t;
+        for (int a = 0; a < 3; ++a) C[3 * v + a] = -(R[a] * t[0] + R[3 + a] * t[1] + R[6 + a] * t[2]);
+    }
+    double* zeta = (double*)malloc(sizeof(double) * n);
+    int* cand = (int*)malloc(sizeof(int) * n);
+    for (int i = 0; i < n; ++i) {
+        const double* Ci = C + 3 * i;
+        const double* Ri = s->v[i].R;
+        int nc = 0;
+        for (int j = 0; j < n; ++j) {
+            zeta[j] = INFINITY;
+            if (j == i) continue;
+            const or_view* Vj = &s->v[j];
+            long na = 0;
+            double sum = 0.0;
+            for (long p = 0; p < n_pts; ++p) {
+                if (!vis[p * n + i] || !vis[p * n + j]) continue;
+                const double* Xp = X + 3 * p;
+                double Xh[3], c[3], ch[3], q[3], qh[3];
+                for (int a = 0; a < 3; ++a) Xh[a] = (1.0 + eps) * Xp[a] - eps * Ci[a];
+                m3_vec(Vj->R, Xp, c);
+                m3_vec(Vj->R, Xh, ch);
+                for (int a = 0; a < 3; ++a) { c[a] += Vj->t[a]; ch[a] += Vj->t[a]; }
+                m3_vec(Vj->K, c, q);
+                m3_vec(Vj->K, ch, qh);
+                double du = qh[0] / qh[2] - q[0] / q[2], dv = qh[1] / qh[2] - q[1] / q[2];
+                sum += sqrt(du * du + dv * dv);
+                na++;
+            }
+            double tau = na ? sum / (double)na : 0.0;
+            const double* Cj = C + 3 * j;
+            double db[3] = {Ci[0] - Cj[0], Ci[1] - Cj[1], Ci[2] - Cj[2]};
+            double b = sqrt(dot3(db, db));
+            double cs = Ri[6] * Vj->R[6] + Ri[7] * Vj->R[7] + Ri[8] * Vj->R[8];
+            double th = acos(cs > 1.0 ? 1.0 : (cs < -1.0 ? -1.0 : cs));
+            if (na > 0 && tau >= t_tau) {
+                zeta[j] = (1.0 / (double)na) * (b < 0.1 ? b : 0.1) * (th < 0.05 ? th : 0.05);
+                cand[nc++] = j;
+            }
+            if (tau_out) tau_out[(long)i * n + j] = tau;
+            if (na_out) na_out[(long)i * n + j] = (int)na;
+            if (zeta_out) zeta_out[(long)i * n + j] = zeta[j];
+        }
+        if (tau_out) tau_out[(long)i * n + i] = 0.0;
+        if (na_out) na_out[(long)i * n + i] = 0;
+        if (zeta_out) zeta_out[(long)i * n + i] = INFINITY;
+        /* sort by (zeta, index): insertion sort */
+        for (int a = 1; a < nc; ++a) {
+            int c = cand[a], b = a - 1;
+            while (b >= 0 && (zeta[cand[b]] > zeta[c] || (zeta[cand[b]] == zeta[c] && cand[b] > c))) {
+                cand[b + 1] = cand[b];
+                b--;
+            }
+            cand[b + 1] = c;
+        }
+        for (int r = 0; r < k; ++r) nbr[(long)i * k + r] = r < nc ? cand[r] : -1;
+    }
+    free(C); free(zeta); free(cand);
 }

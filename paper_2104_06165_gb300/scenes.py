@@ -403,3 +403,81 @@ def scene_batch(seed=0, sizes=((3072, 2048),) * 8 + ((2048, 1365),) * 8 + ((1536
                gt_textured=g0["textured"] if g0 else None, d_lo=2.0, d_hi=8.0, quads=quads)
     sc.gt_views = gts
     return sc, srcs
+
+
+def sparse_points(sc, n_points=4000, seed=0, obs_noise_px=0.5, outlier_frac=0.02):
+    """Synthetic structure-from-motion output for a scene: 3D points on the
+    textured parts of the quads (features are found on texture), each the
+    surface point seen through a uniformly drawn pixel of a random view, their visibility in every view (in front, inside the image and
+    not occluded by another quad), an observation per visible view (the
+    projection plus Gaussian noise of obs_noise_px) and the mean
+    reprojection error of the stored point.  A fraction outlier_frac of the
+    points is stored displaced by 2..10 % of its distance to the first
+    camera (wrong reconstructions, with large reprojection errors).
+
+    Returns dict(X (N, 3), vis (N, n_views) bool, obs (N, n_views, 2) with
+    NaN where not visible, reproj (N,))."""
+    rng = np.random.default_rng(seed)
+    pts = []
+    while len(pts) < n_points:
+        # the surface point seen through a random pixel of a random view
+        v = int(rng.integers(sc.n_views))
+        H, W = sc.images[v].shape
+        u, w = rng.uniform(0, W - 1), rng.uniform(0, H - 1)
+        C = -sc.R[v].T @ sc.t[v]
+        d = sc.R[v].T @ (np.linalg.inv(sc.K[v]) @ np.array([u, w, 1.0]))
+        best, hit = np.inf, None
+        for Q in sc.quads:
+            den = d @ Q.normal
+            if abs(den) < 1e-12:
+                continue
+            s_ = ((Q.center - C) @ Q.normal) / den
+            P = C + s_ * d - Q.center
+            a, b = P @ Q.e1, P @ Q.e2
+            if 0 < s_ < best and abs(a) <= Q.half[0] and abs(b) <= Q.half[1]:
+                best, hit = s_, (Q, a, b)
+        if hit is None:
+            continue
+        Q, a, b = hit
+        if not Q.textured or any(abs(a - c1) <= h1 and abs(b - c2) <= h2 for (c1, c2, h1, h2, _) in Q.blanks):
+            continue
+        pts.append(C + best * d)
+    X = np.array(pts)
+    n = sc.n_views
+    vis = np.zeros((len(X), n), bool)
+    obs = np.full((len(X), n, 2), np.nan)
+    for v in range(n):
+        K, R, t = sc.K[v], sc.R[v], sc.t[v]
+        H, W = sc.images[v].shape
+        C = -R.T @ t
+        q = (X @ R.T + t) @ K.T
+        z = q[:, 2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u, w = q[:, 0] / z, q[:, 1] / z
+        ok = (z > 0) & (u >= 0) & (u <= W - 1) & (w >= 0) & (w <= H - 1)
+        # occlusion: does the segment from the camera centre to X cross a quad?
+        d = X - C
+        for Q in sc.quads:
+            den = d @ Q.normal
+            with np.errstate(divide="ignore", invalid="ignore"):
+                s = ((Q.center - C) @ Q.normal) / den
+            P = C + s[:, None] * d - Q.center
+            hit = (s > 1e-9) & (s < 1.0 - 1e-6) & (np.abs(P @ Q.e1) <= Q.half[0]) & (np.abs(P @ Q.e2) <= Q.half[1])
+            ok &= ~hit
+        vis[:, v] = ok
+        obs[ok, v, 0] = u[ok] + rng.normal(0, obs_noise_px, ok.sum())
+        obs[ok, v, 1] = w[ok] + rng.normal(0, obs_noise_px, ok.sum())
+    # wrong reconstructions: the stored point moves off the surface
+    bad = rng.uniform(size=len(X)) < outlier_frac
+    C0 = -sc.R[0].T @ sc.t[0]
+    dirs = rng.normal(size=(len(X), 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    X = X + bad[:, None] * dirs * np.linalg.norm(X - C0, axis=1, keepdims=True) * rng.uniform(0.02, 0.10, (len(X), 1))
+    rep = np.zeros(len(X))
+    for v in range(n):
+        q = (X @ sc.R[v].T + sc.t[v]) @ sc.K[v].T
+        with np.errstate(divide="ignore", invalid="ignore"):
+            e = np.hypot(q[:, 0] / q[:, 2] - obs[:, v, 0], q[:, 1] / q[:, 2] - obs[:, v, 1])
+        rep += np.where(vis[:, v], e, 0.0)
+    rep /= np.maximum(vis.sum(1), 1)
+    return dict(X=X, vis=vis, obs=obs, reproj=rep)
