@@ -355,6 +355,24 @@ def run_batch(args):
     torch.cuda.synchronize()
     fuse_ms = f0.elapsed_time(f1) / reps
     merged = float(pts[:n_pts, 3].mean().item()) if n_pts else 0.0
+    # neighbouring-image selection (Sec. III-A) from synthetic SfM points
+    sp = scenes.sparse_points(sc, 20000, seed=7 + rank)
+    masks = np.zeros(len(sp["X"]), np.uint64)
+    for v in range(n):
+        masks |= sp["vis"][:, v].astype(np.uint64) << np.uint64(v)
+    d_X = torch.from_numpy(np.ascontiguousarray(sp["X"])).to(dev)
+    d_m = torch.from_numpy(masks.view(np.int64)).to(dev)
+    nbr = torch.zeros((n, 8), dtype=torch.int32, device=dev)
+    mvs.mvs_select_neighbors(ctx.h, d_X, d_m, nbr)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(reps):
+        mvs.mvs_select_neighbors(ctx.h, d_X, d_m, nbr)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    sel_ms = s0.elapsed_time(s1) / reps
+    nb = nbr.cpu().numpy()
+    agree = float(np.mean([len(set(nb[v][nb[v] >= 0].tolist()) & set(srcs[v])) / 8.0 for v in range(n)]))
     line = {"metric": "depth-map Mpix/s (batched PatchMatch + geometric filter)", "value": mpix * args.steps / (ms / 1e3),
             "unit": "Mpix/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -368,6 +386,11 @@ def run_batch(args):
                        "mpix_per_s": mpix / (fuse_ms / 1e3), "points": int(n_pts), "mean_merged": merged,
                        "views": len(refs), "note": "mvs_fuse of the 24 geometric-filter-masked maps, after the "
                                                    "timed steps (not inside them)"},
+            "neighbor_selection": {"ms": sel_ms, "points": int(len(sp["X"])), "views": n, "k": 8,
+                                   "shared_with_angle_rule": agree,
+                                   "note": "mvs_select_neighbors (Eqs. 1-3) from synthetic SfM points, after the "
+                                           "timed steps; shared_with_angle_rule = mean fraction of the 8 chosen "
+                                           "sources that are among the 10 the bench's 15-40 degree rule uses"},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     ctx.close()

@@ -227,6 +227,28 @@ mvs_status mvs_geo_filter(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_
 mvs_status mvs_fuse(mvs_ctx* ctx, int32_t n_views, const int32_t* views, const uint8_t* const* keep_masks,
                     float rel_tol, float* points, int32_t* src, int64_t capacity, int64_t* n_points, int32_t mem);
 
+/* Neighbouring-image selection (Sec. III-A, Eqs. 1-3) for every view of the
+ * context (2..64 views), from sparse 3D points of a structure-from-motion
+ * step.  For reference i and source j, A = the points visible in both;
+ * Eq. 1 disturbs X in A to (1 + eps) X - eps C_i; Eq. 2 gives tau = mean
+ * |x^'_j - x'_j| (pixels); sources with tau < t_tau or no shared point are
+ * removed and the rest sorted by Eq. 3's zeta = min(b_ij, 0.1)
+ * min(theta_ij, 0.05) / N_A (b: baseline, theta: angle between the
+ * principal axes in radians; tie: lower index).  FP64 throughout.
+ *   points: n_points x 3 doubles (world); vis: n_points masks, bit v set when
+ *   the point is visible in view v; eps, t_tau: the disturbance and the
+ *   threshold (the paper gives neither; 0.05 and 1 px are this library's
+ *   defaults); k: neighbours per view (the paper keeps 8).
+ *   neighbors: n_views x k int32, the selected sources per view in order,
+ *   -1 past the kept ones; tau / zeta (n_views x n_views doubles, zeta +inf
+ *   for removed sources) and n_shared (n_views x n_views int32) may be NULL.
+ *   All buffers in `mem`.  The call synchronises.
+ * Errors: MVS_EINVAL (view count, k outside 1..n_views-1, eps <= 0, t_tau < 0,
+ *   NULL buffers), MVS_ENOMEM, MVS_ECUDA. */
+mvs_status mvs_select_neighbors(mvs_ctx* ctx, int64_t n_points, const double* points, const uint64_t* vis,
+                                double eps, double t_tau, int32_t k, int32_t* neighbors, double* tau,
+                                int32_t* n_shared, double* zeta, int32_t mem);
+
 /* Plane hypothesis inference (Sec. III-E) on view `ref`: four line-fit
  * hypotheses per hole, their matching cost through the sources, a pairwise
  * MRF (Eq. 6-9) decoded by TRW at half resolution, closest-hypothesis

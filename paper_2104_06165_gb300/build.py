@@ -17,9 +17,11 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmvs.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
+# host code without fused multiply-add contraction: the FP64 per-view and
+# per-pair constants come out the same on x86-64 and Arm hosts
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-Xptxas", "-warn-spills"]
-SOURCES = ["mvs_api.cu", "pm_kernels.cu", "phi_kernels.cu", "cnn_kernels.cu", "fuse_kernels.cu"]
+SOURCES = ["mvs_api.cu", "pm_kernels.cu", "phi_kernels.cu", "cnn_kernels.cu", "fuse_kernels.cu", "select_kernels.cu"]
 
 
 def _deps():

@@ -685,6 +685,74 @@ mvs_status mvs_fuse(mvs_ctx* c, int32_t n_views, const int32_t* views, const uin
     return MVS_OK;
 }
 
+mvs_status mvs_select_neighbors(mvs_ctx* c, int64_t n_points, const double* points, const uint64_t* vis, double eps,
+                                double t_tau, int32_t k, int32_t* neighbors, double* tau, int32_t* n_shared,
+                                double* zeta, int32_t mem) {
+    if (!c) return MVS_EINVAL;
+    const int n = (int)c->views.size();
+    if (n < 2 || n > MVS_MAX_VIEWS_SELECT) return fail(c, MVS_EINVAL, "need 2..%d views", MVS_MAX_VIEWS_SELECT);
+    if (n_points < 0 || (n_points > 0 && (!points || !vis)) || !neighbors || k < 1 || k > n - 1)
+        return fail(c, MVS_EINVAL, "bad arguments (k must lie in 1..n_views-1)");
+    if (!(eps > 0.0) || !(t_tau >= 0.0)) return fail(c, MVS_EINVAL, "need eps > 0, t_tau >= 0");
+    if (mem != MVS_MEM_DEVICE && mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    CK(c, cudaSetDevice(c->device));
+    // per-view cameras and per-pair constants in FP64 (host): baseline and
+    // angle between the principal axes (third rows of R)
+    std::vector<NbrView> nv(n);
+    std::vector<double> base((size_t)n * n), angle((size_t)n * n);
+    for (int v = 0; v < n; ++v) {
+        const mvs_camera& cam = c->views[v].cam;
+        for (int a = 0; a < 9; ++a) { nv[v].K[a] = cam.K[a]; nv[v].R[a] = cam.R[a]; }
+        for (int a = 0; a < 3; ++a) nv[v].t[a] = cam.t[a];
+        for (int a = 0; a < 3; ++a) nv[v].C[a] = -(cam.R[a] * cam.t[0] + cam.R[3 + a] * cam.t[1] + cam.R[6 + a] * cam.t[2]);
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const double d0 = nv[i].C[0] - nv[j].C[0], d1 = nv[i].C[1] - nv[j].C[1], d2 = nv[i].C[2] - nv[j].C[2];
+            base[(size_t)i * n + j] = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            const double cs = nv[i].R[6] * nv[j].R[6] + nv[i].R[7] * nv[j].R[7] + nv[i].R[8] * nv[j].R[8];
+            angle[(size_t)i * n + j] = std::acos(cs > 1.0 ? 1.0 : (cs < -1.0 ? -1.0 : cs));
+        }
+    // scratch slot 7: views, per-pair constants and results; host inputs
+    const size_t nn = (size_t)n * n;
+    size_t bytes = 256 + sizeof(NbrView) * n + nn * (4 * sizeof(double) + sizeof(int)) + (size_t)n * k * sizeof(int);
+    if (mem == MVS_MEM_HOST) bytes += (size_t)n_points * (3 * sizeof(double) + sizeof(uint64_t)) + 64;
+    cudaError_t e;
+    char* q = (char*)scratch(c, 7, bytes, &e);
+    CK(c, e);
+    auto take = [&](size_t b) { char* r = q; q += (b + 15) & ~(size_t)15; return (void*)r; };
+    NbrView* d_views = (NbrView*)take(sizeof(NbrView) * n);
+    double* d_base = (double*)take(nn * sizeof(double));
+    double* d_angle = (double*)take(nn * sizeof(double));
+    double* d_tau = (double*)take(nn * sizeof(double));
+    double* d_zeta = (double*)take(nn * sizeof(double));
+    int* d_na = (int*)take(nn * sizeof(int));
+    int* d_nbr = (int*)take((size_t)n * k * sizeof(int));
+    const double* d_X = points;
+    const unsigned long long* d_vis = (const unsigned long long*)vis;
+    if (mem == MVS_MEM_HOST && n_points > 0) {
+        double* x = (double*)take((size_t)n_points * 3 * sizeof(double));
+        unsigned long long* m = (unsigned long long*)take((size_t)n_points * sizeof(uint64_t));
+        CK(c, cudaMemcpyAsync(x, points, (size_t)n_points * 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(m, vis, (size_t)n_points * sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream));
+        d_X = x;
+        d_vis = m;
+    }
+    CK(c, cudaMemcpyAsync(d_views, nv.data(), sizeof(NbrView) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(d_base, base.data(), nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(d_angle, angle.data(), nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(c, launch_select_neighbors(d_views, n, d_X, d_vis, n_points, eps, t_tau, k, d_base, d_angle, d_tau, d_na,
+                                  d_zeta, d_nbr, c->stream));
+    const cudaMemcpyKind ko = kind_out(mem);
+    CK(c, cudaMemcpyAsync(neighbors, d_nbr, (size_t)n * k * sizeof(int), ko, c->stream));
+    if (tau) CK(c, cudaMemcpyAsync(tau, d_tau, nn * sizeof(double), ko, c->stream));
+    if (n_shared) CK(c, cudaMemcpyAsync(n_shared, d_na, nn * sizeof(int), ko, c->stream));
+    if (zeta) CK(c, cudaMemcpyAsync(zeta, d_zeta, nn * sizeof(double), ko, c->stream));
+    // the host vectors above are staged by the copies; wait for them
+    CK(c, cudaStreamSynchronize(c->stream));
+    return MVS_OK;
+}
+
 mvs_status mvs_phi_hypotheses(mvs_ctx* c, int32_t W, int32_t H, const float* depth, const uint8_t* known,
                               const mvs_phi_params* phi, float d_lo, float d_hi, float* hyp, uint8_t* valid,
                               int32_t mem) {

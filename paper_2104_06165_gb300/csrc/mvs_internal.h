@@ -130,6 +130,18 @@ cudaError_t launch_fuse(const FuseView* host_views, FuseView* dev_views, int n, 
                         int* block_count, long long* block_off, long long* total, float4* points, int2* src,
                         long long cap, cudaStream_t s);
 
+// neighbouring-image selection (select_kernels.cu): at most 64 views (one
+// visibility bit per view in a 64-bit mask per sparse point)
+#define MVS_MAX_VIEWS_SELECT 64
+struct NbrView {
+    double K[9], R[9], t[3];     // x_cam = R X + t
+    double C[3];                 // camera centre -R^T t
+};
+cudaError_t launch_select_neighbors(const NbrView* dev_views, int n, const double* X, const unsigned long long* vis,
+                                    long long n_pts, double eps, double t_tau, int k, const double* base,
+                                    const double* angle, double* tau, int* na, double* zeta, int* nbr,
+                                    cudaStream_t s);
+
 // learned proposals (cnn_kernels.cu)
 struct mvs_cnn;
 cudaError_t cnn_propose(mvs_cnn* n, const uint8_t* img, const float4* plane, const float* cost, int W, int H,

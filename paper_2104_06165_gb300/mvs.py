@@ -183,6 +183,8 @@ def load():
     L.mvs_propose.argtypes = [vp, i32, vp, fp]
     L.mvs_fuse.restype = i32
     L.mvs_fuse.argtypes = [vp, i32, ip, C.c_void_p, C.c_float, fp, vp, C.c_int64, C.POINTER(C.c_int64), i32]
+    L.mvs_select_neighbors.restype = i32
+    L.mvs_select_neighbors.argtypes = [vp, C.c_int64, vp, vp, C.c_double, C.c_double, i32, vp, vp, vp, vp, i32]
     L.mvs_profile_read.restype = i32
     L.mvs_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_int64)]
@@ -319,6 +321,18 @@ def mvs_fuse(ctx, views, points, src=None, keep_masks=None, rel_tol=0.01):
     _check(load().mvs_fuse(ctx, nv, v, km, C.c_float(rel_tol), _ptr(points)[0], _ptr(src)[0], cap, C.byref(n), mem),
            ctx)
     return n.value
+
+
+def mvs_select_neighbors(ctx, points, vis, neighbors, tau=None, n_shared=None, zeta=None, eps=0.05, t_tau=1.0):
+    """Neighbouring-image selection of every context view from sparse points
+    (n, 3) float64 and visibility masks vis (n,) uint64 (bit v: visible in
+    view v) into neighbors (n_views, k) int32; optional (n_views, n_views)
+    outputs tau / zeta (float64) and n_shared (int32)."""
+    mem = _mem(points, vis, neighbors, tau, n_shared, zeta)
+    k = neighbors.shape[1]
+    _check(load().mvs_select_neighbors(ctx, points.shape[0], _ptr(points)[0], _ptr(vis)[0], float(eps), float(t_tau),
+                                       k, _ptr(neighbors)[0], _ptr(tau)[0], _ptr(n_shared)[0], _ptr(zeta)[0], mem),
+           ctx)
 
 
 def mvs_plane_infer(ctx, ref, srcs, pm: PMParams, phi: PhiParams, keep_mask, plane, cost):
