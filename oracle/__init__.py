@@ -42,7 +42,8 @@ def build(force: bool = False) -> str:
 class _PM(C.Structure):
     _fields_ = [("win_radius", C.c_double), ("win_samples", C.c_int), ("sigma_s", C.c_double),
                 ("sigma_c", C.c_double), ("d_lo", C.c_double), ("d_hi", C.c_double),
-                ("seed", C.c_uint64), ("n_prop", C.c_int), ("props", C.POINTER(C.c_double))]
+                ("seed", C.c_uint64), ("n_prop", C.c_int), ("props", C.POINTER(C.c_double)),
+                ("init_range", C.POINTER(C.c_float))]
 
 
 class _Filter(C.Structure):
@@ -106,6 +107,11 @@ def lib():
             L.or_fuse.argtypes = [vp, C.c_int, ip, C.POINTER(dp), C.POINTER(up), C.c_double,
                                   C.POINTER(C.c_float), ip, C.POINTER(C.c_long), C.c_long]
             L.or_select_neighbors.argtypes = [vp, C.c_long, dp, up, C.c_double, C.c_double, C.c_int, ip, dp, ip, dp]
+            L.or_sparse_features.restype = C.c_long
+            L.or_sparse_features.argtypes = [vp, C.c_int, C.c_long, dp, up, dp, dp, C.c_double,
+                                             C.POINTER(C.c_float), C.POINTER(C.c_float)]
+            L.or_sparse_range.argtypes = [C.c_int, C.c_int, C.c_long, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                          C.c_float, C.c_float, C.POINTER(C.c_float)]
             _lib = L
     return _lib
 
@@ -126,13 +132,15 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def _pm(p, props=None) -> _PM:
-    """props: None or an FP64 array (H, W, K, 4) kept alive by the caller."""
+def _pm(p, props=None, init_range=None) -> _PM:
+    """props: None or an FP64 array (H, W, K, 4); init_range: None or a
+    float32 array (H, W, 2); both kept alive by the caller."""
+    rng = init_range.ctypes.data_as(C.POINTER(C.c_float)) if init_range is not None else None
     if props is None:
         return _PM(float(p.win_radius), int(p.win_samples), float(p.sigma_s), float(p.sigma_c),
-                   float(p.d_lo), float(p.d_hi), int(p.seed) & 0xFFFFFFFFFFFFFFFF, 0, None)
+                   float(p.d_lo), float(p.d_hi), int(p.seed) & 0xFFFFFFFFFFFFFFFF, 0, None, rng)
     return _PM(float(p.win_radius), int(p.win_samples), float(p.sigma_s), float(p.sigma_c),
-               float(p.d_lo), float(p.d_hi), int(p.seed) & 0xFFFFFFFFFFFFFFFF, int(props.shape[2]), _d(props))
+               float(p.d_lo), float(p.d_hi), int(p.seed) & 0xFFFFFFFFFFFFFFFF, int(props.shape[2]), _d(props), rng)
 
 
 class Scene:
@@ -240,13 +248,15 @@ def aggregate(cj, ok):
     return lib().or_aggregate(len(cj), _d(cj), _i(ok))
 
 
-def init(scene, ref, srcs, p, with_cost=True):
-    """Sec. III-B random initialisation (Philox draws) and its cost."""
+def init(scene, ref, srcs, p, with_cost=True, init_range=None):
+    """Sec. III-B random initialisation (Philox draws) and its cost;
+    init_range (H, W, 2) float32 gives per-pixel depth ranges (NaN: none)."""
     H, W = scene.shape(ref)
     s = _srcs(srcs)
     plane = np.zeros((H, W, 4), np.float64)
     cost = np.zeros((H, W), np.float64)
-    lib().or_init(scene.h, ref, _i(s), len(s), C.byref(_pm(p)), _d(plane),
+    rng = None if init_range is None else np.ascontiguousarray(init_range, np.float32)
+    lib().or_init(scene.h, ref, _i(s), len(s), C.byref(_pm(p, init_range=rng)), _d(plane),
                   _d(cost) if with_cost else None)
     return plane, cost
 
@@ -458,3 +468,30 @@ def select_neighbors(scene, X, vis, eps=0.05, t_tau=1.0, k=8):
     lib().or_select_neighbors(scene.h, len(X), _d(X), _u8(vis), float(eps), float(t_tau), int(k), _i(nbr), _d(tau),
                               _i(na), _d(zeta))
     return nbr, tau, na, zeta
+
+
+def sparse_features(scene, ref, X, vis, reproj, obs, max_reproj=2.0):
+    """Sec. III-B features of view ref from sparse points (X (n, 3), vis
+    (n, n_views) bool, reproj (n,), obs (n, 2) observations in ref).
+    Returns (uv (m, 2) float32, depth (m,) float32)."""
+    X = _f64(np.asarray(X).reshape(-1, 3))
+    vis = np.ascontiguousarray(vis, np.uint8)
+    n = len(X)
+    obs = _f64(np.nan_to_num(np.asarray(obs, np.float64).reshape(n, 2)))
+    uv = np.zeros((max(n, 1), 2), np.float32)
+    dep = np.zeros(max(n, 1), np.float32)
+    f32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+    m = lib().or_sparse_features(scene.h, ref, n, _d(X), _u8(vis), _d(_f64(reproj)), _d(obs), float(max_reproj),
+                                 f32(uv), f32(dep))
+    return uv[:m], dep[:m]
+
+
+def sparse_range(W, H, uv, depth, d_lo=2.0, d_hi=8.0):
+    """Per-pixel (d_min, d_max) of the closest features in four quadrants
+    within W / 10 px (NaN: none), (H, W, 2) float32."""
+    uv = np.ascontiguousarray(uv, np.float32).reshape(-1, 2)
+    depth = np.ascontiguousarray(depth, np.float32).ravel()
+    out = np.zeros((H, W, 2), np.float32)
+    f32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+    lib().or_sparse_range(int(W), int(H), len(depth), f32(uv), f32(depth), float(d_lo), float(d_hi), f32(out))
+    return out

@@ -9,7 +9,9 @@
  * blocking, fusion or reordering.
  *
  * Passages followed (section / equation of the paper):
- *   Sec. III-B   random initialisation of depth and normal (theta, phi form)
+ *   Sec. III-B   random initialisation of depth and normal (theta, phi form),
+ *                or the depth drawn between the nearest sparse features in
+ *                four quadrants
  *   Sec. III-C   dilated window (scale s = r_orig / r_now), Eq. 4 ZNCC with
  *                bilinear samples and homography mapping, C(x,j) = 1 - Z,
  *                C_max for out-of-border samples, Eq. 5 aggregation with
@@ -72,6 +74,8 @@ typedef struct {
     uint64_t seed;
     int n_prop;          /* learned proposals per pixel (0: none)           */
     const double* props; /* H*W*n_prop*4 planes (nx, ny, nz, d) or NULL     */
+    const float* init_range; /* H*W*2 (d_min, d_max) of the sparse-feature
+                                initialisation (NaN: none) or NULL          */
 } or_pm;
 
 static void m3_mul(const double* A, const double* B, double* C) {
@@ -436,6 +440,11 @@ void or_init(const or_scene* s, int ref, const int* srcs, int ns, const or_pm* p
             double u[3];
             draws(p, ref, i, -1, u);
             double d = p->d_lo + (p->d_hi - p->d_lo) * u[0];
+            /* Sec. III-B: a depth drawn in [d_min, d_max] of the sparse features */
+            if (p->init_range && p->init_range[2 * i] == p->init_range[2 * i]) {
+                double lo = p->init_range[2 * i], hi = p->init_range[2 * i + 1];
+                d = lo + (hi - lo) * u[0];
+            }
             double th = 2 * OR_PI * u[1];
             double ph = OR_PI * (u[2] - 0.5);
             double n[3], xt[3] = {(double)x, (double)y, 1.0}, r[3];
@@ -1288,4 +1297,83 @@ void or_select_neighbors(const or_scene* s, long n_pts, const double* X, const u
         for (int r = 0; r < k; ++r) nbr[(long)i * k + r] = r < nc ? cand[r] : -1;
     }
     free(C); free(zeta); free(cand);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. III-B: depth initialisation from sparse feature points           */
+/* ------------------------------------------------------------------ */
+/* Features of view ref: the sparse 3D points visible in it whose
+ * re-projection error is below max_reproj (reading: the point's mean error
+ * over its views) and that are visible in at least floor(v - 1) images, v
+ * the mean number of images per point.  Each keeps its observation in ref
+ * (uv, rounded to float) and its z-depth in ref (FP64, rounded to float).
+ * vis[p * n + v] = 1 when point p is visible in view v; obs[2p..2p+1] = its
+ * observation in ref.  Writes uv[2k..], depth[k] in point order and returns
+ * the number of features. */
+long or_sparse_features(const or_scene* s, int ref, long n_pts, const double* X, const unsigned char* vis,
+                        const double* reproj, const double* obs, double max_reproj, float* uv, float* depth) {
+    const int n = s->n;
+    long total = 0;
+    for (long p = 0; p < n_pts; ++p)
+        for (int v = 0; v < n; ++v) total += vis[p * n + v] ? 1 : 0;
+    const double vbar = n_pts ? (double)total / (double)n_pts : 0.0;
+    const int min_views = (int)floor(vbar - 1.0);
+    const double* R = s->v[ref].R;
+    const double* t = s->v[ref].t;
+    long k = 0;
+    for (long p = 0; p < n_pts; ++p) {
+        int cnt = 0;
+        for (int v = 0; v < n; ++v) cnt += vis[p * n + v] ? 1 : 0;
+        if (!vis[p * n + ref] || !(reproj[p] < max_reproj) || cnt < min_views) continue;
+        const double* Xp = X + 3 * p;
+        double z = R[6] * Xp[0] + R[7] * Xp[1] + R[8] * Xp[2] + t[2];
+        uv[2 * k] = (float)obs[2 * p];
+        uv[2 * k + 1] = (float)obs[2 * p + 1];
+        depth[k] = (float)z;
+        k++;
+    }
+    return k;
+}
+
+/* Per pixel of a W x H view, the closest feature in each of the four
+ * quadrants around it (dx >= 0, dy >= 0 / dx < 0, dy >= 0 / dx < 0, dy < 0 /
+ * dx >= 0, dy < 0 with dx = u - x, dy = v - y) within w / 10 pixels, and the
+ * minimum and maximum depth over those features, clamped to [d_lo, d_hi]
+ * (reading); NaN when no feature is that close.  The choice of the closest
+ * feature is an integer decision and is taken in single precision:
+ * r = W / 10, d2 = dx dx + dy dy < r r, every operation rounded on its own;
+ * the first feature wins a tie.  range[2i], range[2i+1] = d_min, d_max. */
+void or_sparse_range(int W, int H, long n_feat, const float* uv, const float* depth, float d_lo, float d_hi,
+                     float* range) {
+    const float r = (float)W / 10.0f;
+    const float r2 = r * r;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            float best[4] = {INFINITY, INFINITY, INFINITY, INFINITY}, bd[4] = {0, 0, 0, 0};
+            for (long f = 0; f < n_feat; ++f) {
+                float dx = uv[2 * f] - (float)x, dy = uv[2 * f + 1] - (float)y;
+                float d2 = dx * dx + dy * dy;
+                if (!(d2 < r2)) continue;
+                int q = dx >= 0.0f ? (dy >= 0.0f ? 0 : 3) : (dy >= 0.0f ? 1 : 2);
+                if (d2 < best[q]) {
+                    best[q] = d2;
+                    bd[q] = depth[f];
+                }
+            }
+            float lo = INFINITY, hi = -INFINITY;
+            for (int q = 0; q < 4; ++q)
+                if (best[q] < INFINITY) {
+                    lo = bd[q] < lo ? bd[q] : lo;
+                    hi = bd[q] > hi ? bd[q] : hi;
+                }
+            long i = (long)y * W + x;
+            if (lo <= hi) {
+                lo = lo < d_lo ? d_lo : (lo > d_hi ? d_hi : lo);
+                hi = hi < d_lo ? d_lo : (hi > d_hi ? d_hi : hi);
+                range[2 * i] = lo;
+                range[2 * i + 1] = hi;
+            } else {
+                range[2 * i] = range[2 * i + 1] = NAN;
+            }
+        }
 }
