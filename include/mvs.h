@@ -55,7 +55,9 @@ typedef struct mvs_ctx mvs_ctx;   /* opaque, owned by the library */
 enum { MVS_MEM_DEVICE = 0, MVS_MEM_HOST = 1 };
 enum { MVS_INIT_RANDOM = 0,       /* Sec. III-B random initialisation        */
        MVS_INIT_GIVEN = 1,        /* start from out->plane and out->cost     */
-       MVS_INIT_GIVEN_RECOST = 2  /* start from out->plane, compute its cost */
+       MVS_INIT_GIVEN_RECOST = 2, /* start from out->plane, compute its cost */
+       MVS_INIT_RANGE = 3         /* Sec. III-B with per-pixel depth ranges
+                                     from sparse features (init_range)       */
 };
 
 /* PatchMatch parameters (Sec. III-B, III-C; defaults in Sec. IV). */
@@ -98,7 +100,13 @@ typedef struct {
                               the propagation step, judged by Eq. 5).  Zero
                               depth marks an unused slot.  NULL with
                               n_prop = 0.                                    */
-    int32_t reserved[2];
+    const float* init_range;/* DEVICE, H*W*2 (d_min, d_max) per pixel for
+                              init_mode MVS_INIT_RANGE, e.g. from
+                              mvs_sparse_depth_range: the initial depth is
+                              d_min + (d_max - d_min) u with the Philox draw u
+                              of the random initialisation; NaN: the whole
+                              range [d_lo, d_hi].  8-byte aligned.  NULL for
+                              the other modes.                               */
 } mvs_pm_params;
 
 /* Depth-map buffers supplied by the caller. */
@@ -248,6 +256,27 @@ mvs_status mvs_fuse(mvs_ctx* ctx, int32_t n_views, const int32_t* views, const u
 mvs_status mvs_select_neighbors(mvs_ctx* ctx, int64_t n_points, const double* points, const uint64_t* vis,
                                 double eps, double t_tau, int32_t k, int32_t* neighbors, double* tau,
                                 int32_t* n_shared, double* zeta, int32_t mem);
+
+/* Per-pixel depth ranges for the initialisation from sparse features
+ * (Sec. III-B) of view `ref`.  Features: the sparse points visible in ref
+ * whose re-projection error is below max_reproj (the paper's 2) and that
+ * are visible in at least floor(v - 1) images, v the mean number of images
+ * per point; each keeps its observation in ref and its z-depth there.  Per
+ * pixel, the closest feature in each of the four quadrants around it within
+ * W / 10 pixels gives [d_min, d_max] over those features, clamped to
+ * [d_lo, d_hi]; NaN where no feature is that close.  The closest-feature
+ * choice is taken in single precision, every operation rounded on its own,
+ * the first point winning a tie.
+ *   points: n_points x 3 doubles (world); vis: n_points masks (bit v:
+ *   visible in view v); reproj: n_points doubles; obs: n_points x 2 doubles,
+ *   the observation of each point in view ref (any value where not visible);
+ *   range: H*W*2 floats (d_min, d_max) out.  All in `mem`.  The call
+ *   synchronises when mem is MVS_MEM_HOST.
+ * Errors: MVS_EINVAL (bad view, NULL buffers, d_lo >= d_hi, more than 64
+ *   views), MVS_ENOMEM, MVS_ECUDA. */
+mvs_status mvs_sparse_depth_range(mvs_ctx* ctx, int32_t ref, int64_t n_points, const double* points,
+                                  const uint64_t* vis, const double* reproj, const double* obs, double max_reproj,
+                                  float d_lo, float d_hi, float* range, int32_t mem);
 
 /* Plane hypothesis inference (Sec. III-E) on view `ref`: four line-fit
  * hypotheses per hole, their matching cost through the sources, a pairwise

@@ -125,6 +125,16 @@ void* scratch(mvs_ctx* c, int slot, size_t bytes, cudaError_t* e) {
     return s.p;
 }
 
+// true when p is device (or managed) memory the kernels can read
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 mvs_status check_view(mvs_ctx* c, int32_t v) {
     if (!c) return MVS_EINVAL;
     if (v < 0 || v >= (int32_t)c->views.size()) return fail(c, MVS_EINVAL, "view index %d out of range", v);
@@ -158,6 +168,7 @@ mvs_status check_pm(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src,
     if ((p->n_prop > 0) != (p->proposals != nullptr))
         return fail(c, MVS_EINVAL, "proposals must be given exactly when n_prop > 0");
     if ((uintptr_t)p->proposals & 15u) return fail(c, MVS_EINVAL, "proposals must be 16-byte aligned");
+    if (p->proposals && !is_device_ptr(p->proposals)) return fail(c, MVS_EINVAL, "proposals must be device memory");
     return MVS_OK;
 }
 
@@ -187,6 +198,7 @@ void make_refconst(const mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n
     rc.precision = p->precision;
     rc.n_prop = p->n_prop;
     rc.props = reinterpret_cast<const float4*>(p->proposals);
+    rc.init_range = p->init_mode == MVS_INIT_RANGE ? reinterpret_cast<const float2*>(p->init_range) : nullptr;
     rc.plane = R.plane;
     rc.cost = R.cost;
     for (int j = 0; j < n_src; ++j) {
@@ -308,8 +320,10 @@ mvs_status mvs_patchmatch(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t 
     if (((uintptr_t)out->plane & 15u) || ((uintptr_t)out->cost & 3u))
         return fail(c, MVS_EINVAL, "plane must be 16-byte and cost 4-byte aligned");
     if (out->mem != MVS_MEM_DEVICE && out->mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
-    if (p->init_mode < MVS_INIT_RANDOM || p->init_mode > MVS_INIT_GIVEN_RECOST)
-        return fail(c, MVS_EINVAL, "bad init_mode");
+    if (p->init_mode < MVS_INIT_RANDOM || p->init_mode > MVS_INIT_RANGE) return fail(c, MVS_EINVAL, "bad init_mode");
+    if ((p->init_mode == MVS_INIT_RANGE) != (p->init_range != nullptr) || ((uintptr_t)p->init_range & 7u))
+        return fail(c, MVS_EINVAL, "init_range (8-byte aligned) must be given exactly with MVS_INIT_RANGE");
+    if (p->init_range && !is_device_ptr(p->init_range)) return fail(c, MVS_EINVAL, "init_range must be device memory");
     int pend = p->phase_end < 0 ? 2 * p->iters : p->phase_end;
     if (p->phase_begin < 0 || pend < p->phase_begin) return fail(c, MVS_EINVAL, "bad phase range");
     CK(c, cudaSetDevice(c->device));
@@ -318,7 +332,7 @@ mvs_status mvs_patchmatch(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t 
     size_t n = (size_t)V.cam.width * V.cam.height;
     RefConst rc;
     make_refconst(c, ref, srcs, n_src, p, rc);
-    if (p->init_mode == MVS_INIT_RANDOM) {
+    if (p->init_mode == MVS_INIT_RANDOM || p->init_mode == MVS_INIT_RANGE) {
         CK(c, launch_init(rc, nullptr, c->stream));
     } else {
         CK(c, cudaMemcpyAsync(V.plane, out->plane, n * sizeof(float4), kind_in(out->mem), c->stream));
@@ -425,6 +439,8 @@ mvs_status mvs_patchmatch_batch(mvs_ctx* c, int32_t n_ref, const int32_t* refs, 
         if (outs[r].mem != outs[0].mem || (outs[r].mem != MVS_MEM_DEVICE && outs[r].mem != MVS_MEM_HOST))
             return fail(c, MVS_EINVAL, "all outputs must be in the same memory kind");
     }
+    if (p->init_mode == MVS_INIT_RANGE)
+        return fail(c, MVS_EUNSUPPORTED, "depth ranges are per view: use mvs_patchmatch");
     if (p->init_mode < MVS_INIT_RANDOM || p->init_mode > MVS_INIT_GIVEN_RECOST)
         return fail(c, MVS_EINVAL, "bad init_mode");
     int pend = p->phase_end < 0 ? 2 * p->iters : p->phase_end;
@@ -750,6 +766,61 @@ mvs_status mvs_select_neighbors(mvs_ctx* c, int64_t n_points, const double* poin
     if (zeta) CK(c, cudaMemcpyAsync(zeta, d_zeta, nn * sizeof(double), ko, c->stream));
     // the host vectors above are staged by the copies; wait for them
     CK(c, cudaStreamSynchronize(c->stream));
+    return MVS_OK;
+}
+
+mvs_status mvs_sparse_depth_range(mvs_ctx* c, int32_t ref, int64_t n_points, const double* points, const uint64_t* vis,
+                                  const double* reproj, const double* obs, double max_reproj, float d_lo, float d_hi,
+                                  float* range, int32_t mem) {
+    mvs_status st = check_view(c, ref);
+    if (st != MVS_OK) return st;
+    if (c->views.size() > MVS_MAX_VIEWS_SELECT) return fail(c, MVS_EINVAL, "at most %d views", MVS_MAX_VIEWS_SELECT);
+    if (n_points < 0 || (n_points > 0 && (!points || !vis || !reproj || !obs)) || !range)
+        return fail(c, MVS_EINVAL, "NULL argument");
+    if (!(d_lo < d_hi)) return fail(c, MVS_EINVAL, "need d_lo < d_hi");
+    if (mem != MVS_MEM_DEVICE && mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    CK(c, cudaSetDevice(c->device));
+    const ViewData& V = c->views[ref];
+    const int W = V.cam.width, H = V.cam.height;
+    const size_t np = (size_t)n_points, npix = (size_t)W * H;
+    auto a16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    size_t bytes = 16 + a16(np * sizeof(float2)) + a16(np * sizeof(float));
+    if (mem == MVS_MEM_HOST) bytes += a16(np * 3 * 8) + a16(np * 8) + a16(np * 8) + a16(np * 2 * 8) + a16(npix * 8);
+    cudaError_t e;
+    char* q = (char*)scratch(c, 7, bytes, &e);
+    CK(c, e);
+    auto take = [&](size_t b) { char* r = q; q += a16(b); return (void*)r; };
+    unsigned long long* total = (unsigned long long*)take(16);
+    float2* uv = (float2*)take(np * sizeof(float2));
+    float* dep = (float*)take(np * sizeof(float));
+    const double* dX = points;
+    const unsigned long long* dvis = (const unsigned long long*)vis;
+    const double* drep = reproj;
+    const double* dobs = obs;
+    float2* drange = (float2*)range;
+    if (mem == MVS_MEM_HOST) {
+        double* x = (double*)take(np * 3 * 8);
+        unsigned long long* m = (unsigned long long*)take(np * 8);
+        double* rp = (double*)take(np * 8);
+        double* ob = (double*)take(np * 2 * 8);
+        drange = (float2*)take(npix * 8);
+        if (np) {
+            CK(c, cudaMemcpyAsync(x, points, np * 3 * 8, cudaMemcpyHostToDevice, c->stream));
+            CK(c, cudaMemcpyAsync(m, vis, np * 8, cudaMemcpyHostToDevice, c->stream));
+            CK(c, cudaMemcpyAsync(rp, reproj, np * 8, cudaMemcpyHostToDevice, c->stream));
+            CK(c, cudaMemcpyAsync(ob, obs, np * 2 * 8, cudaMemcpyHostToDevice, c->stream));
+        }
+        dX = x; dvis = m; drep = rp; dobs = ob;
+    } else if (((uintptr_t)range & 7u)) {
+        return fail(c, MVS_EINVAL, "range must be 8-byte aligned");
+    }
+    const double Rrow2[3] = {V.cam.R[6], V.cam.R[7], V.cam.R[8]};
+    CK(c, launch_sparse_range(ref, (int)c->views.size(), Rrow2, V.cam.t[2], dX, dvis, drep, dobs, (long long)np,
+                              max_reproj, W, H, d_lo, d_hi, total, uv, dep, drange, c->stream));
+    if (mem == MVS_MEM_HOST) {
+        CK(c, cudaMemcpyAsync(range, drange, npix * 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
     return MVS_OK;
 }
 

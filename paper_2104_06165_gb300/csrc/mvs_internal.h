@@ -45,6 +45,7 @@ struct RefConst {
     int precision;             // 0 = FP32, 1 = mixed (half2 bilinear, FP32 moments)
     int n_prop;                // learned proposals per pixel (0 = none)
     const float4* props;       // H*W*n_prop planes (n, depth), or null
+    const float2* init_range;  // H*W (d_min, d_max) of the sparse-feature initialisation (NaN: none), or null
     PairConst pair[MVS_MAX_SRC];
 };
 
@@ -141,6 +142,11 @@ cudaError_t launch_select_neighbors(const NbrView* dev_views, int n, const doubl
                                     long long n_pts, double eps, double t_tau, int k, const double* base,
                                     const double* angle, double* tau, int* na, double* zeta, int* nbr,
                                     cudaStream_t s);
+
+cudaError_t launch_sparse_range(int ref, int n_views, const double Rrow2[3], double t2, const double* X,
+                                const unsigned long long* vis, const double* reproj, const double* obs,
+                                long long n_pts, double max_reproj, int W, int H, float d_lo, float d_hi,
+                                unsigned long long* total, float2* uv, float* depth, float2* range, cudaStream_t s);
 
 // learned proposals (cnn_kernels.cu)
 struct mvs_cnn;

@@ -77,6 +77,10 @@ __global__ void __launch_bounds__(kBlock) k_init(const __grid_constant__ RefCons
         float u[3];
         draws3(rc, a, -1, u);
         float d = rc.d_lo + (rc.d_hi - rc.d_lo) * u[0];
+        if (rc.init_range) {   // Sec. III-B: a depth between the nearest sparse features
+            const float2 r = rc.init_range[a];
+            if (r.x == r.x) d = r.x + (r.y - r.x) * u[0];
+        }
         float th = 2.0f * kPi * u[1];
         float ph = kPi * (u[2] - 0.5f);
         float n0, n1, n2;

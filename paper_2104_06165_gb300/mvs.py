@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libmvs.so")
 
 MVS_OK, MVS_EINVAL, MVS_ENOMEM, MVS_ECUDA, MVS_ETIMEOUT, MVS_ESTATE, MVS_EUNSUPPORTED = range(7)
 MVS_MEM_DEVICE, MVS_MEM_HOST = 0, 1
-MVS_INIT_RANDOM, MVS_INIT_GIVEN, MVS_INIT_GIVEN_RECOST = 0, 1, 2
+MVS_INIT_RANDOM, MVS_INIT_GIVEN, MVS_INIT_GIVEN_RECOST, MVS_INIT_RANGE = 0, 1, 2, 3
 STATUS_NAMES = ["MVS_OK", "MVS_EINVAL", "MVS_ENOMEM", "MVS_ECUDA", "MVS_ETIMEOUT", "MVS_ESTATE",
                 "MVS_EUNSUPPORTED"]
 
@@ -41,7 +41,7 @@ class mvs_pm_params(C.Structure):
                 ("phase_begin", C.c_int32), ("phase_end", C.c_int32), ("init_mode", C.c_int32),
                 ("seed", C.c_uint64), ("precision", C.c_int32), ("lanes_per_pixel", C.c_int32),
                 ("n_prop", C.c_int32), ("reserved0", C.c_int32), ("proposals", C.c_void_p),
-                ("reserved", C.c_int32 * 2)]
+                ("init_range", C.c_void_p)]
 
 
 class mvs_depth_map(C.Structure):
@@ -77,13 +77,15 @@ class PMParams:
     lanes_per_pixel: int = 0
     n_prop: int = 0
     proposals: object = None        # device buffer (H, W, n_prop, 4) float32 or None
+    init_range: object = None       # device buffer (H, W, 2) float32 for MVS_INIT_RANGE, or None
 
     def c(self):
         pp = _ptr(self.proposals)[0] if self.proposals is not None else None
+        rr = _ptr(self.init_range)[0] if self.init_range is not None else None
         return mvs_pm_params(self.win_radius, self.win_samples, self.sigma_s, self.sigma_c, self.d_lo, self.d_hi,
                              self.iters, self.phase_begin, self.phase_end, self.init_mode,
                              int(self.seed) & 0xFFFFFFFFFFFFFFFF, self.precision, self.lanes_per_pixel,
-                             self.n_prop, 0, pp)
+                             self.n_prop, 0, pp, rr)
 
 
 @dataclass
@@ -185,6 +187,8 @@ def load():
     L.mvs_fuse.argtypes = [vp, i32, ip, C.c_void_p, C.c_float, fp, vp, C.c_int64, C.POINTER(C.c_int64), i32]
     L.mvs_select_neighbors.restype = i32
     L.mvs_select_neighbors.argtypes = [vp, C.c_int64, vp, vp, C.c_double, C.c_double, i32, vp, vp, vp, vp, i32]
+    L.mvs_sparse_depth_range.restype = i32
+    L.mvs_sparse_depth_range.argtypes = [vp, i32, C.c_int64, vp, vp, vp, vp, C.c_double, C.c_float, C.c_float, vp, i32]
     L.mvs_profile_read.restype = i32
     L.mvs_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_int64)]
@@ -333,6 +337,16 @@ def mvs_select_neighbors(ctx, points, vis, neighbors, tau=None, n_shared=None, z
     _check(load().mvs_select_neighbors(ctx, points.shape[0], _ptr(points)[0], _ptr(vis)[0], float(eps), float(t_tau),
                                        k, _ptr(neighbors)[0], _ptr(tau)[0], _ptr(n_shared)[0], _ptr(zeta)[0], mem),
            ctx)
+
+
+def mvs_sparse_depth_range(ctx, ref, points, vis, reproj, obs, rng, max_reproj=2.0, d_lo=2.0, d_hi=8.0):
+    """Per-pixel (d_min, d_max) of the sparse-feature initialisation of view
+    ref into rng (H, W, 2) float32: points (n, 3) float64, vis (n,) uint64
+    masks, reproj (n,) float64, obs (n, 2) float64 observations in ref."""
+    mem = _mem(points, vis, reproj, obs, rng)
+    _check(load().mvs_sparse_depth_range(ctx, ref, points.shape[0], _ptr(points)[0], _ptr(vis)[0], _ptr(reproj)[0],
+                                         _ptr(obs)[0], float(max_reproj), C.c_float(d_lo), C.c_float(d_hi),
+                                         _ptr(rng)[0], mem), ctx)
 
 
 def mvs_plane_infer(ctx, ref, srcs, pm: PMParams, phi: PhiParams, keep_mask, plane, cost):
