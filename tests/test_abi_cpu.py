@@ -40,8 +40,8 @@ def test_ctypes_structs_match_c_layout(mvs_lib):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(mvs_camera), sizeof(mvs_pm_params), sizeof(mvs_depth_map),
          sizeof(mvs_filter_params), sizeof(mvs_phi_params));
-  printf("%zu %zu %zu %zu\n", offsetof(mvs_pm_params, seed), offsetof(mvs_pm_params, precision),
-         offsetof(mvs_camera, width), offsetof(mvs_phi_params, hole_cost));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(mvs_pm_params, seed), offsetof(mvs_pm_params, precision),
+         offsetof(mvs_camera, width), offsetof(mvs_phi_params, hole_cost), offsetof(mvs_pm_params, init_range));
   return 0;
 }
 """
@@ -57,7 +57,7 @@ int main(void) {
     assert sizes == [C.sizeof(m.mvs_camera), C.sizeof(m.mvs_pm_params), C.sizeof(m.mvs_depth_map),
                      C.sizeof(m.mvs_filter_params), C.sizeof(m.mvs_phi_params)]
     assert offs == [m.mvs_pm_params.seed.offset, m.mvs_pm_params.precision.offset, m.mvs_camera.width.offset,
-                    m.mvs_phi_params.hole_cost.offset]
+                    m.mvs_phi_params.hole_cost.offset, m.mvs_pm_params.init_range.offset]
 
 
 def test_create_rejects_bad_arguments_before_touching_cuda(mvs_lib):
@@ -95,6 +95,15 @@ def test_null_context_is_rejected(mvs_lib):
     out = mvs_lib.mvs_depth_map(None, None, 0)
     assert lib.mvs_patchmatch(None, 0, srcs, 1, C.byref(p), C.byref(out)) == mvs_lib.MVS_EINVAL
     assert lib.mvs_profile(None, 1) == mvs_lib.MVS_EINVAL
+    views = (C.c_int32 * 1)(0)
+    n = C.c_int64(0)
+    assert lib.mvs_fuse(None, 1, views, None, C.c_float(0.01), None, None, 0, C.byref(n), 0) == mvs_lib.MVS_EINVAL
+    nbr = np.zeros((2, 1), np.int32)
+    assert lib.mvs_select_neighbors(None, 0, None, None, 0.05, 1.0, 1, nbr.ctypes.data, None, None, None,
+                                    0) == mvs_lib.MVS_EINVAL
+    rng = np.zeros((2, 2, 2), np.float32)
+    assert lib.mvs_sparse_depth_range(None, 0, 0, None, None, None, None, 2.0, C.c_float(2.0), C.c_float(8.0),
+                                      rng.ctypes.data, 1) == mvs_lib.MVS_EINVAL
     lib.mvs_destroy(None)   # NULL-safe
 
 

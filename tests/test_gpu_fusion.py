@@ -115,3 +115,19 @@ def test_device_buffers_and_capacity(fused_scene, mvs_lib):
     with pytest.raises(mvs_lib.MvsError):
         mvs_lib.mvs_fuse(ctx.h, order, small, None, keep_masks=[keep[v] for v in order])
     assert np.array_equal(small, h_pts[: n - 7])
+
+
+def test_single_view_and_empty_masks(fused_scene, mvs_lib, oracle_lib):
+    sc, ctx, maps, keep = fused_scene
+    hh, ww = sc.images[0].shape
+    # one view: every kept pixel is its own point
+    pts = np.zeros((hh * ww, 4), np.float32)
+    src = np.zeros((hh * ww, 2), np.int32)
+    n = mvs_lib.mvs_fuse(ctx.h, [3], pts, src, keep_masks=[keep[3]])
+    osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
+    opts, osv, osp = oracle_lib.fuse(osc, [3], {3: maps[3].astype(np.float64)}, keep={3: keep[3]})
+    assert n == len(opts) == int(((maps[3][..., 3] > 0) & (keep[3] > 0)).sum())
+    assert np.array_equal(pts[:n], opts) and (pts[:n, 3] == 1).all() and np.array_equal(src[:n, 1], osp)
+    # nothing kept: no points
+    zero = np.zeros((hh, ww), np.uint8)
+    assert mvs_lib.mvs_fuse(ctx.h, [0, 1], pts, None, keep_masks=[zero, zero]) == 0

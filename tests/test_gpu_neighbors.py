@@ -61,3 +61,11 @@ def test_selection_equals_oracle_on_many_views(mvs_lib, oracle_lib):
     sp = scenes.sparse_points(sc, 6000, seed=4)
     nbr, _ = _compare(mvs_lib, oracle_lib, sc, sp, k=8)
     assert (nbr >= 0).all()
+
+
+def test_short_lists_are_padded(mvs_lib, oracle_lib):
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_scene(W=160, H=120, n_src=6, seed=3, view_angles=[2.0, 8.0, 15.0, 25.0, 35.0, 50.0])
+    sp = scenes.sparse_points(sc, 3000, seed=1)
+    nbr, _ = _compare(mvs_lib, oracle_lib, sc, sp, k=6)
+    assert (nbr[0, 4:] == -1).all()      # two of the six sources fall below t_tau

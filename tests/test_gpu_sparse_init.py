@@ -115,3 +115,20 @@ def test_ranges_must_be_device_memory_and_per_view(sparse_scene, mvs_lib):
     cos = [np.zeros((H, W), np.float32)]
     with pytest.raises(mvs_lib.MvsError):
         mvs_lib.mvs_patchmatch_batch(ctx.h, [0], [[1, 2]], q, pls, cos)
+
+
+def test_no_features_keeps_the_random_initialisation(sparse_scene, mvs_lib):
+    import torch
+    sc, sp, ctx = sparse_scene
+    H, W = sc.images[0].shape
+    empty = {k: v[:0] for k, v in sp.items()}
+    rng = _gpu_range(mvs_lib, ctx, empty, 0, H, W, device=True)
+    assert torch.isnan(rng).all()
+    base = dict(win_radius=5.0, win_samples=6, iters=0, seed=17)
+    outs = []
+    for extra in ({}, dict(init_mode=mvs_lib.MVS_INIT_RANGE, init_range=rng)):
+        pl = np.zeros((H, W, 4), np.float32)
+        co = np.zeros((H, W), np.float32)
+        mvs_lib.mvs_patchmatch(ctx.h, 0, [1, 2, 3, 4], mvs_lib.PMParams(**base, **extra), pl, co)
+        outs.append((pl, co))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
