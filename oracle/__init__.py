@@ -53,7 +53,7 @@ class _Filter(C.Structure):
 
 class _Phi(C.Structure):
     _fields_ = [("k1", C.c_double), ("k2", C.c_double), ("k3", C.c_double), ("n_fit", C.c_int),
-                ("inverse", C.c_int), ("trw_iters", C.c_int)]
+                ("inverse", C.c_int), ("trw_iters", C.c_int), ("min_cost", C.c_int)]
 
 
 def lib():
@@ -92,6 +92,7 @@ def lib():
             L.or_phi_mrf.argtypes = [C.c_int, C.c_int, up, dp, dp, up, dp, C.c_double, C.c_double, C.c_double,
                                      C.c_int, ip, dp]
             L.or_phi_select.argtypes = [vp, C.c_int, up, dp, up, ip, dp, up, dp]
+            L.or_phi_select_min_cost.argtypes = [vp, C.c_int, up, dp, up, dp, dp, up]
             L.or_phi_unary.restype = C.c_double
             L.or_phi_unary.argtypes = [C.c_double, C.c_double, C.c_double]
             L.or_phi_pair.restype = C.c_double
@@ -375,6 +376,18 @@ def phi_select(scene, ref, known, hyp, valid, label, plane):
     return pl, filled
 
 
+def phi_select_min_cost(scene, ref, known, hyp, valid, hcost, plane):
+    """PHI-MVS/M selection (Sec. IV, Table I): each hole takes its valid
+    hypothesis of minimal matching cost, then Eq. 10 normals; returns (plane,
+    filled)."""
+    H, W = scene.shape(ref)
+    pl = _f64(plane).reshape(H, W, 4).copy()
+    filled = np.zeros((H, W), np.uint8)
+    lib().or_phi_select_min_cost(scene.h, ref, _u8(np.ascontiguousarray(known, np.uint8)), _d(_f64(hyp)),
+                                 _u8(np.ascontiguousarray(valid, np.uint8)), _d(_f64(hcost)), _d(pl), _u8(filled))
+    return pl, filled
+
+
 def phi_unary(c, k1=4.0, k2=0.5):
     return lib().or_phi_unary(float(c), float(k1), float(k2))
 
@@ -412,9 +425,11 @@ def eq10_normal(scene, ref, depth, x, y):
 
 
 def plane_infer(scene, ref, srcs, p, known, plane, k1=4.0, k2=0.5, k3=2.0, n_fit=6, inverse=False,
-                trw_iters=1):
+                trw_iters=1, min_cost=False):
     """Sec. III-E: hypotheses, their costs, half-resolution MRF, selection,
-    Eq. 10 normals.  Returns the filled plane map and the intermediates."""
+    Eq. 10 normals (min_cost: PHI-MVS/M, the minimal-cost hypothesis per
+    hole without the MRF).  Returns the filled plane map and the
+    intermediates."""
     H, W = scene.shape(ref)
     s = _srcs(srcs)
     known = np.ascontiguousarray(known, dtype=np.uint8)
@@ -426,7 +441,7 @@ def plane_infer(scene, ref, srcs, p, known, plane, k1=4.0, k2=0.5, k3=2.0, n_fit
     label = np.zeros((gh, gw), np.int32)
     refd = np.zeros((H, W), np.float64)
     filled = np.zeros((H, W), np.uint8)
-    q = _Phi(k1, k2, k3, n_fit, int(inverse), trw_iters)
+    q = _Phi(k1, k2, k3, n_fit, int(inverse), trw_iters, int(bool(min_cost)))
     lib().or_plane_infer(scene.h, ref, _i(s), len(s), C.byref(_pm(p)), C.byref(q), _u8(known), _d(pl),
                          _d(hyp), _u8(valid), _d(hcost), _i(label), _d(refd), _u8(filled))
     return pl, {"hyp": hyp, "valid": valid, "hcost": hcost, "label": label, "refdepth": refd,

@@ -967,6 +967,9 @@ typedef struct {
     int n_fit;             /* six closest reconstructed pixels               */
     int inverse;           /* 0: fit depth (paper), 1: fit inverse depth     */
     int trw_iters;         /* 1                                              */
+    int min_cost;          /* 0: MRF selection (PHI-MVS); 1: each hole takes
+                              its valid hypothesis of minimal matching cost,
+                              no MRF (PHI-MVS/M of Sec. IV, Table I)        */
 } or_phi;
 
 /* MRF stage of Sec. III-E from full-resolution inputs: nodes at pixels
@@ -1024,6 +1027,31 @@ void or_phi_mrf(int W, int H, const unsigned char* known, const double* depth, c
     free(nlab); free(lab); free(un); free(lmap); free(msg); free(label);
 }
 
+/* Last step of Sec. III-E for the chosen depths newd: each hole with a
+ * depth and four neighbours with depth gets its Eq. 10 normal and becomes a
+ * plane (n, d); any other hole is zeroed.  Reconstructed pixels keep their
+ * plane. */
+static void phi_fill_holes(const or_view* V, const unsigned char* known, const double* newd, double* plane,
+                           unsigned char* filled_out) {
+    int W = V->W, H = V->H;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            long i = (long)y * W + x;
+            unsigned char filled = 0;
+            if (!known[i]) {
+                double n[3];
+                if (newd[i] > 0 && eq10_normal(V, newd, x, y, n)) {
+                    plane[4 * i] = n[0]; plane[4 * i + 1] = n[1]; plane[4 * i + 2] = n[2];
+                    plane[4 * i + 3] = newd[i];
+                    filled = 1;
+                } else {
+                    plane[4 * i] = plane[4 * i + 1] = plane[4 * i + 2] = plane[4 * i + 3] = 0.0;
+                }
+            }
+            if (filled_out) filled_out[i] = filled;
+        }
+}
+
 /* Selection stage of Sec. III-E: the decoded depth of node (x/2, y/2)
  * (nearest up-sampling) is the reference; each hole takes its valid
  * hypothesis closest to it (lowest k on a tie); then Eq. 10 normals for the
@@ -1054,30 +1082,37 @@ void or_phi_select(const or_scene* s, int ref, const unsigned char* known, const
                 }
             if (bk >= 0) newd[i] = hyp[4 * i + bk];
         }
-    for (int y = 0; y < H; ++y)
-        for (int x = 0; x < W; ++x) {
-            long i = (long)y * W + x;
-            unsigned char filled = 0;
-            if (!known[i]) {
-                double n[3];
-                if (newd[i] > 0 && eq10_normal(V, newd, x, y, n)) {
-                    plane[4 * i] = n[0]; plane[4 * i + 1] = n[1]; plane[4 * i + 2] = n[2];
-                    plane[4 * i + 3] = newd[i];
-                    filled = 1;
-                } else {
-                    plane[4 * i] = plane[4 * i + 1] = plane[4 * i + 2] = plane[4 * i + 3] = 0.0;
-                }
-            }
-            if (filled_out) filled_out[i] = filled;
-        }
+    phi_fill_holes(V, known, newd, plane, filled_out);
+    free(newd);
+}
+
+/* Selection of PHI-MVS/M (Sec. IV, Table I: the MRF removed): each hole
+ * takes, among its valid hypotheses, the one of minimal matching cost hcost
+ * (the lowest k on a tie); a hole without a valid hypothesis stays empty.
+ * Then Eq. 10 normals as in or_phi_select. */
+void or_phi_select_min_cost(const or_scene* s, int ref, const unsigned char* known, const double* hyp,
+                            const unsigned char* valid, const double* hcost, double* plane,
+                            unsigned char* filled_out) {
+    const or_view* V = &s->v[ref];
+    long N = (long)V->W * V->H;
+    double* newd = (double*)calloc((size_t)N, sizeof(double));
+    for (long i = 0; i < N; ++i) {
+        if (known[i]) { newd[i] = plane[4 * i + 3]; continue; }
+        int bk = -1;
+        for (int k = 0; k < 4; ++k)
+            if (valid[4 * i + k] && (bk < 0 || hcost[4 * i + k] < hcost[4 * i + bk])) bk = k;
+        if (bk >= 0) newd[i] = hyp[4 * i + bk];
+    }
+    phi_fill_holes(V, known, newd, plane, filled_out);
     free(newd);
 }
 
 
 /* The whole PHI step for one reference view: hypotheses, their costs, MRF,
- * selection and Eq. 10 normals.  plane (in/out) H*W*4; known H*W
- * (1 = reconstructed, kept).  Intermediate results go to the optional
- * outputs. */
+ * selection and Eq. 10 normals (q->min_cost: the minimal-cost selection in
+ * place of MRF and closest-hypothesis selection; label_out is then -3
+ * everywhere).  plane (in/out) H*W*4; known H*W (1 = reconstructed, kept).
+ * Intermediate results go to the optional outputs. */
 void or_plane_infer(const or_scene* s, int ref, const int* srcs, int ns, const or_pm* p, const or_phi* q,
                     const unsigned char* known, double* plane, double* hyp_out, unsigned char* valid_out,
                     double* hcost_out, int* label_out, double* refdepth_out, unsigned char* filled_out) {
@@ -1093,10 +1128,16 @@ void or_plane_infer(const or_scene* s, int ref, const int* srcs, int ns, const o
     int* label = (int*)malloc(sizeof(int) * G);
     or_phi_hypotheses(W, H, depth, known, q->n_fit, q->inverse, p->d_lo, p->d_hi, hyp, valid);
     or_phi_cost(s, ref, srcs, ns, p, hyp, valid, hcost, NULL);
-    or_phi_mrf(W, H, known, depth, hyp, valid, hcost, q->k1, q->k2, q->k3, q->trw_iters, label, NULL);
     for (long i = 0; i < N; ++i)
         if (known[i]) plane[4 * i + 3] = depth[i];
-    or_phi_select(s, ref, known, hyp, valid, label, plane, filled_out, refdepth_out);
+    if (q->min_cost) {
+        for (long g = 0; g < G; ++g) label[g] = -3;      /* no MRF */
+        if (refdepth_out) memset(refdepth_out, 0, sizeof(double) * N);
+        or_phi_select_min_cost(s, ref, known, hyp, valid, hcost, plane, filled_out);
+    } else {
+        or_phi_mrf(W, H, known, depth, hyp, valid, hcost, q->k1, q->k2, q->k3, q->trw_iters, label, NULL);
+        or_phi_select(s, ref, known, hyp, valid, label, plane, filled_out, refdepth_out);
+    }
     if (hyp_out) memcpy(hyp_out, hyp, sizeof(double) * 4 * N);
     if (valid_out) memcpy(valid_out, valid, 4 * N);
     if (hcost_out) memcpy(hcost_out, hcost, sizeof(double) * 4 * N);

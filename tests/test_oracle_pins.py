@@ -541,3 +541,82 @@ def test_cost_at_equals_the_cost_map(oracle_lib, tiny):
     ys = np.array([0, 7, 29, 15, 3])
     c, _ = oracle_lib.cost_at(osc, 0, [1, 2], p, xs, ys, pl[ys, xs])
     assert np.array_equal(c, full[ys, xs])
+
+
+# --------------------------------------------------------------------------
+# PHI-MVS/M (Sec. IV, Table I): the MRF removed, each hole takes its valid
+# hypothesis of minimal matching cost
+# --------------------------------------------------------------------------
+def _slanted_hole_case(rng, W=36, H=28):
+    """Slanted plane with a hole; per hole pixel four hypotheses, of which
+    one (a random direction) is the exact planar depth at the lowest cost and
+    the others perturbed depths at higher costs; some invalid, some ties."""
+    from paper_2104_06165_gb300 import scenes
+    n_true = np.array([0.25, -0.3, -1.0])
+    n_true /= np.linalg.norm(n_true)
+    sc = scenes.make_plane_scene(W=W, H=H, n_src=1, seed=3, depth=5.0, normal=n_true)
+    gt = sc.gt_depth
+    known = np.ones((H, W), np.uint8)
+    known[6:22, 8:28] = 0
+    hyp = gt[..., None] * (1.0 + rng.uniform(0.02, 0.1, (H, W, 4)) * rng.choice([-1, 1], (H, W, 4)))
+    hcost = rng.uniform(0.3, 1.9, (H, W, 4))
+    valid = (rng.random((H, W, 4)) < 0.8).astype(np.uint8)
+    best = rng.integers(0, 4, (H, W))
+    yy, xx = np.mgrid[0:H, 0:W]
+    hyp[yy, xx, best] = gt
+    hcost[yy, xx, best] = rng.uniform(0.0, 0.25, (H, W))
+    valid[yy, xx, best] = 1
+    # ties: a perturbed hypothesis at a higher index with the same cost never wins
+    tie = (rng.random((H, W)) < 0.3) & (best < 3)
+    hcost[yy[tie], xx[tie], 3] = hcost[yy[tie], xx[tie], best[tie]]
+    valid[yy[tie], xx[tie], 3] = 1
+    plane = np.concatenate([sc.gt_normal, gt[..., None]], -1) * known[..., None]
+    return sc, n_true, known, hyp, valid, hcost, plane, best
+
+
+def test_min_cost_selection_is_masked_argmin_and_recovers_the_plane(oracle_lib):
+    rng = np.random.default_rng(21)
+    sc, n_true, known, hyp, valid, hcost, plane, best = _slanted_hole_case(rng)
+    osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
+    out, filled = oracle_lib.phi_select_min_cost(osc, 0, known, hyp, valid, hcost, plane)
+    # library routine: numpy's argmin (first minimum) over the masked costs
+    k = np.argmin(np.where(valid == 1, hcost, np.inf), axis=-1)
+    assert np.array_equal(k[known == 0], best[known == 0])
+    hole = known == 0
+    f = filled.astype(bool)
+    assert f[hole].all() and not f[~hole].any()
+    # the exact planar depth is chosen everywhere, so Eq. 10 gives the plane normal
+    assert np.allclose(out[..., 3][f], sc.gt_depth[f], rtol=0, atol=1e-12)
+    assert np.allclose(out[..., :3][f], n_true, atol=1e-9)
+    assert np.array_equal(out[~hole], plane[~hole])
+
+
+def test_min_cost_selection_empty_holes(oracle_lib):
+    rng = np.random.default_rng(5)
+    sc, n_true, known, hyp, valid, hcost, plane, best = _slanted_hole_case(rng)
+    osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
+    valid[10, 12] = 0                      # no hypothesis: stays empty, and so do
+    out, filled = oracle_lib.phi_select_min_cost(osc, 0, known, hyp, valid, hcost, plane)
+    assert (out[10, 12] == 0).all() and not filled[10, 12]
+    # its four neighbours lack one Eq. 10 neighbour and stay empty too
+    for (y, x) in [(9, 12), (11, 12), (10, 11), (10, 13)]:
+        assert (out[y, x] == 0).all() and not filled[y, x]
+
+
+def test_plane_infer_min_cost_fills_a_fronto_parallel_hole(oracle_lib):
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_plane_scene(W=40, H=30, n_src=2, seed=6, depth=5.0, normal=(0, 0, -1.0), baseline=0.2)
+    osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
+    plane = np.concatenate([sc.gt_normal, sc.gt_depth[..., None]], -1)
+    known = np.ones((30, 40), np.uint8)
+    known[8:20, 10:25] = 0
+    plane[known == 0] = 0
+    out, aux = oracle_lib.plane_infer(osc, 0, [1, 2], P(), known, plane, min_cost=True)
+    filled = aux["filled"].astype(bool)
+    assert filled[9:19, 11:24].all()
+    assert np.allclose(out[..., 3][filled], 5.0, atol=1e-9)
+    assert np.allclose(out[..., :3][filled], [0, 0, -1], atol=1e-9)
+    assert (aux["label"] == -3).all()
+    # the same intermediates, selected by minimal cost
+    sel, _ = oracle_lib.phi_select_min_cost(osc, 0, known, aux["hyp"], aux["valid"], aux["hcost"], plane)
+    assert np.array_equal(sel, out)
