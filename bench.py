@@ -34,7 +34,8 @@ WORKLOAD = dict(W=3072, H=2048, n_src=10, win_radius=10.0, win_samples=11, iters
 # smaller case of the same kernels for profiler captures (inputs still larger than L2)
 WORKLOADS = {"highres": WORKLOAD, "mid": dict(WORKLOAD, W=1536, H=1024), "batch24": dict(WORKLOAD),
              "sparse": dict(WORKLOAD),
-             "learned": dict(WORKLOAD, W=1536, H=1024, iters=4), "table3": dict(WORKLOAD)}
+             "learned": dict(WORKLOAD, W=1536, H=1024, iters=4), "table3": dict(WORKLOAD),
+             "table1": dict(WORKLOAD), "pipeline": dict(WORKLOAD)}
 BATCH_SIZES = ((3072, 2048),) * 8 + ((2048, 1365),) * 8 + ((1536, 1024),) * 8
 FLOP_PER_SAMPLE = 26          # algorithmic FP32 flops per window sample of one ZNCC (FMA = 2)
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
@@ -397,6 +398,135 @@ def run_batch(args):
     ctx.close()
 
 
+def run_pipeline(args):
+    """The paper's whole Algorithm 1 on the 24-view scene of batch24, every
+    stage on the GPU inside one timed step: neighbouring-image selection
+    (Eqs. 1-3, top 8) from 20 k synthetic SfM points, per-view depth ranges
+    from the sparse features (Sec. III-B), PatchMatch of all 24 views in one
+    graph from those ranges (8 iterations), the geometric filter, plane
+    hypothesis inference on the filtered maps, the filter again, and the
+    fusion of the 24 maps into one point cloud (Sec. III-F).  value = input
+    Mpix/s of the whole algorithm."""
+    import torch
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2104_06165_gb300 import mvs, scenes
+    mvs.load()
+    t0 = time.perf_counter()
+    sc, angle_srcs = scenes.scene_batch(seed=rank, sizes=BATCH_SIZES, want_gt=True)
+    t_render = time.perf_counter() - t0
+    n = len(sc.images)
+    refs = list(range(n))
+    k_nbr = 8
+    sp = scenes.sparse_points(sc, 20000, seed=7 + rank)
+    masks = np.zeros(len(sp["X"]), np.uint64)
+    for v in range(n):
+        masks |= sp["vis"][:, v].astype(np.uint64) << np.uint64(v)
+    d_X = torch.from_numpy(np.ascontiguousarray(sp["X"])).to(dev)
+    d_m = torch.from_numpy(masks.view(np.int64)).to(dev)
+    d_rep = torch.from_numpy(np.ascontiguousarray(sp["reproj"])).to(dev)
+    d_obs = [torch.from_numpy(np.ascontiguousarray(sp["obs"][:, v])).to(dev) for v in refs]
+    stream = torch.cuda.current_stream(dev)
+    ctx = mvs.Context(sc.K, sc.R, sc.t, sc.images, stream=stream)
+    sizes = [im.shape for im in sc.images]
+    offs = np.concatenate([[0], np.cumsum([h * w for h, w in sizes])])
+    ranges = torch.empty((int(offs[-1]) * 2,), dtype=torch.float32, device=dev)
+    rng_views = [ranges[2 * int(offs[v]):2 * int(offs[v + 1])].view(sizes[v][0], sizes[v][1], 2) for v in refs]
+    planes = [torch.empty(hw + (4,), dtype=torch.float32, device=dev) for hw in sizes]
+    costs = [torch.empty(hw, dtype=torch.float32, device=dev) for hw in sizes]
+    keeps = [torch.empty(hw, dtype=torch.uint8, device=dev) for hw in sizes]
+    nbr = torch.zeros((n, k_nbr), dtype=torch.int32, device=dev)
+    cap = int(offs[-1])
+    pts = torch.empty((cap, 4), dtype=torch.float32, device=dev)
+    params = make_params(mvs, seed=1 + rank)
+    params.init_mode, params.init_range = mvs.MVS_INIT_RANGE, ranges
+    phi = mvs.PhiParams()
+    fp = mvs.FilterParams()
+    evs = {}
+    n_sel = []
+
+    def mark(name):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        evs.setdefault(name, []).append(e)
+
+    def step():
+        mark("select")
+        mvs.mvs_select_neighbors(ctx.h, d_X, d_m, nbr)
+        nb = nbr.cpu().numpy()
+        srcs = []
+        for v in refs:     # pad a short list with the nearest views by angle
+            lst = [int(u) for u in nb[v] if u >= 0]
+            n_sel.append(len(lst))
+            lst += [u for u in angle_srcs[v] if u not in lst][:k_nbr - len(lst)]
+            srcs.append(lst)
+        mark("sparse_range")
+        for v in refs:
+            mvs.mvs_sparse_depth_range(ctx.h, v, d_X, d_m, d_rep, d_obs[v], rng_views[v])
+        mark("patchmatch")
+        mvs.mvs_patchmatch_batch(ctx.h, refs, srcs, params, planes, costs)
+        mark("filter1")
+        for v in refs:
+            mvs.mvs_geo_filter(ctx.h, v, srcs[v], fp, keeps[v])
+        mark("phi")
+        for v in refs:
+            mvs.mvs_plane_infer(ctx.h, v, srcs[v], params, phi, keeps[v], planes[v], costs[v])
+        mark("filter2")
+        for v in refs:
+            mvs.mvs_geo_filter(ctx.h, v, srcs[v], fp, keeps[v])
+        mark("fusion")
+        n_pts = mvs.mvs_fuse(ctx.h, refs, pts, None, keep_masks=keeps)
+        mark("end")
+        return n_pts, srcs
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs.clear()
+    mvs.mvs_profile(ctx.h, 1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            n_pts, srcs = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    _, _, launches, _ = mvs.mvs_profile_read(ctx.h)
+    mvs.mvs_profile(ctx.h, 0)
+    order = ["select", "sparse_range", "patchmatch", "filter1", "phi", "filter2", "fusion", "end"]
+    stage_ms = {a: float(np.mean([evs[a][i].elapsed_time(evs[b][i]) for i in range(args.steps)]))
+                for a, b in zip(order[:-1], order[1:])}
+    # quality against the rendered truth: final kept depths within 1 %
+    comp, acc = [], []
+    for v in refs:
+        g = sc.gt_views[v]["depth"]
+        d = planes[v][..., 3].cpu().numpy()
+        k = keeps[v].cpu().numpy().astype(bool)
+        good = k & (np.abs(d - g) <= 0.01 * g)
+        comp.append(good.mean())
+        acc.append(good.sum() / max(1, k.sum()))
+    mpix = sum(h * w for h, w in sizes) / 1e6
+    line = {"metric": "Algorithm 1 input Mpix/s (selection, sparse init, PatchMatch, filter, PHI, filter, fusion)",
+            "value": mpix * args.steps / (ms / 1e3), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "pipeline: 8x3072x2048 + 8x2048x1365 + 8x1536x1024 views of one scene, "
+                                   f"{k_nbr} selected sources each, 20 k synthetic SfM points, 21x21 window "
+                                   "dil 2, 8 iterations, PHI + 4-label MRF, two geometric filters, fusion",
+                       "render_s": round(t_render, 1), "total_mpix": round(mpix, 2)},
+            "gpu_launches": int(launches), "stage_ms": stage_ms,
+            "quality": {"completeness": float(np.mean(comp)), "kept_within_1pct": float(np.mean(acc)),
+                        "points": int(n_pts),
+                        "note": "per-view means over the 24 final maps: completeness = kept pixels within 1 % of "
+                                "the rendered depth / all pixels; kept_within_1pct = the same / kept pixels"},
+            "sources_from_selection": float(np.mean(n_sel)),
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 PHASE_SOURCES = ["paper_2104_06165_gb300/csrc/pm_kernels.cu", "paper_2104_06165_gb300/csrc/pm_device.cuh",
                  "paper_2104_06165_gb300/csrc/mvs_internal.h"]
 
@@ -590,6 +720,83 @@ def run_sparse(args):
     ctx.close()
 
 
+def run_table1(args):
+    """The paper's PHI ablation (Sec. IV, Table I) on the high-resolution
+    synthetic workload: PatchMatch alone (PHI-MVS/P: pixels whose cost
+    passes the hole threshold), PHI selecting each hole's hypothesis of
+    minimal matching cost (PHI-MVS/M) and PHI with the MRF (PHI-MVS), all
+    from the same 8-iteration PatchMatch map.  Completeness = pixels within
+    1 % of the true depth, over all pixels and over the texture-less ones
+    (F1 on ETH3D in the paper).  value = Mpix/s of PatchMatch + PHI-MVS/M."""
+    import torch
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2104_06165_gb300 import mvs, scenes
+    mvs.load()
+    w = WORKLOAD
+    sc = scenes.scene_highres(seed=rank, W=w["W"], H=w["H"], n_src=w["n_src"])
+    H, W = sc.images[0].shape
+    srcs = list(range(1, len(sc.images)))
+    stream = torch.cuda.current_stream(dev)
+    ctx = mvs.Context(sc.K, sc.R, sc.t, sc.images, stream=stream)
+    params = make_params(mvs, seed=1 + rank)
+    plane0 = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    cost0 = torch.empty((H, W), dtype=torch.float32, device=dev)
+    plane = torch.empty_like(plane0)
+    cost = torch.empty_like(cost0)
+    gt = sc.gt_depth
+    flat = ~sc.gt_textured
+    phi = mvs.PhiParams()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    def comp(d, ok=None):
+        good = np.abs(d - gt) <= 0.01 * gt
+        if ok is not None:
+            good &= ok
+        return float(good.mean()), float(good[flat].mean())
+
+    rows = []
+    with ClockSampler(local) as clk:
+        pm_ms = timed(lambda: mvs.mvs_patchmatch(ctx.h, 0, srcs, params, plane0, cost0))
+        d0 = plane0[..., 3].cpu().numpy()
+        c, cf = comp(d0, cost0.cpu().numpy() < phi.hole_cost)
+        rows.append({"pipeline": "PHI-MVS/P", "phi_ms": 0.0, "completeness": c, "completeness_textureless": cf})
+        for name, sel in (("PHI-MVS/M", mvs.MVS_PHI_SELECT_MIN_COST), ("PHI-MVS", mvs.MVS_PHI_SELECT_MRF)):
+            q = mvs.PhiParams(selection=sel)
+
+            def step():
+                plane.copy_(plane0)
+                cost.copy_(cost0)
+                mvs.mvs_plane_infer(ctx.h, 0, srcs, params, q, None, plane, cost)
+            ms = timed(step)
+            c, cf = comp(plane[..., 3].cpu().numpy())
+            rows.append({"pipeline": name, "phi_ms": ms, "completeness": c, "completeness_textureless": cf})
+    for r in rows:
+        r["mpix_s"] = H * W / 1e3 / (pm_ms + r["phi_ms"])
+    m = [r for r in rows if r["pipeline"] == "PHI-MVS/M"][0]
+    line = {"metric": "depth-map Mpix/s (PatchMatch + PHI-MVS/M)", "value": m["mpix_s"], "unit": "Mpix/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": pm_ms + m["phi_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"table1 {W}x{H} uint8 ref + {len(srcs)} sources, 21x21 window dil 2, "
+                                   "8 iterations, then no PHI / PHI without MRF / PHI with MRF",
+                       "patchmatch_ms": pm_ms, "textureless_frac": float(flat.mean())},
+            "rows": rows, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 TABLE3 = [(5, 5), (5, 6), (6, 6), (5, 7), (7, 7), (5, 8), (8, 8), (5, 9), (9, 9), (5, 10), (10, 10)]
 TABLE3_PAPER_S = {(5, 5): 9.79, (5, 6): 10.02, (6, 6): 12.58, (5, 7): 9.57, (7, 7): 16.41, (5, 8): 10.04,
                   (8, 8): 20.92, (5, 9): 10.51, (9, 9): 25.91, (5, 10): 10.86, (10, 10): 31.60}
@@ -665,7 +872,8 @@ def main():
                     help="highres = the measured workload; mid = 1536x1024 case for profiler captures; "
                          "batch24 = 24 views in one graph; learned = learned proposals vs plain 8 iterations; "
                          "table3 = the paper's window-radius study; sparse = sparse-feature initialisation "
-                         "vs random by iteration count")
+                         "vs random by iteration count; table1 = PatchMatch alone vs PHI without / with the MRF; "
+                         "pipeline = the whole Algorithm 1 on the 24-view scene")
     args = ap.parse_args()
     WORKLOAD.update(WORKLOADS[args.workload])
     if args.impl == "reference":
@@ -678,6 +886,10 @@ def main():
         run_table3(args)
     elif args.workload == "sparse":
         run_sparse(args)
+    elif args.workload == "table1":
+        run_table1(args)
+    elif args.workload == "pipeline":
+        run_pipeline(args)
     else:
         run_ours(args)
 

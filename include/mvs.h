@@ -106,7 +106,9 @@ typedef struct {
                               d_min + (d_max - d_min) u with the Philox draw u
                               of the random initialisation; NaN: the whole
                               range [d_lo, d_hi].  8-byte aligned.  NULL for
-                              the other modes.                               */
+                              the other modes.  mvs_patchmatch_batch: the
+                              ranges of all refs back to back, in refs
+                              order.                                         */
 } mvs_pm_params;
 
 /* Depth-map buffers supplied by the caller. */
@@ -133,7 +135,13 @@ typedef struct {
     int32_t trw_iters;     /* TRW iterations (forward + backward pass): 1    */
     float hole_cost;       /* with keep_mask == NULL, pixels whose stored
                               cost >= hole_cost (or without depth) are holes */
+    int32_t selection;     /* MVS_PHI_SELECT_MRF (0, the paper's PHI-MVS) or
+                              MVS_PHI_SELECT_MIN_COST (1, PHI-MVS/M of
+                              Sec. IV, Table I: no MRF, each hole takes its
+                              valid hypothesis of minimal matching cost)    */
 } mvs_phi_params;
+
+enum { MVS_PHI_SELECT_MRF = 0, MVS_PHI_SELECT_MIN_COST = 1 };
 
 /* ------------------------------------------------------------------------ */
 
@@ -182,9 +190,12 @@ mvs_status mvs_patchmatch(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_
  *   mvs_patchmatch; params->lanes_per_pixel = -1 asks the library to time
  *   the work layouts on the first call (two iterations of the first view,
  *   each from the same initial state, in the view's own buffers before its
- *   real run) and keep the fastest for this window size.
+ *   real run) and keep the fastest for this window size.  With
+ *   MVS_INIT_RANGE, params->init_range holds the ranges of every reference
+ *   back to back in refs order (sum of H*W*2 floats).
  *   The maps stay in the context for mvs_geo_filter.
- * Errors: as mvs_patchmatch, plus MVS_EINVAL for n_ref < 1 or repeated refs. */
+ * Errors: as mvs_patchmatch, plus MVS_EINVAL for n_ref < 1 or repeated refs,
+ *   MVS_EUNSUPPORTED for learned proposals (n_prop > 0: per view only). */
 mvs_status mvs_patchmatch_batch(mvs_ctx* ctx, int32_t n_ref, const int32_t* refs, const int32_t* srcs,
                                 int32_t n_src, const mvs_pm_params* params, mvs_depth_map* outs);
 
@@ -281,14 +292,16 @@ mvs_status mvs_sparse_depth_range(mvs_ctx* ctx, int32_t ref, int64_t n_points, c
 /* Plane hypothesis inference (Sec. III-E) on view `ref`: four line-fit
  * hypotheses per hole, their matching cost through the sources, a pairwise
  * MRF (Eq. 6-9) decoded by TRW at half resolution, closest-hypothesis
- * selection, Eq. 10 normals.
+ * selection, Eq. 10 normals (phi->selection = MVS_PHI_SELECT_MIN_COST: the
+ * minimal-cost hypothesis per hole in place of the MRF and its selection).
  *   keep_mask[H*W] (in `mem`): 1 = reconstructed; NULL derives holes from
  *   the stored cost (cost >= hole_cost or no depth).  inout: the depth map
  *   (MVS_INIT_GIVEN state of the view); on return holes that were filled
  *   carry their plane, remaining holes and dropped pixels have depth 0.  The
  *   context's copy of the view is updated.  pm gives the window / ZNCC
  *   parameters for the hypothesis costs.
- * Errors: MVS_ESTATE if the view has no depth map, MVS_EINVAL, MVS_ECUDA. */
+ * Errors: MVS_ESTATE if the view has no depth map, MVS_EINVAL (also for an
+ *   unknown selection), MVS_ECUDA. */
 mvs_status mvs_plane_infer(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_t n_src,
                            const mvs_pm_params* pm, const mvs_phi_params* phi, const uint8_t* keep_mask,
                            mvs_depth_map* inout);
@@ -304,7 +317,13 @@ mvs_status mvs_plane_infer(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32
  *    label[gh*gw] (chosen hypothesis index 0..3, -1 for a reconstructed node,
  *    -2 for a node without labels), gw = (W+1)/2, gh = (H+1)/2.
  *  mvs_phi_select: labels -> plane[H*W*4] filled with the closest hypothesis
- *    and its Eq. 10 normal (known pixels keep their plane). */
+ *    and its Eq. 10 normal (known pixels keep their plane).
+ *  mvs_phi_select_min_cost: the selection of PHI-MVS/M (Sec. IV, Table I)
+ *    in place of mvs_phi_mrf + mvs_phi_select: each hole takes its valid
+ *    hypothesis of minimal hcost (the lowest index on a tie), then its
+ *    Eq. 10 normal; a hole without a valid hypothesis, or without four
+ *    neighbours with depth, is zeroed.  hyp and hcost 16-byte, valid 4-byte
+ *    aligned. */
 mvs_status mvs_phi_hypotheses(mvs_ctx* ctx, int32_t W, int32_t H, const float* depth, const uint8_t* known,
                               const mvs_phi_params* phi, float d_lo, float d_hi, float* hyp, uint8_t* valid,
                               int32_t mem);
@@ -316,6 +335,8 @@ mvs_status mvs_phi_mrf(mvs_ctx* ctx, int32_t W, int32_t H, const uint8_t* known,
                        int32_t* label, int32_t mem);
 mvs_status mvs_phi_select(mvs_ctx* ctx, int32_t ref, const uint8_t* known, const float* hyp,
                           const uint8_t* valid, const int32_t* label, float* plane, int32_t mem);
+mvs_status mvs_phi_select_min_cost(mvs_ctx* ctx, int32_t ref, const uint8_t* known, const float* hyp,
+                                   const uint8_t* valid, const float* hcost, float* plane, int32_t mem);
 
 /* Allocation-free variant of mvs_phi_hypotheses (the paper has no
  * counterpart; this is a deployment convenience).

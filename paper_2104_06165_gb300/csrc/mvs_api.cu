@@ -312,6 +312,15 @@ void mvs_destroy(mvs_ctx* c) {
 
 const char* mvs_last_error(const mvs_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
+// the initialisation mode and its depth-range buffer
+static mvs_status check_init(mvs_ctx* c, const mvs_pm_params* p) {
+    if (p->init_mode < MVS_INIT_RANDOM || p->init_mode > MVS_INIT_RANGE) return fail(c, MVS_EINVAL, "bad init_mode");
+    if ((p->init_mode == MVS_INIT_RANGE) != (p->init_range != nullptr) || ((uintptr_t)p->init_range & 7u))
+        return fail(c, MVS_EINVAL, "init_range (8-byte aligned) must be given exactly with MVS_INIT_RANGE");
+    if (p->init_range && !is_device_ptr(p->init_range)) return fail(c, MVS_EINVAL, "init_range must be device memory");
+    return MVS_OK;
+}
+
 mvs_status mvs_patchmatch(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src, const mvs_pm_params* p,
                           mvs_depth_map* out) {
     mvs_status st = check_pm(c, ref, srcs, n_src, p);
@@ -320,10 +329,7 @@ mvs_status mvs_patchmatch(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t 
     if (((uintptr_t)out->plane & 15u) || ((uintptr_t)out->cost & 3u))
         return fail(c, MVS_EINVAL, "plane must be 16-byte and cost 4-byte aligned");
     if (out->mem != MVS_MEM_DEVICE && out->mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
-    if (p->init_mode < MVS_INIT_RANDOM || p->init_mode > MVS_INIT_RANGE) return fail(c, MVS_EINVAL, "bad init_mode");
-    if ((p->init_mode == MVS_INIT_RANGE) != (p->init_range != nullptr) || ((uintptr_t)p->init_range & 7u))
-        return fail(c, MVS_EINVAL, "init_range (8-byte aligned) must be given exactly with MVS_INIT_RANGE");
-    if (p->init_range && !is_device_ptr(p->init_range)) return fail(c, MVS_EINVAL, "init_range must be device memory");
+    if ((st = check_init(c, p)) != MVS_OK) return st;
     int pend = p->phase_end < 0 ? 2 * p->iters : p->phase_end;
     if (p->phase_begin < 0 || pend < p->phase_begin) return fail(c, MVS_EINVAL, "bad phase range");
     CK(c, cudaSetDevice(c->device));
@@ -439,19 +445,16 @@ mvs_status mvs_patchmatch_batch(mvs_ctx* c, int32_t n_ref, const int32_t* refs, 
         if (outs[r].mem != outs[0].mem || (outs[r].mem != MVS_MEM_DEVICE && outs[r].mem != MVS_MEM_HOST))
             return fail(c, MVS_EINVAL, "all outputs must be in the same memory kind");
     }
-    if (p->init_mode == MVS_INIT_RANGE)
-        return fail(c, MVS_EUNSUPPORTED, "depth ranges are per view: use mvs_patchmatch");
-    if (p->init_mode < MVS_INIT_RANDOM || p->init_mode > MVS_INIT_GIVEN_RECOST)
-        return fail(c, MVS_EINVAL, "bad init_mode");
+    mvs_status st = check_init(c, p);
+    if (st != MVS_OK) return st;
     int pend = p->phase_end < 0 ? 2 * p->iters : p->phase_end;
     if (p->phase_begin < 0 || pend < p->phase_begin) return fail(c, MVS_EINVAL, "bad phase range");
     CK(c, cudaSetDevice(c->device));
-    mvs_status st;
     for (int r = 0; r < n_ref; ++r)
         if ((st = ensure_map(c, refs[r])) != MVS_OK) return st;
     if (tune && (st = autotune_lanes(c, refs[0], srcs, n_src, p, &q.lanes_per_pixel)) != MVS_OK) return st;
     const int32_t mem = outs[0].mem;
-    if (p->init_mode != MVS_INIT_RANDOM)
+    if (p->init_mode == MVS_INIT_GIVEN || p->init_mode == MVS_INIT_GIVEN_RECOST)
         for (int r = 0; r < n_ref; ++r) {
             ViewData& V = c->views[refs[r]];
             size_t n = (size_t)V.cam.width * V.cam.height;
@@ -465,7 +468,14 @@ mvs_status mvs_patchmatch_batch(mvs_ctx* c, int32_t n_ref, const int32_t* refs, 
         CK(c, cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming));
     }
     std::vector<RefConst> rcs(n_ref);
-    for (int r = 0; r < n_ref; ++r) make_refconst(c, refs[r], srcs + (size_t)r * n_src, n_src, &q, rcs[r]);
+    size_t range_off = 0;   // MVS_INIT_RANGE: the views' ranges lie back to back in refs order
+    for (int r = 0; r < n_ref; ++r) {
+        make_refconst(c, refs[r], srcs + (size_t)r * n_src, n_src, &q, rcs[r]);
+        if (rcs[r].init_range) {
+            rcs[r].init_range += range_off;
+            range_off += (size_t)rcs[r].W * rcs[r].H;
+        }
+    }
     BatchGraph& B = c->batch;
     std::vector<int32_t> kr(refs, refs + n_ref), ks(srcs, srcs + (size_t)n_ref * n_src);
     bool same = B.exec && B.refs == kr && B.srcs == ks && B.lanes == q.lanes_per_pixel &&
@@ -479,7 +489,8 @@ mvs_status mvs_patchmatch_batch(mvs_ctx* c, int32_t n_ref, const int32_t* refs, 
         cudaError_t e = cudaSuccess;
         // view after view: consecutive launches share their source textures in L2
         for (int r = 0; r < n_ref && e == cudaSuccess; ++r) {
-            if (p->init_mode == MVS_INIT_RANDOM) e = launch_init(rcs[r], nullptr, c->gstream);
+            if (p->init_mode == MVS_INIT_RANDOM || p->init_mode == MVS_INIT_RANGE)
+                e = launch_init(rcs[r], nullptr, c->gstream);
             else if (p->init_mode == MVS_INIT_GIVEN_RECOST)
                 e = launch_cost(rcs[r], rcs[r].plane, rcs[r].cost, nullptr, c->gstream);
             for (int ph = p->phase_begin; ph < pend && e == cudaSuccess; ++ph) e = launch_phase(rcs[r], ph, c->gstream);
@@ -1011,6 +1022,55 @@ mvs_status mvs_phi_select(mvs_ctx* c, int32_t ref, const uint8_t* known, const f
     return MVS_OK;
 }
 
+mvs_status mvs_phi_select_min_cost(mvs_ctx* c, int32_t ref, const uint8_t* known, const float* hyp,
+                                   const uint8_t* valid, const float* hcost, float* plane, int32_t mem) {
+    mvs_status st = check_view(c, ref);
+    if (st != MVS_OK) return st;
+    if (!known || !hyp || !valid || !hcost || !plane) return fail(c, MVS_EINVAL, "NULL argument");
+    if (((uintptr_t)plane & 15u) || ((uintptr_t)hyp & 15u) || ((uintptr_t)hcost & 15u) || ((uintptr_t)valid & 3u))
+        return fail(c, MVS_EINVAL, "plane, hyp and hcost must be 16-byte, valid 4-byte aligned");
+    if (mem != MVS_MEM_DEVICE && mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    CK(c, cudaSetDevice(c->device));
+    const ViewData& V = c->views[ref];
+    int W = V.cam.width, H = V.cam.height;
+    size_t n = (size_t)W * H;
+    RefConst rc;
+    std::memset(&rc, 0, sizeof rc);
+    rc.W = W;
+    rc.H = H;
+    for (int i = 0; i < 9; ++i) rc.Kinv[i] = (float)V.Kinv[i];
+    cudaError_t e;
+    float* newd = (float*)scratch(c, 3, n * sizeof(float), &e);
+    CK(c, e);
+    const uint8_t* kd = known;
+    const float* hd = hyp;
+    const float* cd = hcost;
+    const uint8_t* vd = valid;
+    float4* pd = (float4*)plane;
+    if (mem == MVS_MEM_HOST) {
+        // staging: plane(n f4) hyp(4n f) hcost(4n f) valid(4n) known(n), each region 16-byte aligned
+        char* buf = (char*)scratch(c, 0, n * (12 * sizeof(float) + 5) + 64, &e);
+        CK(c, e);
+        float4* p2 = (float4*)buf;
+        float* h2 = (float*)(p2 + n);
+        float* c2 = h2 + 4 * n;
+        uint8_t* v2 = (uint8_t*)(c2 + 4 * n);
+        uint8_t* k2 = v2 + 4 * n;
+        CK(c, cudaMemcpyAsync(p2, plane, n * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(h2, hyp, n * 4 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c2, hcost, n * 4 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(v2, valid, n * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(k2, known, n, cudaMemcpyHostToDevice, c->stream));
+        kd = k2; hd = h2; cd = c2; vd = v2; pd = p2;
+    }
+    CK(c, launch_phi_select_min_cost(rc, kd, hd, vd, cd, pd, newd, c->stream));
+    if (mem == MVS_MEM_HOST) {
+        CK(c, cudaMemcpyAsync(plane, pd, n * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return MVS_OK;
+}
+
 mvs_status mvs_plane_infer(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n_src, const mvs_pm_params* pm,
                            const mvs_phi_params* phi, const uint8_t* keep_mask, mvs_depth_map* inout) {
     mvs_status st = check_pm(c, ref, srcs, n_src, pm);
@@ -1023,6 +1083,8 @@ mvs_status mvs_plane_infer(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t
     if (phi->trw_iters < 0 || phi->trw_iters > 1000) return fail(c, MVS_EINVAL, "trw_iters outside 0..1000");
     if (!(phi->kappa1 > 0) || !(phi->kappa2 > 0) || !(phi->kappa3 > 1))
         return fail(c, MVS_EINVAL, "need kappa1 > 0, kappa2 > 0, kappa3 > 1");
+    if (phi->selection != MVS_PHI_SELECT_MRF && phi->selection != MVS_PHI_SELECT_MIN_COST)
+        return fail(c, MVS_EINVAL, "unknown selection %d", (int)phi->selection);
     CK(c, cudaSetDevice(c->device));
     if ((st = ensure_map(c, ref)) != MVS_OK) return st;
     ViewData& V = c->views[ref];
@@ -1033,16 +1095,17 @@ mvs_status mvs_plane_infer(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t
     CK(c, cudaMemcpyAsync(V.plane, inout->plane, n * sizeof(float4), kind_in(mem), c->stream));
     CK(c, cudaMemcpyAsync(V.cost, inout->cost, n * sizeof(float), kind_in(mem), c->stream));
     cudaError_t e;
-    // layout of scratch slot 4: hyp(4n f) hcost(4n f) depth(n f) newd(n f) label(g i) known(n) valid(4n)
+    // layout of scratch slot 4: hyp(4n f) hcost(4n f) valid(4n) depth(n f) newd(n f) label(g i) known(n);
+    // hyp and hcost are 16-byte and valid 4-byte aligned (per-pixel vector loads)
     char* buf = (char*)scratch(c, 4, n * (10 * sizeof(float) + 5) + g * sizeof(int32_t) + 256, &e);
     CK(c, e);
     float* hyp = (float*)buf;
     float* hcost = hyp + 4 * n;
-    float* depth = hcost + 4 * n;
+    uint8_t* valid = (uint8_t*)(hcost + 4 * n);
+    float* depth = (float*)(valid + 4 * n);
     float* newd = depth + n;
     int32_t* label = (int32_t*)(newd + n);
     uint8_t* known = (uint8_t*)(label + g);
-    uint8_t* valid = known + n;
     int32_t* work = (int32_t*)scratch(c, 1, n * 8 * sizeof(int32_t), &e);
     CK(c, e);
     float* mwork = (float*)scratch(c, 2, phi_mrf_work_floats(W, H) * sizeof(float), &e);
@@ -1058,9 +1121,13 @@ mvs_status mvs_plane_infer(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t
     CK(c, launch_phi_hypotheses(W, H, depth, known, phi->n_fit, phi->fit_inverse, pm->d_lo, pm->d_hi, hyp, valid,
                                 work, c->stream));
     CK(c, launch_phi_cost(rc, hyp, valid, hcost, c->stream));
-    CK(c, launch_phi_mrf(W, H, known, depth, hyp, valid, hcost, phi->kappa1, phi->kappa2, phi->kappa3,
-                         phi->trw_iters, label, mwork, c->stream));
-    CK(c, launch_phi_select(rc, known, hyp, valid, label, V.plane, newd, c->stream));
+    if (phi->selection == MVS_PHI_SELECT_MIN_COST) {
+        CK(c, launch_phi_select_min_cost(rc, known, hyp, valid, hcost, V.plane, newd, c->stream));
+    } else {
+        CK(c, launch_phi_mrf(W, H, known, depth, hyp, valid, hcost, phi->kappa1, phi->kappa2, phi->kappa3,
+                             phi->trw_iters, label, mwork, c->stream));
+        CK(c, launch_phi_select(rc, known, hyp, valid, label, V.plane, newd, c->stream));
+    }
     V.has_map = true;
     CK(c, cudaMemcpyAsync(inout->plane, V.plane, n * sizeof(float4), kind_out(mem), c->stream));
     if (mem == MVS_MEM_HOST) CK(c, cudaStreamSynchronize(c->stream));

@@ -113,6 +113,9 @@ cudaError_t launch_phi_mrf(int W, int H, const uint8_t* known, const float* dept
 size_t phi_mrf_work_floats(int W, int H);
 cudaError_t launch_phi_select(const RefConst& rc, const uint8_t* known, const float* hyp, const uint8_t* valid,
                               const int32_t* label, float4* plane, float* newdepth, cudaStream_t s);
+cudaError_t launch_phi_select_min_cost(const RefConst& rc, const uint8_t* known, const float* hyp,
+                                       const uint8_t* valid, const float* hcost, float4* plane, float* newdepth,
+                                       cudaStream_t s);
 cudaError_t launch_known_from_cost(int W, int H, const float4* plane, const float* cost, float hole_cost,
                                    uint8_t* known, float* depth, cudaStream_t s);
 cudaError_t launch_depth_of(int W, int H, const float4* plane, const uint8_t* known, float* depth, cudaStream_t s);

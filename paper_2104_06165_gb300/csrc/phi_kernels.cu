@@ -396,6 +396,27 @@ __global__ void k_select(int W, int H, const uint8_t* __restrict__ known, const 
     newd[i] = nd;
 }
 
+// PHI-MVS/M (Sec. IV, Table I: the MRF removed): each hole takes its valid
+// hypothesis of minimal matching cost, the lowest k on a tie; a hole without
+// a valid hypothesis gets no depth
+__global__ void k_select_min_cost(long long n, const uint8_t* __restrict__ known, const float* __restrict__ hyp,
+                                  const uint8_t* __restrict__ valid, const float* __restrict__ hcost,
+                                  const float4* __restrict__ plane, float* __restrict__ newd) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (known[i]) { newd[i] = plane[i].w; return; }
+    const float4 h = reinterpret_cast<const float4*>(hyp)[i];
+    const float4 c = reinterpret_cast<const float4*>(hcost)[i];
+    const uchar4 v = reinterpret_cast<const uchar4*>(valid)[i];
+    const float hv[4] = {h.x, h.y, h.z, h.w}, cv[4] = {c.x, c.y, c.z, c.w};
+    const bool ok[4] = {v.x != 0, v.y != 0, v.z != 0, v.w != 0};
+    int bk = -1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (ok[k] && (bk < 0 || cv[k] < cv[bk])) bk = k;
+    newd[i] = bk >= 0 ? hv[bk] : 0.0f;
+}
+
 // Eq. 10 normal from the back-projected 4-neighbours (reading: unit length,
 // oriented towards the camera); a hole without all four neighbours stays
 // empty
@@ -581,6 +602,19 @@ cudaError_t launch_phi_select(const RefConst& rc, const uint8_t* known, const fl
                               const int32_t* label, float4* plane, float* newdepth, cudaStream_t s) {
     long long n = (long long)rc.W * rc.H;
     k_select<<<blocks_for(n, 256), 256, 0, s>>>(rc.W, rc.H, known, hyp, valid, label, plane, newdepth);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_eq10<<<blocks_for(n, 256), 256, 0, s>>>(rc, known, newdepth, plane);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi_select_min_cost(const RefConst& rc, const uint8_t* known, const float* hyp,
+                                       const uint8_t* valid, const float* hcost, float4* plane, float* newdepth,
+                                       cudaStream_t s) {
+    long long n = (long long)rc.W * rc.H;
+    k_select_min_cost<<<blocks_for(n, 256), 256, 0, s>>>(n, known, hyp, valid, hcost, plane, newdepth);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libmvs.so")
 MVS_OK, MVS_EINVAL, MVS_ENOMEM, MVS_ECUDA, MVS_ETIMEOUT, MVS_ESTATE, MVS_EUNSUPPORTED = range(7)
 MVS_MEM_DEVICE, MVS_MEM_HOST = 0, 1
 MVS_INIT_RANDOM, MVS_INIT_GIVEN, MVS_INIT_GIVEN_RECOST, MVS_INIT_RANGE = 0, 1, 2, 3
+MVS_PHI_SELECT_MRF, MVS_PHI_SELECT_MIN_COST = 0, 1
 STATUS_NAMES = ["MVS_OK", "MVS_EINVAL", "MVS_ENOMEM", "MVS_ECUDA", "MVS_ETIMEOUT", "MVS_ESTATE",
                 "MVS_EUNSUPPORTED"]
 
@@ -55,7 +56,8 @@ class mvs_filter_params(C.Structure):
 
 class mvs_phi_params(C.Structure):
     _fields_ = [("kappa1", C.c_float), ("kappa2", C.c_float), ("kappa3", C.c_float), ("n_fit", C.c_int32),
-                ("fit_inverse", C.c_int32), ("trw_iters", C.c_int32), ("hole_cost", C.c_float)]
+                ("fit_inverse", C.c_int32), ("trw_iters", C.c_int32), ("hole_cost", C.c_float),
+                ("selection", C.c_int32)]
 
 
 @dataclass
@@ -113,10 +115,11 @@ class PhiParams:
     fit_inverse: int = 0
     trw_iters: int = 1
     hole_cost: float = 0.5
+    selection: int = 0          # MVS_PHI_SELECT_MRF; MVS_PHI_SELECT_MIN_COST = PHI-MVS/M
 
     def c(self):
         return mvs_phi_params(self.kappa1, self.kappa2, self.kappa3, self.n_fit, self.fit_inverse, self.trw_iters,
-                              self.hole_cost)
+                              self.hole_cost, self.selection)
 
 
 _lib = None
@@ -160,6 +163,8 @@ def load():
     L.mvs_phi_mrf.argtypes = [vp, i32, i32, u8p, fp, fp, u8p, fp, C.POINTER(mvs_phi_params), vp, i32]
     L.mvs_phi_select.restype = i32
     L.mvs_phi_select.argtypes = [vp, i32, u8p, fp, u8p, vp, fp, i32]
+    L.mvs_phi_select_min_cost.restype = i32
+    L.mvs_phi_select_min_cost.argtypes = [vp, i32, u8p, fp, u8p, fp, fp, i32]
     L.mvs_profile.restype = i32
     L.mvs_profile.argtypes = [vp, i32]
     L.mvs_cnn_create.restype = i32
@@ -399,6 +404,12 @@ def mvs_phi_select(ctx, ref, known, hyp, valid, label, plane):
     mem = _mem(known, hyp, valid, label, plane)
     _check(load().mvs_phi_select(ctx, ref, _ptr(known)[0], _ptr(hyp)[0], _ptr(valid)[0], _ptr(label)[0],
                                  _ptr(plane)[0], mem), ctx)
+
+
+def mvs_phi_select_min_cost(ctx, ref, known, hyp, valid, hcost, plane):
+    mem = _mem(known, hyp, valid, hcost, plane)
+    _check(load().mvs_phi_select_min_cost(ctx, ref, _ptr(known)[0], _ptr(hyp)[0], _ptr(valid)[0], _ptr(hcost)[0],
+                                          _ptr(plane)[0], mem), ctx)
 
 
 def mvs_profile(ctx, enable):

@@ -40,8 +40,10 @@ def test_ctypes_structs_match_c_layout(mvs_lib):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(mvs_camera), sizeof(mvs_pm_params), sizeof(mvs_depth_map),
          sizeof(mvs_filter_params), sizeof(mvs_phi_params));
-  printf("%zu %zu %zu %zu %zu\n", offsetof(mvs_pm_params, seed), offsetof(mvs_pm_params, precision),
-         offsetof(mvs_camera, width), offsetof(mvs_phi_params, hole_cost), offsetof(mvs_pm_params, init_range));
+  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(mvs_pm_params, seed), offsetof(mvs_pm_params, precision),
+         offsetof(mvs_camera, width), offsetof(mvs_phi_params, hole_cost), offsetof(mvs_pm_params, init_range),
+         offsetof(mvs_phi_params, selection));
+  printf("%d %d\n", MVS_PHI_SELECT_MRF, MVS_PHI_SELECT_MIN_COST);
   return 0;
 }
 """
@@ -57,7 +59,9 @@ int main(void) {
     assert sizes == [C.sizeof(m.mvs_camera), C.sizeof(m.mvs_pm_params), C.sizeof(m.mvs_depth_map),
                      C.sizeof(m.mvs_filter_params), C.sizeof(m.mvs_phi_params)]
     assert offs == [m.mvs_pm_params.seed.offset, m.mvs_pm_params.precision.offset, m.mvs_camera.width.offset,
-                    m.mvs_phi_params.hole_cost.offset, m.mvs_pm_params.init_range.offset]
+                    m.mvs_phi_params.hole_cost.offset, m.mvs_pm_params.init_range.offset,
+                    m.mvs_phi_params.selection.offset]
+    assert [int(x) for x in lines[2].split()] == [m.MVS_PHI_SELECT_MRF, m.MVS_PHI_SELECT_MIN_COST]
 
 
 def test_create_rejects_bad_arguments_before_touching_cuda(mvs_lib):
@@ -104,6 +108,9 @@ def test_null_context_is_rejected(mvs_lib):
     rng = np.zeros((2, 2, 2), np.float32)
     assert lib.mvs_sparse_depth_range(None, 0, 0, None, None, None, None, 2.0, C.c_float(2.0), C.c_float(8.0),
                                       rng.ctypes.data, 1) == mvs_lib.MVS_EINVAL
+    pl = np.zeros((2, 2, 4), np.float32)
+    assert lib.mvs_phi_select_min_cost(None, 0, None, None, None, None, pl.ctypes.data_as(C.POINTER(C.c_float)),
+                                       1) == mvs_lib.MVS_EINVAL
     lib.mvs_destroy(None)   # NULL-safe
 
 

@@ -102,19 +102,46 @@ def test_sparse_initialisation_converges_faster(sparse_scene, mvs_lib):
     assert sparse > plain
 
 
-def test_ranges_must_be_device_memory_and_per_view(sparse_scene, mvs_lib):
+def test_ranges_must_be_device_memory(sparse_scene, mvs_lib):
     sc, sp, ctx = sparse_scene
     H, W = sc.images[0].shape
     host = np.zeros((H, W, 2), np.float32)
     p = mvs_lib.PMParams(win_radius=5.0, win_samples=6, iters=0, init_mode=mvs_lib.MVS_INIT_RANGE, init_range=host)
     with pytest.raises(mvs_lib.MvsError):
         mvs_lib.mvs_patchmatch(ctx.h, 0, [1, 2], p, np.zeros((H, W, 4), np.float32), np.zeros((H, W), np.float32))
-    rng = _gpu_range(mvs_lib, ctx, sp, 0, H, W, device=True)
-    q = mvs_lib.PMParams(win_radius=5.0, win_samples=6, iters=1, init_mode=mvs_lib.MVS_INIT_RANGE, init_range=rng)
-    pls = [np.zeros((H, W, 4), np.float32)]
-    cos = [np.zeros((H, W), np.float32)]
     with pytest.raises(mvs_lib.MvsError):
-        mvs_lib.mvs_patchmatch_batch(ctx.h, [0], [[1, 2]], q, pls, cos)
+        mvs_lib.mvs_patchmatch_batch(ctx.h, [0], [[1, 2]], p, [np.zeros((H, W, 4), np.float32)],
+                                     [np.zeros((H, W), np.float32)])
+
+
+def test_batch_takes_back_to_back_ranges(sparse_scene, mvs_lib):
+    """The batched graph with every reference's ranges back to back in refs
+    order gives the maps of separate mvs_patchmatch calls, bit for bit."""
+    import torch
+    sc, sp, ctx = sparse_scene
+    H, W = sc.images[0].shape
+    refs, srcs = [2, 0], [[0, 1, 3, 4], [1, 2, 3, 4]]
+    rngs = [_gpu_range(mvs_lib, ctx, sp, r, H, W, device=True) for r in refs]
+    sep = []
+    for r, s, g in zip(refs, srcs, rngs):
+        p = mvs_lib.PMParams(win_radius=5.0, win_samples=6, iters=1, seed=12, init_mode=mvs_lib.MVS_INIT_RANGE,
+                             init_range=g)
+        pl = np.zeros((H, W, 4), np.float32)
+        co = np.zeros((H, W), np.float32)
+        mvs_lib.mvs_patchmatch(ctx.h, r, s, p, pl, co)
+        sep.append((pl, co))
+    both = torch.cat([g.reshape(-1) for g in rngs])
+    q = mvs_lib.PMParams(win_radius=5.0, win_samples=6, iters=1, seed=12, init_mode=mvs_lib.MVS_INIT_RANGE,
+                         init_range=both)
+    for _ in range(2):      # capture, then replay
+        pls = [np.zeros((H, W, 4), np.float32) for _ in refs]
+        cos = [np.zeros((H, W), np.float32) for _ in refs]
+        mvs_lib.mvs_patchmatch_batch(ctx.h, refs, srcs, q, pls, cos)
+        for (a_pl, a_co), b_pl, b_co in zip(sep, pls, cos):
+            assert np.array_equal(a_pl, b_pl) and np.array_equal(a_co, b_co)
+    # the two views' ranges differ, so taking one view's ranges for both would fail
+    assert not torch.equal(rngs[0].isnan(), rngs[1].isnan()) or not torch.equal(rngs[0].nan_to_num(),
+                                                                                   rngs[1].nan_to_num())
 
 
 def test_no_features_keeps_the_random_initialisation(sparse_scene, mvs_lib):

@@ -547,36 +547,10 @@ def test_cost_at_equals_the_cost_map(oracle_lib, tiny):
 # PHI-MVS/M (Sec. IV, Table I): the MRF removed, each hole takes its valid
 # hypothesis of minimal matching cost
 # --------------------------------------------------------------------------
-def _slanted_hole_case(rng, W=36, H=28):
-    """Slanted plane with a hole; per hole pixel four hypotheses, of which
-    one (a random direction) is the exact planar depth at the lowest cost and
-    the others perturbed depths at higher costs; some invalid, some ties."""
-    from paper_2104_06165_gb300 import scenes
-    n_true = np.array([0.25, -0.3, -1.0])
-    n_true /= np.linalg.norm(n_true)
-    sc = scenes.make_plane_scene(W=W, H=H, n_src=1, seed=3, depth=5.0, normal=n_true)
-    gt = sc.gt_depth
-    known = np.ones((H, W), np.uint8)
-    known[6:22, 8:28] = 0
-    hyp = gt[..., None] * (1.0 + rng.uniform(0.02, 0.1, (H, W, 4)) * rng.choice([-1, 1], (H, W, 4)))
-    hcost = rng.uniform(0.3, 1.9, (H, W, 4))
-    valid = (rng.random((H, W, 4)) < 0.8).astype(np.uint8)
-    best = rng.integers(0, 4, (H, W))
-    yy, xx = np.mgrid[0:H, 0:W]
-    hyp[yy, xx, best] = gt
-    hcost[yy, xx, best] = rng.uniform(0.0, 0.25, (H, W))
-    valid[yy, xx, best] = 1
-    # ties: a perturbed hypothesis at a higher index with the same cost never wins
-    tie = (rng.random((H, W)) < 0.3) & (best < 3)
-    hcost[yy[tie], xx[tie], 3] = hcost[yy[tie], xx[tie], best[tie]]
-    valid[yy[tie], xx[tie], 3] = 1
-    plane = np.concatenate([sc.gt_normal, gt[..., None]], -1) * known[..., None]
-    return sc, n_true, known, hyp, valid, hcost, plane, best
-
-
 def test_min_cost_selection_is_masked_argmin_and_recovers_the_plane(oracle_lib):
+    from phi_cases import slanted_hole_case
     rng = np.random.default_rng(21)
-    sc, n_true, known, hyp, valid, hcost, plane, best = _slanted_hole_case(rng)
+    sc, n_true, known, hyp, valid, hcost, plane, best = slanted_hole_case(rng)
     osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
     out, filled = oracle_lib.phi_select_min_cost(osc, 0, known, hyp, valid, hcost, plane)
     # library routine: numpy's argmin (first minimum) over the masked costs
@@ -592,8 +566,9 @@ def test_min_cost_selection_is_masked_argmin_and_recovers_the_plane(oracle_lib):
 
 
 def test_min_cost_selection_empty_holes(oracle_lib):
+    from phi_cases import slanted_hole_case
     rng = np.random.default_rng(5)
-    sc, n_true, known, hyp, valid, hcost, plane, best = _slanted_hole_case(rng)
+    sc, n_true, known, hyp, valid, hcost, plane, best = slanted_hole_case(rng)
     osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
     valid[10, 12] = 0                      # no hypothesis: stays empty, and so do
     out, filled = oracle_lib.phi_select_min_cost(osc, 0, known, hyp, valid, hcost, plane)
