@@ -40,12 +40,14 @@ __global__ void k_build_texture(const uint8_t* __restrict__ img, int W, int H, u
 constexpr int kWarps = kBlock / 32;
 // Checkerboard-phase blocks cover a tile of kTileX x kTileY pixels of the
 // active colour, one warp per pixel, so that the warps sharing an SM's L1
-// gather overlapping windows.
+// gather overlapping windows.  4 x 5 warps (96 registers a thread) hide more
+// gather latency than 4 x 4 at 128 registers: 4 % less time per phase at
+// 3072 x 2048 with 11 x 11 samples; 4 x 3, 3 x 7 and 4 x 6 were slower.
 #ifndef MVS_TILE_X
 #define MVS_TILE_X 4
 #endif
 #ifndef MVS_TILE_Y
-#define MVS_TILE_Y 4
+#define MVS_TILE_Y 5
 #endif
 // Windows of 16 slots per lane need more than 128 registers: their blocks
 // keep to one row of kTileX pixels (3 blocks of 128 threads per SM).
@@ -57,6 +59,7 @@ struct PhaseTile {
     static constexpr int BLOCK = 32 * WARPS;
     static constexpr int MIN_BLOCKS = (S >= 16 ? 384 : 512) / BLOCK > 0 ? (S >= 16 ? 384 : 512) / BLOCK : 1;
 };
+
 
 // ---------------------------------------------------------------------------
 // Sec. III-B: random initialisation, then the cost of the initial plane.
@@ -200,13 +203,32 @@ __host__ __device__ constexpr size_t phase_smem_bytes(int n_src, int warps) {
     return smem_block_bytes(n_src, warps) + (size_t)warps * 32 * (sizeof(float4) + sizeof(float));
 }
 
+// Rows of warps of a phase block: PhaseTile<S>::TY, or fewer when the
+// block's pair lists (which grow with the number of sources) would exceed the
+// per-block shared memory.
+int max_block_smem() {
+    static const int bytes = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return v;
+    }();
+    return bytes;
+}
+template <int S>
+int phase_rows(int n_src) {
+    int ty = PhaseTile<S>::TY;
+    while (ty > 1 && phase_smem_bytes(n_src, PhaseTile<S>::TX * ty) > (size_t)max_block_smem()) --ty;
+    return ty;
+}
+
 // Tiles are visited in super-tiles of 8 x 16 tiles so that the pixels in
 // flight at once form a compact region (a smaller source footprint in L2;
 // within a phase the order of the pixels does not change the result).
 // Pixel of the active colour that warp `warp` takes in tile t, or -1.
-template <int TX, int TY>
-__device__ __forceinline__ long long phase_pixel(const RefConst& rc, long long t, int warp, int color, int& px,
-                                                 int& py) {
+template <int TX>
+__device__ __forceinline__ long long phase_pixel(const RefConst& rc, long long t, int warp, int color, int TY,
+                                                 int& px, int& py) {
     constexpr int kSTX = 8, kSTY = 16;
     const int Wa = (rc.W + 1) >> 1;
     const int ntx = (Wa + TX - 1) / TX, nty = (rc.H + TY - 1) / TY;
@@ -223,9 +245,12 @@ __device__ __forceinline__ long long phase_pixel(const RefConst& rc, long long t
 template <int G, int S, bool MIXED>
 __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
     k_phase(const __grid_constant__ RefConst rc, int phase) {
-    constexpr int kTileX = PhaseTile<S>::TX, kTileY = PhaseTile<S>::TY;
-    constexpr int kWarpsB = PhaseTile<S>::WARPS;
-    extern __shared__ __align__(16) unsigned char smem[];   // phase_smem_bytes(n_src, PhaseTile<S>::WARPS)
+    // the block is kTileX x kTileY warps, kTileY <= PhaseTile<S>::TY chosen by
+    // the host so that the block's shared memory fits
+    constexpr int kTileX = PhaseTile<S>::TX;
+    const int kTileY = (int)(blockDim.x >> 5) / kTileX;
+    const int kWarpsB = kTileX * kTileY;
+    extern __shared__ __align__(16) unsigned char smem[];   // phase_smem_bytes(n_src, kWarpsB)
     ViewSm* views = reinterpret_cast<ViewSm*>(smem);
     load_views(rc, views);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -244,7 +269,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             // pixels, one per lane: delta_d in [-d_hi/4, d_hi/4],
             // delta_theta in [-pi/2, pi/2], delta_phi in [-pi/12, pi/12]
             int qx, qy;
-            const long long q = phase_pixel<kTileX, kTileY>(rc, t + (long long)lane * gridDim.x, warp, color, qx, qy);
+            const long long q = phase_pixel<kTileX>(rc, t + (long long)lane * gridDim.x, warp, color, kTileY, qx, qy);
             float u[3];
             draws3(rc, q < 0 ? 0 : q, phase, u);
             float sdt, cdt, sdp, cdp;
@@ -256,7 +281,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             __syncwarp();
         }
         int px, py;
-        const long long pix = phase_pixel<kTileX, kTileY>(rc, t, warp, color, px, py);
+        const long long pix = phase_pixel<kTileX>(rc, t, warp, color, kTileY, px, py);
         if (pix < 0) continue;   // warp-uniform
         PixWin<S> pw;
         build_window<G, S>(rc, px, py, true, pw);
@@ -366,7 +391,8 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
 
 unsigned pm_grid_for(const void* kernel, long long units, size_t smem, int block) {
     static std::mutex mu;
-    static std::unordered_map<const void*, std::pair<size_t, int>> cache;   // kernel -> (smem, blocks per SM)
+    struct Cfg { size_t smem; int block, per_sm; };
+    static std::unordered_map<const void*, Cfg> cache;   // kernel -> launch shape and blocks per SM
     static int sms = 0;
     int per_sm = 0;
     {
@@ -377,13 +403,13 @@ unsigned pm_grid_for(const void* kernel, long long units, size_t smem, int block
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         }
         auto it = cache.find(kernel);
-        if (it != cache.end() && it->second.first == smem) {
-            per_sm = it->second.second;
+        if (it != cache.end() && it->second.smem == smem && it->second.block == block) {
+            per_sm = it->second.per_sm;
         } else {
             if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
             per_sm = std::max(per_sm, 1);
-            cache[kernel] = {smem, per_sm};
+            cache[kernel] = {smem, block, per_sm};
         }
     }
     long long need = units;   // blocks of work
@@ -429,8 +455,9 @@ cudaError_t prime_launch_configs(const RefConst& rc) {
     do {                                                                                              \
         pm_grid_for((const void*)k_init<G, S, MX>, 1, smem, kBlock);                                  \
         pm_grid_for((const void*)k_cost<G, S, MX>, 1, smem, kBlock);                                  \
-        pm_grid_for((const void*)k_phase<G, S, MX>, 1, phase_smem_bytes(rc.n_src, PhaseTile<S>::WARPS), \
-                    PhaseTile<S>::BLOCK);                                                             \
+        pm_grid_for((const void*)k_phase<G, S, MX>, 1,                                                \
+                    phase_smem_bytes(rc.n_src, PhaseTile<S>::TX * phase_rows<S>(rc.n_src)),          \
+                    32 * PhaseTile<S>::TX * phase_rows<S>(rc.n_src));                                  \
     } while (0)
     if (rc.precision) {
         constexpr bool MX = true;
@@ -491,10 +518,11 @@ cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, fl
 template <int G, int S, bool MX>
 void phase_launch(const RefConst& rc, int phase, cudaStream_t s) {
     using T = PhaseTile<S>;
-    const long long ntiles = (long long)(((rc.W + 1) / 2 + T::TX - 1) / T::TX) * ((rc.H + T::TY - 1) / T::TY);
-    const size_t smem = phase_smem_bytes(rc.n_src, T::WARPS);
-    k_phase<G, S, MX><<<pm_grid_for((const void*)k_phase<G, S, MX>, ntiles, smem, T::BLOCK), T::BLOCK, smem, s>>>(
-        rc, phase);
+    const int ty = phase_rows<S>(rc.n_src), block = 32 * T::TX * ty;
+    const long long ntiles = (long long)(((rc.W + 1) / 2 + T::TX - 1) / T::TX) * ((rc.H + ty - 1) / ty);
+    const size_t smem = phase_smem_bytes(rc.n_src, T::TX * ty);
+    k_phase<G, S, MX><<<pm_grid_for((const void*)k_phase<G, S, MX>, ntiles, smem, block), block, smem, s>>>(rc,
+                                                                                                           phase);
 }
 
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s) {
