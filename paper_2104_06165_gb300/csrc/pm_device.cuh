@@ -106,6 +106,15 @@ __device__ __forceinline__ float tex_sample(const uint2* __restrict__ tex, int p
     return fmaf(V, fmaf(U, cd.y, cd.x), fmaf(U, ab.y, ab.x));
 }
 
+// Geometry of one pixel's window: the corners of the included sample
+// rectangle and the viewing ray (32 bytes; the phase kernel keeps it in
+// shared memory, read where a stage needs it).
+struct __align__(16) WinGeo {
+    float cu_lo, cu_hi, cv_lo, cv_hi;  // corners of the included sample rectangle
+    float rx0, rx1, rx2;  // K^-1 (x, y, 1)
+    float rlen;           // |K^-1 (x, y, 1)|
+};
+
 // Reference side of the window of one pixel.  Every group of G lanes of the
 // warp holds the same pixel's window (sample k = slot * G + lane_in_group).
 template <int S>
@@ -118,9 +127,7 @@ struct PixWin {
     float wr_sum;         // sum w (I_ref - mean) (zero up to rounding)
     float mean;           // weighted mean of the reference samples
     float wsum;
-    float cu_lo, cu_hi, cv_lo, cv_hi;  // corners of the included sample rectangle
-    float rx0, rx1, rx2;  // K^-1 (x, y, 1)
-    float rlen;           // |K^-1 (x, y, 1)|
+    WinGeo geo;
     bool ok;              // pixel exists and its reference patch is not flat
 };
 
@@ -188,16 +195,17 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
     pw.inv_wsum = inv_sw;
     pw.srr = srr;
     pw.ok = exists && sw > 0.0f && srr >= kTauVar * sw && ku_hi >= 0 && kv_hi >= 0;
-    pw.cu_lo = rc.step * ((float)ku_lo - half);
-    pw.cu_hi = rc.step * ((float)ku_hi - half);
-    pw.cv_lo = rc.step * ((float)kv_lo - half);
-    pw.cv_hi = rc.step * ((float)kv_hi - half);
+    WinGeo& g = pw.geo;
+    g.cu_lo = rc.step * ((float)ku_lo - half);
+    g.cu_hi = rc.step * ((float)ku_hi - half);
+    g.cv_lo = rc.step * ((float)kv_lo - half);
+    g.cv_hi = rc.step * ((float)kv_hi - half);
     const float* Ki = rc.Kinv;
     float x = (float)px, y = (float)py;
-    pw.rx0 = fmaf(Ki[0], x, fmaf(Ki[1], y, Ki[2]));
-    pw.rx1 = fmaf(Ki[3], x, fmaf(Ki[4], y, Ki[5]));
-    pw.rx2 = fmaf(Ki[6], x, fmaf(Ki[7], y, Ki[8]));
-    pw.rlen = sqrtf(pw.rx0 * pw.rx0 + pw.rx1 * pw.rx1 + pw.rx2 * pw.rx2);
+    g.rx0 = fmaf(Ki[0], x, fmaf(Ki[1], y, Ki[2]));
+    g.rx1 = fmaf(Ki[3], x, fmaf(Ki[4], y, Ki[5]));
+    g.rx2 = fmaf(Ki[6], x, fmaf(Ki[7], y, Ki[8]));
+    g.rlen = sqrtf(g.rx0 * g.rx0 + g.rx1 * g.rx1 + g.rx2 * g.rx2);
 }
 
 // Source-view constants copied to shared memory once per block (80 bytes,
@@ -246,17 +254,17 @@ struct Cand {
 // plane lies in front of the reference camera; n.r is affine in the sample
 // position, so the four corners decide).
 template <int S>
-__device__ __forceinline__ Cand make_cand(const RefConst& rc, const PixWin<S>& pw, float n0, float n1, float n2,
-                                          float d, bool want) {
+__device__ __forceinline__ Cand make_cand(const RefConst& rc, const PixWin<S>& pw, const WinGeo& g, float n0,
+                                          float n1, float n2, float d, bool want) {
     Cand c;
     c.n0 = n0; c.n1 = n1; c.n2 = n2; c.d = d;
     const float* Ki = rc.Kinv;
-    float nr = n0 * pw.rx0 + n1 * pw.rx1 + n2 * pw.rx2;
+    float nr = n0 * g.rx0 + n1 * g.rx1 + n2 * g.rx2;
     float k0 = Ki[0] * n0 + Ki[3] * n1 + Ki[6] * n2;
     float k1 = Ki[1] * n0 + Ki[4] * n1 + Ki[7] * n2;
-    bool corners = fmaf(pw.cu_lo, k0, fmaf(pw.cv_lo, k1, nr)) < 0.0f && fmaf(pw.cu_hi, k0, fmaf(pw.cv_lo, k1, nr)) < 0.0f &&
-                   fmaf(pw.cu_lo, k0, fmaf(pw.cv_hi, k1, nr)) < 0.0f && fmaf(pw.cu_hi, k0, fmaf(pw.cv_hi, k1, nr)) < 0.0f;
-    c.ok = want && pw.ok && d > 0.0f && d < 3.0e38f && nr < -kGraze * pw.rlen && corners;
+    bool corners = fmaf(g.cu_lo, k0, fmaf(g.cv_lo, k1, nr)) < 0.0f && fmaf(g.cu_hi, k0, fmaf(g.cv_lo, k1, nr)) < 0.0f &&
+                   fmaf(g.cu_lo, k0, fmaf(g.cv_hi, k1, nr)) < 0.0f && fmaf(g.cu_hi, k0, fmaf(g.cv_hi, k1, nr)) < 0.0f;
+    c.ok = want && pw.ok && d > 0.0f && d < 3.0e38f && nr < -kGraze * g.rlen && corners;
     float inv_rho = c.ok ? rcp_approx(d * nr) : 0.0f;
     c.m0 = k0 * inv_rho;
     c.m1 = k1 * inv_rho;
@@ -320,7 +328,7 @@ __device__ __forceinline__ bool same_plane(const float4& a, const float4& b) {
 // Must be called by all 32 lanes with the same nc (warp-uniform).
 template <int G, int S, bool VIEWS, bool MIXED = false>
 __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __restrict__ sv, const PixWin<S>& pw,
-                                            int px, int py, const Cand& my, int nc, PairSm* pairs,
+                                            const WinGeo& geo, int px, int py, const Cand& my, int nc, PairSm* pairs,
                                             float* view_cost, unsigned& n_evals) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
@@ -375,7 +383,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         bool ok = act;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float cu = (k & 1) ? pw.cu_hi : pw.cu_lo, cv = (k & 2) ? pw.cv_hi : pw.cv_lo;
+            float cu = (k & 1) ? geo.cu_hi : geo.cu_lo, cv = (k & 2) ? geo.cv_hi : geo.cv_lo;
             float cx = fmaf(cu, h0x, fmaf(cv, h1x, p0x));
             float cy = fmaf(cu, h0y, fmaf(cv, h1y, p0y));
             float cz = fmaf(cu, h0z, fmaf(cv, h1z, p0z));

@@ -87,12 +87,13 @@ __global__ void __launch_bounds__(kBlock) k_init(const __grid_constant__ RefCons
         float th = 2.0f * kPi * u[1];
         float ph = kPi * (u[2] - 0.5f);
         float n0, n1, n2;
-        normal_from_angles(th, ph, pw.rx0, pw.rx1, pw.rx2, n0, n1, n2);
+        normal_from_angles(th, ph, pw.geo.rx0, pw.geo.rx1, pw.geo.rx2, n0, n1, n2);
         float* vc = view_cost ? view_cost + a * rc.n_src : nullptr;
         float c = kCmax;
         if (pw.ok) {
-            Cand my = make_cand(rc, pw, n0, n1, n2, d, lane == 0);
-            c = eval_batch<G, S, true, MIXED>(rc, views, pw, px, py, my, 1, warp_pairs(smem, rc.n_src, warp), vc, nev);
+            Cand my = make_cand(rc, pw, pw.geo, n0, n1, n2, d, lane == 0);
+            c = eval_batch<G, S, true, MIXED>(rc, views, pw, pw.geo, px, py, my, 1, warp_pairs(smem, rc.n_src, warp),
+                                              vc, nev);
         } else if (vc && lane < rc.n_src) {
             vc[lane] = kCmax;
         }
@@ -122,8 +123,9 @@ __global__ void __launch_bounds__(kBlock) k_cost(const __grid_constant__ RefCons
         float* vc = view_cost ? view_cost + a * rc.n_src : nullptr;
         float c = kCmax;
         if (pw.ok) {
-            Cand my = make_cand(rc, pw, pl.x, pl.y, pl.z, pl.w, lane == 0);
-            c = eval_batch<G, S, true, MIXED>(rc, views, pw, px, py, my, 1, warp_pairs(smem, rc.n_src, warp), vc, nev);
+            Cand my = make_cand(rc, pw, pw.geo, pl.x, pl.y, pl.z, pl.w, lane == 0);
+            c = eval_batch<G, S, true, MIXED>(rc, views, pw, pw.geo, px, py, my, 1, warp_pairs(smem, rc.n_src, warp),
+                                              vc, nev);
         } else if (vc && lane < rc.n_src) {
             vc[lane] = kCmax;
         }
@@ -198,9 +200,10 @@ __device__ __forceinline__ int best_members(const RefConst& rc, int px, int py) 
 
 // Refinement perturbations of one pixel, drawn ahead for the next 32 pixels
 // of a warp (one lane each): delta_d, and cos / sin of delta_theta and of
-// delta_phi.  20 bytes per pixel, after the pair lists.
+// delta_phi.  20 bytes per pixel, after the pair lists; then the window
+// geometry of each warp's current pixel (32 bytes a warp).
 __host__ __device__ constexpr size_t phase_smem_bytes(int n_src, int warps) {
-    return smem_block_bytes(n_src, warps) + (size_t)warps * 32 * (sizeof(float4) + sizeof(float));
+    return smem_block_bytes(n_src, warps) + (size_t)warps * (32 * (sizeof(float4) + sizeof(float)) + sizeof(WinGeo));
 }
 
 // Rows of warps of a phase block: PhaseTile<S>::TY, or fewer when the
@@ -258,6 +261,8 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
     float4* draw4 = reinterpret_cast<float4*>(smem + smem_block_bytes(rc.n_src, kWarpsB)) + warp * 32;
     float* draw1 = reinterpret_cast<float*>(reinterpret_cast<float4*>(smem + smem_block_bytes(rc.n_src, kWarpsB)) +
                                             kWarpsB * 32) + warp * 32;
+    WinGeo* geo_w = reinterpret_cast<WinGeo*>(smem + smem_block_bytes(rc.n_src, kWarpsB) +
+                                              (size_t)kWarpsB * 32 * (sizeof(float4) + sizeof(float))) + warp;
     const int Wa = (rc.W + 1) >> 1;
     const int ntx = (Wa + kTileX - 1) / kTileX, nty = (rc.H + kTileY - 1) / kTileY;
     const int nstx = (ntx + 7) / 8, nsty = (nty + 15) / 16;
@@ -286,6 +291,12 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
         PixWin<S> pw;
         build_window<G, S>(rc, px, py, true, pw);
         if (!pw.ok) continue;                           // flat patch: every hypothesis costs C_max
+        // the window geometry waits in shared memory (fewer live registers
+        // through the evaluation rounds)
+        __syncwarp();
+        if (lane == 0) *geo_w = pw.geo;
+        __syncwarp();
+        const WinGeo& geo = *geo_w;
         float4 cur = rc.plane[pix];
         float cur_c = rc.cost[pix];
 
@@ -304,7 +315,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             float r1 = fmaf(Ki[3], (float)x2, fmaf(Ki[4], (float)y2, Ki[5]));
             float r2 = fmaf(Ki[6], (float)x2, fmaf(Ki[7], (float)y2, Ki[8]));
             float rho = np.w * (np.x * r0 + np.y * r1 + np.z * r2);
-            float den = np.x * pw.rx0 + np.y * pw.rx1 + np.z * pw.rx2;
+            float den = np.x * geo.rx0 + np.y * geo.rx1 + np.z * geo.rx2;
             ok = den < 0.0f;
             d = ok ? rho * rcp_approx(den) : 0.0f;
             ok = ok && d >= rc.d_lo && d <= rc.d_hi;
@@ -355,7 +366,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
                 const float ct2 = ct * r4.y - st * r4.z, st2 = st * r4.y + ct * r4.z;
                 const float cp2 = cp * r4.w - sp * sdp, sp2 = sp * r4.w + cp * sdp;
                 float nn0 = ct2 * sp2, nn1 = st2 * sp2, nn2 = cp2;
-                if (nn0 * pw.rx0 + nn1 * pw.rx1 + nn2 * pw.rx2 > 0.0f) {   // face the camera
+                if (nn0 * geo.rx0 + nn1 * geo.rx1 + nn2 * geo.rx2 > 0.0f) {   // face the camera
                     nn0 = -nn0;
                     nn1 = -nn1;
                     nn2 = -nn2;
@@ -366,8 +377,8 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
                 want = lane < 3;
             }
             const int nc = stage == 0 ? 8 : (stage == 1 ? rc.n_prop : 3);
-            Cand my = make_cand(rc, pw, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
-            float c = eval_batch<G, S, false, MIXED>(rc, views, pw, px, py, my, nc, warp_pairs(smem, rc.n_src, warp),
+            Cand my = make_cand(rc, pw, geo, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
+            float c = eval_batch<G, S, false, MIXED>(rc, views, pw, geo, px, py, my, nc, warp_pairs(smem, rc.n_src, warp),
                                                       nullptr, nev);
             float bc;
             int bi = warp_argmin(my.ok ? c : 3.0e38f, nc, bc);
