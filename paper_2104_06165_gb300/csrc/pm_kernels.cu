@@ -200,10 +200,19 @@ __device__ __forceinline__ int best_members(const RefConst& rc, int px, int py) 
 
 // Refinement perturbations of one pixel, drawn ahead for the next 32 pixels
 // of a warp (one lane each): delta_d, and cos / sin of delta_theta and of
-// delta_phi.  20 bytes per pixel, after the pair lists; then the window
-// geometry of each warp's current pixel (32 bytes a warp).
+// delta_phi.  20 bytes per pixel, after the pair lists; then each warp's
+// PhaseWarp record.
+// Per-warp state of the current pixel kept in shared memory rather than in
+// registers through the evaluation rounds: its window geometry, its plane and
+// cost so far, and the hypothesis each lane proposes in the current stage.
+struct __align__(16) PhaseWarp {
+    WinGeo geo;
+    float4 cur;
+    float cur_c, pad_[3];
+    float4 hyp[32];
+};
 __host__ __device__ constexpr size_t phase_smem_bytes(int n_src, int warps) {
-    return smem_block_bytes(n_src, warps) + (size_t)warps * (32 * (sizeof(float4) + sizeof(float)) + sizeof(WinGeo));
+    return smem_block_bytes(n_src, warps) + (size_t)warps * (32 * (sizeof(float4) + sizeof(float)) + sizeof(PhaseWarp));
 }
 
 // Rows of warps of a phase block: PhaseTile<S>::TY, or fewer when the
@@ -261,8 +270,8 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
     float4* draw4 = reinterpret_cast<float4*>(smem + smem_block_bytes(rc.n_src, kWarpsB)) + warp * 32;
     float* draw1 = reinterpret_cast<float*>(reinterpret_cast<float4*>(smem + smem_block_bytes(rc.n_src, kWarpsB)) +
                                             kWarpsB * 32) + warp * 32;
-    WinGeo* geo_w = reinterpret_cast<WinGeo*>(smem + smem_block_bytes(rc.n_src, kWarpsB) +
-                                              (size_t)kWarpsB * 32 * (sizeof(float4) + sizeof(float))) + warp;
+    PhaseWarp* ws = reinterpret_cast<PhaseWarp*>(smem + smem_block_bytes(rc.n_src, kWarpsB) +
+                                                 (size_t)kWarpsB * 32 * (sizeof(float4) + sizeof(float))) + warp;
     const int Wa = (rc.W + 1) >> 1;
     const int ntx = (Wa + kTileX - 1) / kTileX, nty = (rc.H + kTileY - 1) / kTileY;
     const int nstx = (ntx + 7) / 8, nsty = (nty + 15) / 16;
@@ -291,14 +300,16 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
         PixWin<S> pw;
         build_window<G, S>(rc, px, py, true, pw);
         if (!pw.ok) continue;                           // flat patch: every hypothesis costs C_max
-        // the window geometry waits in shared memory (fewer live registers
-        // through the evaluation rounds)
+        // the window geometry and the pixel's state wait in shared memory
+        // (fewer live registers through the evaluation rounds)
         __syncwarp();
-        if (lane == 0) *geo_w = pw.geo;
+        if (lane == 0) {
+            ws->geo = pw.geo;
+            ws->cur = rc.plane[pix];
+            ws->cur_c = rc.cost[pix];
+        }
         __syncwarp();
-        const WinGeo& geo = *geo_w;
-        float4 cur = rc.plane[pix];
-        float cur_c = rc.cost[pix];
+        const WinGeo& geo = ws->geo;
 
         // ---- propagation: lane g < 8 takes group g's cheapest member and
         // carries its plane over
@@ -325,7 +336,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
         // cannot be strictly cheaper than that plane: it is not evaluated.
         {
             const float4 mine = make_float4(np.x, np.y, np.z, d);
-            bool dup = ok && same_plane(mine, cur);
+            bool dup = ok && same_plane(mine, ws->cur);
 #pragma unroll
             for (int g2 = 0; g2 < 7; ++g2) {
                 const float4 o = make_float4(__shfl_sync(0xffffffffu, np.x, g2), __shfl_sync(0xffffffffu, np.y, g2),
@@ -347,8 +358,9 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
                 if (rc.n_prop == 0) continue;
                 const bool has = lane < rc.n_prop;
                 hyp4 = has ? rc.props[pix * rc.n_prop + lane] : make_float4(0.f, 0.f, -1.f, 0.f);
-                want = has && hyp4.w >= rc.d_lo && hyp4.w <= rc.d_hi && !same_plane(hyp4, cur);
+                want = has && hyp4.w >= rc.d_lo && hyp4.w <= rc.d_hi && !same_plane(hyp4, ws->cur);
             } else if (stage == 2) {
+                const float4 cur = ws->cur;
                 // refinement (Sec. III-C): d + delta_d clamped to the range;
                 // the normal's angles theta = atan2(m1, m0), phi = acos(m2)
                 // (after flipping to m2 >= 0) move by delta_theta, delta_phi,
@@ -377,20 +389,21 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
                 want = lane < 3;
             }
             const int nc = stage == 0 ? 8 : (stage == 1 ? rc.n_prop : 3);
+            ws->hyp[lane] = hyp4;
             Cand my = make_cand(rc, pw, geo, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
             float c = eval_batch<G, S, false, MIXED>(rc, views, pw, geo, px, py, my, nc, warp_pairs(smem, rc.n_src, warp),
-                                                      nullptr, nev);
+                                                      nullptr, nev);   // (ends with a warp barrier)
             float bc;
             int bi = warp_argmin(my.ok ? c : 3.0e38f, nc, bc);
-            if (bc < cur_c) {
-                cur = make_float4(__shfl_sync(0xffffffffu, hyp4.x, bi), __shfl_sync(0xffffffffu, hyp4.y, bi),
-                                  __shfl_sync(0xffffffffu, hyp4.z, bi), __shfl_sync(0xffffffffu, hyp4.w, bi));
-                cur_c = bc;
+            if (bc < ws->cur_c && lane == 0) {
+                ws->cur = ws->hyp[bi];
+                ws->cur_c = bc;
             }
+            __syncwarp();
         }
         if (lane == 0) {
-            rc.plane[pix] = cur;
-            rc.cost[pix] = cur_c;
+            rc.plane[pix] = ws->cur;
+            rc.cost[pix] = ws->cur_c;
         }
     }
     flush_evals(rc.eval_counter, nev);
