@@ -106,13 +106,18 @@ __device__ __forceinline__ float tex_sample(const uint2* __restrict__ tex, int p
     return fmaf(V, fmaf(U, cd.y, cd.x), fmaf(U, ab.y, ab.x));
 }
 
-// Geometry of one pixel's window: the corners of the included sample
-// rectangle and the viewing ray (32 bytes; the phase kernel keeps it in
-// shared memory, read where a stage needs it).
+// The warp-uniform part of one pixel's window: the corners of the included
+// sample rectangle, the viewing ray and the reference moments (48 bytes; the
+// phase kernel keeps it in shared memory, read where a stage or a round needs
+// it).
 struct __align__(16) WinGeo {
     float cu_lo, cu_hi, cv_lo, cv_hi;  // corners of the included sample rectangle
     float rx0, rx1, rx2;  // K^-1 (x, y, 1)
     float rlen;           // |K^-1 (x, y, 1)|
+    float inv_wsum;       // 1 / sum w
+    float srr;            // sum w (I_ref - mean)^2
+    float wr_sum;         // sum w (I_ref - mean) (zero up to rounding)
+    float wsum;
 };
 
 // Reference side of the window of one pixel.  Every group of G lanes of the
@@ -122,11 +127,7 @@ struct PixWin {
     float ou[S], ov[S];   // sample offsets (the first included sample for padding / excluded samples)
     float w[S];           // bilateral weights (0 for padding / excluded)
     float wr[S];          // w * (I_ref - weighted mean)
-    float inv_wsum;       // 1 / sum w
-    float srr;            // sum w (I_ref - mean)^2
-    float wr_sum;         // sum w (I_ref - mean) (zero up to rounding)
     float mean;           // weighted mean of the reference samples
-    float wsum;
     WinGeo geo;
     bool ok;              // pixel exists and its reference patch is not flat
 };
@@ -189,11 +190,11 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
         srr = fmaf(t, d, srr);
     }
     srr = gsum<G>(srr);
-    pw.wr_sum = gsum<G>(wrs);
-    pw.wsum = sw;
+    pw.geo.wr_sum = gsum<G>(wrs);
+    pw.geo.wsum = sw;
     pw.mean = mu;
-    pw.inv_wsum = inv_sw;
-    pw.srr = srr;
+    pw.geo.inv_wsum = inv_sw;
+    pw.geo.srr = srr;
     pw.ok = exists && sw > 0.0f && srr >= kTauVar * sw && ku_hi >= 0 && kv_hi >= 0;
     WinGeo& g = pw.geo;
     g.cu_lo = rc.step * ((float)ku_lo - half);
@@ -472,7 +473,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             // two-pass weighted variance (the form of Eq. 4): the weighted
             // mean first, then the centred second moment
             sa = gsum<G>(sa);
-            const float mu = sa * pw.inv_wsum;
+            const float mu = sa * geo.inv_wsum;
 #pragma unroll
             for (int k = 0; k < S; ++k) {
                 const float e = dv[k] - mu;
@@ -532,17 +533,17 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             sb += __shfl_xor_sync(0xffffffffu, sb, o);
             se += __shfl_xor_sync(0xffffffffu, se, o);
         }
-        const float mean_d = sa * pw.inv_wsum;
+        const float mean_d = sa * geo.inv_wsum;
         // sum w (s - mu)^2 (FP32: already centred; mixed: one-pass, shifted)
         float sdd = MIXED ? fmaf(-mean_d, sa, sb) : sb;
         // sum w r' (s - mu) = sum w r' d - mu_d sum w r'
-        const float srd = fmaf(-mean_d, pw.wr_sum, se);
+        const float srd = fmaf(-mean_d, geo.wr_sum, se);
         if constexpr (MIXED) {
             // a source patch near the flat limit (where the exclusion decision
             // is taken): recompute the variance denominator in FP64
-            const bool near_flat = sdd < 2.0f * kTauVar * pw.wsum && sdd > 0.5f * kTauVar * pw.wsum;
+            const bool near_flat = sdd < 2.0f * kTauVar * geo.wsum && sdd > 0.5f * kTauVar * geo.wsum;
             if (__any_sync(0xffffffffu, near_flat)) {
-                const double mu_d = (double)c0 + (double)sa / (double)pw.wsum;
+                const double mu_d = (double)c0 + (double)sa / (double)geo.wsum;
                 double v = 0.0;
 #pragma unroll
                 for (int k = 0; k < S; ++k) {
@@ -556,8 +557,8 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         }
         // ZNCC, C(x, j) = 1 - Z, and its Eq. 5 weight (all lanes compute,
         // the group's first lane stores)
-        const bool flat = !(sdd >= kTauVar * pw.wsum);
-        const float z = fminf(1.0f, fmaxf(-1.0f, srd * rsqrtf(pw.srr * sdd)));
+        const bool flat = !(sdd >= kTauVar * geo.wsum);
+        const float z = fminf(1.0f, fmaxf(-1.0f, srd * rsqrtf(geo.srr * sdd)));
         const float cj = flat ? kCmax : fminf(1.0f - z, kCmax);
         if (has && lg == 0) {
             if (VIEWS) pairs[it].res = cj;
