@@ -327,10 +327,13 @@ __device__ __forceinline__ bool same_plane(const float4& a, const float4& b) {
 //   3. lane c folds the per-view results of hypothesis c in view order
 //      (Eq. 5, weights 1/max(C, 1e-6)).
 // Must be called by all 32 lanes with the same nc (warp-uniform).
-template <int G, int S, bool VIEWS, bool MIXED = false>
+// OFF_SM: the window's sample offsets are read from shared memory, (ou, ov)
+// of slot k and lane-in-group lg at off_sm[k * G + lg] (pw.ou / pw.ov are not
+// read, so they need not stay in registers).
+template <int G, int S, bool VIEWS, bool MIXED = false, bool OFF_SM = false>
 __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __restrict__ sv, const PixWin<S>& pw,
                                             const WinGeo& geo, int px, int py, const Cand& my, int nc, PairSm* pairs,
-                                            float* view_cost, unsigned& n_evals) {
+                                            float* view_cost, unsigned& n_evals, const float2* off_sm = nullptr) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
     const int V = rc.n_src;
@@ -442,9 +445,10 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                 for (int kk = 0; kk < CH; ++kk) {
                     const int k = k0 + kk;
                     if (k < S) {
-                        float X = fmaf(pw.ou[k], h0x, fmaf(pw.ov[k], h1x, p0x));
-                        float Y = fmaf(pw.ou[k], h0y, fmaf(pw.ov[k], h1y, p0y));
-                        float Z = fmaf(pw.ou[k], h0z, fmaf(pw.ov[k], h1z, p0z));
+                        const float2 o = OFF_SM ? off_sm[k * G + lg] : make_float2(pw.ou[k], pw.ov[k]);
+                        float X = fmaf(o.x, h0x, fmaf(o.y, h1x, p0x));
+                        float Y = fmaf(o.x, h0y, fmaf(o.y, h1y, p0y));
+                        float Z = fmaf(o.x, h0z, fmaf(o.y, h1z, p0z));
                         float iz = rcp_approx(Z);
                         float tx = fmaf(X, iz, kMagic2), ty = fmaf(Y, iz, kMagic2);
                         Us[kk] = fmaf(X, iz, kMagic2 - tx);
@@ -493,9 +497,10 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int kk = k + h < S ? k + h : k;
-                    float X = fmaf(pw.ou[kk], h0x, fmaf(pw.ov[kk], h1x, p0x));
-                    float Y = fmaf(pw.ou[kk], h0y, fmaf(pw.ov[kk], h1y, p0y));
-                    float Z = fmaf(pw.ou[kk], h0z, fmaf(pw.ov[kk], h1z, p0z));
+                    const float2 o = OFF_SM ? off_sm[kk * G + lg] : make_float2(pw.ou[kk], pw.ov[kk]);
+                    float X = fmaf(o.x, h0x, fmaf(o.y, h1x, p0x));
+                    float Y = fmaf(o.x, h0y, fmaf(o.y, h1y, p0y));
+                    float Z = fmaf(o.x, h0z, fmaf(o.y, h1z, p0z));
                     float iz = rcp_approx(Z);
                     float tx = fmaf(X, iz, kMagic2), ty = fmaf(Y, iz, kMagic2);
                     Us[h] = fmaf(X, iz, kMagic2 - tx);
