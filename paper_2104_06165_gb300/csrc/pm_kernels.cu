@@ -66,7 +66,8 @@ struct PhaseTile {
 // One warp per pixel, grid-stride over the pixels.
 // ---------------------------------------------------------------------------
 template <int G, int S, bool MIXED>
-__global__ void __launch_bounds__(kBlock) k_init(const __grid_constant__ RefConst rc, float* view_cost) {
+// (5 blocks of 4 warps per SM: 96 registers, no spills)
+__global__ void __launch_bounds__(kBlock, 5) k_init(const __grid_constant__ RefConst rc, float* view_cost) {
     extern __shared__ __align__(16) unsigned char smem[];
     ViewSm* views = reinterpret_cast<ViewSm*>(smem);
     load_views(rc, views);
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const __grid_constant__ RefCons
 
 // cost of a given plane map
 template <int G, int S, bool MIXED>
-__global__ void __launch_bounds__(kBlock) k_cost(const __grid_constant__ RefConst rc, const float4* __restrict__ plane,
+__global__ void __launch_bounds__(kBlock, 5) k_cost(const __grid_constant__ RefConst rc, const float4* __restrict__ plane,
                                                   float* __restrict__ cost, float* view_cost) {
     extern __shared__ __align__(16) unsigned char smem[];
     ViewSm* views = reinterpret_cast<ViewSm*>(smem);
