@@ -60,14 +60,17 @@ struct PhaseTile {
     static constexpr int MIN_BLOCKS = (S >= 16 ? 384 : 512) / BLOCK > 0 ? (S >= 16 ? 384 : 512) / BLOCK : 1;
 };
 
+// Blocks of the one-hypothesis kernels per SM: 5 (96 registers, no spills)
+// for windows of up to 9 slots per lane; 16 slots need more registers.
+template <int S>
+constexpr int one_hyp_blocks() { return S >= 16 ? 1 : 5; }
 
 // ---------------------------------------------------------------------------
 // Sec. III-B: random initialisation, then the cost of the initial plane.
 // One warp per pixel, grid-stride over the pixels.
 // ---------------------------------------------------------------------------
 template <int G, int S, bool MIXED>
-// (5 blocks of 4 warps per SM: 96 registers, no spills)
-__global__ void __launch_bounds__(kBlock, 5) k_init(const __grid_constant__ RefConst rc, float* view_cost) {
+__global__ void __launch_bounds__(kBlock, one_hyp_blocks<S>()) k_init(const __grid_constant__ RefConst rc, float* view_cost) {
     extern __shared__ __align__(16) unsigned char smem[];
     ViewSm* views = reinterpret_cast<ViewSm*>(smem);
     load_views(rc, views);
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_init(const __grid_constant__ RefC
 
 // cost of a given plane map
 template <int G, int S, bool MIXED>
-__global__ void __launch_bounds__(kBlock, 5) k_cost(const __grid_constant__ RefConst rc, const float4* __restrict__ plane,
+__global__ void __launch_bounds__(kBlock, one_hyp_blocks<S>()) k_cost(const __grid_constant__ RefConst rc, const float4* __restrict__ plane,
                                                   float* __restrict__ cost, float* view_cost) {
     extern __shared__ __align__(16) unsigned char smem[];
     ViewSm* views = reinterpret_cast<ViewSm*>(smem);
