@@ -114,10 +114,10 @@ struct __align__(16) WinGeo {
     float cu_lo, cu_hi, cv_lo, cv_hi;  // corners of the included sample rectangle
     float rx0, rx1, rx2;  // K^-1 (x, y, 1)
     float rlen;           // |K^-1 (x, y, 1)|
-    // reference moments, read together once per round: x = 1 / sum w,
-    // y = sum w (I_ref - mean)^2, z = sum w (I_ref - mean) (zero up to
-    // rounding), w = sum w
-    float4 mom;
+    float inv_wsum;       // 1 / sum w
+    float srr;            // sum w (I_ref - mean)^2
+    float wr_sum;         // sum w (I_ref - mean) (zero up to rounding)
+    float wsum;
 };
 
 // Reference side of the window of one pixel.  Every group of G lanes of the
@@ -190,8 +190,11 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
         srr = fmaf(t, d, srr);
     }
     srr = gsum<G>(srr);
-    pw.geo.mom = make_float4(inv_sw, srr, gsum<G>(wrs), sw);
+    pw.geo.wr_sum = gsum<G>(wrs);
+    pw.geo.wsum = sw;
     pw.mean = mu;
+    pw.geo.inv_wsum = inv_sw;
+    pw.geo.srr = srr;
     pw.ok = exists && sw > 0.0f && srr >= kTauVar * sw && ku_hi >= 0 && kv_hi >= 0;
     WinGeo& g = pw.geo;
     g.cu_lo = rc.step * ((float)ku_lo - half);
@@ -324,14 +327,13 @@ __device__ __forceinline__ bool same_plane(const float4& a, const float4& b) {
 //   3. lane c folds the per-view results of hypothesis c in view order
 //      (Eq. 5, weights 1/max(C, 1e-6)).
 // Must be called by all 32 lanes with the same nc (warp-uniform).
-// OFF_SM: the window's sample offsets are read from shared memory, those of
-// slots 2i and 2i + 1 of lane-in-group lg as one 16-byte word
-// off_sm[i * G + lg] = (ou_2i, ov_2i, ou_2i+1, ov_2i+1) (pw.ou / pw.ov are not
+// OFF_SM: the window's sample offsets are read from shared memory, (ou, ov)
+// of slot k and lane-in-group lg at off_sm[k * G + lg] (pw.ou / pw.ov are not
 // read, so they need not stay in registers).
 template <int G, int S, bool VIEWS, bool MIXED = false, bool OFF_SM = false>
 __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __restrict__ sv, const PixWin<S>& pw,
                                             const WinGeo& geo, int px, int py, const Cand& my, int nc, PairSm* pairs,
-                                            float* view_cost, unsigned& n_evals, const float4* off_sm = nullptr) {
+                                            float* view_cost, unsigned& n_evals, const float2* off_sm = nullptr) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
     const int V = rc.n_src;
@@ -435,7 +437,6 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             // the fp16 coefficient a (one mixed add)
             constexpr int CH = S <= 9 ? S : 8;
             float nc0 = 0.0f, dv[S];
-            float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int k0 = 0; k0 < S; k0 += CH) {
                 uint2 tq[CH];
@@ -444,9 +445,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                 for (int kk = 0; kk < CH; ++kk) {
                     const int k = k0 + kk;
                     if (k < S) {
-                        if (OFF_SM && (k & 1) == 0) o4 = off_sm[(k >> 1) * G + lg];
-                        const float2 o = OFF_SM ? ((k & 1) ? make_float2(o4.z, o4.w) : make_float2(o4.x, o4.y))
-                                                : make_float2(pw.ou[k], pw.ov[k]);
+                        const float2 o = OFF_SM ? off_sm[k * G + lg] : make_float2(pw.ou[k], pw.ov[k]);
                         float X = fmaf(o.x, h0x, fmaf(o.y, h1x, p0x));
                         float Y = fmaf(o.x, h0y, fmaf(o.y, h1y, p0y));
                         float Z = fmaf(o.x, h0z, fmaf(o.y, h1z, p0z));
@@ -478,7 +477,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             // two-pass weighted variance (the form of Eq. 4): the weighted
             // mean first, then the centred second moment
             sa = gsum<G>(sa);
-            const float mu = sa * geo.mom.x;
+            const float mu = sa * geo.inv_wsum;
 #pragma unroll
             for (int k = 0; k < S; ++k) {
                 const float e = dv[k] - mu;
@@ -495,12 +494,10 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             for (int k = 0; k < S; k += 2) {
                 float Us[2], Vs[2];
                 uint2 q[2];
-                const float4 o4 = OFF_SM ? off_sm[(k >> 1) * G + lg] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int kk = k + h < S ? k + h : k;
-                    const float2 o = OFF_SM ? (h ? make_float2(o4.z, o4.w) : make_float2(o4.x, o4.y))
-                                            : make_float2(pw.ou[kk], pw.ov[kk]);
+                    const float2 o = OFF_SM ? off_sm[kk * G + lg] : make_float2(pw.ou[kk], pw.ov[kk]);
                     float X = fmaf(o.x, h0x, fmaf(o.y, h1x, p0x));
                     float Y = fmaf(o.x, h0y, fmaf(o.y, h1y, p0y));
                     float Z = fmaf(o.x, h0z, fmaf(o.y, h1z, p0z));
@@ -541,18 +538,17 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             sb += __shfl_xor_sync(0xffffffffu, sb, o);
             se += __shfl_xor_sync(0xffffffffu, se, o);
         }
-        const float4 mom = geo.mom;   // (1 / sum w, sum w r'^2, sum w r', sum w)
-        const float mean_d = sa * mom.x;
+        const float mean_d = sa * geo.inv_wsum;
         // sum w (s - mu)^2 (FP32: already centred; mixed: one-pass, shifted)
         float sdd = MIXED ? fmaf(-mean_d, sa, sb) : sb;
         // sum w r' (s - mu) = sum w r' d - mu_d sum w r'
-        const float srd = fmaf(-mean_d, mom.z, se);
+        const float srd = fmaf(-mean_d, geo.wr_sum, se);
         if constexpr (MIXED) {
             // a source patch near the flat limit (where the exclusion decision
             // is taken): recompute the variance denominator in FP64
-            const bool near_flat = sdd < 2.0f * kTauVar * mom.w && sdd > 0.5f * kTauVar * mom.w;
+            const bool near_flat = sdd < 2.0f * kTauVar * geo.wsum && sdd > 0.5f * kTauVar * geo.wsum;
             if (__any_sync(0xffffffffu, near_flat)) {
-                const double mu_d = (double)c0 + (double)sa / (double)mom.w;
+                const double mu_d = (double)c0 + (double)sa / (double)geo.wsum;
                 double v = 0.0;
 #pragma unroll
                 for (int k = 0; k < S; ++k) {
@@ -566,8 +562,8 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         }
         // ZNCC, C(x, j) = 1 - Z, and its Eq. 5 weight (all lanes compute,
         // the group's first lane stores)
-        const bool flat = !(sdd >= kTauVar * mom.w);
-        const float z = fminf(1.0f, fmaxf(-1.0f, srd * rsqrtf(mom.y * sdd)));
+        const bool flat = !(sdd >= kTauVar * geo.wsum);
+        const float z = fminf(1.0f, fmaxf(-1.0f, srd * rsqrtf(geo.srr * sdd)));
         const float cj = flat ? kCmax : fminf(1.0f - z, kCmax);
         if (has && lg == 0) {
             if (VIEWS) pairs[it].res = cj;

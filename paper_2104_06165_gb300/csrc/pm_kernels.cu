@@ -214,9 +214,7 @@ struct __align__(16) PhaseWarp {
     float4 cur;
     float cur_c, pad_[3];
     float4 hyp[32];
-    // sample offsets of slots 2i and 2i + 1: off[i * G + lane_in_group] =
-    // (ou_2i, ov_2i, ou_2i+1, ov_2i+1), when G * S <= 128
-    float4 off[64];
+    float2 off[128];   // sample offsets (ou, ov), slot-major: off[slot * G + lane_in_group], when G * S <= 128
 };
 __host__ __device__ constexpr size_t phase_smem_bytes(int n_src, int warps) {
     return smem_block_bytes(n_src, warps) + (size_t)warps * (32 * (sizeof(float4) + sizeof(float)) + sizeof(PhaseWarp));
@@ -318,9 +316,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
         constexpr bool kOffSm = G * S <= 128;
         if (kOffSm && lane < G) {
 #pragma unroll
-            for (int k = 0; k < S; k += 2)
-                ws->off[(k >> 1) * G + lane] = make_float4(pw.ou[k], pw.ov[k], k + 1 < S ? pw.ou[k + 1] : 0.0f,
-                                                           k + 1 < S ? pw.ov[k + 1] : 0.0f);
+            for (int k = 0; k < S; ++k) ws->off[k * G + lane] = make_float2(pw.ou[k], pw.ov[k]);
         }
         __syncwarp();
         const WinGeo& geo = ws->geo;
