@@ -40,17 +40,19 @@ __global__ void k_build_texture(const uint8_t* __restrict__ img, int W, int H, u
 constexpr int kWarps = kBlock / 32;
 // Checkerboard-phase blocks cover a tile of kTileX x kTileY pixels of the
 // active colour, one warp per pixel, so that the warps sharing an SM's L1
-// gather overlapping windows.  4 x 5 warps (96 registers a thread) hide more
-// gather latency than 4 x 4 at 128 registers: 4 % less time per phase at
-// 3072 x 2048 with 11 x 11 samples; 4 x 3, 3 x 7 and 4 x 6 were slower.
+// gather overlapping windows.  20 warps at 96 registers a thread hide more
+// gather latency than 16 at 128 (4 % less time per phase at 3072 x 2048
+// with 11 x 11 samples; 12, 21 and 24 warps were slower), and a tall tile
+// of 2 x 10 warps (4 x 10 pixels) shares more of the L1 than 4 x 5 (4 %
+// less again; 10 x 2 and 5 x 4 were slower, 1 x 20 the same).
 #ifndef MVS_TILE_X
-#define MVS_TILE_X 4
+#define MVS_TILE_X 2
 #endif
 #ifndef MVS_TILE_Y
-#define MVS_TILE_Y 5
+#define MVS_TILE_Y 10
 #endif
 // Windows of 16 slots per lane need more than 128 registers: their blocks
-// keep to one row of kTileX pixels (3 blocks of 128 threads per SM).
+// keep to one row of kTileX pixels (12 warps per SM).
 template <int S>
 struct PhaseTile {
     static constexpr int TX = MVS_TILE_X;
