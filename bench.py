@@ -876,6 +876,9 @@ def main():
                          "pipeline = the whole Algorithm 1 on the 24-view scene")
     args = ap.parse_args()
     WORKLOAD.update(WORKLOADS[args.workload])
+    studies = ("batch24", "learned", "table3", "sparse", "table1", "pipeline")
+    if args.impl != "reference" and args.workload in studies and _env_rank()[0] != 0:
+        return   # the single-GPU studies run on rank 0 only; the other ranks exit without work
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch24":
