@@ -141,3 +141,19 @@ def test_table1_patchmatch_vs_phi_m_vs_phi(mvs_lib):
         assert res[k].mean() > res["P"].mean() + 0.02
     # the paper's finding: choosing by the MRF beats choosing by cost alone
     assert res["full"][flat].mean() > res["M"][flat].mean()
+
+
+def test_unknown_selection_is_rejected(mvs_lib):
+    from paper_2104_06165_gb300 import scenes
+    sc = scenes.make_plane_scene(W=32, H=24, n_src=2, seed=1)
+    p = mvs_lib.PMParams(win_radius=5.0, win_samples=6, iters=1, seed=3)
+    ctx = _ctx(mvs_lib, sc)
+    try:
+        pl = np.zeros((24, 32, 4), np.float32)
+        co = np.zeros((24, 32), np.float32)
+        mvs_lib.mvs_patchmatch(ctx.h, 0, [1, 2], p, pl, co)
+        with pytest.raises(mvs_lib.MvsError) as e:
+            mvs_lib.mvs_plane_infer(ctx.h, 0, [1, 2], p, mvs_lib.PhiParams(selection=2), None, pl, co)
+        assert e.value.status == mvs_lib.MVS_EINVAL
+    finally:
+        ctx.close()
