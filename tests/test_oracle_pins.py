@@ -595,3 +595,27 @@ def test_plane_infer_min_cost_fills_a_fronto_parallel_hole(oracle_lib):
     # the same intermediates, selected by minimal cost
     sel, _ = oracle_lib.phi_select_min_cost(osc, 0, known, aux["hyp"], aux["valid"], aux["hcost"], plane)
     assert np.array_equal(sel, out)
+
+
+def test_min_cost_and_mrf_selections_agree_with_one_hypothesis_per_hole(oracle_lib):
+    """With exactly one valid hypothesis in every hole (so no MRF node lacks
+    a label) both selections must take it: the MRF pipeline and PHI-MVS/M
+    give the same map, whatever the costs."""
+    from phi_cases import slanted_hole_case
+    rng = np.random.default_rng(9)
+    sc, n_true, known, hyp, valid, hcost, plane, best = slanted_hole_case(rng)
+    osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
+    H, W = known.shape
+    pick = rng.integers(0, 4, (H, W))           # a random, generally perturbed, hypothesis
+    one = np.zeros_like(valid)
+    yy, xx = np.mgrid[0:H, 0:W]
+    one[yy, xx, pick] = 1
+    depth = plane[..., 3]
+    label, _ = oracle_lib.phi_mrf(known, depth, hyp, one, hcost)
+    assert (label[known[::2, ::2] == 0] >= 0).all()
+    a, fa = oracle_lib.phi_select(osc, 0, known, hyp, one, label, plane)
+    b, fb = oracle_lib.phi_select_min_cost(osc, 0, known, hyp, one, hcost, plane)
+    assert np.array_equal(fa, fb) and fa[known == 0].mean() > 0.5
+    assert np.array_equal(a, b)
+    chosen = hyp[yy, xx, pick]
+    assert np.array_equal(b[..., 3][fb == 1], chosen[fb == 1])
