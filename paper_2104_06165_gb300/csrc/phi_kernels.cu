@@ -249,8 +249,14 @@ __global__ void __launch_bounds__(kBlock, 3) k_phi_cost(const __grid_constant__ 
 // by a grid barrier (ns + nb - 1 of them instead of gw + gh - 1), and the
 // anti-diagonals of a tile by a block barrier.  Inside a tile one warp takes
 // one node: lane (d, lq, l) evaluates the min-sum term of own label l towards
-// label lq of the d-th outgoing neighbour.  Messages are written by other
-// multiprocessors, so they are read and written at L2 (ld/st .cg).  The
+// label lq of the d-th outgoing neighbour.  At the start of a stage the block
+// stages its tile in shared memory (unaries, label depths, the messages that
+// do not change during the pass, the messages entering the tile from the
+// tiles finished at the previous stage, written by other multiprocessors and
+// read at L2); inside the stage a message to the lower node passes through
+// shared memory and one to the right node stays in the warp's registers, so
+// the anti-diagonal steps wait on no global memory.  Every message is also
+// written to global memory (.cg) for the other pass and the decoding.  The
 // backward pass runs the same schedule on the mirrored grid.
 // ---------------------------------------------------------------------------
 constexpr int kTrwRows = 32, kTrwCols = 32, kTrwBlock = 32 * kTrwRows;
@@ -290,63 +296,174 @@ __global__ void k_mrf_setup(int W, int H, MrfBufs mb, const uint8_t* __restrict_
     for (int k = 0; k < 16; ++k) mb.msg[16 * g + k] = 0.0f;
 }
 
+// ((((a + b) + c) + d) + e): the belief sum in message-slot order
+__device__ __forceinline__ float un_add4(float a, float b, float c, float d, float e) {
+    return (((a + b) + c) + d) + e;
+}
+
 // -log of Eq. 7: phi_e = [k3 - min(1, relative difference)]^2
 __device__ __forceinline__ float pair_energy(float h1, float h2, float k3) {
     float rel = h1 > h2 ? (h1 - h2) / h2 : (h2 - h1) / h1;
     return -2.0f * logf(k3 - fminf(1.0f, rel));
 }
 
-// Messages of node (x, y) to its later (forward) or earlier (backward)
-// neighbours; called by a whole warp.
-__device__ __forceinline__ void trw_node_warp(const MrfBufs& mb, int x, int y, bool forward, float k3) {
-    const int lane = threadIdx.x & 31;
-    const long long i = (long long)y * mb.gw + x;
-    const int L = mb.nlab[i];
-    if (!L) return;                                       // warp-uniform
-    const int nbx[4] = {0, 0, -1, 1}, nby[4] = {-1, 1, 0, 0};
-    int before = 0, after = 0, Lq = 0;
-    const int dsel = lane >> 4, lq = (lane >> 2) & 3, l = lane & 3;
-    const int dir = forward ? (dsel ? 3 : 1) : (dsel ? 2 : 0);
-    long long q = 0;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        const int qx = x + nbx[d], qy = y + nby[d];
-        const bool in = qx >= 0 && qx < mb.gw && qy >= 0 && qy < mb.gh;
-        const long long qi = (long long)qy * mb.gw + qx;
-        const int nq = in ? mb.nlab[qi] : 0;
-        if (nq > 0) { if (d == 0 || d == 2) before++; else after++; }
-        if (d == dir) { Lq = nq; q = qi; }
-    }
-    const int mx = max(before, after);
-    const float gamma = mx > 0 ? 1.0f / (float)mx : 1.0f;
-    // belief of own label l: unary + the four incoming messages
-    float bel = mb.un[4 * i + l];
-#pragma unroll
-    for (int d = 0; d < 4; ++d) bel += __ldcg(mb.msg + 16 * i + 4 * d + l);
-    float e = 3.0e38f;
-    if (l < L && lq < Lq)
-        e = gamma * bel - __ldcg(mb.msg + 16 * i + 4 * dir + l) + pair_energy(mb.lab[4 * i + l], mb.lab[4 * q + lq], k3);
-    // minimum over own labels, then over the target's labels (normalisation)
-    e = fminf(e, __shfl_xor_sync(0xffffffffu, e, 1));
-    e = fminf(e, __shfl_xor_sync(0xffffffffu, e, 2));
-    float mn = fminf(e, __shfl_xor_sync(0xffffffffu, e, 4));
-    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 8));
-    if (l == 0 && lq < Lq) __stcg(mb.msg + 16 * q + 4 * (dir ^ 1) + lq, e - mn);
-}
+// Per-stage tile record in dynamic shared memory: the static data of the
+// tile's 32 x 32 nodes (pass-local row-major), of the targets just below and
+// right of it, the messages entering its first row and column from the
+// tiles finished at the previous stage, and the wavefront's downward
+// messages (double-buffered by step parity).
+struct TrwTileSm {
+    float4 un[kTrwRows * kTrwCols];    // unaries of the four labels
+    float4 lab[kTrwRows * kTrwCols];   // label depths
+    float4 msv[kTrwRows * kTrwCols];   // static message from the pass-local lower neighbour
+    float4 msh[kTrwRows * kTrwCols];   // static message from the pass-local right neighbour
+    float gamma[kTrwRows * kTrwCols];
+    int nl[kTrwRows * kTrwCols];       // labels (0: absent or outside the grid)
+    float4 lab_d[kTrwCols], lab_r[kTrwRows];   // targets below the last row / right of the last column
+    int nl_d[kTrwCols], nl_r[kTrwRows];
+    float4 up_b[kTrwCols], left_b[kTrwRows];   // messages into the first row / first column
+    float4 up_w[2][kTrwRows + 1];              // downward messages of the current wavefront
+};
 
 __global__ void __launch_bounds__(kTrwBlock, 1) k_trw_strips(MrfBufs mb, bool forward, float k3) {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
-    const int warp = threadIdx.x >> 5;
+    extern __shared__ __align__(16) unsigned char trw_smem[];
+    TrwTileSm& T = *reinterpret_cast<TrwTileSm*>(trw_smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ns = (mb.gh + kTrwRows - 1) / kTrwRows, nb = (mb.gw + kTrwCols - 1) / kTrwCols;
+    // message slots (dir 0 up, 1 down, 2 left, 3 right) in pass-local terms:
+    // the static ones come from the lower / right neighbours, the dynamic
+    // ones from the upper / left neighbours updated earlier in this pass
+    const int sv = forward ? 1 : 0, sh = forward ? 3 : 2, dv = forward ? 0 : 1, dh = forward ? 2 : 3;
+    // original node index of pass-local (xf, yf), or -1 outside the grid
+    auto node = [&](int xf, int yf) -> long long {
+        if (xf < 0 || yf < 0 || xf >= mb.gw || yf >= mb.gh) return -1;
+        const int x = forward ? xf : mb.gw - 1 - xf, y = forward ? yf : mb.gh - 1 - yf;
+        return (long long)y * mb.gw + x;
+    };
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k = 0; k < ns + nb - 1; ++k) {
         for (int st = blockIdx.x; st < ns; st += gridDim.x) {
             const int c = k - st;
             if (c < 0 || c >= nb) continue;              // block-uniform
+            const int x0 = c * kTrwCols, y0 = st * kTrwRows;
+            // ---- load the tile (one node per thread) and its borders
+            {
+                const int r = tid / kTrwCols, cc = tid % kTrwCols;
+                const long long i = node(x0 + cc, y0 + r);
+                int L = 0;
+                float gm = 1.0f;
+                float4 un = z4, lb = z4, mv = z4, mh = z4;
+                if (i >= 0) {
+                    L = mb.nlab[i];
+                    const int x = (int)(i % mb.gw), y = (int)(i / mb.gw);
+                    const int nbx[4] = {0, 0, -1, 1}, nby[4] = {-1, 1, 0, 0};
+                    int before = 0, after = 0;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        const int qx = x + nbx[d], qy = y + nby[d];
+                        const bool in = qx >= 0 && qx < mb.gw && qy >= 0 && qy < mb.gh;
+                        const int nq = in ? mb.nlab[(long long)qy * mb.gw + qx] : 0;
+                        if (nq > 0) { if (d == 0 || d == 2) before++; else after++; }
+                    }
+                    const int mx = max(before, after);
+                    gm = mx > 0 ? 1.0f / (float)mx : 1.0f;
+                    un = reinterpret_cast<const float4*>(mb.un)[i];
+                    lb = reinterpret_cast<const float4*>(mb.lab)[i];
+                    mv = __ldcg(reinterpret_cast<const float4*>(mb.msg + 16 * i + 4 * sv));
+                    mh = __ldcg(reinterpret_cast<const float4*>(mb.msg + 16 * i + 4 * sh));
+                }
+                T.nl[tid] = L;
+                T.gamma[tid] = gm;
+                T.un[tid] = un;
+                T.lab[tid] = lb;
+                T.msv[tid] = mv;
+                T.msh[tid] = mh;
+                if (tid < kTrwCols) {                     // targets below the tile
+                    const long long q = node(x0 + tid, y0 + kTrwRows);
+                    T.nl_d[tid] = q >= 0 ? mb.nlab[q] : 0;
+                    T.lab_d[tid] = q >= 0 ? reinterpret_cast<const float4*>(mb.lab)[q] : z4;
+                } else if (tid < kTrwCols + kTrwRows) {   // targets right of the tile
+                    const int rr = tid - kTrwCols;
+                    const long long q = node(x0 + kTrwCols, y0 + rr);
+                    T.nl_r[rr] = q >= 0 ? mb.nlab[q] : 0;
+                    T.lab_r[rr] = q >= 0 ? reinterpret_cast<const float4*>(mb.lab)[q] : z4;
+                } else if (tid < 2 * kTrwCols + kTrwRows) {   // into the first row (previous stage)
+                    const int c2 = tid - kTrwCols - kTrwRows;
+                    const long long q = node(x0 + c2, y0);
+                    T.up_b[c2] = q >= 0 ? __ldcg(reinterpret_cast<const float4*>(mb.msg + 16 * q + 4 * dv)) : z4;
+                } else if (tid < 2 * kTrwCols + 2 * kTrwRows) {   // into the first column
+                    const int r2 = tid - 2 * kTrwCols - kTrwRows;
+                    const long long q = node(x0, y0 + r2);
+                    T.left_b[r2] = q >= 0 ? __ldcg(reinterpret_cast<const float4*>(mb.msg + 16 * q + 4 * dh)) : z4;
+                }
+            }
+            __syncthreads();
+            // ---- the tile's anti-diagonals: warp = row, lane (dsel, lq, l)
+            // evaluates the min-sum term of own label l towards label lq of
+            // the lower (dsel 0) or right (dsel 1) neighbour
+            const int dsel = lane >> 4, lq = (lane >> 2) & 3, l = lane & 3;
+            const int dir = forward ? (dsel ? 3 : 1) : (dsel ? 2 : 0);
+            float left_in = 0.0f;                         // message from the left node, kept by this warp
             for (int t = 0; t < kTrwRows + kTrwCols - 1; ++t) {
                 const int u = t - warp;                   // tile column of this warp's node
-                const int xf = c * kTrwCols + u, yf = st * kTrwRows + warp;   // pass-local coordinates
-                if (u >= 0 && u < kTrwCols && xf < mb.gw && yf < mb.gh)
-                    trw_node_warp(mb, forward ? xf : mb.gw - 1 - xf, forward ? yf : mb.gh - 1 - yf, forward, k3);
+                float out_v = 0.0f, out_h = 0.0f;         // messages sent down / right (0: none)
+                if (u >= 0 && u < kTrwCols) {
+                    const int n = warp * kTrwCols + u;
+                    const int L = T.nl[n];
+                    if (L > 0) {                          // warp-uniform
+                        const float4 un4 = T.un[n], mv4 = T.msv[n], mh4 = T.msh[n], lb4 = T.lab[n];
+                        const float unl = l == 0 ? un4.x : l == 1 ? un4.y : l == 2 ? un4.z : un4.w;
+                        const float mvl = l == 0 ? mv4.x : l == 1 ? mv4.y : l == 2 ? mv4.z : mv4.w;
+                        const float mhl = l == 0 ? mh4.x : l == 1 ? mh4.y : l == 2 ? mh4.z : mh4.w;
+                        const float labl = l == 0 ? lb4.x : l == 1 ? lb4.y : l == 2 ? lb4.z : lb4.w;
+                        const float4 upv = warp == 0 ? T.up_b[u] : T.up_w[(t - 1) & 1][warp];
+                        const float dynv = l == 0 ? upv.x : l == 1 ? upv.y : l == 2 ? upv.z : upv.w;
+                        float dynh = left_in;
+                        if (u == 0) {
+                            const float4 lf = T.left_b[warp];
+                            dynh = l == 0 ? lf.x : l == 1 ? lf.y : l == 2 ? lf.z : lf.w;
+                        }
+                        // belief of own label l: unary + the four incoming messages in slot order
+                        const float bel = forward ? un_add4(unl, dynv, mvl, dynh, mhl) : un_add4(unl, mvl, dynv, mhl, dynh);
+                        int Lq;
+                        float4 lq4;
+                        if (dsel == 0) {
+                            Lq = warp + 1 < kTrwRows ? T.nl[n + kTrwCols] : T.nl_d[u];
+                            lq4 = warp + 1 < kTrwRows ? T.lab[n + kTrwCols] : T.lab_d[u];
+                        } else {
+                            Lq = u + 1 < kTrwCols ? T.nl[n + 1] : T.nl_r[warp];
+                            lq4 = u + 1 < kTrwCols ? T.lab[n + 1] : T.lab_r[warp];
+                        }
+                        const float labq = lq == 0 ? lq4.x : lq == 1 ? lq4.y : lq == 2 ? lq4.z : lq4.w;
+                        const float mdir = dsel ? mhl : mvl;
+                        float e = 3.0e38f;
+                        if (l < L && lq < Lq) e = T.gamma[n] * bel - mdir + pair_energy(labl, labq, k3);
+                        // minimum over own labels, then over the target's labels (normalisation)
+                        e = fminf(e, __shfl_xor_sync(0xffffffffu, e, 1));
+                        e = fminf(e, __shfl_xor_sync(0xffffffffu, e, 2));
+                        float mn = fminf(e, __shfl_xor_sync(0xffffffffu, e, 4));
+                        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 8));
+                        const float o = lq < Lq ? e - mn : 0.0f;
+                        if (l == 0 && lq < Lq) {
+                            const long long q = dsel == 0 ? node(x0 + u, y0 + warp + 1) : node(x0 + u + 1, y0 + warp);
+                            __stcg(mb.msg + 16 * q + 4 * (dir ^ 1) + lq, o);
+                        }
+                        // lane j < 4: the message to label j of the node below
+                        // (sent by lane 4 j); every lane: the message to label l
+                        // of the right node (sent by lane 16 + 4 l)
+                        out_v = __shfl_sync(0xffffffffu, o, 4 * l);
+                        out_h = __shfl_sync(0xffffffffu, o, 16 + 4 * l);
+                    }
+                }
+                // the node below reads the downward message at the next step
+                // (lanes 0..3 write its four labels), the right node is this
+                // warp's next node
+                if (lane < 4) {
+                    float* w = reinterpret_cast<float*>(&T.up_w[t & 1][warp + 1]);
+                    w[lane] = out_v;
+                }
+                left_in = out_h;
                 __syncthreads();
             }
         }
@@ -580,7 +697,8 @@ cudaError_t launch_phi_mrf(int W, int H, const uint8_t* known, const float* dept
             int dev = 0, sms = 0, per_sm = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trw_strips, kTrwBlock, 0);
+            cudaFuncSetAttribute(k_trw_strips, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrwTileSm));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trw_strips, kTrwBlock, sizeof(TrwTileSm));
             max_blocks = std::max(1, sms * per_sm);
         }
     }
@@ -590,7 +708,7 @@ cudaError_t launch_phi_mrf(int W, int H, const uint8_t* known, const float* dept
         for (int pass = 0; pass < 2; ++pass) {
             bool forward = pass == 0;
             void* args[] = {(void*)&mb, (void*)&forward, (void*)&k3};
-            e = cudaLaunchCooperativeKernel((const void*)k_trw_strips, grid, block, args, 0, s);
+            e = cudaLaunchCooperativeKernel((const void*)k_trw_strips, grid, block, args, sizeof(TrwTileSm), s);
             count_launch();
             if (e != cudaSuccess) return e;
         }
