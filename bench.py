@@ -272,7 +272,8 @@ def run_ours(args):
         "config": {"precision": args.precision, "workload": f"{args.workload} {W}x{H} uint8 ref + {len(srcs)} sources, 21x21 window dil 2 "
                                "(11x11 samples), 8 iterations, PHI + 4-label MRF", "parallelism": f"replicas{world}",
                    "lanes_per_pixel": args.lanes,
-                   "l2": "inputs larger than L2 (11 x 100 MB textures)", "render_s": round(t_render, 1)},
+                   "l2": f"inputs larger than L2 ({len(sc.images)} textures of {(W + 1) * (H + 1) * 8 / 1e6:.0f} MB)",
+                   "render_s": round(t_render, 1)},
         "e2e": {"value": world * mpix / e2e_s, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
@@ -630,7 +631,7 @@ def run_learned(args):
         "data": "synthetic",
         "config": {"workload": f"learned {W}x{H} uint8 ref + {len(srcs)} sources, ~50% texture-less, 21x21 window "
                                "dil 2, 1 plain iteration + proposal network + 3 iterations with 4 proposals/pixel",
-                   "render_s": round(t_render, 1), "l2": "inputs larger than L2 (11 x 25 MB textures)"},
+                   "render_s": round(t_render, 1), "l2": "inputs larger than L2 (11 textures of 13 MB)"},
         "completeness": comp_l,
         "plain8": {"value": mpix / (ms_p / 1e3), "ms_per_step": ms_p, "completeness": comp_p},
         "gpu_launches": int(launches),
