@@ -256,14 +256,16 @@ mvs_status mvs_fuse(mvs_ctx* ctx, int32_t n_views, const int32_t* views, const u
  * principal axes in radians; tie: lower index).  FP64 throughout.
  *   points: n_points x 3 doubles (world); vis: n_points masks, bit v set when
  *   the point is visible in view v; eps, t_tau: the disturbance and the
- *   threshold (the paper gives neither; 0.05 and 1 px are this library's
- *   defaults); k: neighbours per view (the paper keeps 8).
+ *   threshold in pixels (Sec. IV uses eps = 0.002 and t_tau = 0.1:
+ *   MVS_NBR_EPS, MVS_NBR_T_TAU); k: neighbours per view (the paper keeps 8).
  *   neighbors: n_views x k int32, the selected sources per view in order,
  *   -1 past the kept ones; tau / zeta (n_views x n_views doubles, zeta +inf
  *   for removed sources) and n_shared (n_views x n_views int32) may be NULL.
  *   All buffers in `mem`.  The call synchronises.
  * Errors: MVS_EINVAL (view count, k outside 1..n_views-1, eps <= 0, t_tau < 0,
  *   NULL buffers), MVS_ENOMEM, MVS_ECUDA. */
+#define MVS_NBR_EPS 0.002   /* Eq. 1's disturbance, Sec. IV */
+#define MVS_NBR_T_TAU 0.1   /* Eq. 2's threshold in pixels, Sec. IV */
 mvs_status mvs_select_neighbors(mvs_ctx* ctx, int64_t n_points, const double* points, const uint64_t* vis,
                                 double eps, double t_tau, int32_t k, int32_t* neighbors, double* tau,
                                 int32_t* n_shared, double* zeta, int32_t mem);

@@ -469,9 +469,10 @@ def fuse(scene, order, planes, keep=None, rel_tol=0.01):
     return pts[:m], sv[:m], sp[:m]
 
 
-def select_neighbors(scene, X, vis, eps=0.05, t_tau=1.0, k=8):
+def select_neighbors(scene, X, vis, eps=0.002, t_tau=0.1, k=8):
     """Sec. III-A neighbouring-image selection (Eqs. 1-3) from sparse points
-    X (n, 3) and their visibility vis (n, n_views) bool.  Returns (neighbours
+    X (n, 3) and their visibility vis (n, n_views) bool; eps and t_tau
+    default to Sec. IV's 0.002 and 0.1 px, k to the paper's eight.  Returns (neighbours
     (n_views, k) int, -1 padded; tau, n_shared, zeta (n_views, n_views))."""
     X = _f64(np.asarray(X).reshape(-1, 3))
     vis = np.ascontiguousarray(vis, np.uint8)

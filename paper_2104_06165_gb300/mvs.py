@@ -332,11 +332,12 @@ def mvs_fuse(ctx, views, points, src=None, keep_masks=None, rel_tol=0.01):
     return n.value
 
 
-def mvs_select_neighbors(ctx, points, vis, neighbors, tau=None, n_shared=None, zeta=None, eps=0.05, t_tau=1.0):
+def mvs_select_neighbors(ctx, points, vis, neighbors, tau=None, n_shared=None, zeta=None, eps=0.002, t_tau=0.1):
     """Neighbouring-image selection of every context view from sparse points
     (n, 3) float64 and visibility masks vis (n,) uint64 (bit v: visible in
     view v) into neighbors (n_views, k) int32; optional (n_views, n_views)
-    outputs tau / zeta (float64) and n_shared (int32)."""
+    outputs tau / zeta (float64) and n_shared (int32).  eps and t_tau default
+    to the values of Sec. IV (0.002, 0.1 px)."""
     mem = _mem(points, vis, neighbors, tau, n_shared, zeta)
     k = neighbors.shape[1]
     _check(load().mvs_select_neighbors(ctx, points.shape[0], _ptr(points)[0], _ptr(vis)[0], float(eps), float(t_tau),

@@ -103,7 +103,7 @@ def test_null_context_is_rejected(mvs_lib):
     n = C.c_int64(0)
     assert lib.mvs_fuse(None, 1, views, None, C.c_float(0.01), None, None, 0, C.byref(n), 0) == mvs_lib.MVS_EINVAL
     nbr = np.zeros((2, 1), np.int32)
-    assert lib.mvs_select_neighbors(None, 0, None, None, 0.05, 1.0, 1, nbr.ctypes.data, None, None, None,
+    assert lib.mvs_select_neighbors(None, 0, None, None, 0.002, 0.1, 1, nbr.ctypes.data, None, None, None,
                                     0) == mvs_lib.MVS_EINVAL
     rng = np.zeros((2, 2, 2), np.float32)
     assert lib.mvs_sparse_depth_range(None, 0, 0, None, None, None, None, 2.0, C.c_float(2.0), C.c_float(8.0),

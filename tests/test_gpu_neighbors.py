@@ -1,5 +1,6 @@
 """Neighbouring-image selection (Sec. III-A) on the GPU against the FP64
-oracle, on synthetic structure-from-motion points of rendered scenes."""
+oracle, on synthetic structure-from-motion points of rendered scenes, with
+Sec. IV's eps = 0.002 and t_tau = 0.1 px (the defaults of both sides)."""
 import numpy as np
 import pytest
 
@@ -33,12 +34,12 @@ def _compare(mvs_lib, oracle_lib, sc, sp, k):
     finally:
         ctx.close()
     osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
-    onbr, otau, ona, ozeta = oracle_lib.select_neighbors(osc, sp["X"], sp["vis"], eps=0.05, t_tau=1.0, k=k)
+    onbr, otau, ona, ozeta = oracle_lib.select_neighbors(osc, sp["X"], sp["vis"], k=k)
     assert np.array_equal(na, ona)
     assert np.allclose(tau, otau, rtol=1e-12, atol=0)
     # no source sits within rounding of the threshold, so the removals are unique
     off = ~np.eye(n, dtype=bool)
-    assert (np.abs(otau[off] - 1.0) > 1e-9).all()
+    assert (np.abs(otau[off] - 0.1) > 1e-9).all()
     assert np.array_equal(np.isinf(zeta), np.isinf(ozeta))
     fin = np.isfinite(ozeta)
     assert np.allclose(zeta[fin], ozeta[fin], rtol=1e-12, atol=0)
@@ -51,8 +52,10 @@ def test_selection_equals_oracle_on_a_ring(mvs_lib, oracle_lib):
     sc = scenes.make_scene(W=160, H=120, n_src=6, seed=3, view_angles=[2.0, 8.0, 15.0, 25.0, 35.0, 50.0])
     sp = scenes.sparse_points(sc, 3000, seed=1)
     nbr, tau = _compare(mvs_lib, oracle_lib, sc, sp, k=4)
-    # the source at 2 degrees moves projections by less than t_tau: removed
-    assert tau[0, 1] < 1.0 and 1 not in nbr[0].tolist()
+    # at this image size (f = 150 px) the sources at 2, 8 and 15 degrees move
+    # projections by less than t_tau = 0.1 px: removed
+    assert (tau[0, 1:4] < 0.1).all() and not {1, 2, 3} & set(nbr[0].tolist())
+    assert nbr[0].tolist() == [5, 6, 4, -1]
 
 
 def test_selection_equals_oracle_on_many_views(mvs_lib, oracle_lib):
@@ -68,4 +71,4 @@ def test_short_lists_are_padded(mvs_lib, oracle_lib):
     sc = scenes.make_scene(W=160, H=120, n_src=6, seed=3, view_angles=[2.0, 8.0, 15.0, 25.0, 35.0, 50.0])
     sp = scenes.sparse_points(sc, 3000, seed=1)
     nbr, _ = _compare(mvs_lib, oracle_lib, sc, sp, k=6)
-    assert (nbr[0, 4:] == -1).all()      # two of the six sources fall below t_tau
+    assert (nbr[0, 3:] == -1).all()      # three of the six sources fall below t_tau

@@ -17,7 +17,7 @@ def test_tau_closed_form_for_parallel_cameras(oracle_lib):
     """Reference at the origin, sources shifted by b along x, all looking
     along +z, points on the plane z = Z: the disturbance of Eq. 1 moves every
     projection into source j by f b eps / ((1 + eps) Z) along x (Eq. 2)."""
-    f, eps = 400.0, 0.05
+    f, eps = 400.0, 0.002
     bs = [0.0, 0.2, 0.5, 1.0]
     n = len(bs)
     K = np.tile(np.array([[f, 0, 399.5], [0, f, 299.5], [0, 0, 1]]), (n, 1, 1))
@@ -63,10 +63,11 @@ def test_ranking_by_shared_points_and_tau_filter(oracle_lib):
     vis[:, 0] = True
     for j, m in enumerate(shared, start=1):
         vis[:m, j] = True
-    nbr, tau, na, zeta = oracle_lib.select_neighbors(sc, X, vis, eps=0.05, t_tau=1.0, k=8)
+    nbr, tau, na, zeta = oracle_lib.select_neighbors(sc, X, vis, k=8)
     expect = [1 + j for j in sorted(range(9), key=lambda j: -shared[j])][:8]
     assert nbr[0].tolist() == expect
-    assert tau[0, 10] < 1.0 and np.isinf(zeta[0, 10]) and na[0, 10] == 100
+    assert tau[0, 10] < 0.1 and np.isinf(zeta[0, 10]) and na[0, 10] == 100
+    assert (tau[0, 1:10] > 0.1).all()
     for j in range(1, 10):
         assert math.isclose(zeta[0, j], 0.1 * 0.05 / shared[j - 1], rel_tol=1e-12)
 
@@ -74,10 +75,12 @@ def test_ranking_by_shared_points_and_tau_filter(oracle_lib):
 def test_small_angle_is_not_truncated(oracle_lib):
     """A source at 2 degrees (theta = 0.0349 rad < 0.05, baseline 0.17 > 0.1)
     keeps its own angle in Eq. 3: zeta = 0.1 theta / N_A, which puts it ahead
-    of a source sharing more points."""
+    of a source sharing more points.  The focal length is that of a
+    3072-pixel-wide image, where Eq. 2 moves its projections by 0.2 px,
+    above Sec. IV's t_tau = 0.1."""
     alphas = [2.0, 20.0, 30.0]
     shared = [80, 100, 60]
-    K, R, t = _ring(alphas)
+    K, R, t = _ring(alphas, f=2880.0)
     n = len(alphas) + 1
     sc = oracle_lib.Scene(K, R, t, [np.zeros((1000, 1000), np.uint8)] * n)
     X = _grid_points()
@@ -85,7 +88,8 @@ def test_small_angle_is_not_truncated(oracle_lib):
     vis[:, 0] = True
     for j, m in enumerate(shared, start=1):
         vis[:m, j] = True
-    nbr, tau, na, zeta = oracle_lib.select_neighbors(sc, X, vis, eps=0.05, t_tau=1.0, k=8)
+    nbr, tau, na, zeta = oracle_lib.select_neighbors(sc, X, vis, k=8)
+    assert tau[0, 1] > 0.1
     th = math.radians(2.0)
     assert math.isclose(zeta[0, 1], 0.1 * th / 80, rel_tol=1e-9)
     # 0.1 * 0.0349 / 80 < 0.005 / 100 < 0.005 / 60; truncating theta to 0.05
@@ -93,3 +97,28 @@ def test_small_angle_is_not_truncated(oracle_lib):
     assert nbr[0, :3].tolist() == [1, 2, 3] and nbr[0, 3] == -1
     # the symmetric pair shares the same points
     assert na[1, 0] == na[0, 1] == 80
+
+
+def test_defaults_are_the_papers():
+    """The oracle's and the binding's defaults for Eq. 1's eps and Eq. 2's
+    t_tau are the values Sec. IV gives (tests/golden/paper_constants.json),
+    and so are the C header's named constants."""
+    import inspect
+    import json
+    import os
+    import re
+
+    import oracle
+    from paper_2104_06165_gb300 import mvs
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "tests", "golden", "paper_constants.json")) as fh:
+        pc = json.load(fh)
+    for fn in (oracle.select_neighbors, mvs.mvs_select_neighbors):
+        sig = inspect.signature(fn)
+        assert sig.parameters["eps"].default == pc["epsilon"]
+        assert sig.parameters["t_tau"].default == pc["t_tau"]
+    assert inspect.signature(oracle.select_neighbors).parameters["k"].default == 8
+    with open(os.path.join(root, "include", "mvs.h")) as fh:
+        hdr = fh.read()
+    assert float(re.search(r"#define MVS_NBR_EPS ([0-9.]+)", hdr).group(1)) == pc["epsilon"]
+    assert float(re.search(r"#define MVS_NBR_T_TAU ([0-9.]+)", hdr).group(1)) == pc["t_tau"]
