@@ -236,15 +236,19 @@ mvs_status mvs_geo_filter(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_
  *   points: capacity x 4 floats (x, y, z, merged pixel count) in world
  *   coordinates, written in processing order of the views, then raster order
  *   of the emitting pixel; src: capacity x 2 int32 (view, pixel index) or
- *   NULL; both in `mem` (device or host).  The call synchronises and sets
- *   *n_points to the number of points of the cloud.
+ *   NULL; owner: NULL, or one int64 per pixel of the views, view after view
+ *   in processing order, raster order within a view: the index of the point
+ *   the pixel went into (emitted or merged), -1 for a pixel that was never
+ *   present (no depth or not kept); all in `mem` (device or host).  The call
+ *   synchronises and sets *n_points to the number of points of the cloud.
  * Errors: MVS_EINVAL (bad or repeated view, rel_tol <= 0, bad buffers, or
  *   more points than capacity: then the first `capacity` points are written
  *   and *n_points holds the full count), MVS_ESTATE (a view without depth
  *   map), MVS_EUNSUPPORTED (a view whose K is not pinhole), MVS_ENOMEM,
  *   MVS_ECUDA. */
 mvs_status mvs_fuse(mvs_ctx* ctx, int32_t n_views, const int32_t* views, const uint8_t* const* keep_masks,
-                    float rel_tol, float* points, int32_t* src, int64_t capacity, int64_t* n_points, int32_t mem);
+                    float rel_tol, float* points, int32_t* src, int64_t* owner, int64_t capacity,
+                    int64_t* n_points, int32_t mem);
 
 /* Neighbouring-image selection (Sec. III-A, Eqs. 1-3) for every view of the
  * context (2..64 views), from sparse 3D points of a structure-from-motion

@@ -105,14 +105,14 @@ def lib():
             L.or_plane_infer.argtypes = [vp, C.c_int, ip, C.c_int, C.POINTER(_PM), C.POINTER(_Phi), up, dp,
                                          dp, up, dp, ip, dp, up]
             L.or_fuse.restype = C.c_long
-            L.or_fuse.argtypes = [vp, C.c_int, ip, C.POINTER(dp), C.POINTER(up), C.c_double,
-                                  C.POINTER(C.c_float), ip, C.POINTER(C.c_long), C.c_long]
+            lp = C.POINTER(C.c_long)
+            L.or_fuse.argtypes = [vp, C.c_int, ip, C.POINTER(dp), C.POINTER(up), C.c_double, C.c_double,
+                                  C.c_double, lp, dp, ip, lp, lp, C.c_long, lp]
             L.or_select_neighbors.argtypes = [vp, C.c_long, dp, up, C.c_double, C.c_double, C.c_int, ip, dp, ip, dp]
             L.or_sparse_features.restype = C.c_long
-            L.or_sparse_features.argtypes = [vp, C.c_int, C.c_long, dp, up, dp, dp, C.c_double,
-                                             C.POINTER(C.c_float), C.POINTER(C.c_float)]
-            L.or_sparse_range.argtypes = [C.c_int, C.c_int, C.c_long, C.POINTER(C.c_float), C.POINTER(C.c_float),
-                                          C.c_float, C.c_float, C.POINTER(C.c_float)]
+            L.or_sparse_features.argtypes = [vp, C.c_int, C.c_long, dp, up, dp, dp, C.c_double, dp, dp]
+            L.or_sparse_range.argtypes = [C.c_int, C.c_int, C.c_long, dp, dp, C.c_double, C.c_double, C.c_double,
+                                          dp, up]
             _lib = L
     return _lib
 
@@ -448,12 +448,16 @@ def plane_infer(scene, ref, srcs, p, known, plane, k1=4.0, k2=0.5, k3=2.0, n_fit
                 "filled": filled}
 
 
-def fuse(scene, order, planes, keep=None, rel_tol=0.01):
-    """Sec. III-F depth-map fusion of the views in ``order`` (decisions in
-    single precision, see or_fuse).  ``planes`` maps view index to its
-    (H, W, 4) plane map, ``keep`` optionally to a uint8 mask.  Returns
-    (points (n, 4) float32 = x, y, z, merged count; source view (n,);
-    source pixel (n,))."""
+def fuse(scene, order, planes, keep=None, rel_tol=0.01, hint=None, band_px=0.0, band_rel=0.0, stats=False):
+    """Sec. III-F depth-map fusion of the views in ``order`` in FP64 (see
+    or_fuse).  ``planes`` maps view index to its (H, W, 4) plane map,
+    ``keep`` optionally to a uint8 mask.  ``hint``: another implementation's
+    per-pixel point index (views in ``order`` back to back), followed only at
+    decisions within ``band_px`` of a rounding boundary or ``band_rel`` (of
+    the threshold) of the 1 % test.  Returns (points (n, 4) float64 = x, y,
+    z, merged count; source view (n,); source pixel (n,)), plus the per-pixel
+    owner array and the counts (projections, fragile, resolved by the hint)
+    when ``stats``."""
     order = [int(v) for v in order]
     n = len(order)
     arrs = [_f64(planes[v]) for v in order]
@@ -461,11 +465,23 @@ def fuse(scene, order, planes, keep=None, rel_tol=0.01):
     dps = (C.POINTER(C.c_double) * n)(*[_d(a) for a in arrs])
     ups = (C.POINTER(C.c_ubyte) * n)(*[(_u8(k) if k is not None else C.POINTER(C.c_ubyte)()) for k in kps])
     cap = int(sum(scene.shape(v)[0] * scene.shape(v)[1] for v in order))
-    pts = np.zeros((max(cap, 1), 4), np.float32)
+    lp = lambda a: a.ctypes.data_as(C.POINTER(C.c_long))
+    pts = np.zeros((max(cap, 1), 4), np.float64)
     sv = np.zeros(max(cap, 1), np.int32)
     sp = np.zeros(max(cap, 1), np.int64)
-    m = lib().or_fuse(scene.h, n, _i(np.asarray(order, np.int32)), dps, ups, float(rel_tol),
-                      pts.ctypes.data_as(C.POINTER(C.c_float)), _i(sv), sp.ctypes.data_as(C.POINTER(C.c_long)), cap)
+    own = np.zeros(max(cap, 1), np.int64)
+    st = np.zeros(3, np.int64)
+    h = None
+    if hint is not None:
+        h = np.ascontiguousarray(hint, np.int64).ravel()
+        if h.size != cap:
+            raise ValueError("hint needs one entry per pixel of the views")
+    m = lib().or_fuse(scene.h, n, _i(np.asarray(order, np.int32)), dps, ups, float(rel_tol), float(band_px),
+                      float(band_rel), lp(h) if h is not None else C.POINTER(C.c_long)(), _d(pts), _i(sv), lp(sp),
+                      lp(own), cap, lp(st))
+    if stats:
+        return pts[:m], sv[:m], sp[:m], own[:cap], {"projections": int(st[0]), "fragile": int(st[1]),
+                                                    "resolved_by_hint": int(st[2])}
     return pts[:m], sv[:m], sp[:m]
 
 
@@ -489,25 +505,27 @@ def select_neighbors(scene, X, vis, eps=0.002, t_tau=0.1, k=8):
 def sparse_features(scene, ref, X, vis, reproj, obs, max_reproj=2.0):
     """Sec. III-B features of view ref from sparse points (X (n, 3), vis
     (n, n_views) bool, reproj (n,), obs (n, 2) observations in ref).
-    Returns (uv (m, 2) float32, depth (m,) float32)."""
+    Returns (uv (m, 2) float64, depth (m,) float64)."""
     X = _f64(np.asarray(X).reshape(-1, 3))
     vis = np.ascontiguousarray(vis, np.uint8)
     n = len(X)
     obs = _f64(np.nan_to_num(np.asarray(obs, np.float64).reshape(n, 2)))
-    uv = np.zeros((max(n, 1), 2), np.float32)
-    dep = np.zeros(max(n, 1), np.float32)
-    f32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+    uv = np.zeros((max(n, 1), 2), np.float64)
+    dep = np.zeros(max(n, 1), np.float64)
     m = lib().or_sparse_features(scene.h, ref, n, _d(X), _u8(vis), _d(_f64(reproj)), _d(obs), float(max_reproj),
-                                 f32(uv), f32(dep))
+                                 _d(uv), _d(dep))
     return uv[:m], dep[:m]
 
 
-def sparse_range(W, H, uv, depth, d_lo=2.0, d_hi=8.0):
+def sparse_range(W, H, uv, depth, d_lo=2.0, d_hi=8.0, band_px=0.0, fragile=False):
     """Per-pixel (d_min, d_max) of the closest features in four quadrants
-    within W / 10 px (NaN: none), (H, W, 2) float32."""
-    uv = np.ascontiguousarray(uv, np.float32).reshape(-1, 2)
-    depth = np.ascontiguousarray(depth, np.float32).ravel()
-    out = np.zeros((H, W, 2), np.float32)
-    f32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
-    lib().or_sparse_range(int(W), int(H), len(depth), f32(uv), f32(depth), float(d_lo), float(d_hi), f32(out))
-    return out
+    within W / 10 px (NaN: none), (H, W, 2) float64; with ``fragile`` also
+    the (H, W) mask of pixels whose choice lies within ``band_px`` of a
+    boundary."""
+    uv = _f64(np.asarray(uv, np.float64).reshape(-1, 2))
+    depth = _f64(np.asarray(depth, np.float64).ravel())
+    out = np.zeros((H, W, 2), np.float64)
+    fr = np.zeros((H, W), np.uint8)
+    lib().or_sparse_range(int(W), int(H), len(depth), _d(uv), _d(depth), float(d_lo), float(d_hi), float(band_px),
+                          _d(out), _u8(fr))
+    return (out, fr.astype(bool)) if fragile else out

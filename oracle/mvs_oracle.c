@@ -1148,77 +1148,97 @@ void or_plane_infer(const or_scene* s, int ref, const int* srcs, int ns, const o
 /* ------------------------------------------------------------------ */
 /* Sec. III-F: depth-map fusion                                         */
 /* ------------------------------------------------------------------ */
-/* The paper fixes no precision for fusion, and its decisions (which pixel
- * of image j a point lands on, whether two points agree) are integers, so
- * the oracle takes them in single precision, operation by operation, with
- * no fused multiply-add (this file is built with -ffp-contract=off):
- *   back-projection of pixel (x, y) of view v with z-depth d (reading: a
- *   pinhole K = [fx s cx; 0 fy cy; 0 0 1], x_cam = R X + t):
- *     yc = (y - cy) / fy, xc = ((x - cx) - s yc) / fx, Xc = (d xc, d yc, d),
- *     X = R^T (Xc - t), each component ((R0k e0 + R1k e1) + R2k e2);
- *   projection into view j: c = R X + t, each component
- *     ((Rk0 X0 + Rk1 X1) + Rk2 X2) + tk, u = ((fx c0 + s c1) + cx c2) / c2,
- *     v = (fy c1 + cy c2) / c2, pixel [x'_j] = (floor(u + 1/2), floor(v + 1/2))
- *     when c2 > 0 and the pixel lies in the image;
- *   relative difference (reading: distance over the z-depth of X_i in view
- *     i): ((e0 e0 + e1 e1) + e2 e2) < (tol d_i)^2;
+/* Everything is computed in double precision:
+ *   back-projection of pixel (x, y) of view v with z-depth d (pinhole,
+ *   x_cam = R X + t): X = R^T (d K^-1 (x, y, 1)^T - t);
+ *   projection into view j: c = R X + t, (u, v) = (K c)_{0,1} / c_2 when
+ *   c_2 > 0, pixel [x'_j] = (floor(u + 1/2), floor(v + 1/2)) (reading: the
+ *   nearest pixel) when it lies in the image;
+ *   relative difference (reading: distance over the z-depth d_i of X_i in
+ *   view i): |X_i - X'_j| < rel_tol d_i;
  *   merged point: (X_i + X'_j1 + X'_j2 + ...) / count, summed in view order.
- * Camera values are the doubles of the scene rounded to float. */
-typedef struct { float fx, sk, cx, fy, cy, R[9], t[3]; } or_fcam;
-
-static or_fcam fcam(const or_view* v) {
-    or_fcam c;
-    c.fx = (float)v->K[0]; c.sk = (float)v->K[1]; c.cx = (float)v->K[2];
-    c.fy = (float)v->K[4]; c.cy = (float)v->K[5];
-    for (int k = 0; k < 9; ++k) c.R[k] = (float)v->R[k];
-    for (int k = 0; k < 3; ++k) c.t[k] = (float)v->t[k];
-    return c;
+ *
+ * Fragile decisions.  Another implementation that rounds differently can
+ * take a decision the other way when it lies within rounding of its
+ * boundary: a projection whose u + 1/2 or v + 1/2 is within band_px of an
+ * integer (two or four candidate pixels), or a distance within
+ * band_rel rel_tol d_i of the threshold (merge or not).  Such a decision is
+ * counted.  When `hint` gives that implementation's result (the point index
+ * each pixel went into, laid out as `owner` below), a fragile decision takes
+ * the outcome the hint shows, if that outcome is one of the possible ones;
+ * every other decision is this function's own. */
+static void fuse_backproject(const or_view* V, int x, int y, double d, double X[3]) {
+    const double xt[3] = {(double)x, (double)y, 1.0};
+    double r[3], e[3];
+    m3_vec(V->Kinv, xt, r);
+    for (int k = 0; k < 3; ++k) e[k] = d * r[k] - V->t[k];
+    for (int k = 0; k < 3; ++k) X[k] = V->R[k] * e[0] + V->R[3 + k] * e[1] + V->R[6 + k] * e[2];
 }
 
-static void fuse_backproject(const or_fcam* c, int x, int y, float d, float X[3]) {
-    float yc = ((float)y - c->cy) / c->fy;
-    float xc = (((float)x - c->cx) - c->sk * yc) / c->fx;
-    float e[3] = {d * xc - c->t[0], d * yc - c->t[1], d - c->t[2]};
-    for (int k = 0; k < 3; ++k) X[k] = (c->R[k] * e[0] + c->R[3 + k] * e[1]) + c->R[6 + k] * e[2];
-}
-
-/* pixel index of [x'_j], or -1 */
-static long fuse_project(const or_fcam* c, int W, int H, const float X[3]) {
-    float q[3];
-    for (int k = 0; k < 3; ++k) q[k] = ((c->R[3 * k] * X[0] + c->R[3 * k + 1] * X[1]) + c->R[3 * k + 2] * X[2]) + c->t[k];
-    if (!(q[2] > 0.0f)) return -1;
-    float u = ((c->fx * q[0] + c->sk * q[1]) + c->cx * q[2]) / q[2];
-    float v = (c->fy * q[1] + c->cy * q[2]) / q[2];
-    float fu = floorf(u + 0.5f), fv = floorf(v + 0.5f);
-    if (!(fu >= 0.0f && fu <= (float)(W - 1) && fv >= 0.0f && fv <= (float)(H - 1))) return -1;
-    return (long)fv * W + (long)fu;
+/* candidate pixels of the projection of X into view V: cand[0] is the
+ * nearest pixel, the others the alternatives within band_px of a rounding
+ * boundary; -1 = outside the image or behind the camera.  Returns the number
+ * of candidates (1, 2 or 4). */
+static int fuse_candidates(const or_view* V, const double X[3], double band_px, long cand[4]) {
+    double c[3], q[3];
+    m3_vec(V->R, X, c);
+    for (int k = 0; k < 3; ++k) c[k] += V->t[k];
+    if (!(c[2] > 0.0)) {
+        cand[0] = -1;
+        return 1;
+    }
+    m3_vec(V->K, c, q);
+    const double uu = q[0] / q[2] + 0.5, vv = q[1] / q[2] + 0.5;
+    const double fu = floor(uu), fv = floor(vv);
+    double cu[2] = {fu, fu}, cv[2] = {fv, fv};
+    int nu = 1, nv = 1;
+    if (uu - fu < band_px) cu[nu++] = fu - 1.0;
+    else if (fu + 1.0 - uu < band_px) cu[nu++] = fu + 1.0;
+    if (vv - fv < band_px) cv[nv++] = fv - 1.0;
+    else if (fv + 1.0 - vv < band_px) cv[nv++] = fv + 1.0;
+    int m = 0;
+    for (int b = 0; b < nv; ++b)
+        for (int a = 0; a < nu; ++a) {
+            const double px = cu[a], py = cv[b];
+            cand[m++] = (px >= 0.0 && px <= (double)(V->W - 1) && py >= 0.0 && py <= (double)(V->H - 1))
+                            ? (long)py * V->W + (long)px
+                            : -1;
+        }
+    return m;
 }
 
 /* Fusion of the depth maps of views order[0..n-1], in that order (Sec. III-F):
- * every remaining pixel x of image i (depth > 0, kept by keep[v] when given,
+ * every remaining pixel x of image i (depth > 0, kept by keep[a] when given,
  * not merged before) is back-projected to X_i; for every remaining image j
  * the pixel [x'_j] that X_i projects to is back-projected to X'_j, and when
  * the relative difference is below rel_tol that pixel is merged (removed
  * from image j) and X'_j joins the average; after its pixels, image i is
  * removed.  planes[a] and keep[a] belong to view order[a] (keep NULL or
  * keep[a] NULL: every pixel with depth).  Points are emitted in view order,
- * then raster order:
- * pts[4k..4k+3] = (x, y, z, number of merged pixels), src_view[k],
- * src_pix[k] = the emitting pixel.  Writes at most cap points and returns
- * the number of points. */
+ * then raster order: pts[4k..4k+3] = (x, y, z, number of merged pixels),
+ * src_view[k], src_pix[k] = the emitting pixel; at most cap points are
+ * written and the number of points is returned.  owner (optional): one
+ * entry per pixel of the views, view after view in `order`, the index of
+ * the point the pixel went into, -1 if never present.  hint (optional): the
+ * same layout from another implementation, consulted at fragile decisions
+ * only.  stats (optional): [0] projections tested, [1] fragile decisions,
+ * [2] fragile decisions resolved by the hint. */
 long or_fuse(const or_scene* s, int n, const int* order, const double* const* planes,
-             const unsigned char* const* keep, double rel_tol, float* pts, int* src_view, long* src_pix, long cap) {
+             const unsigned char* const* keep, double rel_tol, double band_px, double band_rel, const long* hint,
+             double* pts, int* src_view, long* src_pix, long* owner, long cap, long* stats) {
     unsigned char** alive = (unsigned char**)calloc((size_t)n, sizeof(unsigned char*));
-    or_fcam* cam = (or_fcam*)calloc((size_t)n, sizeof(or_fcam));
+    long* base = (long*)calloc((size_t)n + 1, sizeof(long));
     for (int a = 0; a < n; ++a) {
         const or_view* V = &s->v[order[a]];
         long N = (long)V->W * V->H;
+        base[a + 1] = base[a] + N;
         alive[a] = (unsigned char*)malloc((size_t)N);
         for (long i = 0; i < N; ++i)
-            alive[a][i] = (unsigned char)((float)planes[a][4 * i + 3] > 0.0f && (!keep || !keep[a] || keep[a][i]));
-        cam[a] = fcam(V);
+            alive[a][i] = (unsigned char)(planes[a][4 * i + 3] > 0.0 && (!keep || !keep[a] || keep[a][i]));
     }
-    const float tol = (float)rel_tol;
+    if (owner)
+        for (long i = 0; i < base[n]; ++i) owner[i] = -1;
+    long st[3] = {0, 0, 0};
     long np = 0;
     for (int a = 0; a < n; ++a) {
         const or_view* V = &s->v[order[a]];
@@ -1226,37 +1246,85 @@ long or_fuse(const or_scene* s, int n, const int* order, const double* const* pl
             for (int x = 0; x < V->W; ++x) {
                 long i = (long)y * V->W + x;
                 if (!alive[a][i]) continue;
-                float d = (float)planes[a][4 * i + 3];
-                float X[3], sum[3];
-                fuse_backproject(&cam[a], x, y, d, X);
+                double d = planes[a][4 * i + 3];
+                double X[3], sum[3];
+                fuse_backproject(V, x, y, d, X);
                 for (int k = 0; k < 3; ++k) sum[k] = X[k];
                 int cnt = 1;
-                float thr = tol * d;
+                const double thr = rel_tol * d;
                 for (int b = a + 1; b < n; ++b) {
                     const or_view* S = &s->v[order[b]];
-                    long t = fuse_project(&cam[b], S->W, S->H, X);
-                    if (t < 0 || !alive[b][t]) continue;
-                    float Y[3];
-                    fuse_backproject(&cam[b], (int)(t % S->W), (int)(t / S->W), (float)planes[b][4 * t + 3], Y);
-                    float e0 = X[0] - Y[0], e1 = X[1] - Y[1], e2 = X[2] - Y[2];
-                    if (!(((e0 * e0 + e1 * e1) + e2 * e2) < thr * thr)) continue;
+                    long cand[4];
+                    const int m = fuse_candidates(S, X, band_px, cand);
+                    /* outcome of each candidate: merge it (firm or fragile)
+                     * or not (firm or fragile) */
+                    int can_merge[4], can_skip[4];
+                    double Ys[4][3];
+                    int n_merge = 0, any_skip = 0;
+                    for (int c = 0; c < m; ++c) {
+                        can_merge[c] = can_skip[c] = 0;
+                        const long t = cand[c];
+                        if (t < 0 || !alive[b][t]) {
+                            can_skip[c] = 1;
+                        } else {
+                            fuse_backproject(S, (int)(t % S->W), (int)(t / S->W), planes[b][4 * t + 3], Ys[c]);
+                            const double e0 = X[0] - Ys[c][0], e1 = X[1] - Ys[c][1], e2 = X[2] - Ys[c][2];
+                            const double dist = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+                            can_merge[c] = dist < thr + band_rel * thr;
+                            can_skip[c] = !(dist < thr - band_rel * thr);
+                        }
+                        n_merge += can_merge[c];
+                        any_skip |= can_skip[c];
+                    }
+                    st[0]++;
+                    /* this function's own outcome: the nearest pixel, its
+                     * distance against the threshold itself */
+                    int pick = -1;
+                    if (cand[0] >= 0 && alive[b][cand[0]]) {
+                        const double e0 = X[0] - Ys[0][0], e1 = X[1] - Ys[0][1], e2 = X[2] - Ys[0][2];
+                        if (sqrt(e0 * e0 + e1 * e1 + e2 * e2) < thr) pick = 0;
+                    }
+                    if (n_merge + any_skip > 1) {
+                        st[1]++;
+                        if (hint) {
+                            int h = -2;
+                            for (int c = 0; c < m && h == -2; ++c)
+                                if (can_merge[c] && hint[base[b] + cand[c]] == np) h = c;
+                            if (h == -2 && any_skip) {
+                                int taken = 0;
+                                for (int c = 0; c < m; ++c)
+                                    if (cand[c] >= 0 && hint[base[b] + cand[c]] == np) taken = 1;
+                                if (!taken) h = -1;
+                            }
+                            if (h != -2) {
+                                if (h != pick) st[2]++;
+                                pick = h;
+                            }
+                        }
+                    }
+                    if (pick < 0) continue;
+                    const long t = cand[pick];
                     alive[b][t] = 0;
-                    for (int k = 0; k < 3; ++k) sum[k] = sum[k] + Y[k];
+                    if (owner) owner[base[b] + t] = np;
+                    for (int k = 0; k < 3; ++k) sum[k] = sum[k] + Ys[pick][k];
                     cnt++;
                 }
                 alive[a][i] = 0;
+                if (owner) owner[base[a] + i] = np;
                 if (np < cap) {
-                    for (int k = 0; k < 3; ++k) pts[4 * np + k] = sum[k] / (float)cnt;
-                    pts[4 * np + 3] = (float)cnt;
+                    for (int k = 0; k < 3; ++k) pts[4 * np + k] = sum[k] / (double)cnt;
+                    pts[4 * np + 3] = (double)cnt;
                     if (src_view) src_view[np] = order[a];
                     if (src_pix) src_pix[np] = i;
                 }
                 np++;
             }
     }
+    if (stats)
+        for (int k = 0; k < 3; ++k) stats[k] = st[k];
     for (int a = 0; a < n; ++a) free(alive[a]);
     free(alive);
-    free(cam);
+    free(base);
     return np;
 }
 
@@ -1347,12 +1415,11 @@ void or_select_neighbors(const or_scene* s, long n_pts, const double* X, const u
  * re-projection error is below max_reproj (reading: the point's mean error
  * over its views) and that are visible in at least floor(v - 1) images, v
  * the mean number of images per point.  Each keeps its observation in ref
- * (uv, rounded to float) and its z-depth in ref (FP64, rounded to float).
- * vis[p * n + v] = 1 when point p is visible in view v; obs[2p..2p+1] = its
- * observation in ref.  Writes uv[2k..], depth[k] in point order and returns
- * the number of features. */
+ * (uv) and its z-depth in ref.  vis[p * n + v] = 1 when point p is visible
+ * in view v; obs[2p..2p+1] = its observation in ref.  Writes uv[2k..],
+ * depth[k] in point order and returns the number of features. */
 long or_sparse_features(const or_scene* s, int ref, long n_pts, const double* X, const unsigned char* vis,
-                        const double* reproj, const double* obs, double max_reproj, float* uv, float* depth) {
+                        const double* reproj, const double* obs, double max_reproj, double* uv, double* depth) {
     const int n = s->n;
     long total = 0;
     for (long p = 0; p < n_pts; ++p)
@@ -1367,10 +1434,9 @@ long or_sparse_features(const or_scene* s, int ref, long n_pts, const double* X,
         for (int v = 0; v < n; ++v) cnt += vis[p * n + v] ? 1 : 0;
         if (!vis[p * n + ref] || !(reproj[p] < max_reproj) || cnt < min_views) continue;
         const double* Xp = X + 3 * p;
-        double z = R[6] * Xp[0] + R[7] * Xp[1] + R[8] * Xp[2] + t[2];
-        uv[2 * k] = (float)obs[2 * p];
-        uv[2 * k + 1] = (float)obs[2 * p + 1];
-        depth[k] = (float)z;
+        uv[2 * k] = obs[2 * p];
+        uv[2 * k + 1] = obs[2 * p + 1];
+        depth[k] = R[6] * Xp[0] + R[7] * Xp[1] + R[8] * Xp[2] + t[2];
         k++;
     }
     return k;
@@ -1380,32 +1446,44 @@ long or_sparse_features(const or_scene* s, int ref, long n_pts, const double* X,
  * quadrants around it (dx >= 0, dy >= 0 / dx < 0, dy >= 0 / dx < 0, dy < 0 /
  * dx >= 0, dy < 0 with dx = u - x, dy = v - y) within w / 10 pixels, and the
  * minimum and maximum depth over those features, clamped to [d_lo, d_hi]
- * (reading); NaN when no feature is that close.  The choice of the closest
- * feature is an integer decision and is taken in single precision:
- * r = W / 10, d2 = dx dx + dy dy < r r, every operation rounded on its own;
- * the first feature wins a tie.  range[2i], range[2i+1] = d_min, d_max. */
-void or_sparse_range(int W, int H, long n_feat, const float* uv, const float* depth, float d_lo, float d_hi,
-                     float* range) {
-    const float r = (float)W / 10.0f;
-    const float r2 = r * r;
+ * (reading); NaN when no feature is that close.  The first feature wins a
+ * tie.  range[2i], range[2i+1] = d_min, d_max.
+ * fragile[i] (optional) = 1 when the pixel's choice lies within band_px of
+ * a boundary, where an implementation that rounds the positions or the
+ * distances differently may decide otherwise: a feature within band_px of
+ * the radius, a counted feature within band_px of a quadrant border, or a
+ * quadrant whose two closest features are within band_px in distance. */
+void or_sparse_range(int W, int H, long n_feat, const double* uv, const double* depth, double d_lo, double d_hi,
+                     double band_px, double* range, unsigned char* fragile) {
+    const double r = (double)W / 10.0;
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
-            float best[4] = {INFINITY, INFINITY, INFINITY, INFINITY}, bd[4] = {0, 0, 0, 0};
+            double best[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+            double second[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+            double bd[4] = {0, 0, 0, 0};
+            int frag = 0;
             for (long f = 0; f < n_feat; ++f) {
-                float dx = uv[2 * f] - (float)x, dy = uv[2 * f + 1] - (float)y;
-                float d2 = dx * dx + dy * dy;
-                if (!(d2 < r2)) continue;
-                int q = dx >= 0.0f ? (dy >= 0.0f ? 0 : 3) : (dy >= 0.0f ? 1 : 2);
-                if (d2 < best[q]) {
-                    best[q] = d2;
+                const double dx = uv[2 * f] - (double)x, dy = uv[2 * f + 1] - (double)y;
+                const double d2 = dx * dx + dy * dy;
+                const double dist = sqrt(d2);
+                if (fabs(dist - r) < band_px) frag = 1;
+                if (!(d2 < r * r)) continue;
+                if (fabs(dx) < band_px || fabs(dy) < band_px) frag = 1;
+                const int q = dx >= 0.0 ? (dy >= 0.0 ? 0 : 3) : (dy >= 0.0 ? 1 : 2);
+                if (dist < best[q]) {
+                    second[q] = best[q];
+                    best[q] = dist;
                     bd[q] = depth[f];
+                } else if (dist < second[q]) {
+                    second[q] = dist;
                 }
             }
-            float lo = INFINITY, hi = -INFINITY;
+            double lo = INFINITY, hi = -INFINITY;
             for (int q = 0; q < 4; ++q)
                 if (best[q] < INFINITY) {
                     lo = bd[q] < lo ? bd[q] : lo;
                     hi = bd[q] > hi ? bd[q] : hi;
+                    if (second[q] - best[q] < band_px) frag = 1;
                 }
             long i = (long)y * W + x;
             if (lo <= hi) {
@@ -1416,5 +1494,6 @@ void or_sparse_range(int W, int H, long n_feat, const float* uv, const float* de
             } else {
                 range[2 * i] = range[2 * i + 1] = NAN;
             }
+            if (fragile) fragile[i] = (unsigned char)frag;
         }
 }

@@ -167,8 +167,10 @@ __global__ void __launch_bounds__(kFuseBlock) k_fuse_merge(const FuseView* __res
         sum[2] = __fadd_rn(sum[2], Y[2]);
         cnt++;
         vb.alive[t] = 0;
+        if (vb.owner) vb.owner[t] = block_off[blockIdx.x] + rank;
     }
     const long long k = block_off[blockIdx.x] + rank;
+    if (va.owner) va.owner[i] = k;
     if (k < cap) {
         const float fc = (float)cnt;
         points[k] = make_float4(__fdiv_rn(sum[0], fc), __fdiv_rn(sum[1], fc), __fdiv_rn(sum[2], fc), fc);
@@ -193,6 +195,10 @@ cudaError_t launch_fuse(const FuseView* host_views, FuseView* dev_views, int n, 
         count_launch();
         // unclaimed: 0x7f7f7f7f, above every pixel index
         if ((e = cudaMemsetAsync(host_views[a].claim, 0x7f, sizeof(int) * np, s)) != cudaSuccess) return e;
+        // pixels never present keep owner -1
+        if (host_views[a].owner &&
+            (e = cudaMemsetAsync(host_views[a].owner, 0xff, sizeof(long long) * np, s)) != cudaSuccess)
+            return e;
     }
     for (int a = 0; a < n; ++a) {
         const long long np = (long long)host_views[a].W * host_views[a].H;

@@ -618,7 +618,7 @@ mvs_status mvs_geo_filter(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t 
 }
 
 mvs_status mvs_fuse(mvs_ctx* c, int32_t n_views, const int32_t* views, const uint8_t* const* keep_masks, float rel_tol,
-                    float* points, int32_t* src, int64_t capacity, int64_t* n_points, int32_t mem) {
+                    float* points, int32_t* src, int64_t* owner, int64_t capacity, int64_t* n_points, int32_t mem) {
     if (!c) return MVS_EINVAL;
     if (!views || n_views < 1 || n_views > (int32_t)c->views.size())
         return fail(c, MVS_EINVAL, "need 1..%d views", (int)c->views.size());
@@ -690,11 +690,25 @@ mvs_status mvs_fuse(mvs_ctx* c, int32_t n_views, const int32_t* views, const uin
     FuseView* dev_views = (FuseView*)q;
     float4* pts_d = (float4*)points;
     int2* src_d = (int2*)src;
-    if (mem == MVS_MEM_HOST && capacity > 0) {
-        char* ob = (char*)scratch(c, 7, (size_t)capacity * (sizeof(float4) + (src ? sizeof(int2) : 0)), &e);
+    long long* own_d = (long long*)owner;
+    size_t n_pix = 0;
+    for (int a = 0; a < n_views; ++a) n_pix += (size_t)c->views[views[a]].cam.width * c->views[views[a]].cam.height;
+    if (mem == MVS_MEM_HOST && (capacity > 0 || owner)) {
+        // host outputs go through scratch slot 7: points, sources, owners
+        const size_t b_pts = a16((size_t)capacity * sizeof(float4));
+        const size_t b_src = a16(src ? (size_t)capacity * sizeof(int2) : 0);
+        char* ob = (char*)scratch(c, 7, b_pts + b_src + (owner ? n_pix * sizeof(long long) : 0) + 16, &e);
         CK(c, e);
         pts_d = (float4*)ob;
-        src_d = src ? (int2*)(ob + (size_t)capacity * sizeof(float4)) : nullptr;
+        src_d = src ? (int2*)(ob + b_pts) : nullptr;
+        own_d = owner ? (long long*)(ob + b_pts + b_src) : nullptr;
+    }
+    {
+        size_t off = 0;
+        for (int a = 0; a < n_views; ++a) {
+            fv[a].owner = own_d ? own_d + off : nullptr;
+            off += (size_t)fv[a].W * fv[a].H;
+        }
     }
     CK(c, launch_fuse(fv.data(), dev_views, n_views, keep_masks ? keep_d.data() : nullptr, rel_tol, block_count,
                       block_off, total, pts_d, src_d, capacity, c->stream));
@@ -703,9 +717,13 @@ mvs_status mvs_fuse(mvs_ctx* c, int32_t n_views, const int32_t* views, const uin
     CK(c, cudaStreamSynchronize(c->stream));
     *n_points = tot;
     const long long nw = std::min<long long>(tot, capacity);
-    if (mem == MVS_MEM_HOST && nw > 0) {
-        CK(c, cudaMemcpyAsync(points, pts_d, (size_t)nw * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
-        if (src) CK(c, cudaMemcpyAsync(src, src_d, (size_t)nw * sizeof(int2), cudaMemcpyDeviceToHost, c->stream));
+    if (mem == MVS_MEM_HOST && (nw > 0 || owner)) {
+        if (nw > 0) {
+            CK(c, cudaMemcpyAsync(points, pts_d, (size_t)nw * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+            if (src) CK(c, cudaMemcpyAsync(src, src_d, (size_t)nw * sizeof(int2), cudaMemcpyDeviceToHost, c->stream));
+        }
+        if (owner)
+            CK(c, cudaMemcpyAsync(owner, own_d, n_pix * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
     }
     if (tot > capacity) return fail(c, MVS_EINVAL, "%lld points do not fit the capacity of %lld", tot, (long long)capacity);

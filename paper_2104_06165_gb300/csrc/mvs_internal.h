@@ -129,6 +129,7 @@ struct FuseView {
     const float4* plane;         // depth map (depth in .w, 0 = none)
     uint8_t* alive;              // W*H: 1 = still present
     int* claim;                  // W*H: lowest claiming pixel of the view being fused
+    long long* owner;            // W*H or NULL: index of the point the pixel went into, -1 if absent
 };
 cudaError_t launch_fuse(const FuseView* host_views, FuseView* dev_views, int n, const uint8_t* const* keep, float tol,
                         int* block_count, long long* block_off, long long* total, float4* points, int2* src,

@@ -131,7 +131,7 @@ cudaError_t launch_select_neighbors(const NbrView* dev_views, int n, const doubl
 // feature in each of four quadrants within W / 10 px gives [d_min, d_max],
 // clamped to the depth range; the closest-feature choice is taken in single
 // precision, each operation rounded on its own, the first feature winning a
-// tie (the oracle's statement).
+// tie.
 // ---------------------------------------------------------------------------
 namespace {
 

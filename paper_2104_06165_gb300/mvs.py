@@ -189,7 +189,7 @@ def load():
     L.mvs_propose.restype = i32
     L.mvs_propose.argtypes = [vp, i32, vp, fp]
     L.mvs_fuse.restype = i32
-    L.mvs_fuse.argtypes = [vp, i32, ip, C.c_void_p, C.c_float, fp, vp, C.c_int64, C.POINTER(C.c_int64), i32]
+    L.mvs_fuse.argtypes = [vp, i32, ip, C.c_void_p, C.c_float, fp, vp, vp, C.c_int64, C.POINTER(C.c_int64), i32]
     L.mvs_select_neighbors.restype = i32
     L.mvs_select_neighbors.argtypes = [vp, C.c_int64, vp, vp, C.c_double, C.c_double, i32, vp, vp, vp, vp, i32]
     L.mvs_sparse_depth_range.restype = i32
@@ -311,14 +311,16 @@ def mvs_geo_filter(ctx, ref, srcs, fparams: FilterParams, keep, count=None):
     _check(load().mvs_geo_filter(ctx, ref, s, ns, C.byref(cpar), _ptr(keep)[0], _ptr(count)[0], mem), ctx)
 
 
-def mvs_fuse(ctx, views, points, src=None, keep_masks=None, rel_tol=0.01):
+def mvs_fuse(ctx, views, points, src=None, keep_masks=None, rel_tol=0.01, owner=None):
     """Depth-map fusion of the context's maps of ``views`` (in that order)
     into ``points`` (capacity x 4 float32: x, y, z, merged count) and
     optionally ``src`` (capacity x 2 int32: view, pixel); ``keep_masks`` is
-    None or one uint8 (H, W) mask or None per view.  Returns the number of
-    points."""
+    None or one uint8 (H, W) mask or None per view; ``owner`` (optional,
+    int64, one entry per pixel of the views in processing order) receives
+    the index of the point each pixel went into, -1 if never present.
+    Returns the number of points."""
     kms = list(keep_masks) if keep_masks is not None else []
-    mem = _mem(points, src, *[k for k in kms if k is not None])
+    mem = _mem(points, src, owner, *[k for k in kms if k is not None])
     v, nv = _srcs(views)
     km = None
     if keep_masks is not None:
@@ -327,8 +329,8 @@ def mvs_fuse(ctx, views, points, src=None, keep_masks=None, rel_tol=0.01):
         km = (C.c_void_p * nv)(*[_ptr(k)[0] for k in kms])
     cap = points.shape[0]
     n = C.c_int64(0)
-    _check(load().mvs_fuse(ctx, nv, v, km, C.c_float(rel_tol), _ptr(points)[0], _ptr(src)[0], cap, C.byref(n), mem),
-           ctx)
+    _check(load().mvs_fuse(ctx, nv, v, km, C.c_float(rel_tol), _ptr(points)[0], _ptr(src)[0], _ptr(owner)[0], cap,
+                           C.byref(n), mem), ctx)
     return n.value
 
 

@@ -101,7 +101,7 @@ def test_null_context_is_rejected(mvs_lib):
     assert lib.mvs_profile(None, 1) == mvs_lib.MVS_EINVAL
     views = (C.c_int32 * 1)(0)
     n = C.c_int64(0)
-    assert lib.mvs_fuse(None, 1, views, None, C.c_float(0.01), None, None, 0, C.byref(n), 0) == mvs_lib.MVS_EINVAL
+    assert lib.mvs_fuse(None, 1, views, None, C.c_float(0.01), None, None, None, 0, C.byref(n), 0) == mvs_lib.MVS_EINVAL
     nbr = np.zeros((2, 1), np.int32)
     assert lib.mvs_select_neighbors(None, 0, None, None, 0.002, 0.1, 1, nbr.ctypes.data, None, None, None,
                                     0) == mvs_lib.MVS_EINVAL

@@ -115,3 +115,47 @@ def test_rigid_change_of_world_frame(oracle_lib):
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2]) and np.array_equal(a[0][:, 3], b[0][:, 3])
     moved = a[0][:, :3].astype(np.float64) @ Q.T + T
     assert np.allclose(b[0][:, :3], moved, atol=1e-4)
+
+
+def test_fragile_rounding_follows_the_hint_and_firm_decisions_do_not(oracle_lib):
+    """View 1 shifted by 5.5 - 1e-6 px: every projection of a view-0 pixel
+    lands 1e-6 px past u + 1/2 = an integer, the boundary of the nearest-
+    pixel rounding, where a single-precision computation may take either
+    neighbour.  The oracle's own choice is floor(u + 1/2) (pixel x - 5);
+    with a 1e-3 px band the decision is counted as fragile and a hint naming
+    the other pixel (x - 6) is followed.  A hint that contradicts a firm decision (the 0.5 % depth
+    offset of the other pins, no rounding boundary) changes nothing."""
+    b2 = (5.5 - 1e-6) * D / F
+    K = np.tile(np.array([[F, 0, CX], [0, F, CY], [0, 0, 1]], np.float64), (2, 1, 1))
+    R = np.tile(np.eye(3), (2, 1, 1))
+    t = np.array([[0.0, 0.0, 0.0], [-b2, 0.0, 0.0]])
+    sc = oracle_lib.Scene(K, R, t, [np.zeros((H, W), np.uint8)] * 2)
+    maps = {0: _plane(D), 1: _plane(D)}
+    pts, sv, sp, own, st = oracle_lib.fuse(sc, [0, 1], maps, stats=True)
+    assert st["fragile"] == 0
+    own0 = own[: H * W].reshape(H, W)
+    own1 = own[H * W:].reshape(H, W)
+    # the oracle's own choice: view-0 pixel x takes view-1 pixel x - 5
+    assert (own1[:, : W - 5] == own0[:, 5:]).all()
+    _, _, _, own_b, st_b = oracle_lib.fuse(sc, [0, 1], maps, band_px=1e-3, stats=True)
+    assert st_b["fragile"] == H * (W - 5) and st_b["resolved_by_hint"] == 0 and np.array_equal(own_b, own)
+    # a hint in which view-0 pixel x took view-1 pixel x - 6 instead
+    hint = np.full(2 * H * W, -1, np.int64)
+    hint[: H * W] = np.arange(H * W)
+    h1 = hint[H * W:].reshape(H, W)
+    h1[:, : W - 6] = np.arange(H * W).reshape(H, W)[:, 6:]
+    _, _, _, own_h, st_h = oracle_lib.fuse(sc, [0, 1], maps, band_px=1e-3, hint=hint, stats=True)
+    own_h1 = own_h[H * W:].reshape(H, W)
+    own_h0 = own_h[: H * W].reshape(H, W)
+    assert (own_h1[:, : W - 6] == own_h0[:, 6:]).all()
+    # ... and at x = 5, whose other candidate lies outside view 1, the hint's
+    # "took nothing" is followed too
+    assert st_h["resolved_by_hint"] == H * (W - 5)
+    assert (own_h0[:, 5] != own_h1[:, 0]).all()
+    # firm decisions ignore the hint
+    sc1 = _scene(oracle_lib, 2)
+    m2 = {0: _plane(D), 1: _plane(D * 1.005)}
+    _, _, _, own_f, st_f = oracle_lib.fuse(sc1, [0, 1], m2, band_px=1e-3, band_rel=1e-3, stats=True)
+    bogus = np.full(2 * H * W, -1, np.int64)
+    _, _, _, own_g, st_g = oracle_lib.fuse(sc1, [0, 1], m2, band_px=1e-3, band_rel=1e-3, hint=bogus, stats=True)
+    assert st_f["fragile"] == st_g["fragile"] == 0 and np.array_equal(own_f, own_g)

@@ -1,13 +1,19 @@
 """Depth initialisation from sparse features (Sec. III-B) on the GPU against
-the oracle: the per-pixel ranges bit for bit (the closest-feature choice is
-taken in single precision on both sides), the initial state within the
-initialisation tolerances, and the faster convergence the paper argues for."""
+the FP64 oracle: the per-pixel ranges bit for bit (the library rounds the
+feature depths to float) wherever the closest-feature choice is firm, with
+the pixels whose choice lies within BAND_PX of a boundary counted, printed
+and bounded; the initial state within the initialisation tolerances, and
+the faster convergence the paper argues for."""
 import copy
 
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
+
+# the library keeps feature positions in float (< 1e-5 px of rounding at
+# these sizes) and distances in float; the band is a hundred times that
+BAND_PX = 1e-3
 
 
 def _masks(vis):
@@ -51,9 +57,18 @@ def test_ranges_equal_oracle(sparse_scene, mvs_lib, oracle_lib, ref):
     g = _gpu_range(mvs_lib, ctx, sp, ref, H, W)
     osc = oracle_lib.Scene(sc.K, sc.R, sc.t, sc.images)
     uv, dep = oracle_lib.sparse_features(osc, ref, sp["X"], sp["vis"], sp["reproj"], sp["obs"][:, ref])
-    o = oracle_lib.sparse_range(W, H, uv, dep, d_lo=2.0, d_hi=8.0)
-    assert np.array_equal(np.isnan(g), np.isnan(o))
-    assert np.array_equal(g[~np.isnan(g)], o[~np.isnan(o)])
+    o, frag = oracle_lib.sparse_range(W, H, uv, dep, d_lo=2.0, d_hi=8.0, band_px=BAND_PX, fragile=True)
+    print(f"sparse ranges: {frag.sum()} of {frag.size} pixels fragile ({frag.mean():.2e})")
+    assert frag.mean() < 0.01
+    firm = ~frag
+    o32 = o.astype(np.float32)
+    assert np.array_equal(np.isnan(g[firm]), np.isnan(o32[firm]))
+    ok = ~np.isnan(o32[firm])
+    assert np.array_equal(g[firm][ok], o32[firm][ok])
+    # a fragile pixel still gets a valid range
+    gf = g[frag]
+    gf = gf[~np.isnan(gf[:, 0])]
+    assert ((gf[:, 0] <= gf[:, 1]) & (gf[:, 0] >= 2.0) & (gf[:, 1] <= 8.0)).all()
     assert (~np.isnan(o[..., 0])).mean() > 0.5      # most pixels get a range
     # device buffers give the same ranges
     d = _gpu_range(mvs_lib, ctx, sp, ref, H, W, device=True).cpu().numpy()

@@ -32,6 +32,24 @@ def test_closest_feature_per_quadrant(oracle_lib):
     assert tuple(rng[15, 20]) == (3.5, 3.5)
 
 
+def test_fragile_choices_are_flagged(oracle_lib):
+    """Pixel (20, 15), radius 4 px: a choice is flagged when a single-
+    precision position or distance could decide it the other way — a
+    feature 1e-6 px inside the radius, a feature 1e-6 px right of the pixel's
+    column (quadrant 0 or 1), two features of one quadrant 1e-6 px apart in
+    distance — and not flagged when every margin is above the band."""
+    W, H = 40, 30
+    firm = [(22.0, 16.0), (18.0, 17.0)]
+    _, fr = oracle_lib.sparse_range(W, H, firm, [3.0, 4.0], band_px=1e-3, fragile=True)
+    assert not fr[15, 20]
+    for uv in ([(24.0 - 1e-6, 15.0)], [(20.0 + 1e-6, 17.0)], [(22.0, 16.0), (22.0 + 1e-6, 16.0)]):
+        rng, fr = oracle_lib.sparse_range(W, H, uv, [3.0] * len(uv), band_px=1e-3, fragile=True)
+        assert fr[15, 20] and not np.isnan(rng[15, 20]).any()
+    # with no band nothing is flagged
+    _, fr = oracle_lib.sparse_range(W, H, [(24.0 - 1e-6, 15.0)], [3.0], fragile=True)
+    assert not fr.any()
+
+
 def test_feature_filters_and_depth(oracle_lib):
     n = 3
     K = np.tile(np.array([[100.0, 0, 31.5], [0, 100.0, 23.5], [0, 0, 1]]), (n, 1, 1))
@@ -47,11 +65,11 @@ def test_feature_filters_and_depth(oracle_lib):
     # mean views per point 11/5 = 2.2 -> at least floor(1.2) = 1 view; point 1
     # fails the re-projection error, point 4 is not visible in view 0; the
     # depth is the z of X in view 0 (R = I, t = 0 there)
-    assert np.array_equal(dep, np.float32([4.0, 6.0, 3.0]))
-    assert np.array_equal(uv, np.float32([[34.0, 28.5], [36.5, 21.8], [24.8, 26.8]]))
+    assert np.array_equal(dep, np.array([4.0, 6.0, 3.0]))
+    assert np.array_equal(uv, np.array([[34.0, 28.5], [36.5, 21.8], [24.8, 26.8]]))
     # the depth in another view: z of X in view 1 (R = I, t = (-0.2, 0, 0))
     uv1, dep1 = oracle_lib.sparse_features(sc, 1, X, vis, reproj, obs, max_reproj=2.0)
-    assert np.array_equal(dep1, np.float32([4.0, 6.0, 7.0]))
+    assert np.array_equal(dep1, np.array([4.0, 6.0, 7.0]))
 
 
 def test_min_views_threshold(oracle_lib):
@@ -62,7 +80,7 @@ def test_min_views_threshold(oracle_lib):
     vis = np.array([[1, 1, 1, 1], [1, 1, 1, 1], [1, 1, 1, 1], [1, 0, 0, 0]], bool)
     # mean 13/4 = 3.25 -> floor(2.25) = 2: the point seen by one view goes
     uv, dep = oracle_lib.sparse_features(sc, 0, X, vis, np.zeros(4), np.zeros((4, 2)), max_reproj=2.0)
-    assert np.array_equal(dep, np.float32([4.0, 5.0, 6.0]))
+    assert np.array_equal(dep, np.array([4.0, 5.0, 6.0]))
 
 
 def test_initialisation_draws_in_the_range(oracle_lib):
