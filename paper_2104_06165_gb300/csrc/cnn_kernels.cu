@@ -11,6 +11,7 @@
 // same kernel run on the output gradient with flipped, transposed weights;
 // the weight gradient is a shared-memory-tiled reduction over pixels.
 // Master weights, gradients and Adam moments are fp32.
+#include <atomic>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -429,10 +430,17 @@ cudaError_t wgrad_launch(const bf16* x, int Cin, const bf16* dy, int Cout, int W
     const int rows = 4;
     dim3 grid(Cout / 16, Cin / 16, (H + rows - 1) / rows);
     size_t smem = (size_t)(W * 16 + 3 * (W + 2) * 16) * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
+    // the shared-memory opt-in is a property of the current device
+    static std::atomic<bool> attr[128];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    if (!attr[dev].load()) {
+        if ((e = cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) !=
+            cudaSuccess)
+            return e;
+        attr[dev].store(true);
     }
     k_conv_wgrad<<<grid, 256, smem, s>>>(x, Cin, dy, Cout, W, H, taps, rows, dw, db);
     count_launch();

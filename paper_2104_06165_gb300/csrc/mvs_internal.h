@@ -81,6 +81,8 @@ int pm_group_lanes(int n_samples);
 // grid of a grid-stride kernel: `units` blocks of work, capped at the blocks
 // of `block` threads and `smem_bytes` shared memory that fit the device at once
 unsigned pm_grid_for(const void* kernel, long long units, size_t smem_bytes, int block);
+// error of this thread's last failed pm_grid_for query (cleared on read)
+cudaError_t pm_grid_error();
 
 struct FilterConst {
     int W, H;

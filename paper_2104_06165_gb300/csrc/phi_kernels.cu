@@ -663,7 +663,8 @@ cudaError_t launch_phi_cost(const RefConst& rc, const float* hyp, const uint8_t*
     MVS_DISPATCH(rc.n, CALL);
 #undef CALL
     count_launch();
-    return cudaGetLastError();
+    const cudaError_t g = pm_grid_error();
+    return g != cudaSuccess ? g : cudaGetLastError();
 }
 
 size_t phi_mrf_work_floats(int W, int H) {
@@ -688,19 +689,29 @@ cudaError_t launch_phi_mrf(int W, int H, const uint8_t* known, const float* dept
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // one block per strip, at most as many as are co-resident
-    static int max_blocks = 0;
+    // one block per strip, at most as many as are co-resident; the shared-
+    // memory opt-in and the occupancy belong to the current device
+    int max_blocks = 0;
     {
         static std::mutex mu;
+        static int per_dev[128] = {};
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
         std::lock_guard<std::mutex> lk(mu);
-        if (!max_blocks) {
-            int dev = 0, sms = 0, per_sm = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaFuncSetAttribute(k_trw_strips, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrwTileSm));
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trw_strips, kTrwBlock, sizeof(TrwTileSm));
-            max_blocks = std::max(1, sms * per_sm);
+        if (!per_dev[dev]) {
+            int sms = 0, per_sm = 0;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaFuncSetAttribute(k_trw_strips, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(TrwTileSm))) != cudaSuccess)
+                return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trw_strips, kTrwBlock,
+                                                                   sizeof(TrwTileSm))) != cudaSuccess)
+                return e;
+            if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+            per_dev[dev] = sms * per_sm;
         }
+        max_blocks = per_dev[dev];
     }
     const int want = (mb.gh + kTrwRows - 1) / kTrwRows;
     dim3 grid(std::max(1, std::min(want, max_blocks))), block(kTrwBlock);

@@ -4,6 +4,7 @@
 //   Sec. III-C  Eq. 4 weighted ZNCC, Eq. 5 aggregation, refinement
 //   Sec. III    red-black checkerboard updating
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <unordered_map>
 
@@ -426,32 +427,72 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
 // once (occupancy query, cached per kernel), at most one warp per unit
 }  // namespace
 
+namespace {
+thread_local cudaError_t t_grid_err = cudaSuccess;
+}
+
+// Launch-shape cache per (device, kernel): the SM count, the dynamic shared
+// memory opt-in and the occupancy query are all properties of the current
+// device.  A failed query leaves grid 0 (the launch then fails) and the
+// query's own error for pm_grid_error().
 unsigned pm_grid_for(const void* kernel, long long units, size_t smem, int block) {
     static std::mutex mu;
     struct Cfg { size_t smem; int block, per_sm; };
-    static std::unordered_map<const void*, Cfg> cache;   // kernel -> launch shape and blocks per SM
-    static int sms = 0;
-    int per_sm = 0;
+    static std::map<std::pair<int, const void*>, Cfg> cache;
+    static std::map<int, int> sms_of;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        t_grid_err = e;
+        return 0;
+    }
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (!sms) {
-            int dev = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        auto si = sms_of.find(dev);
+        if (si == sms_of.end()) {
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
+                t_grid_err = e;
+                return 0;
+            }
+            sms_of[dev] = sms;
+        } else {
+            sms = si->second;
         }
-        auto it = cache.find(kernel);
+        const auto key = std::make_pair(dev, kernel);
+        auto it = cache.find(key);
         if (it != cache.end() && it->second.smem == smem && it->second.block == block) {
             per_sm = it->second.per_sm;
         } else {
-            if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+            if (smem > 48 * 1024 &&
+                (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                    cudaSuccess) {
+                t_grid_err = e;
+                return 0;
+            }
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem)) != cudaSuccess) {
+                t_grid_err = e;
+                return 0;
+            }
             per_sm = std::max(per_sm, 1);
-            cache[kernel] = {smem, block, per_sm};
+            cache[key] = {smem, block, per_sm};
         }
     }
     long long need = units;   // blocks of work
     long long full = (long long)sms * per_sm;
     return (unsigned)std::max<long long>(1, std::min(need, full));
+}
+
+cudaError_t pm_grid_error() {
+    const cudaError_t e = t_grid_err;
+    t_grid_err = cudaSuccess;
+    return e;
+}
+
+// the error of the launch-shape queries of this thread, else of the launches
+static cudaError_t launch_status() {
+    const cudaError_t g = pm_grid_error();
+    const cudaError_t l = cudaGetLastError();
+    return g != cudaSuccess ? g : l;
 }
 
 // Lanes per pixel group (G) and slots per lane (S) for an n x n window:
@@ -504,7 +545,7 @@ cudaError_t prime_launch_configs(const RefConst& rc) {
         MVS_DISPATCH(rc.n, rc.lanes_hint, CALL);
     }
 #undef CALL
-    return cudaGetLastError();
+    return launch_status();
 }
 
 cudaError_t launch_build_texture(const uint8_t* img, int W, int H, uint2* tex, cudaStream_t s) {
@@ -530,7 +571,7 @@ cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s) {
     }
 #undef CALL
     count_launch();
-    return cudaGetLastError();
+    return launch_status();
 }
 
 cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, float* view_cost, cudaStream_t s) {
@@ -549,7 +590,7 @@ cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, fl
     }
 #undef CALL
     count_launch();
-    return cudaGetLastError();
+    return launch_status();
 }
 
 template <int G, int S, bool MX>
@@ -573,5 +614,5 @@ cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s) {
 #undef CALL
     }
     count_launch();
-    return cudaGetLastError();
+    return launch_status();
 }

@@ -28,22 +28,33 @@ def owner_of(assignment):
     return {v: r for r, views in enumerate(assignment) for v in views}
 
 
-def exchange_plane_maps(maps, shapes, assignment, group=None):
+def exchange_plane_maps(maps, shapes, assignment, group=None, device=None):
     """maps: {view: tensor (H, W, 4)} for the views this rank owns.
     Returns {view: tensor} for all views (own tensors kept, others received
-    by broadcast from their owner)."""
+    by broadcast from their owner).  Received tensors are allocated on
+    ``device`` when given, else on the device of this rank's own maps, else
+    on the current CUDA device under NCCL and on the CPU otherwise (a rank
+    may own no view).  ``assignment`` lists the views of each rank of
+    ``group`` by group rank."""
     import torch
     import torch.distributed as dist
     rank = dist.get_rank(group)
     own = owner_of(assignment)
+    if device is None:
+        if maps:
+            device = next(iter(maps.values())).device
+        elif dist.get_backend(group) == "nccl":
+            device = torch.device("cuda", torch.cuda.current_device())
+        else:
+            device = torch.device("cpu")
     out = {}
-    device = next(iter(maps.values())).device if maps else torch.device("cpu")
     for v in sorted(own):
         H, W = shapes[v]
         if own[v] == rank:
             t = maps[v].contiguous()
         else:
             t = torch.empty((H, W, 4), dtype=torch.float32, device=device)
-        dist.broadcast(t, src=own[v], group=group)
+        src = own[v] if group is None else dist.get_global_rank(group, own[v])
+        dist.broadcast(t, src=src, group=group)
         out[v] = t
     return out

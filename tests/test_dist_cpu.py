@@ -48,12 +48,15 @@ def _worker(rank, world, port, shapes, q):
         dist.destroy_process_group()
 
 
-def test_gloo_world2_exchange():
-    shapes = [(6, 8), (5, 7), (6, 8), (3, 4), (4, 4)]
+@pytest.mark.parametrize("world, shapes", [(2, [(6, 8), (5, 7), (6, 8), (3, 4), (4, 4)]),
+                                           (3, [(6, 8), (5, 7)])])
+def test_gloo_exchange(world, shapes):
+    """World 2 with five views, and world 3 with two views (one rank owns
+    none and receives both)."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, shapes, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, shapes, q)) for r in range(world)]
     for p in procs:
         p.start()
     res = [q.get(timeout=120) for _ in procs]
@@ -63,3 +66,38 @@ def test_gloo_world2_exchange():
     for rank, ok, views in res:
         assert ok and views == list(range(len(shapes)))
     assert set(owner_of(assign_views([48, 35, 48, 12, 16], 2)).values()) == {0, 1}
+
+
+def _sub_worker(rank, world, port, shapes, q):
+    """Ranks 1 and 2 of a world of 3 exchange in a subgroup: the owner's
+    group rank is mapped to its global rank for the broadcast."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        g = dist.new_group([1, 2])
+        if rank in (1, 2):
+            parts = assign_views([h * w for h, w in shapes], 2)
+            gr = dist.get_rank(g)
+            mine = {v: torch.full(shapes[v] + (4,), float(10 * v + 1)) for v in parts[gr]}
+            allm = exchange_plane_maps(mine, shapes, parts, group=g)
+            ok = all(torch.equal(allm[v], torch.full(shapes[v] + (4,), float(10 * v + 1))) for v in range(len(shapes)))
+            q.put((rank, ok))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_subgroup_exchange():
+    shapes = [(6, 8), (5, 7), (4, 4)]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sub_worker, args=(r, 3, port, shapes, q)) for r in range(3)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(1, True), (2, True)]

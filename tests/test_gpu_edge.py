@@ -128,3 +128,30 @@ def test_many_sources_match_the_oracle(mvs_lib, oracle_lib, n_src):
     firm = (rel <= 1e-5) & (np.abs(pl[..., :3] - opl[..., :3]).max(-1) <= 1e-4)
     assert firm.mean() >= 0.95
     assert (np.abs(co - oco)[firm] <= 1e-4).mean() >= 0.995
+
+
+def test_contexts_on_two_devices_in_turn(mvs_lib):
+    """Launch shapes, shared-memory opt-ins and occupancy are per device: a
+    context on a second device, created after one on the first, runs the
+    phase kernels and the cooperative TRW-S pass of plane inference and
+    gives the first device's maps bit for bit."""
+    import torch
+    from paper_2104_06165_gb300 import scenes
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs")
+    sc = scenes.make_scene(W=96, H=72, n_src=3, seed=5, baseline_frac=0.1)
+    H, W = sc.images[0].shape
+    p = mvs_lib.PMParams(win_radius=5.0, win_samples=6, iters=1, seed=3)
+    out = []
+    for dev in (0, 1):
+        with torch.cuda.device(dev):
+            ctx = mvs_lib.Context(sc.K, sc.R, sc.t, sc.images, stream=torch.cuda.current_stream())
+            try:
+                pl = np.zeros((H, W, 4), np.float32)
+                co = np.zeros((H, W), np.float32)
+                mvs_lib.mvs_patchmatch(ctx.h, 0, [1, 2, 3], p, pl, co)
+                mvs_lib.mvs_plane_infer(ctx.h, 0, [1, 2, 3], p, mvs_lib.PhiParams(), None, pl, co)
+                out.append((pl, co))
+            finally:
+                ctx.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
