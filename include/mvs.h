@@ -450,6 +450,32 @@ mvs_status mvs_cnn_forward(mvs_cnn* net, const uint8_t* img, const float* plane,
 mvs_status mvs_cnn_backward(mvs_cnn* net, const uint8_t* img, const float* plane, const float* cost, int32_t W,
                             int32_t H, const float* target, const uint8_t* mask, float* loss_out);
 
+/* Stored tensors of the last mvs_cnn_forward / mvs_cnn_backward, for
+ * layer-by-layer checking (no counterpart in the paper).  Channels-last
+ * bfloat16 (raw 16-bit words), except MVS_CNN_T_HEAD (fp32), at the size of
+ * the last call: level l holds (W >> l) x (H >> l) pixels.
+ *   MVS_CNN_T_INPUT       level 0, 16 channels (network input)
+ *   MVS_CNN_T_ENC         e_l, l = 0..4 (32, 48, 64, 96, 128 channels)
+ *   MVS_CNN_T_POOL        avgpool2(e_l) at level l + 1, l = 0..3
+ *   MVS_CNN_T_CAT         [up2(d_{l+1} or e_4) | e_l], l = 0..3
+ *                         (224, 160, 112, 80 channels for l = 3..0)
+ *   MVS_CNN_T_DEC         d_l, l = 0..3 (32, 48, 64, 96 channels)
+ *   MVS_CNN_T_HEAD        head output, level 0, 16 fp32 channels
+ *   MVS_CNN_T_GRAD_HEAD   d loss / d head output rounded to bf16
+ *   MVS_CNN_T_GRAD_DEC    d loss / d (pre-ReLU) d_l, l = 0..3
+ *   MVS_CNN_T_GRAD_CAT    d loss / d cat_l, l = 0..3
+ *   MVS_CNN_T_GRAD_ENC    d loss / d (pre-ReLU) e_l, l = 0..4
+ *   MVS_CNN_T_GRAD_POOL   d loss / d pool_l (before the pooling's backward)
+ * host_out receives `bytes` bytes, which must equal the tensor's size.
+ * The call synchronises.  Errors: MVS_EINVAL (no such tensor, size
+ * mismatch, no call yet), MVS_ECUDA. */
+enum {
+    MVS_CNN_T_INPUT = 0, MVS_CNN_T_ENC = 1, MVS_CNN_T_POOL = 2, MVS_CNN_T_CAT = 3, MVS_CNN_T_DEC = 4,
+    MVS_CNN_T_HEAD = 5, MVS_CNN_T_GRAD_HEAD = 6, MVS_CNN_T_GRAD_DEC = 7, MVS_CNN_T_GRAD_CAT = 8,
+    MVS_CNN_T_GRAD_ENC = 9, MVS_CNN_T_GRAD_POOL = 10
+};
+mvs_status mvs_cnn_read(mvs_cnn* net, int32_t tensor, int32_t level, void* host_out, int64_t bytes);
+
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with
  * learning rate lr on the gradients of the last mvs_cnn_backward. */
 mvs_status mvs_cnn_adam_step(mvs_cnn* net, float lr);

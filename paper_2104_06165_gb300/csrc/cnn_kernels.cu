@@ -389,6 +389,7 @@ struct mvs_cnn {
     float* gy = nullptr;
     float* loss = nullptr;
     int steps = 0;
+    int lastW = 0, lastH = 0;      // size of the last forward pass
     std::string err;
     std::vector<void*> allocs;
 };
@@ -750,6 +751,8 @@ static mvs_status run_forward(mvs_cnn* n, const uint8_t* img, const float4* plan
     count_launch();
     CNK(n, cudaGetLastError());
     CNK(n, cnn_forward(n, W, H));
+    n->lastW = W;
+    n->lastH = H;
     return MVS_OK;
 }
 
@@ -791,6 +794,37 @@ mvs_status mvs_cnn_propose(mvs_cnn* n, const uint8_t* img, const float* plane, c
     if (((uintptr_t)plane & 15u) || ((uintptr_t)cost & 3u) || ((uintptr_t)proposals & 15u))
         return cnn_fail(n, MVS_EINVAL, "plane and proposals must be 16-byte, cost 4-byte aligned");
     CNK(n, cnn_propose(n, img, (const float4*)plane, cost, W, H, Kinv, (float4*)proposals, n->stream));
+    return MVS_OK;
+}
+
+mvs_status mvs_cnn_read(mvs_cnn* n, int32_t tensor, int32_t level, void* host_out, int64_t bytes) {
+    if (!n || !host_out) return MVS_EINVAL;
+    if (!n->lastW) return cnn_fail(n, MVS_EINVAL, "no forward pass yet");
+    const void* src = nullptr;
+    int ch = 0, lv = level;
+    size_t elem = sizeof(bf16);
+    auto in_range = [&](int hi) { return level >= 0 && level <= hi; };
+    switch (tensor) {
+        case MVS_CNN_T_INPUT: if (level == 0) { src = n->x; ch = 16; } break;
+        case MVS_CNN_T_ENC: if (in_range(4)) { src = n->e[level]; ch = kLayerCout[E0 + level]; } break;
+        case MVS_CNN_T_POOL: if (in_range(3)) { src = n->p[level]; ch = kLayerCout[E0 + level]; lv = level + 1; } break;
+        case MVS_CNN_T_CAT: if (in_range(3)) { src = n->c[level]; ch = kLayerCin[D3 + (3 - level)]; } break;
+        case MVS_CNN_T_DEC: if (in_range(3)) { src = n->d[level]; ch = kLayerCout[D3 + (3 - level)]; } break;
+        case MVS_CNN_T_HEAD: if (level == 0) { src = n->y; ch = 16; elem = sizeof(float); } break;
+        case MVS_CNN_T_GRAD_HEAD: if (level == 0) { src = n->gyb; ch = 16; } break;
+        case MVS_CNN_T_GRAD_DEC: if (in_range(3)) { src = n->gd[level]; ch = kLayerCout[D3 + (3 - level)]; } break;
+        case MVS_CNN_T_GRAD_CAT: if (in_range(3)) { src = n->gc[level]; ch = kLayerCin[D3 + (3 - level)]; } break;
+        case MVS_CNN_T_GRAD_ENC: if (in_range(4)) { src = n->ge[level]; ch = kLayerCout[E0 + level]; } break;
+        case MVS_CNN_T_GRAD_POOL:
+            if (in_range(3)) { src = n->gp[level]; ch = kLayerCout[E0 + level]; lv = level + 1; }
+            break;
+        default: break;
+    }
+    if (!src) return cnn_fail(n, MVS_EINVAL, "no such tensor");
+    const size_t need = (size_t)(n->lastW >> lv) * (size_t)(n->lastH >> lv) * ch * elem;
+    if ((int64_t)need != bytes) return cnn_fail(n, MVS_EINVAL, "size mismatch");
+    CNK(n, cudaMemcpyAsync(host_out, src, need, cudaMemcpyDeviceToHost, n->stream));
+    CNK(n, cudaStreamSynchronize(n->stream));
     return MVS_OK;
 }
 

@@ -21,6 +21,11 @@ MVS_OK, MVS_EINVAL, MVS_ENOMEM, MVS_ECUDA, MVS_ETIMEOUT, MVS_ESTATE, MVS_EUNSUPP
 MVS_MEM_DEVICE, MVS_MEM_HOST = 0, 1
 MVS_INIT_RANDOM, MVS_INIT_GIVEN, MVS_INIT_GIVEN_RECOST, MVS_INIT_RANGE = 0, 1, 2, 3
 MVS_PHI_SELECT_MRF, MVS_PHI_SELECT_MIN_COST = 0, 1
+(MVS_CNN_T_INPUT, MVS_CNN_T_ENC, MVS_CNN_T_POOL, MVS_CNN_T_CAT, MVS_CNN_T_DEC, MVS_CNN_T_HEAD, MVS_CNN_T_GRAD_HEAD,
+ MVS_CNN_T_GRAD_DEC, MVS_CNN_T_GRAD_CAT, MVS_CNN_T_GRAD_ENC, MVS_CNN_T_GRAD_POOL) = range(11)
+_CNN_ENC_CH = (32, 48, 64, 96, 128)
+_CNN_DEC_CH = (32, 48, 64, 96)
+_CNN_CAT_CH = (80, 112, 160, 224)
 STATUS_NAMES = ["MVS_OK", "MVS_EINVAL", "MVS_ENOMEM", "MVS_ECUDA", "MVS_ETIMEOUT", "MVS_ESTATE",
                 "MVS_EUNSUPPORTED"]
 
@@ -182,6 +187,8 @@ def load():
     L.mvs_cnn_forward.argtypes = [vp, u8p, fp, fp, i32, i32, fp]
     L.mvs_cnn_backward.restype = i32
     L.mvs_cnn_backward.argtypes = [vp, u8p, fp, fp, i32, i32, fp, u8p, C.POINTER(C.c_float)]
+    L.mvs_cnn_read.restype = i32
+    L.mvs_cnn_read.argtypes = [vp, i32, i32, vp, C.c_int64]
     L.mvs_cnn_adam_step.restype = i32
     L.mvs_cnn_adam_step.argtypes = [vp, C.c_float]
     L.mvs_cnn_propose.restype = i32
@@ -474,6 +481,29 @@ def mvs_cnn_get_grads(net):
     a = np.zeros(mvs_cnn_n_params(net), np.float32)
     _check_cnn(load().mvs_cnn_get_grads(net, a.ctypes.data), net)
     return a
+
+
+def mvs_cnn_read(net, tensor, level, W, H):
+    """A stored tensor of the last forward / backward pass at size W x H:
+    (H >> l, W >> l, channels) float32 (bf16 values widened exactly)."""
+    ch = {MVS_CNN_T_INPUT: 16, MVS_CNN_T_HEAD: 16, MVS_CNN_T_GRAD_HEAD: 16}.get(tensor)
+    lv = level
+    if tensor in (MVS_CNN_T_ENC, MVS_CNN_T_GRAD_ENC):
+        ch = _CNN_ENC_CH[level]
+    elif tensor in (MVS_CNN_T_POOL, MVS_CNN_T_GRAD_POOL):
+        ch, lv = _CNN_ENC_CH[level], level + 1
+    elif tensor in (MVS_CNN_T_CAT, MVS_CNN_T_GRAD_CAT):
+        ch = _CNN_CAT_CH[level]
+    elif tensor in (MVS_CNN_T_DEC, MVS_CNN_T_GRAD_DEC):
+        ch = _CNN_DEC_CH[level]
+    shape = (H >> lv, W >> lv, ch)
+    if tensor == MVS_CNN_T_HEAD:
+        a = np.zeros(shape, np.float32)
+        _check_cnn(load().mvs_cnn_read(net, tensor, level, a.ctypes.data, a.nbytes), net)
+        return a
+    a = np.zeros(shape, np.uint16)
+    _check_cnn(load().mvs_cnn_read(net, tensor, level, a.ctypes.data, a.nbytes), net)
+    return (a.astype(np.uint32) << 16).view(np.float32)
 
 
 def mvs_cnn_forward(net, img, plane, cost, out):
