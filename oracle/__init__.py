@@ -73,6 +73,7 @@ def lib():
             L.or_window_offsets.argtypes = [C.POINTER(_PM), dp]
             L.or_homography.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, dp, C.c_double, dp]
             L.or_plane_cost.argtypes = [vp, C.c_int, ip, C.c_int, C.POINTER(_PM), dp, dp, dp, dp]
+            L.or_window_extent.argtypes = [vp, C.c_int, ip, C.c_int, C.POINTER(_PM), dp, dp]
             L.or_wzncc.restype = C.c_double
             L.or_wzncc.argtypes = [C.c_int, dp, dp, dp]
             L.or_aggregate.restype = C.c_double
@@ -222,6 +223,18 @@ def plane_cost(scene, ref, srcs, p, plane, with_views=False):
     mg = np.zeros((H, W), np.float64)
     lib().or_plane_cost(scene.h, ref, _i(s), len(s), C.byref(_pm(p)), _d(pl), _d(cost), _d(vc), _d(mg))
     return (cost, vc, mg) if with_views else cost
+
+
+def window_extent(scene, ref, srcs, p, plane):
+    """Per pixel and source view, the extent (source pixels) of the window's
+    image under the pixel's plane (a comparison diagnostic; see
+    or_window_extent).  Returns (H, W, n_src)."""
+    H, W = scene.shape(ref)
+    s = _srcs(srcs)
+    pl = _f64(plane).reshape(H, W, 4)
+    ext = np.zeros((H, W, len(s)), np.float64)
+    lib().or_window_extent(scene.h, ref, _i(s), len(s), C.byref(_pm(p)), _d(pl), _d(ext))
+    return ext
 
 
 def cost_at(scene, ref, srcs, p, xs, ys, planes):

@@ -404,6 +404,49 @@ void or_plane_cost(const or_scene* s, int ref, const int* srcs, int ns, const or
     free(win);
 }
 
+/* Extent of each view's image of the window (a comparison diagnostic, not
+ * part of the method): for every pixel and source view, the largest
+ * distance max(|u_i - u_c|, |v_i - v_c|) in source pixels between the
+ * projection of an included window sample and that of the pixel itself,
+ * under the pixel's plane; 0 when the plane is not usable there or a sample
+ * falls behind the source.  An implementation that evaluates the samples
+ * relative to the projected centre in single precision carries position
+ * errors proportional to this extent.  extent = H*W*ns. */
+void or_window_extent(const or_scene* s, int ref, const int* srcs, int ns, const or_pm* p, const double* plane,
+                      double* extent) {
+    const or_view* V = &s->v[ref];
+    or_window* win = (or_window*)malloc(sizeof(or_window));
+    for (int y = 0; y < V->H; ++y)
+        for (int x = 0; x < V->W; ++x) {
+            long i = (long)y * V->W + x;
+            ref_window(s, ref, p, x, y, win);
+            const double* n = plane + 4 * i;
+            const double d = plane[4 * i + 3];
+            const int usable = hyp_valid(s, ref, x, y, n, d, win);
+            for (int j = 0; j < ns; ++j) {
+                double e = 0.0;
+                if (usable) {
+                    double Hm[9], c[3], q[3];
+                    const double xc[3] = {(double)x, (double)y, 1.0};
+                    or_homography(s, ref, srcs[j], x, y, n, d, Hm);
+                    m3_vec(Hm, xc, c);
+                    for (int k = 0; k < win->m; ++k) {
+                        const double et[3] = {x + win->ou[k], y + win->ov[k], 1.0};
+                        m3_vec(Hm, et, q);
+                        if (!(q[2] > 0.0) || !(c[2] > 0.0)) {
+                            e = 0.0;
+                            break;
+                        }
+                        const double du = fabs(q[0] / q[2] - c[0] / c[2]), dv = fabs(q[1] / q[2] - c[1] / c[2]);
+                        e = fmax(e, fmax(du, dv));
+                    }
+                }
+                extent[(long)ns * i + j] = e;
+            }
+        }
+    free(win);
+}
+
 /* weighted ZNCC of two given patches (Eq. 4 with weights); for tests */
 double or_wzncc(int m, const double* w, const double* a, const double* b) {
     double sw = 0, sa = 0, sb = 0;

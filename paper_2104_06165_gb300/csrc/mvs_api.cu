@@ -22,6 +22,8 @@ struct ViewData {
     uint2* tex = nullptr;      // bilinear-coefficient texels (fp16 x 4)
     float4* plane = nullptr;   // depth map state (library-owned)
     float* cost = nullptr;
+    uint32_t* memo = nullptr;  // per pixel: candidates scored at the last visit (RefConst::memo)
+    uint32_t* gen = nullptr;   // per pixel: plane generation (RefConst::gen)
     bool has_map = false;
 };
 
@@ -201,6 +203,8 @@ void make_refconst(const mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n
     rc.init_range = p->init_mode == MVS_INIT_RANGE ? reinterpret_cast<const float2*>(p->init_range) : nullptr;
     rc.plane = R.plane;
     rc.cost = R.cost;
+    rc.memo = R.memo;
+    rc.gen = R.gen;
     for (int j = 0; j < n_src; ++j) {
         const ViewData& S = c->views[srcs[j]];
         double Rr[9], tr[3], T[9], A[9];
@@ -208,9 +212,21 @@ void make_refconst(const mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n
         m3_mul(S.cam.K, Rr, T);
         m3_mul(T, R.Kinv, A);
         PairConst& P = rc.pair[j];
-        for (int i = 0; i < 9; ++i) P.A[i] = (float)A[i];
-        for (int a = 0; a < 3; ++a)
-            P.b[a] = (float)(S.cam.K[3 * a] * tr[0] + S.cam.K[3 * a + 1] * tr[1] + S.cam.K[3 * a + 2] * tr[2]);
+        double b[3];
+        for (int a = 0; a < 3; ++a) b[a] = S.cam.K[3 * a] * tr[0] + S.cam.K[3 * a + 1] * tr[1] + S.cam.K[3 * a + 2] * tr[2];
+        // doubled, half-shifted rows (see PairConst), split into hi + lo floats
+        auto split = [](double v, float& hi, float& lo) {
+            hi = (float)v;
+            lo = (float)(v - (double)hi);
+        };
+        for (int k = 0; k < 3; ++k) {
+            split(2.0 * A[k] - A[6 + k], P.Gh[k], P.Gl[k]);
+            split(2.0 * A[3 + k] - A[6 + k], P.Gh[3 + k], P.Gl[3 + k]);
+            split(A[6 + k], P.Gh[6 + k], P.Gl[6 + k]);
+        }
+        split(2.0 * b[0] - b[2], P.Bh[0], P.Bl[0]);
+        split(2.0 * b[1] - b[2], P.Bh[1], P.Bl[1]);
+        split(b[2], P.Bh[2], P.Bl[2]);
         P.tex = S.tex;
         P.W = S.cam.width;
         P.H = S.cam.height;
@@ -225,6 +241,9 @@ mvs_status ensure_map(mvs_ctx* c, int32_t v) {
     size_t n = (size_t)V.cam.width * V.cam.height;
     CK(c, cudaMalloc(&V.plane, n * sizeof(float4)));
     CK(c, cudaMalloc(&V.cost, n * sizeof(float)));
+    CK(c, cudaMalloc(&V.memo, n * MVS_MEMO_WORDS * sizeof(uint32_t)));
+    CK(c, cudaMalloc(&V.gen, n * sizeof(uint32_t)));
+    CK(c, cudaMemsetAsync(V.gen, 0, n * sizeof(uint32_t), c->stream));
     return MVS_OK;
 }
 
@@ -300,6 +319,8 @@ void mvs_destroy(mvs_ctx* c) {
         cudaFree(V.tex);
         cudaFree(V.plane);
         cudaFree(V.cost);
+        cudaFree(V.memo);
+        cudaFree(V.gen);
     }
     for (auto& s : c->scratch) cudaFree(s.p);
     for (auto e : c->ev) cudaEventDestroy(e);
@@ -349,6 +370,7 @@ mvs_status mvs_patchmatch(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t 
     }
     RefConst rcp = rc;
     if (c->prof) rcp.eval_counter = c->evals;
+    CK(c, launch_memo_reset(rc, c->stream));
     for (int ph = p->phase_begin; ph < pend; ++ph) {
         if (c->prof) {
             while (c->ev.size() < c->ev_used + 2) {
@@ -411,6 +433,7 @@ static mvs_status autotune_lanes(mvs_ctx* c, int32_t ref, const int32_t* srcs, i
             CK(c, cudaMemcpyAsync(V.cost, keep + n * sizeof(float4), n * sizeof(float), cudaMemcpyDeviceToDevice,
                                   c->stream));
             CK(c, cudaEventRecord(t0, c->stream));
+            CK(c, launch_memo_reset(rc, c->stream));
             for (int ph = 0; ph < 4; ++ph) CK(c, launch_phase(rc, ph, c->stream));
             CK(c, cudaEventRecord(t1, c->stream));
         }
@@ -493,6 +516,7 @@ mvs_status mvs_patchmatch_batch(mvs_ctx* c, int32_t n_ref, const int32_t* refs, 
                 e = launch_init(rcs[r], nullptr, c->gstream);
             else if (p->init_mode == MVS_INIT_GIVEN_RECOST)
                 e = launch_cost(rcs[r], rcs[r].plane, rcs[r].cost, nullptr, c->gstream);
+            if (e == cudaSuccess) e = launch_memo_reset(rcs[r], c->gstream);
             for (int ph = p->phase_begin; ph < pend && e == cudaSuccess; ++ph) e = launch_phase(rcs[r], ph, c->gstream);
         }
         cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);

@@ -6,15 +6,24 @@
 
 #define MVS_MAX_SRC 32
 #define MVS_MAX_WIN 22
+#define MVS_MEMO_WORDS 9
 
 // One source view as seen from a reference view.
-//   A = K_j R_rel K_ref^-1, b = K_j t_rel (row-major, float, computed in double
-//   on the host), so that the plane-induced homography of a plane (n, d) at
-//   reference pixel x is H = A + b m^T with m = K_ref^-T n / rho,
-//   rho = d n.K_ref^-1 x  (Sec. III-C homography mapping).
+//   A = K_j R_rel K_ref^-1, b = K_j t_rel, so that the plane-induced
+//   homography of a plane (n, d) at reference pixel x is H = A + b m^T with
+//   m = K_ref^-T n / rho, rho = d n.K_ref^-1 x (Sec. III-C homography
+//   mapping), and m^T x = 1 / d at the pixel itself.  Kernels work in
+//   doubled, half-shifted source coordinates xs2 = 2 u - 1, ys2 = 2 v - 1 of
+//   a source point (u, v) = (q_x, q_y) / q_z, q = H x, i.e. with the rows
+//     G = (2 A_0 - A_2, 2 A_1 - A_2, A_2),  B = (2 b_0 - b_2, 2 b_1 - b_2, b_2):
+//   (xs2, ys2) = (G_0 x + B_0 m^T x, G_1 x + B_1 m^T x) / (G_2 x + B_2 m^T x).
+//   Each entry is held as an unevaluated sum hi + lo of floats that equals its
+//   double value (computed on the host) to about 2^-48 relative, so that the
+//   kernels can evaluate source positions to far below a float ulp of an
+//   image coordinate.
 struct PairConst {
-    float A[9];
-    float b[3];
+    float Gh[9], Gl[9];  // G row-major, hi and lo parts
+    float Bh[3], Bl[3];  // B, hi and lo parts
     const uint2* tex;    // bilinear-coefficient texels of the source, see below
     int W, H;            // source image size
     int pitch;           // texel row pitch = W + 1
@@ -40,6 +49,17 @@ struct RefConst {
     unsigned long long seed;
     float4* plane;             // state: (n.x, n.y, n.z, depth) per pixel
     float* cost;               // state: aggregated cost per pixel
+    // Candidate memo of the checkerboard phases (exact work skipping): per
+    // pixel MVS_MEMO_WORDS words, word g < 8 the key (member << 28 | plane
+    // generation of that member) of the plane propagation group g offered
+    // at the pixel's last visit, word 8 the mask of learned proposals scored
+    // so far; all ones = nothing recorded.  gen: per pixel, a counter bumped
+    // whenever the pixel's plane changes.  A pixel's cost never rises, so a
+    // plane it scored (or found equal to a scored one) at an earlier visit of
+    // the same call cannot be strictly cheaper now: such candidates are not
+    // scored again, and the results are the same as without the memo.
+    uint32_t* memo;
+    uint32_t* gen;
     unsigned long long* eval_counter;  // measurement: evaluated (pixel, hypothesis, view) triples, or null
     int lanes_hint;            // lanes per pixel group (0 = default)
     int precision;             // 0 = FP32, 1 = mixed (half2 bilinear, FP32 moments)
@@ -48,6 +68,7 @@ struct RefConst {
     const float2* init_range;  // H*W (d_min, d_max) of the sparse-feature initialisation (NaN: none), or null
     PairConst pair[MVS_MAX_SRC];
 };
+static_assert(sizeof(RefConst) <= 4096, "RefConst is passed as a kernel parameter (4 KB)");
 
 // Bilinear-coefficient texel layout.  Texel (i, j), i in [-1, W-1],
 // j in [-1, H-1], stored at ((j + 1) * (W + 1) + (i + 1)), holds four fp16
@@ -76,6 +97,8 @@ cudaError_t launch_build_texture(const uint8_t* img, int W, int H, uint2* tex, c
 cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s);
 cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, float* view_cost, cudaStream_t s);
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s);
+// clears the candidate memo of rc's view (before the first phase of a call)
+cudaError_t launch_memo_reset(const RefConst& rc, cudaStream_t s);
 cudaError_t prime_launch_configs(const RefConst& rc);
 int pm_group_lanes(int n_samples);
 // grid of a grid-stride kernel: `units` blocks of work, capped at the blocks

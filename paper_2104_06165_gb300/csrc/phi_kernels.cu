@@ -224,8 +224,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_phi_cost(const __grid_constant__ 
         float h = lane < 4 ? hyp[4 * a + lane] : 1.0f;
         float c = kCmax;
         if (pw.ok) {
+            PixView* pv = warp_pixviews(smem, rc.n_src, warp);
+            pix_views(rc, views, px, py, pv);
             Cand my = make_cand(rc, pw, pw.geo, 0.0f, 0.0f, -1.0f, h, v);
-            c = eval_batch<G, S, false>(rc, views, pw, pw.geo, px, py, my, 4, warp_pairs(smem, rc.n_src, warp), nullptr,
+            c = eval_batch<G, S, false>(rc, views, pw, pw.geo, pv, my, 4, warp_pairs(smem, rc.n_src, warp), nullptr,
                                         nev);
         }
         if (lane < 4) hcost[4 * a + lane] = v ? c : kCmax;

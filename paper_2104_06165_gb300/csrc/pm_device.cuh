@@ -87,16 +87,19 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 }
 
 // Four times the bilinear value of a coefficient texture at (x + 1/2, y + 1/2)
-// given xs2 = 2x, ys2 = 2y (the caller folds the shift and the factor 2 into
-// its homography).  Adding 1.5 * 2^24 rounds 2x to the nearest even integer
-// 2i, so U = 2x - 2i lies in [-1, 1] and the bits of the sum give i.  The
-// texel index is clamped into the array, so any input (even NaN) reads
-// inside the buffer.
-__device__ __forceinline__ float tex_sample(const uint2* __restrict__ tex, int pitch, uint32_t n_tex, float xs2,
-                                            float ys2) {
-    float tx = __fadd_rn(xs2, kMagic2), ty = __fadd_rn(ys2, kMagic2);
-    float U = __fsub_rn(xs2, __fsub_rn(tx, kMagic2));
-    float V = __fsub_rn(ys2, __fsub_rn(ty, kMagic2));
+// given the doubled coordinates 2x = rx + ax, 2y = ry + ay, split into a small
+// part (rx, ry) and an even integer (ax, ay) passed as 1.5 * 2^24 + ax (the
+// caller folds the shift by 1/2 and the factor 2 into its coordinates).
+// Adding the magic number rounds 2x to the nearest even integer 2i in one
+// FMA-free add, so U = 2x - 2i lies in [-1, 1] and the bits of the sum give
+// i; carrying the large integer part in the magic number keeps rx, and with
+// it U, exact to a float ulp of a small number.  The texel index is clamped
+// into the array, so any input (even NaN) reads inside the buffer.
+__device__ __forceinline__ float tex_sample(const uint2* __restrict__ tex, int pitch, uint32_t n_tex, float rx,
+                                            float ry, float mag_x, float mag_y) {
+    float tx = __fadd_rn(rx, mag_x), ty = __fadd_rn(ry, mag_y);
+    float U = __fadd_rn(rx, __fsub_rn(mag_x, tx));
+    float V = __fadd_rn(ry, __fsub_rn(mag_y, ty));
     uint32_t idx = (uint32_t)__float_as_int(ty) * (uint32_t)pitch + (uint32_t)__float_as_int(tx) +
                    (uint32_t)(pitch + 1) * (uint32_t)(1 - kMagic2Bits);
     idx = min(idx, n_tex - 1u);
@@ -104,6 +107,50 @@ __device__ __forceinline__ float tex_sample(const uint2* __restrict__ tex, int p
     float2 ab = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
     float2 cd = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
     return fmaf(V, fmaf(U, cd.y, cd.x), fmaf(U, ab.y, ab.x));
+}
+
+// Error-free transformations (Knuth's TwoSum, the FMA TwoProduct) for the
+// double-float evaluation of source positions; the _rn intrinsics keep the
+// compiler from contracting or reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (h0 + l0) x + (h1 + l1) y + (h2 + l2) as hi + lo for integers x, y < 2^24:
+// the large products and sums are carried exactly, the lo parts and the
+// rounding errors are summed in float.
+__device__ __forceinline__ void df_affine(float h0, float h1, float h2, float l0, float l1, float l2, float x,
+                                          float y, float& hi, float& lo) {
+    const float p0 = __fmul_rn(h0, x), e0 = fmaf(h0, x, -p0);
+    const float p1 = __fmul_rn(h1, y), e1 = fmaf(h1, y, -p1);
+    float s, es, s2, es2;
+    two_sum(p0, p1, s, es);
+    two_sum(s, h2, s2, es2);
+    const float rest = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(es, es2)), fmaf(l0, x, fmaf(l1, y, l2)));
+    hi = __fadd_rn(s2, rest);
+    lo = __fsub_rn(rest, __fsub_rn(hi, s2));
+}
+
+// Numerator of an anchored source coordinate: (g - a gz) + (B - a Bz) / d,
+// for g, gz, B, Bz given as hi + lo, an integer a (|a| < 2^15) and the
+// depth d with invd ~ 1/d.  g - a gz and B - a Bz are carried exactly as
+// sums (TwoProduct, TwoSum); their large parts cancel against each other
+// (the anchor sits next to the projection), and B / d is split as q + r / d
+// with the exact remainder r = B - q d, so the result is accurate to a few
+// ulps of itself.
+__device__ __forceinline__ float anchored_num(float gh, float gl, float gzh, float gzl, float Bh, float Bl,
+                                              float Bzh, float Bzl, float a, float d, float invd) {
+    float s, es, sb, esb;
+    const float p = __fmul_rn(a, gzh), ep = fmaf(a, gzh, -p);
+    two_sum(gh, -p, s, es);
+    const float tl = __fsub_rn(__fadd_rn(__fsub_rn(es, ep), gl), __fmul_rn(a, gzl));
+    const float pb = __fmul_rn(a, Bzh), epb = fmaf(a, Bzh, -pb);
+    two_sum(Bh, -pb, sb, esb);
+    const float bl = __fsub_rn(__fadd_rn(__fsub_rn(esb, epb), Bl), __fmul_rn(a, Bzl));
+    const float q = __fmul_rn(sb, invd), r = fmaf(-q, d, sb);
+    return __fadd_rn(__fadd_rn(s, q), fmaf(__fadd_rn(r, bl), invd, tl));
 }
 
 // The warp-uniform part of one pixel's window: the corners of the included
@@ -165,7 +212,8 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
         float ou = rc.step * ((float)ku - half), ov = rc.step * ((float)kv - half);
         float r = 0.0f, w = 0.0f;
         if (in) {
-            r = tex_sample(rc.tex, rc.pitch, rc.n_tex, 2.0f * ((float)px + ou) - 1.0f, 2.0f * ((float)py + ov) - 1.0f);
+            r = tex_sample(rc.tex, rc.pitch, rc.n_tex, fmaf(2.0f, ou, -1.0f), fmaf(2.0f, ov, -1.0f),
+                           kMagic2 + 2.0f * (float)px, kMagic2 + 2.0f * (float)py);
             float dc = r - rcen;
             w = __expf(fmaf(rc.sp_coef, ou * ou + ov * ov, rc.col_coef * dc * dc));
         }
@@ -209,37 +257,76 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
     g.rlen = sqrtf(g.rx0 * g.rx0 + g.rx1 * g.rx1 + g.rx2 * g.rx2);
 }
 
-// Source-view constants copied to shared memory once per block (80 bytes,
-// read as 16-byte words).
+// Source-view constants copied to shared memory once per block (128 bytes,
+// read as 16-byte words): the texture, and the doubled, half-shifted
+// homography rows G and B of PairConst with their hi and lo parts.
 struct __align__(16) ViewSm {
     const uint2* tex;
     // index of texel (i + 1, j + 1) = bits(1.5 * 2^24 + 2 j) * pitch
     // + bits(1.5 * 2^24 + 2 i) + toff (mod 2^32), see tex_sample
     uint32_t pitch, toff;
     uint32_t last, pad_;  // last texel index (W + 1) (H + 1) - 1
-    float wm1, hm1;       // W - 1, H - 1
-    float A[9];
-    float b[3];
+    float xmax2, ymax2;   // 2 W - 3, 2 H - 3: doubled, half-shifted image bounds
+    float gx0, gx1, gy0, gy1;   // G_0, G_1 columns 0 and 1 (hi)
+    float gz0, gz1, bxh, byh;   // G_2 columns 0 and 1 (hi); B_0, B_1 (hi)
+    float bzh, bxl, byl, bzl;   // B_2 (hi); B (lo)
+    float gx2, gy2, gz2, gz2l;  // column 2 of G (hi), G_2 column 2 (lo)
+    float gx0l, gx1l, gx2l, gy0l;
+    float gy1l, gy2l, gz0l, gz1l;
 };
 
-static_assert(sizeof(ViewSm) == 80 && offsetof(ViewSm, pitch) == 8 && offsetof(ViewSm, toff) == 12 &&
-                  offsetof(ViewSm, last) == 16 && offsetof(ViewSm, wm1) == 24 && offsetof(ViewSm, A) == 32 &&
-                  offsetof(ViewSm, b) == 68,
-              "eval_batch reads ViewSm as 128-bit words");
+static_assert(sizeof(ViewSm) == 128 && offsetof(ViewSm, pitch) == 8 && offsetof(ViewSm, toff) == 12 &&
+                  offsetof(ViewSm, last) == 16 && offsetof(ViewSm, xmax2) == 24 && offsetof(ViewSm, gx0) == 32 &&
+                  offsetof(ViewSm, gz0) == 48 && offsetof(ViewSm, bzh) == 64 && offsetof(ViewSm, gx2) == 80 &&
+                  offsetof(ViewSm, gx0l) == 96 && offsetof(ViewSm, gy1l) == 112,
+              "eval_batch and pix_views read ViewSm as 128-bit words");
 
 __device__ __forceinline__ void load_views(const RefConst& rc, ViewSm* sv) {
     for (int j = threadIdx.x; j < rc.n_src; j += blockDim.x) {
         const PairConst& P = rc.pair[j];
-        for (int i = 0; i < 9; ++i) sv[j].A[i] = P.A[i];
-        for (int i = 0; i < 3; ++i) sv[j].b[i] = P.b[i];
-        sv[j].wm1 = (float)(P.W - 1);
-        sv[j].hm1 = (float)(P.H - 1);
-        sv[j].pitch = (uint32_t)P.pitch;
-        sv[j].last = P.n_tex - 1u;
-        sv[j].tex = P.tex;
-        sv[j].toff = (uint32_t)(P.pitch + 1) * (uint32_t)(1 - kMagic2Bits);
+        ViewSm& v = sv[j];
+        v.tex = P.tex;
+        v.pitch = (uint32_t)P.pitch;
+        v.toff = (uint32_t)(P.pitch + 1) * (uint32_t)(1 - kMagic2Bits);
+        v.last = P.n_tex - 1u;
+        v.pad_ = 0u;
+        v.xmax2 = (float)(2 * P.W - 3);
+        v.ymax2 = (float)(2 * P.H - 3);
+        v.gx0 = P.Gh[0]; v.gx1 = P.Gh[1]; v.gx2 = P.Gh[2];
+        v.gy0 = P.Gh[3]; v.gy1 = P.Gh[4]; v.gy2 = P.Gh[5];
+        v.gz0 = P.Gh[6]; v.gz1 = P.Gh[7]; v.gz2 = P.Gh[8];
+        v.gx0l = P.Gl[0]; v.gx1l = P.Gl[1]; v.gx2l = P.Gl[2];
+        v.gy0l = P.Gl[3]; v.gy1l = P.Gl[4]; v.gy2l = P.Gl[5];
+        v.gz0l = P.Gl[6]; v.gz1l = P.Gl[7]; v.gz2l = P.Gl[8];
+        v.bxh = P.Bh[0]; v.byh = P.Bh[1]; v.bzh = P.Bh[2];
+        v.bxl = P.Bl[0]; v.byl = P.Bl[1]; v.bzl = P.Bl[2];
     }
     __syncthreads();
+}
+
+// Per (reference pixel, source view): G x~ of the pixel (the source point at
+// infinite depth in doubled, half-shifted homogeneous coordinates) as hi + lo
+// floats, computed once per pixel by lane j for view j.
+struct __align__(16) PixView {
+    float gxh, gxl, gyh, gyl;
+    float gzh, gzl, pad0_, pad1_;
+};
+
+__device__ __forceinline__ void pix_views(const RefConst& rc, const ViewSm* __restrict__ sv, int px, int py,
+                                          PixView* pv) {
+    const int j = threadIdx.x & 31;
+    if (j < rc.n_src) {
+        const float4* w = reinterpret_cast<const float4*>(sv + j);
+        const float4 w2 = w[2], w3 = w[3], w5 = w[5], w6 = w[6], w7 = w[7];
+        const float x = (float)px, y = (float)py;
+        PixView r;
+        df_affine(w2.x, w2.y, w5.x, w6.x, w6.y, w6.z, x, y, r.gxh, r.gxl);
+        df_affine(w2.z, w2.w, w5.y, w6.w, w7.x, w7.y, x, y, r.gyh, r.gyl);
+        df_affine(w3.x, w3.y, w5.z, w7.z, w7.w, w5.w, x, y, r.gzh, r.gzl);
+        r.pad0_ = r.pad1_ = 0.0f;
+        pv[j] = r;
+    }
+    __syncwarp();
 }
 
 // A plane hypothesis held by one lane: (n, d), validity and the homography
@@ -266,6 +353,9 @@ __device__ __forceinline__ Cand make_cand(const RefConst& rc, const PixWin<S>& p
     bool corners = fmaf(g.cu_lo, k0, fmaf(g.cv_lo, k1, nr)) < 0.0f && fmaf(g.cu_hi, k0, fmaf(g.cv_lo, k1, nr)) < 0.0f &&
                    fmaf(g.cu_lo, k0, fmaf(g.cv_hi, k1, nr)) < 0.0f && fmaf(g.cu_hi, k0, fmaf(g.cv_hi, k1, nr)) < 0.0f;
     c.ok = want && pw.ok && d > 0.0f && d < 3.0e38f && nr < -kGraze * g.rlen && corners;
+    // approximate reciprocals: 1/d enters the anchored source positions
+    // only through a correction term of anchored_num's exact-remainder
+    // division, and m only through the window's (small) derivatives
     float inv_rho = c.ok ? rcp_approx(d * nr) : 0.0f;
     c.m0 = k0 * inv_rho;
     c.m1 = k1 * inv_rho;
@@ -274,27 +364,33 @@ __device__ __forceinline__ Cand make_cand(const RefConst& rc, const PixWin<S>& p
 }
 
 // One listed (hypothesis, view) pair in shared memory (three 16-byte
-// words): the homography columns H e1, H e2 and H x (x, y rows shifted by
-// -1/2 and doubled for tex_sample), the view, and after evaluation its
-// per-view cost C(x, j) (C_max when excluded), the hypothesis and the view.
+// words).  Its source positions are anchored: with (ax, ay) even integers
+// next to the doubled, half-shifted projection of the window centre, a
+// sample at offset (ou, ov) from the pixel lands at
+//   xs2 = ax + (nx + ou j0x + ov j1x) / (pz + ou h0z + ov h1z),
+//   ys2 = ay + (ny + ou j0y + ov j1y) / (pz + ou h0z + ov h1z),
+// so the float arithmetic per sample works on numbers of the size of the
+// window's image, not of the source image.  The record also holds the magic
+// numbers 1.5 * 2^24 + (ax, ay) of tex_sample and (hypothesis | view << 8).
 struct __align__(16) PairSm {
-    float h0x, h0y, h0z, h1x;
-    float h1y, h1z, p0x, p0y;
-    float p0z, res;
-    int c, j;
+    float j0x, j0y, h0z, j1x;
+    float j1y, h1z, nx, ny;
+    float pz, mx, my;
+    int cj;
 };
 
-static_assert(sizeof(PairSm) == 48 && offsetof(PairSm, h1y) == 16 && offsetof(PairSm, p0z) == 32 &&
-                  offsetof(PairSm, res) == 36 && offsetof(PairSm, c) == 40 && offsetof(PairSm, j) == 44,
+static_assert(sizeof(PairSm) == 48 && offsetof(PairSm, j1y) == 16 && offsetof(PairSm, pz) == 32 &&
+                  offsetof(PairSm, cj) == 44,
               "eval_batch reads and writes PairSm as 128-bit words");
 
 // Shared-memory bytes of a block: the view table and, per warp, room for
-// 8 hypotheses x n_src pairs followed by their 8 x n_src Eq. 5 weights.
+// 8 hypotheses x n_src pairs, their 8 x n_src Eq. 5 weights and the pixel's
+// n_src PixView records.
 __host__ __device__ constexpr size_t smem_views_bytes(int n_src) {
-    return ((size_t)n_src * sizeof(ViewSm) + 15) & ~(size_t)15;
+    return (size_t)n_src * sizeof(ViewSm);
 }
 __host__ __device__ constexpr size_t smem_warp_bytes(int n_src) {
-    return (size_t)8 * n_src * (sizeof(PairSm) + sizeof(float));   // 416 n_src: a multiple of 16
+    return (size_t)8 * n_src * (sizeof(PairSm) + sizeof(float)) + (size_t)n_src * sizeof(PixView);   // 448 n_src
 }
 __host__ __device__ constexpr size_t smem_block_bytes(int n_src, int warps) {
     return smem_views_bytes(n_src) + (size_t)warps * smem_warp_bytes(n_src);
@@ -302,6 +398,11 @@ __host__ __device__ constexpr size_t smem_block_bytes(int n_src, int warps) {
 // pair list of warp `warp` in a block's dynamic shared memory
 __device__ __forceinline__ PairSm* warp_pairs(unsigned char* smem, int n_src, int warp) {
     return reinterpret_cast<PairSm*>(smem + smem_views_bytes(n_src) + (size_t)warp * smem_warp_bytes(n_src));
+}
+// the PixView records of warp `warp`'s current pixel
+__device__ __forceinline__ PixView* warp_pixviews(unsigned char* smem, int n_src, int warp) {
+    return reinterpret_cast<PixView*>(smem + smem_views_bytes(n_src) + (size_t)warp * smem_warp_bytes(n_src) +
+                                      (size_t)8 * n_src * (sizeof(PairSm) + sizeof(float)));
 }
 
 // Two planes (n, depth at the pixel) equal up to float rounding (1e-6
@@ -317,8 +418,8 @@ __device__ __forceinline__ bool same_plane(const float4& a, const float4& b) {
 //   1. the (hypothesis, view) pairs of the usable hypotheses whose window
 //      maps inside the source image (corner test: the image of the window is
 //      convex, w > 0 included) are listed in `pairs` (per-warp shared memory,
-//      nc * n_src entries) in hypothesis-major, view-minor order, with their
-//      homography;
+//      nc * n_src entries) in view-major order, with their anchored
+//      homography (PairSm);
 //   2. each group of G lanes takes the next pair: S bilinear gathers per
 //      lane, the weighted mean, then the centred moments (group reductions),
 //      ZNCC (Eq. 4),
@@ -326,18 +427,20 @@ __device__ __forceinline__ bool same_plane(const float4& a, const float4& b) {
 //      1e-6 on the [0,1] scale (reading);
 //   3. lane c folds the per-view results of hypothesis c in view order
 //      (Eq. 5, weights 1/max(C, 1e-6)).
-// Must be called by all 32 lanes with the same nc (warp-uniform).
+// pv: the pixel's PixView records (pix_views).  Must be called by all 32
+// lanes with the same nc (warp-uniform); VIEWS (per-view costs out) needs
+// nc == 1.
 // OFF_SM: the window's sample offsets are read from shared memory, (ou, ov)
 // of slot k and lane-in-group lg at off_sm[k * G + lg] (pw.ou / pw.ov are not
 // read, so they need not stay in registers).
 template <int G, int S, bool VIEWS, bool MIXED = false, bool OFF_SM = false>
 __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __restrict__ sv, const PixWin<S>& pw,
-                                            const WinGeo& geo, int px, int py, const Cand& my, int nc, PairSm* pairs,
-                                            float* view_cost, unsigned& n_evals, const float2* off_sm = nullptr) {
+                                            const WinGeo& geo, const PixView* __restrict__ pv, const Cand& my, int nc,
+                                            PairSm* pairs, float* view_cost, unsigned& n_evals,
+                                            const float2* off_sm = nullptr) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
     const int V = rc.n_src;
-    const float x = (float)px, y = (float)py;
     // ---- 1. list the pairs that map inside the source images, over the
     // usable hypotheses only: lane r < nok holds the lane of the r-th one
     const unsigned okm = __ballot_sync(0xffffffffu, lane < nc && my.ok);
@@ -354,8 +457,13 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
     // view 1, ...): the groups of a round then gather from the same source,
     // usually around the same place (neighbouring planes).  Their Eq. 5
     // weights go to tab[hypothesis][view], so that each hypothesis still
-    // folds its views in view order.
+    // folds its views in view order; with VIEWS the per-view costs go to
+    // row 1 of the same table.
     float* tab = reinterpret_cast<float*>(pairs + 8 * V);
+    if (VIEWS) {
+        if (lane < V) tab[V + lane] = kCmax;
+        __syncwarp();
+    }
     const int P = nok * V;
     int count = 0;
     // floor(i / nok) = (i * ceil(2^16 / nok)) >> 16 exactly for i < 2^16 / nok
@@ -367,40 +475,50 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         int j = act ? (int)(((uint32_t)i * kmagic) >> 16) : 0;
         int cr = act ? i - j * nok : 0;
         int c = __shfl_sync(0xffffffffu, hyp_of, cr);
-        float m0 = __shfl_sync(0xffffffffu, my.m0, c);
-        float m1 = __shfl_sync(0xffffffffu, my.m1, c);
-        float invd = __shfl_sync(0xffffffffu, my.invd, c);
-        // the view record as 128-bit words: (wm1, hm1) in word 1, A and b in 2..4
+        const float m0 = __shfl_sync(0xffffffffu, my.m0, c);
+        const float m1 = __shfl_sync(0xffffffffu, my.m1, c);
+        const float invd = __shfl_sync(0xffffffffu, my.invd, c);
+        const float dd = __shfl_sync(0xffffffffu, my.d, c);
+        // the view record (ViewSm words 1..4) and the pixel's G x~ for view j
         const float4* vw = reinterpret_cast<const float4*>(sv + j);
         const float4 w1 = vw[1], w2 = vw[2], w3 = vw[3], w4 = vw[4];
-        const float A0 = w2.x, A1 = w2.y, A2 = w2.z, A3 = w2.w, A4 = w3.x, A5 = w3.y, A6 = w3.z, A7 = w3.w;
-        const float A8 = w4.x, b0 = w4.y, b1 = w4.z, b2 = w4.w;
-        float h0z = fmaf(b2, m0, A6), h1z = fmaf(b2, m1, A7);
-        float p0z = fmaf(b2, invd, fmaf(A6, x, fmaf(A7, y, A8)));
-        // coordinates shifted by -1/2 (tex_sample's convention)
-        float h0x = fmaf(-0.5f, h0z, fmaf(b0, m0, A0));
-        float h0y = fmaf(-0.5f, h0z, fmaf(b1, m0, A3));
-        float h1x = fmaf(-0.5f, h1z, fmaf(b0, m1, A1));
-        float h1y = fmaf(-0.5f, h1z, fmaf(b1, m1, A4));
-        float p0x = fmaf(-0.5f, p0z, fmaf(b0, invd, fmaf(A0, x, fmaf(A1, y, A2))));
-        float p0y = fmaf(-0.5f, p0z, fmaf(b1, invd, fmaf(A3, x, fmaf(A4, y, A5))));
+        const float4 g0 = reinterpret_cast<const float4*>(pv + j)[0];   // gxh, gxl, gyh, gyl
+        const float4 g1 = reinterpret_cast<const float4*>(pv + j)[1];   // gzh, gzl
+        // columns of H = A + b m^T (doubled, half-shifted rows) for offsets
+        // along x and y, and the window centre's homogeneous depth
+        const float h0z = fmaf(w4.x, m0, w3.x), h1z = fmaf(w4.x, m1, w3.y);
+        const float h0x = fmaf(w3.z, m0, w2.x), h1x = fmaf(w3.z, m1, w2.y);
+        const float h0y = fmaf(w3.w, m0, w2.z), h1y = fmaf(w3.w, m1, w2.w);
+        const float pz = fmaf(w4.x, invd, __fadd_rn(g1.x, g1.y));
+        // anchors: the centre's doubled coordinates rounded to even integers
+        // (clamped, so that a pair rejected below still computes finite values)
+        const float ipz = rcp_approx(pz);
+        const float xc = fmaf(w3.z, invd, g0.x) * ipz, yc = fmaf(w3.w, invd, g0.z) * ipz;
+        const float ax = fminf(fmaxf(__fsub_rn(__fadd_rn(xc, kMagic2), kMagic2), -4.0f), w1.z + 5.0f);
+        const float ay = fminf(fmaxf(__fsub_rn(__fadd_rn(yc, kMagic2), kMagic2), -4.0f), w1.w + 5.0f);
+        const float nx = anchored_num(g0.x, g0.y, g1.x, g1.y, w3.z, w4.y, w4.x, w4.w, ax, dd, invd);
+        const float ny = anchored_num(g0.z, g0.w, g1.x, g1.y, w3.w, w4.z, w4.x, w4.w, ay, dd, invd);
+        const float j0x = fmaf(-ax, h0z, h0x), j1x = fmaf(-ax, h1z, h1x);
+        const float j0y = fmaf(-ay, h0z, h0y), j1y = fmaf(-ay, h1z, h1y);
+        // every corner in front of the source and inside its image:
+        // doubled coordinates in [-1, 2W - 3] x [-1, 2H - 3]
         bool ok = act;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float cu = (k & 1) ? geo.cu_hi : geo.cu_lo, cv = (k & 2) ? geo.cv_hi : geo.cv_lo;
-            float cx = fmaf(cu, h0x, fmaf(cv, h1x, p0x));
-            float cy = fmaf(cu, h0y, fmaf(cv, h1y, p0y));
-            float cz = fmaf(cu, h0z, fmaf(cv, h1z, p0z));
+            float cx = fmaf(cu, j0x, fmaf(cv, j1x, nx));
+            float cy = fmaf(cu, j0y, fmaf(cv, j1y, ny));
+            float cz = fmaf(cu, h0z, fmaf(cv, h1z, pz));
             float icz = rcp_approx(cz);
             float xs = cx * icz, ys = cy * icz;
-            ok = ok && cz > 0.0f && xs >= -0.5f && xs <= w1.z - 0.5f && ys >= -0.5f && ys <= w1.w - 0.5f;
+            ok = ok && cz > 0.0f && xs >= -1.0f - ax && xs <= w1.z - ax && ys >= -1.0f - ay && ys <= w1.w - ay;
         }
         unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (ok) {   // stored with x and y doubled (tex_sample's convention)
+        if (ok) {
             float4* qw = reinterpret_cast<float4*>(pairs + count + __popc(m & ((1u << lane) - 1u)));
-            qw[0] = make_float4(2.0f * h0x, 2.0f * h0y, h0z, 2.0f * h1x);
-            qw[1] = make_float4(2.0f * h1y, h1z, 2.0f * p0x, 2.0f * p0y);
-            qw[2] = make_float4(p0z, 0.0f, __int_as_float(c), __int_as_float(j));
+            qw[0] = make_float4(j0x, j0y, h0z, j1x);
+            qw[1] = make_float4(j1y, h1z, nx, ny);
+            qw[2] = make_float4(pz, kMagic2 + ax, kMagic2 + ay, __int_as_float(c | (j << 8)));
         } else if (act) {
             tab[c * V + j] = 0.0f;   // view excluded for this hypothesis
         }
@@ -413,22 +531,24 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         bool has = it < count;
         const float4* qw = reinterpret_cast<const float4*>(pairs + (has ? it : 0));
         const float4 qa = qw[0], qb = qw[1], qc = qw[2];
-        const float h0x = qa.x, h0y = qa.y, h0z = qa.z, h1x = qa.w;
-        const float h1y = qb.x, h1z = qb.y, p0x = qb.z, p0y = qb.w, p0z = qc.x;
+        const float j0x = qa.x, j0y = qa.y, h0z = qa.z, j1x = qa.w;
+        const float j1y = qb.x, h1z = qb.y, nx = qb.z, ny = qb.w;
+        const float pz = qc.x, mx = qc.y, my_ = qc.z;
+        const int cj = __float_as_int(qc.w), pj = cj >> 8, pc = cj & 255;
         // view words 0 (texels, pitch, toff) and 1 (last texel)
-        const uint4 v0 = reinterpret_cast<const uint4*>(sv + __float_as_int(qc.w))[0];
-        const uint32_t v_last = reinterpret_cast<const uint4*>(sv + __float_as_int(qc.w))[1].x;
+        const uint4 v0 = reinterpret_cast<const uint4*>(sv + pj)[0];
+        const uint32_t v_last = reinterpret_cast<const uint4*>(sv + pj)[1].x;
         const uint2* v_tex = reinterpret_cast<const uint2*>(((unsigned long long)v0.y << 32) | v0.x);
         float sa = 0.0f, sb = 0.0f, se = 0.0f;
         float sval[S], c0 = 0.0f;   // mixed precision only: the samples and their shift
         if constexpr (!MIXED) {
-            // Sample k at doubled, half-shifted source coordinates (X/Z, Y/Z).
-            // One FMA rounds X/Z + 1.5 * 2^24 to the nearest even integer 2i
-            // (its bits give i), a second gives U = X/Z - 2i in [-1, 1]
-            // rounded once.  The texel index is clamped into the array: the
-            // listed window corners lie inside the source, but FP32 positions
-            // of other samples of a plane seen almost edge-on by the source
-            // need not.
+            // Sample k: anchored numerators (X, Y) and depth Z; one FMA adds
+            // X/Z to the pair's magic number 1.5 * 2^24 + ax, rounding to the
+            // nearest even integer 2i (its bits give i), a second gives
+            // U = ax + X/Z - 2i in [-1, 1] rounded once.  The texel index is
+            // clamped into the array: the listed window corners lie inside
+            // the source, but float positions of other samples of a plane
+            // seen almost edge-on by the source need not.
             const uint2* tex = v_tex;
             const uint32_t pitch = v0.z, toff = v0.w, last = v_last;
             // gathers in chunks of up to 8 slots (registers); the intensities
@@ -446,13 +566,13 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                     const int k = k0 + kk;
                     if (k < S) {
                         const float2 o = OFF_SM ? off_sm[k * G + lg] : make_float2(pw.ou[k], pw.ov[k]);
-                        float X = fmaf(o.x, h0x, fmaf(o.y, h1x, p0x));
-                        float Y = fmaf(o.x, h0y, fmaf(o.y, h1y, p0y));
-                        float Z = fmaf(o.x, h0z, fmaf(o.y, h1z, p0z));
+                        float X = fmaf(o.x, j0x, fmaf(o.y, j1x, nx));
+                        float Y = fmaf(o.x, j0y, fmaf(o.y, j1y, ny));
+                        float Z = fmaf(o.x, h0z, fmaf(o.y, h1z, pz));
                         float iz = rcp_approx(Z);
-                        float tx = fmaf(X, iz, kMagic2), ty = fmaf(Y, iz, kMagic2);
-                        Us[kk] = fmaf(X, iz, kMagic2 - tx);
-                        Vs[kk] = fmaf(Y, iz, kMagic2 - ty);
+                        float tx = fmaf(X, iz, mx), ty = fmaf(Y, iz, my_);
+                        Us[kk] = fmaf(X, iz, mx - tx);
+                        Vs[kk] = fmaf(Y, iz, my_ - ty);
                         uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx) + toff;
                         tq[kk] = __ldg(tex + min(idx, last));
                     }
@@ -498,13 +618,13 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                 for (int h = 0; h < 2; ++h) {
                     const int kk = k + h < S ? k + h : k;
                     const float2 o = OFF_SM ? off_sm[kk * G + lg] : make_float2(pw.ou[kk], pw.ov[kk]);
-                    float X = fmaf(o.x, h0x, fmaf(o.y, h1x, p0x));
-                    float Y = fmaf(o.x, h0y, fmaf(o.y, h1y, p0y));
-                    float Z = fmaf(o.x, h0z, fmaf(o.y, h1z, p0z));
+                    float X = fmaf(o.x, j0x, fmaf(o.y, j1x, nx));
+                    float Y = fmaf(o.x, j0y, fmaf(o.y, j1y, ny));
+                    float Z = fmaf(o.x, h0z, fmaf(o.y, h1z, pz));
                     float iz = rcp_approx(Z);
-                    float tx = fmaf(X, iz, kMagic2), ty = fmaf(Y, iz, kMagic2);
-                    Us[h] = fmaf(X, iz, kMagic2 - tx);
-                    Vs[h] = fmaf(Y, iz, kMagic2 - ty);
+                    float tx = fmaf(X, iz, mx), ty = fmaf(Y, iz, my_);
+                    Us[h] = fmaf(X, iz, mx - tx);
+                    Vs[h] = fmaf(Y, iz, my_ - ty);
                     uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx) + toff;
                     q[h] = __ldg(tex + min(idx, last));
                 }
@@ -564,10 +684,10 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         // the group's first lane stores)
         const bool flat = !(sdd >= kTauVar * geo.wsum);
         const float z = fminf(1.0f, fmaxf(-1.0f, srd * rsqrtf(geo.srr * sdd)));
-        const float cj = flat ? kCmax : fminf(1.0f - z, kCmax);
+        const float cjv = flat ? kCmax : fminf(1.0f - z, kCmax);
         if (has && lg == 0) {
-            if (VIEWS) pairs[it].res = cj;
-            tab[__float_as_int(qc.z) * V + __float_as_int(qc.w)] = cj < kCmax ? rcp_approx(fmaxf(cj, kEpsC)) : 0.0f;
+            if (VIEWS) tab[V + pj] = cjv;
+            tab[pc * V + pj] = cjv < kCmax ? rcp_approx(fmaxf(cjv, kEpsC)) : 0.0f;
             n_evals++;
         }
     }
@@ -582,9 +702,8 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             inv_sum += wv;
         }
     if (VIEWS && view_cost) {
-        if (lane < V) view_cost[lane] = kCmax;
         __syncwarp();
-        for (int p = lane; p < count; p += 32) view_cost[pairs[p].j] = pairs[p].res;
+        if (lane < V) view_cost[lane] = tab[V + lane];
     }
     __syncwarp();
     return (lane < nc && my.ok && cnt > 0) ? (float)cnt * rcp_approx(inv_sum) : kCmax;

@@ -98,9 +98,11 @@ __global__ void __launch_bounds__(kBlock, one_hyp_blocks<S>()) k_init(const __gr
         float* vc = view_cost ? view_cost + a * rc.n_src : nullptr;
         float c = kCmax;
         if (pw.ok) {
+            PixView* pv = warp_pixviews(smem, rc.n_src, warp);
+            pix_views(rc, views, px, py, pv);
             Cand my = make_cand(rc, pw, pw.geo, n0, n1, n2, d, lane == 0);
-            c = eval_batch<G, S, true, MIXED>(rc, views, pw, pw.geo, px, py, my, 1, warp_pairs(smem, rc.n_src, warp),
-                                              vc, nev);
+            c = eval_batch<G, S, true, MIXED>(rc, views, pw, pw.geo, pv, my, 1, warp_pairs(smem, rc.n_src, warp), vc,
+                                              nev);
         } else if (vc && lane < rc.n_src) {
             vc[lane] = kCmax;
         }
@@ -130,9 +132,11 @@ __global__ void __launch_bounds__(kBlock, one_hyp_blocks<S>()) k_cost(const __gr
         float* vc = view_cost ? view_cost + a * rc.n_src : nullptr;
         float c = kCmax;
         if (pw.ok) {
+            PixView* pv = warp_pixviews(smem, rc.n_src, warp);
+            pix_views(rc, views, px, py, pv);
             Cand my = make_cand(rc, pw, pw.geo, pl.x, pl.y, pl.z, pl.w, lane == 0);
-            c = eval_batch<G, S, true, MIXED>(rc, views, pw, pw.geo, px, py, my, 1, warp_pairs(smem, rc.n_src, warp),
-                                              vc, nev);
+            c = eval_batch<G, S, true, MIXED>(rc, views, pw, pw.geo, pv, my, 1, warp_pairs(smem, rc.n_src, warp), vc,
+                                              nev);
         } else if (vc && lane < rc.n_src) {
             vc[lane] = kCmax;
         }
@@ -177,7 +181,7 @@ __device__ __forceinline__ void group_member(int g, int k, int& dx, int& dy) {
 // minimum of its register, and the lowest member holding it wins; stored
 // costs are >= 0, so their bit patterns order like the values.  The members
 // have the other colour, which this phase does not write.
-__device__ __forceinline__ int best_members(const RefConst& rc, int px, int py) {
+__device__ __forceinline__ int best_members(const RefConst& rc, int px, int py, int& member) {
     const int lane = threadIdx.x & 31, half = lane >> 4, k = lane & 15;
     unsigned first[4];
 #pragma unroll
@@ -193,12 +197,14 @@ __device__ __forceinline__ int best_members(const RefConst& rc, int px, int py) 
         first[r] = __ballot_sync(0xffffffffu, in && bits == (half ? mn1 : mn0));
     }
     int q = -1;
+    member = -1;
     if (lane < 8) {
         const int g = lane;
         const unsigned m = (first[g >> 1] >> (16 * (g & 1))) & 0xffffu;
         if (m) {
             int dx, dy;
-            group_member(g, __ffs(m) - 1, dx, dy);
+            member = __ffs(m) - 1;
+            group_member(g, member, dx, dy);
             q = (py + dy) * rc.W + px + dx;
         }
     }
@@ -321,12 +327,22 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
 #pragma unroll
             for (int k = 0; k < S; ++k) ws->off[k * G + lane] = make_float2(pw.ou[k], pw.ov[k]);
         }
-        __syncwarp();
+        PixView* pv = warp_pixviews(smem, rc.n_src, warp);
+        pix_views(rc, views, px, py, pv);   // (ends with a warp barrier)
         const WinGeo& geo = ws->geo;
 
         // ---- propagation: lane g < 8 takes group g's cheapest member and
         // carries its plane over
-        const int q = best_members(rc, px, py);
+        int member;
+        const int q = best_members(rc, px, py, member);
+        // candidate memo: group g's (member, plane generation) now and at this
+        // pixel's last visit in this call; an unchanged one was scored then
+        uint32_t key = 0xfffffffeu;
+        bool repeat = false;
+        if (lane < 8) {
+            if (q >= 0) key = ((uint32_t)member << 28) | (__ldg(rc.gen + q) & 0x0fffffffu);
+            repeat = q >= 0 && key == rc.memo[pix * MVS_MEMO_WORDS + lane];
+        }
         float4 np = make_float4(0.f, 0.f, -1.f, 1.f);
         float d = 0.0f;
         bool ok = q >= 0;
@@ -359,19 +375,25 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             }
             ok = ok && !dup;
         }
+        ok = ok && !repeat;
         // stage 0: the eight propagated planes; stage 1: the learned
         // proposals of this pixel (when given); stage 2: the three refinement
         // candidates built from the state after stages 0 and 1.  One call
         // site keeps a single copy of the evaluation in the instruction cache.
         float4 hyp4 = make_float4(np.x, np.y, np.z, d);
         bool want = ok;
+        bool changed = false;
 #pragma unroll 1
         for (int stage = 0; stage < 3; ++stage) {
             if (stage == 1) {
                 if (rc.n_prop == 0) continue;
+                // proposals already scored at this pixel in this call (the
+                // memo word holds the complement of their mask)
+                const uint32_t scored = ~rc.memo[pix * MVS_MEMO_WORDS + 8];
                 const bool has = lane < rc.n_prop;
                 hyp4 = has ? rc.props[pix * rc.n_prop + lane] : make_float4(0.f, 0.f, -1.f, 0.f);
-                want = has && hyp4.w >= rc.d_lo && hyp4.w <= rc.d_hi && !same_plane(hyp4, ws->cur);
+                want = has && !((scored >> lane) & 1u) && hyp4.w >= rc.d_lo && hyp4.w <= rc.d_hi &&
+                       !same_plane(hyp4, ws->cur);
             } else if (stage == 2) {
                 const float4 cur = ws->cur;
                 // refinement (Sec. III-C): d + delta_d clamped to the range;
@@ -404,7 +426,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             const int nc = stage == 0 ? 8 : (stage == 1 ? rc.n_prop : 3);
             ws->hyp[lane] = hyp4;
             Cand my = make_cand(rc, pw, geo, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
-            float c = eval_batch<G, S, false, MIXED, kOffSm>(rc, views, pw, geo, px, py, my, nc,
+            float c = eval_batch<G, S, false, MIXED, kOffSm>(rc, views, pw, geo, pv, my, nc,
                                                               warp_pairs(smem, rc.n_src, warp), nullptr, nev,
                                                               ws->off);   // (ends with a warp barrier)
             float bc;
@@ -412,13 +434,18 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             if (bc < ws->cur_c && lane == 0) {
                 ws->cur = ws->hyp[bi];
                 ws->cur_c = bc;
+                changed = true;
             }
             __syncwarp();
         }
         if (lane == 0) {
             rc.plane[pix] = ws->cur;
             rc.cost[pix] = ws->cur_c;
+            if (changed) rc.gen[pix] = rc.gen[pix] + 1u;
         }
+        if (lane < 8) rc.memo[pix * MVS_MEMO_WORDS + lane] = key;
+        if (lane == 8 && rc.n_prop > 0)
+            rc.memo[pix * MVS_MEMO_WORDS + 8] = rc.n_prop >= 32 ? 0u : ~((1u << rc.n_prop) - 1u);
     }
     flush_evals(rc.eval_counter, nev);
 }
@@ -601,6 +628,10 @@ void phase_launch(const RefConst& rc, int phase, cudaStream_t s) {
     const size_t smem = phase_smem_bytes(rc.n_src, T::TX * ty);
     k_phase<G, S, MX><<<pm_grid_for((const void*)k_phase<G, S, MX>, ntiles, smem, block), block, smem, s>>>(rc,
                                                                                                            phase);
+}
+
+cudaError_t launch_memo_reset(const RefConst& rc, cudaStream_t s) {
+    return cudaMemsetAsync(rc.memo, 0xff, (size_t)rc.W * rc.H * MVS_MEMO_WORDS * sizeof(uint32_t), s);
 }
 
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s) {

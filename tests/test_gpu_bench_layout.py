@@ -11,7 +11,12 @@ per-view costs agree within 1e-4.  Two windows are checked: 21 x 21 at
 dilation 2 (the benchmark's) and the paper's r_now / r_orig = 5 / 7
 (s = 1.4, reference samples interpolated too).  The 16-slot layouts of the
 undilated 15 x 15 and 21 x 21 windows (Table III's 7/7 and 10/10 rows) run
-the same lockstep on the small scene, and 10/10 runs free as well."""
+the same lockstep on the small scene, and 10/10 runs free as well.
+
+Costs are compared for identical planes (the GPU's), with the tolerance
+1e-4 on every view whose window image in the source is at most 256 px
+across, and 1e-4 per 128 px of that extent beyond (grazing planes; the
+count is printed and bounded)."""
 import copy
 
 import numpy as np
@@ -22,6 +27,20 @@ pytestmark = pytest.mark.gpu
 COST_TOL = 1e-4
 TIE_BAND = 2e-4
 MARGIN = 1e-3
+# Source positions are evaluated in float relative to the projected window
+# centre, so their rounding grows with the extent of the window's image in
+# the source (oracle.window_extent): about 2^-23 of it per sample, which the
+# texture gradient turns into a cost error of a few 1e-7 per source pixel of
+# extent.  Views up to EXTENT_PX across get COST_TOL; wider ones (grazing
+# planes whose 21-pixel window spreads over hundreds of source pixels, 1-2 %
+# of random initial planes) get COST_TOL per 128 px of extent (twice the
+# largest error measured on GB300), and are counted.
+EXTENT_PX = 256.0
+WIDE_FRACTION = 0.03
+
+
+def _view_tol(ext):
+    return COST_TOL * np.maximum(1.0, ext / 128.0)
 X0, Y0, CW, CH = 256, 1024, 192, 128      # crop of the 3072 x 2048 reference
 
 
@@ -52,11 +71,13 @@ def _lockstep(mvs, oracle, ctx, osc, srcs, p, n_phases):
     pl = np.zeros((H, W, 4), np.float32)
     co = np.zeros((H, W), np.float32)
     mvs.mvs_patchmatch(ctx.h, 0, srcs, q, pl, co)
-    opl, oco = oracle.init(osc, 0, srcs, p)
+    opl, _ = oracle.init(osc, 0, srcs, p, with_cost=False)
     assert np.abs(pl[..., 3] - opl[..., 3]).max() <= 1e-6 * 8
     assert np.abs(pl[..., :3] - opl[..., :3]).max() <= 2e-6
-    _, _, mg = oracle.plane_cost(osc, 0, srcs, p, pl.astype(np.float64), with_views=True)
-    assert np.abs(co - oco)[mg > MARGIN].max() <= COST_TOL
+    # costs of the same (float) planes on both sides: at 3072 px the float
+    # rounding of a plane alone moves a far-off random plane's window by
+    # ~1e-4 px in the source, so only identical planes give comparable costs
+    _check_costs(mvs, oracle, ctx, osc, srcs, p, pl, co, np.ones(co.shape, bool), "init")
     yy, xx = np.mgrid[0:H, 0:W]
     report = []
     for ph in range(n_phases):
@@ -76,21 +97,42 @@ def _lockstep(mvs, oracle, ctx, osc, srcs, p, n_phases):
         detail = [(int(y), int(x), float(diag["gap_prop"][y, x]), float(diag["gap_ref"][y, x]),
                    float(diag["margin"][y, x]), float(g_co[y, x]), float(o_co[y, x])) for y, x in bad]
         assert unexplained.sum() == 0, f"phase {ph}: {unexplained.sum()} decisions differ outside the tie band: {detail}"
-        agree = active & same & (diag["margin"] >= MARGIN)
-        assert np.abs(g_co - o_co)[agree].max() <= COST_TOL
-        # per-view costs of the planes the GPU chose, on both sides
-        vc = np.zeros((H, W, len(srcs)), np.float32)
-        c2 = np.zeros((H, W), np.float32)
-        mvs.mvs_plane_cost(ctx.h, 0, srcs, p, g_pl, c2, vc)
-        oc2, ovc, mg2 = oracle.plane_cost(osc, 0, srcs, p, g_pl.astype(np.float64), with_views=True)
-        firm = mg2 > MARGIN
-        assert np.abs(vc - ovc)[firm].max() <= COST_TOL
-        assert np.abs(c2 - oc2)[firm].max() <= COST_TOL
+        # costs and per-view costs of the planes the GPU chose, on both sides
+        # (the oracle's own choice differs from the GPU's plane by float
+        # rounding, see above)
+        _check_costs(mvs, oracle, ctx, osc, srcs, p, g_pl, g_co, active, f"phase {ph}")
         changed = active & ((g_pl != pl).any(-1))
         report.append((ph, int(active.sum()), int(changed.sum()), int((active & tie & ~same).sum()),
                        float((active & tie).mean())))
         pl, co = g_pl, g_co
     return report
+
+
+def _check_costs(mvs, oracle, ctx, osc, srcs, p, pl, stored, sel, name):
+    """Per-view and aggregated costs of the plane map pl on both sides, and
+    the stored costs of the pixels in sel, within the extent-scaled tolerance
+    wherever the oracle's decision margin is firm."""
+    H, W = stored.shape
+    vc = np.zeros((H, W, len(srcs)), np.float32)
+    c2 = np.zeros((H, W), np.float32)
+    mvs.mvs_plane_cost(ctx.h, 0, srcs, p, pl, c2, vc)
+    f64 = pl.astype(np.float64)
+    oc, ovc, mg = oracle.plane_cost(osc, 0, srcs, p, f64, with_views=True)
+    ext = oracle.window_extent(osc, 0, srcs, p, f64)
+    firm = mg > MARGIN
+    tv = _view_tol(ext)
+    tp = tv.max(-1)
+    ev = np.abs(vc - ovc)
+    ordinary = firm[..., None] & (ext <= EXTENT_PX)
+    wide = firm[..., None] & (ext > EXTENT_PX)
+    assert (ev[ordinary] <= COST_TOL).all()
+    print(f"{name}: per-view cost error max {ev[ordinary].max():.2e} (p99.9 {np.quantile(ev[ordinary], 0.999):.2e}) "
+          f"on {ordinary.sum()} views up to {EXTENT_PX:.0f} px; {wide.sum()} wider views, max error / tolerance "
+          f"{(ev / tv)[wide].max() if wide.any() else 0.0:.2f}")
+    assert (ev <= tv)[firm].all()
+    assert (np.abs(c2 - oc) <= tp)[firm].all()
+    assert (np.abs(stored - oc) <= tp)[firm & sel].all()
+    assert wide.sum() <= WIDE_FRACTION * ordinary.sum()
 
 
 @pytest.mark.parametrize("r_orig", [10.0, 7.0], ids=["21x21-dilation2", "paper-5-7"])
@@ -141,3 +183,46 @@ def test_free_running_sixteen_slot_layout(small_scene, mvs_lib, oracle_lib):
     frac = (np.abs(pl[..., 3] - opl[..., 3]) <= 0.005 * opl[..., 3]).mean()
     print(f"21x21 free-running: depth within 0.5% on {frac:.5f} of pixels")
     assert frac >= 0.999
+
+
+@pytest.mark.parametrize("which", ["crop", "small"])
+def test_candidate_memo_is_exact(crop_scene, small_scene, mvs_lib, which):
+    """Within one call the phase kernel does not score again a propagated
+    plane that a pixel scored (or found equal to a scored one) at its
+    previous visit.  Running the same phases as separate one-phase calls
+    (the memo starts empty in every call) gives the same plane and cost maps
+    bit for bit, with more ZNCC evaluations."""
+    import torch
+    if which == "crop":
+        K, R, t, imgs, _ = crop_scene
+        ctx = mvs_lib.Context(K, R, t, imgs, stream=torch.cuda.current_stream())
+        srcs, p = list(range(1, 11)), _params(mvs_lib, 10.0, 11, iters=4, seed=3)
+    else:
+        sc, ctx, _ = small_scene
+        srcs, p = [1, 2, 3, 4], _params(mvs_lib, 5.0, 6, iters=4, seed=3)
+    try:
+        H, W = ctx.shapes[0]
+        mvs_lib.mvs_profile(ctx.h, 1)
+        a_pl = np.zeros((H, W, 4), np.float32)
+        a_co = np.zeros((H, W), np.float32)
+        mvs_lib.mvs_patchmatch(ctx.h, 0, srcs, p, a_pl, a_co)
+        ev_one = mvs_lib.mvs_profile_read(ctx.h)[3]
+        mvs_lib.mvs_profile(ctx.h, 1)
+        b_pl = np.zeros((H, W, 4), np.float32)
+        b_co = np.zeros((H, W), np.float32)
+        q = copy.copy(p)
+        q.iters, q.phase_begin, q.phase_end = 0, 0, 0
+        mvs_lib.mvs_patchmatch(ctx.h, 0, srcs, q, b_pl, b_co)
+        for ph in range(2 * p.iters):
+            q = copy.copy(p)
+            q.phase_begin, q.phase_end, q.init_mode = ph, ph + 1, mvs_lib.MVS_INIT_GIVEN
+            mvs_lib.mvs_patchmatch(ctx.h, 0, srcs, q, b_pl, b_co)
+        ev_sep = mvs_lib.mvs_profile_read(ctx.h)[3]
+        mvs_lib.mvs_profile(ctx.h, 0)
+    finally:
+        if which == "crop":
+            ctx.close()
+    assert np.array_equal(a_pl, b_pl) and np.array_equal(a_co, b_co)
+    print(f"{which}: {ev_one} ZNCC evaluations in one call, {ev_sep} in one-phase calls "
+          f"({1 - ev_one / ev_sep:.1%} skipped)")
+    assert ev_one < ev_sep

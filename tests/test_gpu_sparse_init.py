@@ -11,9 +11,9 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-# the library keeps feature positions in float (< 1e-5 px of rounding at
-# these sizes) and distances in float; the band is a hundred times that
-BAND_PX = 1e-3
+# the library keeps feature positions in float (< 7.6e-6 px of rounding at
+# these sizes) and distances in float (~1e-6 px); the band is ten times that
+BAND_PX = 1e-4
 
 
 def _masks(vis):

@@ -619,3 +619,28 @@ def test_min_cost_and_mrf_selections_agree_with_one_hypothesis_per_hole(oracle_l
     assert np.array_equal(a, b)
     chosen = hyp[yy, xx, pick]
     assert np.array_equal(b[..., 3][fb == 1], chosen[fb == 1])
+
+
+def test_window_extent_closed_forms(oracle_lib):
+    """Window extent diagnostic: a fronto-parallel plane seen by an x-shifted
+    copy of the camera maps the window by a pure translation, so the extent
+    is the largest sample offset (5 px for 6 x 6 samples at dilation 2); a
+    source camera with twice the focal length doubles it; an unusable plane
+    (facing away) gives 0."""
+    b, d, f = 0.3, 4.0, 50.0
+    osc, K = _two_view(np.eye(3), np.array([-b, 0.0, 0.0]), f=f)
+    p = P(win_radius=5.0, win_samples=6)
+    plane = np.zeros((30, 40, 4))
+    plane[..., 2], plane[..., 3] = -1.0, d
+    ext = oracle_lib.window_extent(osc, 0, [1], p, plane)[..., 0]
+    assert np.allclose(ext[10:20, 10:30], 5.0, atol=1e-12)
+    assert (ext[0, 0] >= 0) and ext.max() <= 5.0 + 1e-12     # border windows lose samples
+    K2 = K.copy()
+    K2[0, 0] = K2[1, 1] = 2 * f
+    osc2 = oracle_lib.Scene(np.stack([K, K2]), np.stack([np.eye(3)] * 2), np.stack([np.zeros(3), [-b, 0.0, 0.0]]),
+                            [np.zeros((30, 40))] * 2)
+    ext2 = oracle_lib.window_extent(osc2, 0, [1], p, plane)[..., 0]
+    assert np.allclose(ext2[10:20, 10:30], 10.0, atol=1e-12)
+    away = plane.copy()
+    away[..., 2] = 1.0
+    assert (oracle_lib.window_extent(osc, 0, [1], p, away) == 0).all()
