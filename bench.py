@@ -38,7 +38,89 @@ WORKLOADS = {"highres": WORKLOAD, "mid": dict(WORKLOAD, W=1536, H=1024), "batch2
              "table1": dict(WORKLOAD), "pipeline": dict(WORKLOAD)}
 BATCH_SIZES = ((3072, 2048),) * 8 + ((2048, 1365),) * 8 + ((1536, 1024),) * 8
 FLOP_PER_SAMPLE = 26          # algorithmic FP32 flops per window sample of one ZNCC (FMA = 2)
+GATHERS_PER_SAMPLE = 1        # one 8-byte coefficient texel per window sample
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def l2_bytes_per_sample(n, step):
+    """Algorithmic L2 bytes per window sample when each (pixel, view) pair
+    fetches its window's rows from L2 once (no reuse across pairs): a row of
+    n samples `step` texels apart spans (n - 1) step + 1 texels of 8 bytes,
+    counted in 32-byte sectors (one more for alignment)."""
+    span = (n - 1) * step + 1
+    sectors = int(np.ceil(span * 8 / 32)) + 1
+    return n * sectors * 32 / (n * n)
+
+
+def measured_peaks(mvs, device):
+    """FP32 flop/s, L1 gathers/s and L2 bytes/s of this GPU, measured by the
+    library's own micro-benchmarks (mvs_measure_peaks) right before the
+    timed region, with the SM clock sampled while they run."""
+    with ClockSampler(device) as clk:
+        f, g, b = mvs.mvs_measure_peaks(device)
+    return {"fp32_tflops": f / 1e12, "l1_gathers_per_s": g, "l2_gbs": b / 1e9, "clocks": clk.summary(),
+            "how": "mvs_measure_peaks: FFMA chains, 8-byte L1 gathers in the window-sample pattern, "
+                   "64 MB L2-resident stream; one timed launch each after a warm-up"}
+
+
+def roofline_fractions(sample_evals_per_s, peaks, n, step):
+    """Fractions of the three rooflines of the phase kernel from algorithmic
+    counts per window sample; the binding one is the largest."""
+    fr = {"fp32": FLOP_PER_SAMPLE * sample_evals_per_s / (peaks["fp32_tflops"] * 1e12),
+          "l1": GATHERS_PER_SAMPLE * sample_evals_per_s / peaks["l1_gathers_per_s"],
+          "l2": l2_bytes_per_sample(n, step) * sample_evals_per_s / (peaks["l2_gbs"] * 1e9)}
+    return fr, max(fr, key=fr.get)
+
+
+def _oracle_worker(args):
+    """One oracle process of the N-core CPU baseline: the full path on one
+    crop of the shared scene (images read from shared memory)."""
+    shm_name, shapes, K, R, t, params, crop, seed = args
+    from multiprocessing import shared_memory
+    import oracle
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        imgs, off = [], 0
+        for (h, w) in shapes:
+            imgs.append(np.ndarray((h, w), np.uint8, buffer=shm.buf, offset=off).copy())
+            off += h * w
+    finally:
+        shm.close()
+
+    class _S:
+        pass
+    sc = _S()
+    sc.K, sc.R, sc.t, sc.images = K, R, t, imgs
+    return oracle_sample(sc, params, crop, n_crops=1, seed=seed)
+
+
+def oracle_throughput(sc, params, crop, crops_per_core=2, seed=0):
+    """N-core CPU baseline: one oracle process per host core (spawned, after
+    CUDA is up in this process), each on independent crops.  Returns
+    (pixels per second over the wall time of the parallel section, cores,
+    pixels)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    cores = os.cpu_count() or 1
+    total = sum(im.size for im in sc.images)
+    shm = shared_memory.SharedMemory(create=True, size=total)
+    try:
+        off = 0
+        for im in sc.images:
+            np.ndarray(im.shape, np.uint8, buffer=shm.buf, offset=off)[...] = im
+            off += im.size
+        shapes = [im.shape for im in sc.images]
+        jobs = [(shm.name, shapes, sc.K, sc.R, sc.t, params, crop, seed + k) for k in range(cores * crops_per_core)]
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_oracle_worker, jobs[:cores])       # start-up (imports, oracle build check) untimed
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, jobs)
+            wall = time.perf_counter() - t0
+    finally:
+        shm.close()
+        shm.unlink()
+    px = sum(r[1] for r in res)
+    return px / wall, cores, px
 
 
 def _env_rank():
@@ -201,6 +283,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    peaks = measured_peaks(mvs, local)
     if world > 1:
         dist.barrier()
     mvs.mvs_profile(ctx.h, 1)
@@ -263,7 +346,9 @@ def run_ours(args):
     n2 = w["win_samples"] ** 2
     phase_flops = evals * n2 * FLOP_PER_SAMPLE
     achieved = phase_flops / (phase_ms / 1e3) / 1e12 if phase_ms > 0 else None
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = peaks["fp32_tflops"]
+    step_px = w["win_radius"] / (0.5 * (w["win_samples"] - 1))
+    fracs, binding = roofline_fractions(evals * n2 / (phase_ms / 1e3), peaks, w["win_samples"], step_px)
     line = {
         "metric": "depth-map Mpix/s (full PatchMatch + PHI)",
         "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -284,7 +369,15 @@ def run_ours(args):
                      "traffic": (tpp * H * W if (tpp := phase_traffic_per_pixel()) else None),
                      "traffic_unit": "bytes per launch (ncu dram read+write, 1536x1024 capture scaled by pixels)",
                      "kernel": "k_phase (checkerboard propagation + refinement)",
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
+                     "peak_basis": "measured FFMA rate of this GPU (mvs_measure_peaks), see peaks",
+                     "fractions": {k: round(v, 4) for k, v in fracs.items()}, "binding": binding,
+                     "fraction_basis": {"fp32": f"{FLOP_PER_SAMPLE} flop per window sample / measured FFMA peak",
+                                        "l1": f"{GATHERS_PER_SAMPLE} 8-byte gather per window sample / measured "
+                                              "L1 gather peak in the same pattern",
+                                        "l2": f"{l2_bytes_per_sample(w['win_samples'], step_px):.1f} bytes per "
+                                              "window sample (each pair's window rows from L2 once) / measured "
+                                              "L2 read bandwidth"},
+                     "peaks": peaks},
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -293,8 +386,13 @@ def run_ours(args):
             line["cpu_baseline"] = {"value": px / t_ / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                                     "sample": "4 random 24x16 crops of the 3072x2048 reference, full-size "
                                               "sources, full path (init, 8 iterations, PHI)"}
+            v_n, cores, px_n = oracle_throughput(sc, params, (24, 16), crops_per_core=2, seed=11)
+            line["cpu_baseline_all_cores"] = {"value": v_n / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                                              "sample": f"{2 * cores} random 24x16 crops, one oracle process per "
+                                                        f"host core (os.cpu_count() = {cores}), full path"}
         except Exception as e:  # the baseline is informative only
-            line["cpu_baseline"] = {"error": str(e)[:200]}
+            line["cpu_baseline"] = line.get("cpu_baseline") or {"error": str(e)[:200]}
+            line["cpu_baseline_all_cores"] = {"error": str(e)[:200]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

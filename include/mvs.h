@@ -387,6 +387,21 @@ mvs_status mvs_profile(mvs_ctx* ctx, int32_t enable);
 mvs_status mvs_profile_read(mvs_ctx* ctx, double* phase_ms, int64_t* phase_launches, int64_t* kernel_launches,
                             int64_t* phase_evals);
 
+/* Measured peaks of device `device` for the roofline of the PatchMatch
+ * kernels (no counterpart in the paper), each from one timed launch after a
+ * warm-up launch of a small kernel of this library:
+ *   fp32_flops: FP32 FMA rate (flop/s, FMA = 2) of 16 independent chains per
+ *     thread on every SM;
+ *   gathers: 8-byte loads per second served from L1 in the window-sample
+ *     pattern of the phase kernel (two groups of 16 lanes per warp, texels
+ *     two apart, eight independent loads in flight per thread);
+ *   l2_bytes: read bandwidth (bytes/s) of a 64 MB buffer resident in L2.
+ * Figures depend on the clocks of the moment; callers sample them.  Any
+ * output may be NULL (not measured).  Allocates and frees its own device
+ * buffers (about 70 MB) and synchronises.
+ * Errors: MVS_EINVAL (bad device, all outputs NULL), MVS_ENOMEM, MVS_ECUDA. */
+mvs_status mvs_measure_peaks(int32_t device, double* fp32_flops, double* gathers, double* l2_bytes);
+
 /* ------------------------------------------------------------------------
  * Learned plane proposals (no counterpart in the paper).
  *

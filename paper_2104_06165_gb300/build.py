@@ -21,7 +21,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # per-pair constants come out the same on x86-64 and Arm hosts
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-Xptxas", "-warn-spills"]
-SOURCES = ["mvs_api.cu", "pm_kernels.cu", "phi_kernels.cu", "cnn_kernels.cu", "fuse_kernels.cu", "select_kernels.cu"]
+SOURCES = ["mvs_api.cu", "pm_kernels.cu", "phi_kernels.cu", "cnn_kernels.cu", "fuse_kernels.cu", "select_kernels.cu",
+           "peak_kernels.cu"]
 
 
 def _deps():

@@ -187,6 +187,8 @@ def load():
     L.mvs_cnn_forward.argtypes = [vp, u8p, fp, fp, i32, i32, fp]
     L.mvs_cnn_backward.restype = i32
     L.mvs_cnn_backward.argtypes = [vp, u8p, fp, fp, i32, i32, fp, u8p, C.POINTER(C.c_float)]
+    L.mvs_measure_peaks.restype = i32
+    L.mvs_measure_peaks.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.mvs_cnn_read.restype = i32
     L.mvs_cnn_read.argtypes = [vp, i32, i32, vp, C.c_int64]
     L.mvs_cnn_adam_step.restype = i32
@@ -420,6 +422,15 @@ def mvs_phi_select_min_cost(ctx, ref, known, hyp, valid, hcost, plane):
     mem = _mem(known, hyp, valid, hcost, plane)
     _check(load().mvs_phi_select_min_cost(ctx, ref, _ptr(known)[0], _ptr(hyp)[0], _ptr(valid)[0], _ptr(hcost)[0],
                                           _ptr(plane)[0], mem), ctx)
+
+
+def mvs_measure_peaks(device=0):
+    """(FP32 flop/s, L1 gathers/s, L2 read bytes/s) measured on `device`."""
+    f, g, b = C.c_double(), C.c_double(), C.c_double()
+    st = load().mvs_measure_peaks(int(device), C.byref(f), C.byref(g), C.byref(b))
+    if st != MVS_OK:
+        raise MvsError(st, "mvs_measure_peaks failed")
+    return f.value, g.value, b.value
 
 
 def mvs_profile(ctx, enable):
