@@ -402,15 +402,21 @@ def run_ours(args):
 def run_batch(args):
     """24 reference views at mixed resolutions, each with 10 sources, in one
     captured CUDA graph (autotuned work layout), then the geometric filter of
-    every view against its sources."""
+    every view against its sources.  Under several ranks the 24 views are
+    sharded by pixel count (dist.filter_sharded: each rank's views in one
+    graph, the plane maps exchanged over NCCL, each rank filters its own
+    views): strong scaling of the one scene."""
     import torch
     rank, world, local = _env_rank()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2104_06165_gb300 import mvs, scenes
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2104_06165_gb300 import dist as pdist, mvs, scenes
     mvs.load()
     t0 = time.perf_counter()
-    sc, srcs = scenes.scene_batch(seed=rank, sizes=BATCH_SIZES)
+    sc, srcs = scenes.scene_batch(seed=0, sizes=BATCH_SIZES)
     t_render = time.perf_counter() - t0
     n = len(sc.images)
     refs = list(range(n))
@@ -422,7 +428,14 @@ def run_batch(args):
     keeps = [torch.empty(im.shape, dtype=torch.uint8, device=dev) for im in sc.images]
     fp = mvs.FilterParams()
 
+    shapes = [im.shape for im in sc.images]
+
     def step():
+        if world > 1:
+            ks, _ = pdist.filter_sharded(mvs, ctx, shapes, srcs, params, fp, device=dev)
+            for v, k in ks.items():
+                keeps[v] = k
+            return
         mvs.mvs_patchmatch_batch(ctx.h, refs, srcs, params, planes, costs)
         for r in refs:
             mvs.mvs_geo_filter(ctx.h, r, srcs[r], fp, keeps[r])
@@ -433,6 +446,8 @@ def run_batch(args):
     mvs.mvs_profile(ctx.h, 1)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
         ev0.record(stream)
         for _ in range(args.steps):
             step()
@@ -441,6 +456,23 @@ def run_batch(args):
     ms = ev0.elapsed_time(ev1)
     _, _, launches, _ = mvs.mvs_profile_read(ctx.h)
     mpix = sum(im.size for im in sc.images) / 1e6
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        if rank == 0:
+            print(json.dumps({"metric": "depth-map Mpix/s (batched PatchMatch + geometric filter, views sharded)",
+                              "value": mpix * args.steps / (ms / 1e3), "unit": "Mpix/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                              "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+                              "data": "synthetic", "gpu_launches": int(launches),
+                              "config": {"workload": "batch24, views sharded by pixel count over the ranks "
+                                                     "(dist.filter_sharded), one exchange of the plane maps",
+                                         "total_mpix": round(mpix, 2)},
+                              "clocks": clk.summary()}), flush=True)
+        ctx.close()
+        dist.destroy_process_group()
+        return
     kept = float(sum(k.float().mean().item() * k.numel() for k in keeps) / (mpix * 1e6))
     # depth-map fusion (Sec. III-F) of the 24 filtered maps into one cloud
     cap = int(mpix * 1e6)

@@ -199,6 +199,18 @@ mvs_status mvs_patchmatch(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_
 mvs_status mvs_patchmatch_batch(mvs_ctx* ctx, int32_t n_ref, const int32_t* refs, const int32_t* srcs,
                                 int32_t n_src, const mvs_pm_params* params, mvs_depth_map* outs);
 
+/* Store a depth map of `view` that was computed elsewhere (another
+ * process or GPU, after the exchange before the geometric filter) in the
+ * context, as mvs_patchmatch would have left it, for mvs_geo_filter,
+ * mvs_fuse and mvs_plane_infer (no counterpart in the paper).
+ *   plane: H*W*4 floats (n.x, n.y, n.z, depth; depth 0 = none), cost: H*W
+ *   floats or NULL (then the stored costs are C_max = 2); both in `mem`,
+ *   plane 16-byte and cost 4-byte aligned.  Copied; the caller keeps its
+ *   buffers.  Stream-ordered (synchronises for host buffers).
+ * Errors: MVS_EINVAL (bad view, NULL plane, alignment, mem kind),
+ *   MVS_ENOMEM, MVS_ECUDA. */
+mvs_status mvs_set_depth_map(mvs_ctx* ctx, int32_t view, const float* plane, const float* cost, int32_t mem);
+
 /* Aggregated cost (Eq. 4/5) of a given plane map of view `ref`.
  *   plane: H*W*4 input, cost: H*W output, view_cost: H*W*n_src output of the
  *   per-view costs C(x, j) (C_max = 2 for an excluded view) or NULL.  All

@@ -247,6 +247,11 @@ mvs_status ensure_map(mvs_ctx* c, int32_t v) {
     return MVS_OK;
 }
 
+// fills n floats with v
+__global__ void k_fill(float* __restrict__ a, size_t n, float v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] = v;
+}
+
 cudaMemcpyKind kind_in(int32_t mem) { return mem == MVS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
 cudaMemcpyKind kind_out(int32_t mem) { return mem == MVS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
 
@@ -581,6 +586,31 @@ mvs_status mvs_plane_cost(mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t 
             CK(c, cudaMemcpyAsync(view_cost, vc_d, n * n_src * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
     }
+    return MVS_OK;
+}
+
+mvs_status mvs_set_depth_map(mvs_ctx* c, int32_t view, const float* plane, const float* cost, int32_t mem) {
+    if (!c) return MVS_EINVAL;
+    if (view < 0 || view >= (int32_t)c->views.size()) return fail(c, MVS_EINVAL, "bad view %d", view);
+    if (!plane) return fail(c, MVS_EINVAL, "plane is NULL");
+    if (((uintptr_t)plane & 15u) || ((uintptr_t)cost & 3u))
+        return fail(c, MVS_EINVAL, "plane must be 16-byte and cost 4-byte aligned");
+    if (mem != MVS_MEM_DEVICE && mem != MVS_MEM_HOST) return fail(c, MVS_EINVAL, "bad mem kind");
+    CK(c, cudaSetDevice(c->device));
+    mvs_status st = ensure_map(c, view);
+    if (st != MVS_OK) return st;
+    ViewData& V = c->views[view];
+    const size_t n = (size_t)V.cam.width * V.cam.height;
+    CK(c, cudaMemcpyAsync(V.plane, plane, n * sizeof(float4), kind_in(mem), c->stream));
+    if (cost) {
+        CK(c, cudaMemcpyAsync(V.cost, cost, n * sizeof(float), kind_in(mem), c->stream));
+    } else {
+        k_fill<<<(unsigned)std::min<size_t>((n + 255) / 256, 152 * 16), 256, 0, c->stream>>>(V.cost, n, 2.0f);
+        count_launch();
+        CK(c, cudaGetLastError());
+    }
+    V.has_map = true;
+    if (mem == MVS_MEM_HOST) CK(c, cudaStreamSynchronize(c->stream));
     return MVS_OK;
 }
 

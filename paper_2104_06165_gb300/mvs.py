@@ -187,6 +187,8 @@ def load():
     L.mvs_cnn_forward.argtypes = [vp, u8p, fp, fp, i32, i32, fp]
     L.mvs_cnn_backward.restype = i32
     L.mvs_cnn_backward.argtypes = [vp, u8p, fp, fp, i32, i32, fp, u8p, C.POINTER(C.c_float)]
+    L.mvs_set_depth_map.restype = i32
+    L.mvs_set_depth_map.argtypes = [vp, i32, vp, vp, i32]
     L.mvs_measure_peaks.restype = i32
     L.mvs_measure_peaks.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.mvs_cnn_read.restype = i32
@@ -311,6 +313,13 @@ def mvs_plane_cost(ctx, ref, srcs, params: PMParams, plane, cost, view_cost=None
     cpar = params.c()
     _check(load().mvs_plane_cost(ctx, ref, s, ns, C.byref(cpar), _ptr(plane)[0], _ptr(cost)[0],
                                  _ptr(view_cost)[0], mem), ctx)
+
+
+def mvs_set_depth_map(ctx, view, plane, cost=None):
+    """Store a depth map computed elsewhere (plane (H, W, 4), cost (H, W) or
+    None) as view's state in the context."""
+    mem = _mem(plane, cost)
+    _check(load().mvs_set_depth_map(ctx, int(view), _ptr(plane)[0], _ptr(cost)[0], mem), ctx)
 
 
 def mvs_geo_filter(ctx, ref, srcs, fparams: FilterParams, keep, count=None):

@@ -101,3 +101,78 @@ def test_gloo_subgroup_exchange():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert res == [(1, True), (2, True)]
+
+
+# --------------------------------------------------------------------------
+# the sharded depth-map stage on gloo ranks with the FP64 oracle as the
+# per-rank compute: views by assign_views, the exchange, the filter on the
+# received maps, against one process doing everything
+# --------------------------------------------------------------------------
+def _small_scene():
+    from paper_2104_06165_gb300 import scenes
+    return scenes.make_scene(W=40, H=30, n_src=3, seed=4, baseline_frac=0.1)
+
+
+class _P:
+    def __init__(self):
+        self.win_radius, self.win_samples = 5.0, 6
+        self.sigma_s, self.sigma_c = 5.0, 0.2
+        self.d_lo, self.d_hi, self.seed = 2.0, 8.0, 3
+
+
+def _oracle_maps(osc, views, n):
+    import oracle
+    out = {}
+    for v in views:
+        pl, _ = oracle.patchmatch(osc, v, [u for u in range(n) if u != v], _P(), 1)
+        out[v] = pl
+    return out
+
+
+def _sharded_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import numpy as np
+        import oracle
+        sc = _small_scene()
+        n = sc.n_views
+        osc = oracle.Scene(sc.K, sc.R, sc.t, sc.images)
+        shapes = [im.shape for im in sc.images]
+        parts = assign_views([h * w for h, w in shapes], world)
+        mine = _oracle_maps(osc, parts[rank], n)
+        # plane maps travel as float32, the library's format
+        allm = exchange_plane_maps({v: torch.from_numpy(m.astype(np.float32)) for v, m in mine.items()}, shapes,
+                                   parts)
+        planes = {v: t.numpy().astype(np.float64) for v, t in allm.items()}
+        keeps = {v: oracle.geo_filter(osc, v, [u for u in range(n) if u != v], planes)[0] for v in parts[rank]}
+        q.put((rank, keeps))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_sharded_filter_equals_one_process():
+    import numpy as np
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    sc = _small_scene()
+    n = sc.n_views
+    osc = oracle.Scene(sc.K, sc.R, sc.t, sc.images)
+    planes = {v: m.astype(np.float32).astype(np.float64) for v, m in _oracle_maps(osc, range(n), n).items()}
+    got = {v: k for r in res.values() for v, k in r.items()}
+    assert sorted(got) == list(range(n)) and set(res[0]).isdisjoint(res[1])
+    for v in range(n):
+        ref = oracle.geo_filter(osc, v, [u for u in range(n) if u != v], planes)[0]
+        assert np.array_equal(got[v], ref)
+    assert any(k.any() for k in got.values())
