@@ -503,6 +503,17 @@ enum {
 };
 mvs_status mvs_cnn_read(mvs_cnn* net, int32_t tensor, int32_t level, void* host_out, int64_t bytes);
 
+/* The convolutions wait on their operand copies and tensor-core products
+ * through mbarriers with a bound of about a second; a wait that runs out
+ * makes the kernel give up (after draining what it issued) and the next
+ * call on `net` that synchronises (get_params, get_grads, set_params,
+ * backward with loss_out, read, test_timeout) returns MVS_ETIMEOUT once.
+ * mvs_cnn_test_timeout runs one small convolution whose first wait targets
+ * a barrier that nothing completes, with a wait limit of about 0.1 ms, and
+ * returns what that reports (MVS_ETIMEOUT): a check of the path, no
+ * counterpart in the paper.  It overwrites the first encoder activations. */
+mvs_status mvs_cnn_test_timeout(mvs_cnn* net);
+
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with
  * learning rate lr on the gradients of the last mvs_cnn_backward. */
 mvs_status mvs_cnn_adam_step(mvs_cnn* net, float lr);

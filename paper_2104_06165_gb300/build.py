@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-Xptxas", "-warn-spills"]
 SOURCES = ["mvs_api.cu", "pm_kernels.cu", "phi_kernels.cu", "cnn_kernels.cu", "fuse_kernels.cu", "select_kernels.cu",
-           "peak_kernels.cu"]
+           "peak_kernels.cu", "conv_tc.cu"]
 
 
 def _deps():

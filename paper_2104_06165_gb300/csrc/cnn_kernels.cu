@@ -5,12 +5,13 @@
 // Eq. 4/5 still decides.)
 //
 // Tensors are channels-last bfloat16 (pixel-major, channels contiguous, a
-// multiple of 16 channels); convolutions are implicit GEMMs on the tensor
-// cores (mma.sync m16n8k16, bf16 inputs, fp32 accumulation): M = pixels,
-// N = output channels, K = taps x input channels.  The data gradient is the
-// same kernel run on the output gradient with flipped, transposed weights;
-// the weight gradient is a shared-memory-tiled reduction over pixels.
-// Master weights, gradients and Adam moments are fp32.
+// multiple of 16 channels); convolutions are implicit GEMMs on the
+// fifth-generation tensor cores (conv_tc.cu: TMA-staged operands,
+// tcgen05.mma bf16 x bf16 -> fp32 in tensor memory): M = pixels, N = output
+// channels, K = taps x input channels.  The data gradient is the same kernel
+// run on the output gradient with flipped, transposed weights; the weight
+// gradient is a shared-memory-tiled reduction over pixels.  Master weights,
+// gradients and Adam moments are fp32.
 #include <atomic>
 #include <cuda_bf16.h>
 
@@ -20,6 +21,7 @@
 #include <vector>
 
 #include "../../include/mvs.h"
+#include "conv_tc.h"
 #include "mvs_internal.h"
 #include "pm_device.cuh"
 
@@ -30,79 +32,6 @@ typedef __nv_bfloat16 bf16;
 struct Mat3 {
     float m[9];
 };
-
-// ---------------------------------------------------------------------------
-// convolution (3x3 or 1x1, stride 1, zero padding) as an implicit GEMM
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-// One warp computes 16 consecutive pixels (row-major order, rows may wrap)
-// x NC output channels [n_off, n_off + NC) of a convolution with `taps`
-// taps (9 = 3x3, 1 = 1x1).  in: H*W*Cin; w: [n_total][taps][Cin];
-// out: H*W*out_ch, this call writing channels [out_off, out_off + NC).
-// Cin is a multiple of 16; pixels past W*H are neither read nor written.
-template <int NC, bool RELU, bool OUT_F32>
-__global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ in, int Cin, int W, int H,
-                                              const bf16* __restrict__ w, const float* __restrict__ bias, int taps,
-                                              int n_off, void* __restrict__ out, int out_ch, int out_off) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long npix = (long long)W * H;
-    const long long p0 = ((long long)blockIdx.x * 4 + warp) * 16;
-    if (p0 >= npix) return;
-    const int g = lane >> 2, t = lane & 3;
-    // the two pixels whose rows of A this lane supplies (fragment rows g, g + 8)
-    const long long pa_ = p0 + g, pb_ = p0 + g + 8;
-    const bool va = pa_ < npix, vb = pb_ < npix;
-    const int ya0 = (int)(pa_ / W), xa0 = (int)(pa_ % W);
-    const int yb0 = (int)(pb_ / W), xb0 = (int)(pb_ % W);
-    float acc[NC / 8][4];
-#pragma unroll
-    for (int i = 0; i < NC / 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
-    for (int tap = 0; tap < taps; ++tap) {
-        const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
-        const int ya = ya0 + dy, xa = xa0 + dx, yb = yb0 + dy, xb = xb0 + dx;
-        const bool oka = va && ya >= 0 && ya < H && xa >= 0 && xa < W;
-        const bool okb = vb && yb >= 0 && yb < H && xb >= 0 && xb < W;
-        const bf16* pa = in + (oka ? ((long long)ya * W + xa) * Cin : 0) + 2 * t;
-        const bf16* pb = in + (okb ? ((long long)yb * W + xb) * Cin : 0) + 2 * t;
-        for (int c0 = 0; c0 < Cin; c0 += 16) {
-            uint32_t a0 = oka ? ld32(pa + c0) : 0u, a1 = okb ? ld32(pb + c0) : 0u;
-            uint32_t a2 = oka ? ld32(pa + c0 + 8) : 0u, a3 = okb ? ld32(pb + c0 + 8) : 0u;
-#pragma unroll
-            for (int nt = 0; nt < NC / 8; ++nt) {
-                const bf16* wp = w + ((long long)(n_off + nt * 8 + g) * taps + tap) * Cin + c0 + 2 * t;
-                mma_bf16(acc[nt], a0, a1, a2, a3, ld32(wp), ld32(wp + 8));
-            }
-        }
-    }
-#pragma unroll
-    for (int nt = 0; nt < NC / 8; ++nt) {
-        const int n = nt * 8 + 2 * t;
-        float b0 = bias ? bias[n_off + n] : 0.0f, b1 = bias ? bias[n_off + n + 1] : 0.0f;
-        float v0 = acc[nt][0] + b0, v1 = acc[nt][1] + b1, v2 = acc[nt][2] + b0, v3 = acc[nt][3] + b1;
-        if (RELU) {
-            v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); v2 = fmaxf(v2, 0.0f); v3 = fmaxf(v3, 0.0f);
-        }
-        if (OUT_F32) {
-            float* o = (float*)out;
-            if (va) { o[pa_ * out_ch + out_off + n] = v0; o[pa_ * out_ch + out_off + n + 1] = v1; }
-            if (vb) { o[pb_ * out_ch + out_off + n] = v2; o[pb_ * out_ch + out_off + n + 1] = v3; }
-        } else {
-            bf16* o = (bf16*)out;
-            if (va) *reinterpret_cast<__nv_bfloat162*>(o + pa_ * out_ch + out_off + n) = __floats2bfloat162_rn(v0, v1);
-            if (vb) *reinterpret_cast<__nv_bfloat162*>(o + pb_ * out_ch + out_off + n) = __floats2bfloat162_rn(v2, v3);
-        }
-    }
-}
 
 // Weight gradient: dw[co][tap][ci] += sum_p dy[p][co] * x[p + tap][ci],
 // db[co] += sum_p dy[p][co].  A block of 16 x 16 threads owns 16 output x 16
@@ -231,21 +160,6 @@ __global__ void k_f32_to_bf16(const float* __restrict__ a, bf16* __restrict__ b,
         b[i] = __float2bfloat16(a[i]);
 }
 
-// weights [co][tap][ci] (fp32) -> bf16 copy and the flipped transpose
-// [ci][8 - tap][co] used by the data gradient
-__global__ void k_weights_bf16(const float* __restrict__ w, int co_n, int taps, int ci_n, bf16* __restrict__ wb,
-                               bf16* __restrict__ wf) {
-    long long n = (long long)co_n * taps * ci_n;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int ci = (int)(i % ci_n);
-        long long r = i / ci_n;
-        int tap = (int)(r % taps), co = (int)(r / taps);
-        bf16 v = __float2bfloat16(w[i]);
-        wb[i] = v;
-        wf[((long long)ci * taps + (taps - 1 - tap)) * co_n + co] = v;
-    }
-}
-
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
                        long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -360,7 +274,7 @@ struct Layer {
     bool relu;
     size_t nw;                     // cout * taps * cin
     float *w, *b, *gw, *gb, *mw, *vw, *mb, *vb;
-    bf16 *wb, *wf;                 // bf16 weights and flipped transpose
+    bf16 *wt, *wtf;                // bf16 B operands of the tensor-core convolution: forward, data gradient
 };
 
 // channel plan (level l has 1/2^l resolution)
@@ -388,6 +302,7 @@ struct mvs_cnn {
     bf16 *gyb = nullptr, *gd[4] = {}, *gc[4] = {}, *ge[5] = {}, *gp[4] = {};
     float* gy = nullptr;
     float* loss = nullptr;
+    int* status = nullptr;         // device word: MVS_DEV_TIMEOUT once a bounded wait of a convolution ran out
     int steps = 0;
     int lastW = 0, lastH = 0;      // size of the last forward pass
     std::string err;
@@ -403,28 +318,14 @@ cudaError_t cnn_alloc(mvs_cnn* n, T** p, size_t count) {
     return e;
 }
 
-// Outputs [n_off, n_off + nc) with nc in {64, 48, 32, 16}.
-cudaError_t conv_launch(const bf16* in, int Cin, int W, int H, const bf16* w, const float* bias, int taps, int Cout,
-                        bool relu, bool out_f32, void* out, int out_ch, int out_off, cudaStream_t s) {
-    long long tiles = ((long long)W * H + 15) / 16;
-    unsigned grid = (unsigned)((tiles + 3) / 4);
-    for (int n_off = 0; n_off < Cout;) {
-        int rem = Cout - n_off;
-        int nc = rem >= 64 ? 64 : (rem >= 48 ? 48 : (rem >= 32 ? 32 : 16));
-#define LAUNCH(NC)                                                                                          \
-    if (out_f32)                                                                                            \
-        k_conv<NC, false, true><<<grid, 128, 0, s>>>(in, Cin, W, H, w, bias, taps, n_off, out, out_ch, out_off + n_off); \
-    else if (relu)                                                                                          \
-        k_conv<NC, true, false><<<grid, 128, 0, s>>>(in, Cin, W, H, w, bias, taps, n_off, out, out_ch, out_off + n_off); \
-    else                                                                                                    \
-        k_conv<NC, false, false><<<grid, 128, 0, s>>>(in, Cin, W, H, w, bias, taps, n_off, out, out_ch, out_off + n_off)
-        if (nc == 64) { LAUNCH(64); } else if (nc == 48) { LAUNCH(48); } else if (nc == 32) { LAUNCH(32); } else { LAUNCH(16); }
-#undef LAUNCH
-        count_launch();
-        n_off += nc;
-    }
-    return cudaGetLastError();
-}
+// wait limit of the convolutions' mbarriers (polls, with a 64 ns back-off):
+// about a second
+constexpr unsigned kConvWaitLimit = 1u << 24;
+
+// One tensor-core convolution; `status` collects a timed-out wait.
+cudaError_t conv_launch(mvs_cnn* n, const bf16* in, int Cin, int W, int H, const bf16* wt, const float* bias,
+                        int taps, int Cout, bool relu, bool out_f32, void* out, int out_ch, int out_off,
+                        cudaStream_t s);
 
 cudaError_t wgrad_launch(const bf16* x, int Cin, const bf16* dy, int Cout, int W, int H, int taps, float* dw, float* db,
                          cudaStream_t s) {
@@ -457,10 +358,17 @@ cudaError_t wgrad_launch(const bf16* x, int Cin, const bf16* dy, int Cout, int W
 cudaError_t refresh_bf16(mvs_cnn* n) {
     for (int i = 0; i < NL; ++i) {
         Layer& L = n->L[i];
-        k_weights_bf16<<<blocks((long long)L.nw), 256, 0, n->stream>>>(L.w, L.cout, L.taps, L.cin, L.wb, L.wf);
-        count_launch();
+        CUK(conv_tc_weights(L.w, L.cout, L.taps, L.cin, 0, L.wt, n->stream));
+        CUK(conv_tc_weights(L.w, L.cout, L.taps, L.cin, 1, L.wtf, n->stream));
     }
     return cudaGetLastError();
+}
+
+cudaError_t conv_launch(mvs_cnn* n, const bf16* in, int Cin, int W, int H, const bf16* wt, const float* bias,
+                        int taps, int Cout, bool relu, bool out_f32, void* out, int out_ch, int out_off,
+                        cudaStream_t s) {
+    return conv_tc_launch(in, Cin, W, H, wt, bias, taps, Cout, relu, out_f32, out, out_ch, out_off, n->status, 0,
+                          kConvWaitLimit, s);
 }
 
 // forward pass; x must hold the 16-channel input of a W x H image
@@ -479,7 +387,7 @@ cudaError_t cnn_forward(mvs_cnn* n, int W, int H) {
             count_launch();
             in = n->p[l - 1];
         }
-        CUK(conv_launch(in, L.cin, Ws[l], Hs[l], L.wb, L.b, 9, L.cout, true, false, n->e[l], L.cout, 0, s));
+        CUK(conv_launch(n, in, L.cin, Ws[l], Hs[l], L.wt, L.b, 9, L.cout, true, false, n->e[l], L.cout, 0, s));
     }
     // decoder: level l = 3..0, c[l] = [up(prev) | e[l]]
     const bf16* prev = n->e[4];
@@ -492,12 +400,12 @@ cudaError_t cnn_forward(mvs_cnn* n, int W, int H) {
         k_copy_ch<<<blocks((long long)Ws[l] * Hs[l] * C(E0 + l).cout), 256, 0, s>>>(
             n->e[l], C(E0 + l).cout, 0, n->c[l], ch, prev_ch, C(E0 + l).cout, (long long)Ws[l] * Hs[l], 0);
         count_launch();
-        CUK(conv_launch(n->c[l], ch, Ws[l], Hs[l], L.wb, L.b, 9, L.cout, true, false, n->d[l], L.cout, 0, s));
+        CUK(conv_launch(n, n->c[l], ch, Ws[l], Hs[l], L.wt, L.b, 9, L.cout, true, false, n->d[l], L.cout, 0, s));
         prev = n->d[l];
         prev_ch = L.cout;
     }
     const Layer& Hd = C(HEAD);
-    CUK(conv_launch(n->d[0], Hd.cin, W, H, Hd.wb, Hd.b, 1, Hd.cout, false, true, n->y, Hd.cout, 0, s));
+    CUK(conv_launch(n, n->d[0], Hd.cin, W, H, Hd.wt, Hd.b, 1, Hd.cout, false, true, n->y, Hd.cout, 0, s));
     return cudaGetLastError();
 }
 
@@ -515,7 +423,7 @@ cudaError_t cnn_backward(mvs_cnn* n, int W, int H) {
     count_launch();
     Layer& Hd = n->L[HEAD];
     CUK(wgrad_launch(n->d[0], Hd.cin, n->gyb, Hd.cout, W, H, 1, Hd.gw, Hd.gb, s));
-    CUK(conv_launch(n->gyb, Hd.cout, W, H, Hd.wf, nullptr, 1, Hd.cin, false, false, n->gd[0], Hd.cin, 0, s));
+    CUK(conv_launch(n, n->gyb, Hd.cout, W, H, Hd.wtf, nullptr, 1, Hd.cin, false, false, n->gd[0], Hd.cin, 0, s));
     // decoder levels 0..3: gd[l] is the gradient of d[l]
     for (int l = 0; l <= 3; ++l) {
         Layer& L = n->L[D3 + (3 - l)];
@@ -523,7 +431,8 @@ cudaError_t cnn_backward(mvs_cnn* n, int W, int H) {
         k_relu_mask<<<blocks(np * L.cout), 256, 0, s>>>(n->gd[l], n->d[l], np * L.cout);
         count_launch();
         CUK(wgrad_launch(n->c[l], L.cin, n->gd[l], L.cout, Ws[l], Hs[l], 9, L.gw, L.gb, s));
-        CUK(conv_launch(n->gd[l], L.cout, Ws[l], Hs[l], L.wf, nullptr, 9, L.cin, false, false, n->gc[l], L.cin, 0, s));
+        CUK(conv_launch(n, n->gd[l], L.cout, Ws[l], Hs[l], L.wtf, nullptr, 9, L.cin, false, false, n->gc[l], L.cin, 0,
+                        s));
         // split gc[l] = [g up(prev) | g e[l] (skip)]
         int up_ch = L.cin - n->L[E0 + l].cout;
         k_copy_ch<<<blocks(np * n->L[E0 + l].cout), 256, 0, s>>>(n->gc[l], L.cin, up_ch, n->ge[l], n->L[E0 + l].cout,
@@ -543,8 +452,8 @@ cudaError_t cnn_backward(mvs_cnn* n, int W, int H) {
         const bf16* in = l > 0 ? n->p[l - 1] : n->x;
         CUK(wgrad_launch(in, L.cin, n->ge[l], L.cout, Ws[l], Hs[l], 9, L.gw, L.gb, s));
         if (l > 0) {
-            CUK(conv_launch(n->ge[l], L.cout, Ws[l], Hs[l], L.wf, nullptr, 9, L.cin, false, false, n->gp[l - 1], L.cin,
-                            0, s));
+            CUK(conv_launch(n, n->ge[l], L.cout, Ws[l], Hs[l], L.wtf, nullptr, 9, L.cin, false, false, n->gp[l - 1],
+                            L.cin, 0, s));
             long long npf = (long long)Ws[l - 1] * Hs[l - 1];
             k_pool_bwd<<<blocks(npf * L.cin), 256, 0, s>>>(n->gp[l - 1], Ws[l - 1], Hs[l - 1], L.cin, n->ge[l - 1], 1);
             count_launch();
@@ -637,8 +546,8 @@ mvs_status mvs_cnn_create(int32_t max_width, int32_t max_height, float d_lo, flo
         if (e == cudaSuccess) e = cnn_alloc(n, &L.gb, L.cout);
         if (e == cudaSuccess) e = cnn_alloc(n, &L.mb, L.cout);
         if (e == cudaSuccess) e = cnn_alloc(n, &L.vb, L.cout);
-        if (e == cudaSuccess) e = cnn_alloc(n, &L.wb, L.nw);
-        if (e == cudaSuccess) e = cnn_alloc(n, &L.wf, L.nw);
+        if (e == cudaSuccess) e = cnn_alloc(n, &L.wt, L.nw);
+        if (e == cudaSuccess) e = cnn_alloc(n, &L.wtf, L.nw);
         if (e != cudaSuccess) break;
         // He initialisation (Box-Muller on a splitmix64 stream); the first
         // layer's padding channels (6..15) and the head start small
@@ -676,6 +585,8 @@ mvs_status mvs_cnn_create(int32_t max_width, int32_t max_height, float d_lo, flo
     if (e == cudaSuccess) e = cnn_alloc(n, &n->gy, np * 16);
     if (e == cudaSuccess) e = cnn_alloc(n, &n->gyb, np * 16);
     if (e == cudaSuccess) e = cnn_alloc(n, &n->loss, 1);
+    if (e == cudaSuccess) e = cnn_alloc(n, &n->status, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->status, 0, sizeof(int), n->stream);
     if (e == cudaSuccess) e = refresh_bf16(n);
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
     if (e != cudaSuccess) {
@@ -706,6 +617,17 @@ mvs_status mvs_cnn_n_params(const mvs_cnn* n, int64_t* count) {
     return MVS_OK;
 }
 
+// MVS_ETIMEOUT once a convolution's bounded wait ran out since the last
+// check (the status word is cleared); call after synchronising the stream
+static mvs_status check_status(mvs_cnn* n) {
+    int st = 0;
+    CNK(n, cudaMemcpyAsync(&st, n->status, sizeof st, cudaMemcpyDeviceToHost, n->stream));
+    CNK(n, cudaStreamSynchronize(n->stream));
+    if (st == 0) return MVS_OK;
+    CNK(n, cudaMemsetAsync(n->status, 0, sizeof(int), n->stream));
+    return cnn_fail(n, MVS_ETIMEOUT, "a tensor-core convolution gave up waiting for its operands");
+}
+
 static mvs_status copy_params(mvs_cnn* n, float* host, bool grads, bool set) {
     size_t off = 0;
     for (int i = 0; i < NL; ++i) {
@@ -723,7 +645,7 @@ static mvs_status copy_params(mvs_cnn* n, float* host, bool grads, bool set) {
     }
     if (set) CNK(n, refresh_bf16(n));
     CNK(n, cudaStreamSynchronize(n->stream));
-    return MVS_OK;
+    return check_status(n);
 }
 
 mvs_status mvs_cnn_get_params(mvs_cnn* n, float* host_out) {
@@ -782,6 +704,7 @@ mvs_status mvs_cnn_backward(mvs_cnn* n, const uint8_t* img, const float* plane, 
     if (loss_out) {
         CNK(n, cudaMemcpyAsync(loss_out, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->stream));
         CNK(n, cudaStreamSynchronize(n->stream));
+        return check_status(n);
     }
     return MVS_OK;
 }
@@ -825,7 +748,17 @@ mvs_status mvs_cnn_read(mvs_cnn* n, int32_t tensor, int32_t level, void* host_ou
     if ((int64_t)need != bytes) return cnn_fail(n, MVS_EINVAL, "size mismatch");
     CNK(n, cudaMemcpyAsync(host_out, src, need, cudaMemcpyDeviceToHost, n->stream));
     CNK(n, cudaStreamSynchronize(n->stream));
-    return MVS_OK;
+    return check_status(n);
+}
+
+mvs_status mvs_cnn_test_timeout(mvs_cnn* n) {
+    if (!n) return MVS_EINVAL;
+    // one 16 x 16 convolution of the input buffer whose first wait targets a
+    // barrier that nothing completes, with a wait limit of about 0.1 ms
+    CNK(n, conv_tc_launch(n->x, 16, 16, 16, n->L[E0].wt, n->L[E0].b, 9, n->L[E0].cout, true, false, n->e[0],
+                          n->L[E0].cout, 0, n->status, 1, 1500u, n->stream));
+    CNK(n, cudaStreamSynchronize(n->stream));
+    return check_status(n);
 }
 
 mvs_status mvs_cnn_adam_step(mvs_cnn* n, float lr) {

@@ -191,6 +191,8 @@ def load():
     L.mvs_set_depth_map.argtypes = [vp, i32, vp, vp, i32]
     L.mvs_measure_peaks.restype = i32
     L.mvs_measure_peaks.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.mvs_cnn_test_timeout.restype = i32
+    L.mvs_cnn_test_timeout.argtypes = [vp]
     L.mvs_cnn_read.restype = i32
     L.mvs_cnn_read.argtypes = [vp, i32, i32, vp, C.c_int64]
     L.mvs_cnn_adam_step.restype = i32
@@ -501,6 +503,12 @@ def mvs_cnn_get_grads(net):
     a = np.zeros(mvs_cnn_n_params(net), np.float32)
     _check_cnn(load().mvs_cnn_get_grads(net, a.ctypes.data), net)
     return a
+
+
+def mvs_cnn_test_timeout(net):
+    """Runs the bounded-wait check of the convolutions; returns the status
+    code (MVS_ETIMEOUT expected) without raising."""
+    return load().mvs_cnn_test_timeout(net)
 
 
 def mvs_cnn_read(net, tensor, level, W, H):

@@ -200,3 +200,28 @@ def test_every_layer_in_lockstep(mvs_lib, W, H):
         m.mvs_cnn_destroy(net)
     for name, n, frac in stats:
         print(f"{W}x{H} {name}: {n} values, {frac:.6f} bit-exact")
+
+
+def test_bounded_wait_reports_timeout_and_recovers(mvs_lib):
+    """A convolution whose wait targets a barrier that nothing completes gives
+    up after its bound and reports MVS_ETIMEOUT once; the network then runs
+    normally (the same forward pass gives the same head output as before)."""
+    import torch
+    m = mvs_lib
+    W, H = 64, 48
+    rng = np.random.default_rng(3)
+    img, plane, cost = _state(rng, W, H)
+    net = m.mvs_cnn_create(W, H, D_LO, D_HI, 5, torch.cuda.current_stream())
+    try:
+        dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (img, plane, cost)]
+        out0 = torch.zeros((H, W, 16), dtype=torch.float32, device="cuda")
+        m.mvs_cnn_forward(net, *dev, out0)
+        torch.cuda.synchronize()
+        assert m.mvs_cnn_test_timeout(net) == m.MVS_ETIMEOUT
+        assert m.mvs_cnn_test_timeout(net) == m.MVS_ETIMEOUT        # each check reports its own
+        out1 = torch.zeros_like(out0)
+        m.mvs_cnn_forward(net, *dev, out1)
+        m.mvs_cnn_get_params(net)                                    # synchronises: no pending timeout
+        assert torch.equal(out0, out1)
+    finally:
+        m.mvs_cnn_destroy(net)
