@@ -83,19 +83,6 @@ __global__ void __launch_bounds__(256) k_conv_wgrad(const bf16* __restrict__ x, 
 // ---------------------------------------------------------------------------
 // elementwise pieces
 // ---------------------------------------------------------------------------
-__global__ void k_pool_fwd(const bf16* __restrict__ in, int W, int H, int C, bf16* __restrict__ out) {
-    long long n = (long long)(W / 2) * (H / 2) * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int c = (int)(i % C);
-        long long p = i / C;
-        int x = (int)(p % (W / 2)), y = (int)(p / (W / 2));
-        float s = 0.0f;
-        for (int j = 0; j < 2; ++j)
-            for (int k = 0; k < 2; ++k) s += __bfloat162float(in[((long long)(2 * y + j) * W + 2 * x + k) * C + c]);
-        out[i] = __float2bfloat16(0.25f * s);
-    }
-}
-
 // din (W x H, C) += 1/4 of dout at the parent pixel (accumulate when add != 0)
 __global__ void k_pool_bwd(const bf16* __restrict__ dout, int W, int H, int C, bf16* __restrict__ din, int add) {
     long long n = (long long)W * H * C;
@@ -106,18 +93,6 @@ __global__ void k_pool_bwd(const bf16* __restrict__ dout, int W, int H, int C, b
         float v = 0.25f * __bfloat162float(dout[((long long)(y / 2) * (W / 2) + x / 2) * C + c]);
         if (add) v += __bfloat162float(din[i]);
         din[i] = __float2bfloat16(v);
-    }
-}
-
-// nearest up-sampling of in (W/2 x H/2, C) into channels [0, C) of out
-// (W x H, out_ch)
-__global__ void k_up_fwd(const bf16* __restrict__ in, int W, int H, int C, bf16* __restrict__ out, int out_ch) {
-    long long n = (long long)W * H * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int c = (int)(i % C);
-        long long p = i / C;
-        int x = (int)(p % W), y = (int)(p / W);
-        out[p * out_ch + c] = in[((long long)(y / 2) * (W / 2) + x / 2) * C + c];
     }
 }
 
@@ -146,6 +121,51 @@ __global__ void k_copy_ch(const bf16* __restrict__ src, int s_ch, int s_off, bf1
         float v = __bfloat162float(src[p * s_ch + s_off + c]);
         if (add) v += __bfloat162float(dst[p * d_ch + d_off + c]);
         dst[p * d_ch + d_off + c] = __float2bfloat16(v);
+    }
+}
+
+// Forward-pass data movement in 16-byte vectors (8 channels per thread,
+// channel counts are multiples of 16, rows of pixels at most 8192 wide).
+// 2 x 2 average pooling: out (W/2 x H/2, C) from in (W x H, C), summed in
+// the order (0,0), (0,1), (1,0), (1,1) and scaled by 1/4 in fp32.
+__global__ void k_pool_fwd_v(const uint4* __restrict__ in, int W, int H, int C, uint4* __restrict__ out) {
+    const int cv = C / 8, Wo = W / 2;
+    const long long n = (long long)Wo * (H / 2) * cv;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % cv);
+        const int p = (int)(i / cv), x = p % Wo, y = p / Wo;
+        const uint4 q[4] = {in[((long long)(2 * y) * W + 2 * x) * cv + c], in[((long long)(2 * y) * W + 2 * x + 1) * cv + c],
+                            in[((long long)(2 * y + 1) * W + 2 * x) * cv + c],
+                            in[((long long)(2 * y + 1) * W + 2 * x + 1) * cv + c]};
+        uint32_t r[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 s = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t w = (&q[j].x)[k];
+                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+                s.x += f.x;
+                s.y += f.y;
+            }
+            __nv_bfloat162 h = __floats2bfloat162_rn(0.25f * s.x, 0.25f * s.y);
+            r[k] = *reinterpret_cast<uint32_t*>(&h);
+        }
+        out[i] = make_uint4(r[0], r[1], r[2], r[3]);
+    }
+}
+
+// decoder input: out (W x H, up_ch + C) = [nearest up-sampling of prev
+// (W/2 x H/2, up_ch) | skip (W x H, C)], copies of 16-byte vectors
+__global__ void k_concat_up(const uint4* __restrict__ prev, int up_ch, const uint4* __restrict__ skip, int C, int W,
+                            int H, uint4* __restrict__ out) {
+    const int uv = up_ch / 8, sv = C / 8, ov = uv + sv;
+    const long long n = (long long)W * H * ov;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % ov);
+        const long long p = i / ov;
+        const int x = (int)(p % W), y = (int)(p / W);
+        out[i] = c < uv ? prev[((long long)(y / 2) * (W / 2) + x / 2) * uv + c] : skip[p * sv + (c - uv)];
     }
 }
 
@@ -252,9 +272,16 @@ __global__ void k_make_input(const uint8_t* __restrict__ img, const float4* __re
     if (i >= npix) return;
     float4 p = plane[i];
     float rho = p.w > 0.0f ? 1.0f / p.w : hc.rho_lo;
-    float v[16] = {img[i] / 255.0f, (rho - hc.rho_lo) / (hc.rho_hi - hc.rho_lo), p.x, p.y, p.z, cost[i] * 0.5f,
-                   0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int c = 0; c < 16; ++c) in[16 * i + c] = __float2bfloat16(v[c]);
+    float v[6] = {img[i] / 255.0f, (rho - hc.rho_lo) / (hc.rho_hi - hc.rho_lo), p.x, p.y, p.z, cost[i] * 0.5f};
+    uint32_t w[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+        w[c] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    uint4* o = reinterpret_cast<uint4*>(in + 16 * i);
+    o[0] = make_uint4(w[0], w[1], w[2], 0u);
+    o[1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 unsigned blocks(long long n, int b = 256) {
@@ -382,8 +409,9 @@ cudaError_t cnn_forward(mvs_cnn* n, int W, int H) {
     for (int l = 0; l <= 4; ++l) {
         const Layer& L = C(E0 + l);
         if (l > 0) {
-            k_pool_fwd<<<blocks((long long)Ws[l] * Hs[l] * C(E0 + l - 1).cout), 256, 0, s>>>(
-                n->e[l - 1], Ws[l - 1], Hs[l - 1], C(E0 + l - 1).cout, n->p[l - 1]);
+            k_pool_fwd_v<<<blocks((long long)Ws[l] * Hs[l] * C(E0 + l - 1).cout / 8), 256, 0, s>>>(
+                reinterpret_cast<const uint4*>(n->e[l - 1]), Ws[l - 1], Hs[l - 1], C(E0 + l - 1).cout,
+                reinterpret_cast<uint4*>(n->p[l - 1]));
             count_launch();
             in = n->p[l - 1];
         }
@@ -395,10 +423,9 @@ cudaError_t cnn_forward(mvs_cnn* n, int W, int H) {
     for (int l = 3; l >= 0; --l) {
         const Layer& L = C(D3 + (3 - l));
         int ch = L.cin;
-        k_up_fwd<<<blocks((long long)Ws[l] * Hs[l] * prev_ch), 256, 0, s>>>(prev, Ws[l], Hs[l], prev_ch, n->c[l], ch);
-        count_launch();
-        k_copy_ch<<<blocks((long long)Ws[l] * Hs[l] * C(E0 + l).cout), 256, 0, s>>>(
-            n->e[l], C(E0 + l).cout, 0, n->c[l], ch, prev_ch, C(E0 + l).cout, (long long)Ws[l] * Hs[l], 0);
+        k_concat_up<<<blocks((long long)Ws[l] * Hs[l] * ch / 8), 256, 0, s>>>(
+            reinterpret_cast<const uint4*>(prev), prev_ch, reinterpret_cast<const uint4*>(n->e[l]), C(E0 + l).cout,
+            Ws[l], Hs[l], reinterpret_cast<uint4*>(n->c[l]));
         count_launch();
         CUK(conv_launch(n, n->c[l], ch, Ws[l], Hs[l], L.wt, L.b, 9, L.cout, true, false, n->d[l], L.cout, 0, s));
         prev = n->d[l];

@@ -3,13 +3,21 @@
 // hypotheses).  One CTA of four warps computes an implicit GEMM tile:
 //   M = 128 pixels (a Wt x Ht block of the image, Wt Ht = 128),
 //   N = all output channels (16..224, one MMA width),
-//   K = taps x input channels, in k-steps of one tap and up to 64 channels.
+//   K = taps x input channels, in k-steps of one chunk of up to 64 input
+//   channels (all nine taps, halo tiles) or of one tap and one chunk.
 // Operands are staged in shared memory by the tensor-memory accelerator in
 // the K-major, non-swizzled core-matrix layout of tcgen05 (8 rows x 16 bytes
-// per core matrix): the activations by one 3D tiled copy per tap and group
-// of 8 channels (channels-last tensor, box 8 x Wt x Ht; taps that leave the
-// image read the copy's zero fill, which is the convolution's padding), the
-// weights by one bulk copy per k-step from a layout prepared in that order.
+// per core matrix), taps that leave the image reading the copy's zero fill
+// (the convolution's padding):
+//  - rows of at least 128 pixels (3 x 3 filters): a tile is 128 pixels of
+//    one row and each group of 8 input channels is copied once with its
+//    halo, box 8 x 130 x 3; the nine taps are nine descriptors into that box
+//    (start shifted by the tap's row and column), so the activations are
+//    read three times instead of nine;
+//  - narrower images and 1 x 1 filters: a tile is a Wt x Ht block and each
+//    tap and group of 8 channels is one box 8 x Wt x Ht.
+// The weights come by one bulk copy per k-step from a layout prepared in the
+// operand's order, chunk-major: [chunk][tap][channels of the chunk / 8][N][8].
 // One thread issues the copies and the tcgen05.mma instructions (bf16 x bf16,
 // fp32 accumulation in tensor memory) through a ring of 2-4 stages guarded
 // by mbarriers; then every thread reads its pixel's accumulators with
@@ -32,16 +40,20 @@ namespace {
 
 constexpr int kTcThreads = 128;
 constexpr int kTileM = 128;
-constexpr int kChunk = 64;                   // input channels per k-step
-constexpr uint32_t kBoxBytes = kTileM * 16;  // one 8-channel box of the tile
+constexpr uint32_t kBoxBytes = kTileM * 16;  // one 8-channel box of a block tile
+constexpr int kHaloW = kTileM + 2, kHaloH = 3;
+constexpr uint32_t kHaloBytes = kHaloW * kHaloH * 16;            // one 8-channel box with its halo
+constexpr uint32_t kHaloStride = (kHaloBytes + 127u) & ~127u;     // boxes 128-byte aligned
+constexpr size_t kStageBudget = 200 * 1024;
 
 struct TcArgs {
     int W, H, Cin, Cout, taps;
     int Wt, Ht, tiles_x;
-    int nchunk, stages;
+    int halo;                        // 1: 128-pixel row tiles with a shared halo box
+    int kc, nchunk, stages;          // input channels per chunk, chunks, pipeline stages
     uint32_t stage_bytes, a_bytes;   // per stage: A part then B part (both 1024-aligned offsets)
     int relu, out_f32;
-    const __nv_bfloat16* wt;         // [tap][Cin / 8][Cout][8]
+    const __nv_bfloat16* wt;         // [chunk][tap][chunk channels / 8][Cout][8]
     const float* bias;               // Cout, or null
     void* out;
     int out_ch, out_off;
@@ -174,7 +186,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     const int tile = blockIdx.x;
     const int x0 = (tile % a.tiles_x) * a.Wt, y0 = (tile / a.tiles_x) * a.Ht;
-    const int ksteps = a.taps * a.nchunk;
+    const int ksteps = a.halo ? a.nchunk : a.taps * a.nchunk;
     const uint32_t idesc = mma_idesc((uint32_t)a.Cout);
     const uint32_t done_bar = smem_u32(bars + 2 * S);
     bool failed = false;
@@ -192,18 +204,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     failed = true;
                     break;
                 }
-                const int tap = i / a.nchunk, chunk = i % a.nchunk;
-                const int kc = min(kChunk, a.Cin - chunk * kChunk);
-                const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
+                const int tap = a.halo ? 0 : i / a.nchunk, chunk = a.halo ? i : i % a.nchunk;
+                const int kc = min(a.kc, a.Cin - chunk * a.kc);
                 const uint32_t sa = smem_u32(smem + (size_t)s * a.stage_bytes);
                 const uint32_t sb = sa + a.a_bytes;
-                const uint32_t bbytes = (uint32_t)kc * (uint32_t)a.Cout * 2u;
                 const uint32_t full = smem_u32(bars + s);
-                mbar_expect_tx(full, (uint32_t)(kc / 8) * kBoxBytes + bbytes);
-                for (int b = 0; b < kc / 8; ++b)
-                    tma_load_3d(sa + (uint32_t)b * kBoxBytes, &amap, chunk * kChunk + 8 * b, x0 + dx, y0 + dy, full);
-                const __nv_bfloat16* wsrc = a.wt + ((size_t)tap * (a.Cin / 8) + (size_t)chunk * (kChunk / 8)) *
-                                                       (size_t)a.Cout * 8;
+                // weights of the chunk (all taps with halo tiles, else one tap)
+                const __nv_bfloat16* wsrc =
+                    a.wt + (size_t)chunk * a.taps * a.kc * a.Cout + (size_t)tap * kc * a.Cout;
+                const uint32_t bbytes = (uint32_t)((a.halo ? a.taps : 1) * kc) * (uint32_t)a.Cout * 2u;
+                if (a.halo) {
+                    mbar_expect_tx(full, (uint32_t)(kc / 8) * kHaloBytes + bbytes);
+                    for (int b = 0; b < kc / 8; ++b)
+                        tma_load_3d(sa + (uint32_t)b * kHaloStride, &amap, chunk * a.kc + 8 * b, x0 - 1, y0 - 1, full);
+                } else {
+                    const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
+                    mbar_expect_tx(full, (uint32_t)(kc / 8) * kBoxBytes + bbytes);
+                    for (int b = 0; b < kc / 8; ++b)
+                        tma_load_3d(sa + (uint32_t)b * kBoxBytes, &amap, chunk * a.kc + 8 * b, x0 + dx, y0 + dy, full);
+                }
                 bulk_load(sb, wsrc, bbytes, full);
                 issued = i + 1;
             }
@@ -215,15 +234,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const int chunk = j % a.nchunk;
-                const int kc = min(kChunk, a.Cin - chunk * kChunk);
+                const int chunk = a.halo ? j : j % a.nchunk;
+                const int kc = min(a.kc, a.Cin - chunk * a.kc);
                 const uint32_t sa = smem_u32(smem + (size_t)s * a.stage_bytes);
                 const uint32_t sb = sa + a.a_bytes;
-                for (int kk = 0; kk < kc / 16; ++kk) {
-                    const uint64_t ad = smem_desc(sa + (uint32_t)kk * 2u * kBoxBytes, kBoxBytes, 128u);
-                    const uint64_t bd =
-                        smem_desc(sb + (uint32_t)kk * 2u * (uint32_t)a.Cout * 16u, (uint32_t)a.Cout * 16u, 128u);
-                    mma_bf16(tmem, ad, bd, idesc, (j > 0 || kk > 0) ? 1u : 0u);
+                const uint32_t nb = (uint32_t)a.Cout * 16u;   // bytes of one 8-channel group of the weights
+                if (a.halo) {
+                    // tap (dy, dx): the 128 rows starting at halo row (dy + 1, dx + 1)
+                    for (int t = 0; t < 9; ++t) {
+                        const uint32_t shift = (uint32_t)((t / 3) * kHaloW + t % 3) * 16u;
+                        for (int kk = 0; kk < kc / 16; ++kk) {
+                            const uint64_t ad = smem_desc(sa + (uint32_t)kk * 2u * kHaloStride + shift, kHaloStride, 128u);
+                            const uint64_t bd = smem_desc(sb + ((uint32_t)t * (uint32_t)(kc / 8) + 2u * kk) * nb, nb, 128u);
+                            mma_bf16(tmem, ad, bd, idesc, (j > 0 || t > 0 || kk > 0) ? 1u : 0u);
+                        }
+                    }
+                } else {
+                    for (int kk = 0; kk < kc / 16; ++kk) {
+                        const uint64_t ad = smem_desc(sa + (uint32_t)kk * 2u * kBoxBytes, kBoxBytes, 128u);
+                        const uint64_t bd = smem_desc(sb + 2u * kk * nb, nb, 128u);
+                        mma_bf16(tmem, ad, bd, idesc, (j > 0 || kk > 0) ? 1u : 0u);
+                    }
                 }
                 mma_commit(smem_u32(bars + S + s));   // stage s free once these MMAs have read it
                 consumed = j + 1;
@@ -283,21 +314,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
 }
 
-// weights [co][tap][ci] (fp32) -> the core-matrix order of the B operand,
-// [tap][ci / 8][co][8], as bf16; `flip` gives the data-gradient form (the
-// transposed, flipped filter: output channel ci, input channel co, tap
-// taps - 1 - tap)
-__global__ void k_weights_tc(const float* __restrict__ w, int co_n, int taps, int ci_n, int flip,
+// weights [co][tap][ci] (fp32) -> the B operand as bf16 in the order
+// conv_tc_launch reads: chunk-major over the convolution's input channels K
+// (chunks of kc, the last one shorter), then tap, then groups of 8 input
+// channels, output channels N, 8 input channels: element (t, k, n) at
+//   c taps kc N + t kcc N + ((k - c kc) / 8) N 8 + n 8 + (k - c kc) % 8,
+// c = k / kc, kcc = the size of chunk c.  `flip` gives the data-gradient
+// filter: N = ci, K = co, taps reversed.
+__global__ void k_weights_tc(const float* __restrict__ w, int co_n, int taps, int ci_n, int flip, int kc,
                              __nv_bfloat16* __restrict__ out) {
     const long long n = (long long)co_n * taps * ci_n;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int ci = (int)(i % ci_n);
         const long long r = i / ci_n;
         const int tap = (int)(r % taps), co = (int)(r / taps);
-        // GEMM view: N = output channels of this convolution, K = its input channels
         const int nn = flip ? ci : co, kk = flip ? co : ci, t = flip ? taps - 1 - tap : tap;
         const int N = flip ? ci_n : co_n, K = flip ? co_n : ci_n;
-        out[(((long long)t * (K / 8) + kk / 8) * N + nn) * 8 + kk % 8] = __float2bfloat16(w[i]);
+        const int c = kk / kc, kin = kk - c * kc, kcc = min(kc, K - c * kc);
+        const long long o = (long long)c * taps * kc * N + (long long)t * kcc * N + (long long)(kin / 8) * N * 8 +
+                            (long long)nn * 8 + kin % 8;
+        out[o] = __float2bfloat16(w[i]);
     }
 }
 
@@ -326,24 +362,37 @@ int next_pow2(int v) {
 
 }  // namespace
 
+// input channels per chunk of a convolution with K input and N output
+// channels: the largest of 64, 32, 16 whose halo-tile stage (taps = 9) or
+// block-tile stage fits twice in the stage budget
+int conv_tc_chunk(int K, int N, int taps) {
+    for (int kc : {64, 32, 16}) {
+        const int k = std::min(kc, K);
+        const size_t a = taps == 9 ? (size_t)(k / 8) * kHaloStride : (size_t)(k / 8) * kBoxBytes;
+        const size_t b = (size_t)taps * k * N * 2;
+        const size_t stage = ((a + 1023) & ~(size_t)1023) + ((b + 1023) & ~(size_t)1023);
+        if (2 * stage <= kStageBudget || kc == 16) return std::min(kc, K);
+    }
+    return 16;
+}
+
 cudaError_t conv_tc_weights(const float* w, int co_n, int taps, int ci_n, int flip, __nv_bfloat16* out,
                             cudaStream_t s) {
     const long long n = (long long)co_n * taps * ci_n;
+    const int kc = flip ? conv_tc_chunk(co_n, ci_n, taps) : conv_tc_chunk(ci_n, co_n, taps);
     k_weights_tc<<<(unsigned)std::min<long long>((n + 255) / 256, 152LL * 16), 256, 0, s>>>(w, co_n, taps, ci_n,
-                                                                                           flip, out);
+                                                                                           flip, kc, out);
     count_launch();
     return cudaGetLastError();
 }
 
-size_t conv_tc_smem_bytes(int Cin, int Cout, int* stages) {
-    const int kc = std::min(kChunk, Cin);
-    const size_t a_bytes = ((size_t)(kc / 8) * kBoxBytes + 1023) & ~(size_t)1023;
-    const size_t b_bytes = ((size_t)kc * Cout * 2 + 1023) & ~(size_t)1023;
-    const size_t stage = a_bytes + b_bytes;
-    int S = (int)std::min<size_t>(4, (size_t)(200 * 1024) / stage);
-    S = std::max(S, 2);
-    if (stages) *stages = S;
-    return (size_t)S * stage + (2 * S + 1) * 8 + 16 + 1024;
+// per-stage bytes (A part, whole stage) of a launch
+static void stage_bytes(int Cin, int Cout, int taps, int kc, bool halo, uint32_t* a_bytes, uint32_t* stage) {
+    const size_t a = halo ? (size_t)(kc / 8) * kHaloStride : (size_t)(kc / 8) * kBoxBytes;
+    const size_t b = (size_t)(halo ? taps : 1) * kc * Cout * 2;
+    *a_bytes = (uint32_t)((a + 1023) & ~(size_t)1023);
+    *stage = *a_bytes + (uint32_t)((b + 1023) & ~(size_t)1023);
+    (void)Cin;
 }
 
 cudaError_t conv_tc_launch(const __nv_bfloat16* in, int Cin, int W, int H, const __nv_bfloat16* wt, const float* bias,
@@ -358,15 +407,16 @@ cudaError_t conv_tc_launch(const __nv_bfloat16* in, int Cin, int W, int H, const
     if (!enc) return cudaErrorNotSupported;
     TcArgs a{};
     a.W = W; a.H = H; a.Cin = Cin; a.Cout = Cout; a.taps = taps;
-    a.Wt = std::min(kTileM, next_pow2(W));
+    a.halo = taps == 9 && W >= kTileM;
+    a.Wt = a.halo ? kTileM : std::min(kTileM, next_pow2(W));
     a.Ht = kTileM / a.Wt;
     a.tiles_x = (W + a.Wt - 1) / a.Wt;
     const int tiles_y = (H + a.Ht - 1) / a.Ht;
-    a.nchunk = (Cin + kChunk - 1) / kChunk;
-    const size_t smem = conv_tc_smem_bytes(Cin, Cout, &a.stages);
-    const int kc = std::min(kChunk, Cin);
-    a.a_bytes = (uint32_t)(((size_t)(kc / 8) * kBoxBytes + 1023) & ~(size_t)1023);
-    a.stage_bytes = a.a_bytes + (uint32_t)(((size_t)kc * Cout * 2 + 1023) & ~(size_t)1023);
+    a.kc = conv_tc_chunk(Cin, Cout, taps);
+    a.nchunk = (Cin + a.kc - 1) / a.kc;
+    stage_bytes(Cin, Cout, taps, a.kc, a.halo, &a.a_bytes, &a.stage_bytes);
+    a.stages = (int)std::max<size_t>(2, std::min<size_t>(4, kStageBudget / a.stage_bytes));
+    const size_t smem = (size_t)a.stages * a.stage_bytes + (2 * a.stages + 1) * 8 + 16 + 1024;
     a.relu = relu; a.out_f32 = out_f32;
     a.wt = wt; a.bias = bias; a.out = out; a.out_ch = out_ch; a.out_off = out_off;
     a.status = status; a.force_timeout = force_timeout; a.wait_limit = wait_limit;
@@ -374,7 +424,7 @@ cudaError_t conv_tc_launch(const __nv_bfloat16* in, int Cin, int W, int H, const
     CUtensorMap map;
     const cuuint64_t dims[3] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H};
     const cuuint64_t strides[2] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2};
-    const cuuint32_t box[3] = {8, (cuuint32_t)a.Wt, (cuuint32_t)a.Ht};
+    const cuuint32_t box[3] = {8, (cuuint32_t)(a.halo ? kHaloW : a.Wt), (cuuint32_t)(a.halo ? kHaloH : a.Ht)};
     const cuuint32_t estr[3] = {1, 1, 1};
     if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(in), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,

@@ -4,12 +4,12 @@
 #include <cuda_runtime.h>
 
 // weights [co][tap][ci] (fp32) -> bf16 B operand in the order conv_tc_launch
-// reads, [tap][K / 8][N][8]; flip = 1 gives the data-gradient filter (N = ci,
-// K = co, taps reversed)
+// reads (chunk-major, see conv_tc.cu); flip = 1 gives the data-gradient
+// filter (N = ci, K = co, taps reversed)
 cudaError_t conv_tc_weights(const float* w, int co_n, int taps, int ci_n, int flip, __nv_bfloat16* out,
                             cudaStream_t s);
-// dynamic shared memory of one CTA and its number of pipeline stages
-size_t conv_tc_smem_bytes(int Cin, int Cout, int* stages);
+// input channels per pipeline chunk of a convolution (K inputs, N outputs)
+int conv_tc_chunk(int K, int N, int taps);
 // out[p][out_off + n] = act(bias[n] + sum over taps t and input channels k of
 // in[p + offset(t)][k] wt[t][k][n]) for the W x H channels-last tensor `in`
 // (Cin channels, zero outside the image), n < Cout; taps 9 (3 x 3) or 1.
