@@ -60,7 +60,7 @@ def measured_peaks(mvs, device):
         f, g, b = mvs.mvs_measure_peaks(device)
     return {"fp32_tflops": f / 1e12, "l1_gathers_per_s": g, "l2_gbs": b / 1e9, "clocks": clk.summary(),
             "how": "mvs_measure_peaks: FFMA chains, 8-byte L1 gathers in the window-sample pattern, "
-                   "64 MB L2-resident stream; one timed launch each after a warm-up"}
+                   "64 MB L2-resident stream; fastest of five timed launches each after a warm-up"}
 
 
 def roofline_fractions(sample_evals_per_s, peaks, n, step):

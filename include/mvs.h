@@ -400,8 +400,8 @@ mvs_status mvs_profile_read(mvs_ctx* ctx, double* phase_ms, int64_t* phase_launc
                             int64_t* phase_evals);
 
 /* Measured peaks of device `device` for the roofline of the PatchMatch
- * kernels (no counterpart in the paper), each from one timed launch after a
- * warm-up launch of a small kernel of this library:
+ * kernels (no counterpart in the paper), each the fastest of five timed
+ * launches after a warm-up launch of a small kernel of this library:
  *   fp32_flops: FP32 FMA rate (flop/s, FMA = 2) of 16 independent chains per
  *     thread on every SM;
  *   gathers: 8-byte loads per second served from L1 in the window-sample

@@ -185,8 +185,8 @@ void make_refconst(const mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n
     for (int i = 0; i < 9; ++i) rc.Kinv[i] = (float)R.Kinv[i];
     rc.tex = R.tex;
     rc.img = R.img;
-    rc.pitch = rc.W + 1;
-    rc.n_tex = (uint32_t)((rc.W + 1) * (rc.H + 1));
+    rc.pitch = tex_pitch(rc.W);
+    rc.n_tex = (uint32_t)rc.pitch * (uint32_t)(rc.H + 1);
     rc.n = p->win_samples;
     double r_now = 0.5 * (p->win_samples - 1);
     rc.step = (float)(p->win_radius / r_now);
@@ -230,8 +230,8 @@ void make_refconst(const mvs_ctx* c, int32_t ref, const int32_t* srcs, int32_t n
         P.tex = S.tex;
         P.W = S.cam.width;
         P.H = S.cam.height;
-        P.pitch = P.W + 1;
-        P.n_tex = (uint32_t)((P.W + 1) * (P.H + 1));
+        P.pitch = tex_pitch(P.W);
+        P.n_tex = (uint32_t)P.pitch * (uint32_t)(P.H + 1);
     }
 }
 
@@ -294,9 +294,10 @@ mvs_status mvs_create(const mvs_camera* cams, const uint8_t* const* images, int3
         V.cam = cams[i];
         m3_inv(V.cam.K, V.Kinv);
         size_t n = (size_t)V.cam.width * V.cam.height;
-        size_t nt = (size_t)(V.cam.width + 1) * (V.cam.height + 1);
+        size_t nt = (size_t)tex_pitch(V.cam.width) * (V.cam.height + 1);
         e = cudaMalloc(&V.img, n);
         if (e == cudaSuccess) e = cudaMalloc(&V.tex, nt * sizeof(uint2));
+        if (e == cudaSuccess) e = cudaMemsetAsync(V.tex, 0, nt * sizeof(uint2), c->stream);   // row padding
         if (e == cudaSuccess) e = cudaMemcpyAsync(V.img, images[i], n, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = launch_build_texture(V.img, V.cam.width, V.cam.height, V.tex, c->stream);
         if (e != cudaSuccess) {

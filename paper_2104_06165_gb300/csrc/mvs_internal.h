@@ -26,8 +26,8 @@ struct PairConst {
     float Bh[3], Bl[3];  // B, hi and lo parts
     const uint2* tex;    // bilinear-coefficient texels of the source, see below
     int W, H;            // source image size
-    int pitch;           // texel row pitch = W + 1
-    uint32_t n_tex;      // (W + 1) * (H + 1)
+    int pitch;           // texel row pitch, tex_pitch(W)
+    uint32_t n_tex;      // pitch * (H + 1)
 };
 
 // Per reference-view launch constants (kernel parameter, < 4 KB).
@@ -38,8 +38,8 @@ struct RefConst {
     float Kinv[9];
     const uint2* tex;          // reference bilinear-coefficient texels
     const uint8_t* img;        // reference image (uint8)
-    int pitch;                 // W + 1
-    uint32_t n_tex;
+    int pitch;                 // tex_pitch(W)
+    uint32_t n_tex;            // pitch * (H + 1)
     // window (Sec. III-C): n samples per axis, offsets step * (k - (n-1)/2)
     int n;
     float step;
@@ -70,8 +70,29 @@ struct RefConst {
 };
 static_assert(sizeof(RefConst) <= 4096, "RefConst is passed as a kernel parameter (4 KB)");
 
+// Row pitch (texels) of a bilinear-coefficient texture and the offsets that
+// let the kernels form a texel index in one integer multiply-add.  A sample
+// at doubled, half-shifted coordinates rounds to texel (i + 1, j + 1)
+// through the sums 1.5 * 2^24 + 2 (i + 1 + alpha) and 1.5 * 2^24 +
+// 2 (j + 1 + beta) (bits M + i + 1 + alpha and M + j + 1 + beta); their
+// product-sum bits(y) p + bits(x) equals the index (j + 1) p + (i + 1)
+// modulo 2^32 when beta p + alpha = -M (p + 1) modulo 2^32.  For p >= 1029
+// that holds with beta < 2^22 - 2^14 and alpha < p, so both sums stay in the
+// binade of 1.5 * 2^24 (exact integers); narrower images take the smallest
+// p >= W + 1 with p + 1 a multiple of 1024, where M (p + 1) vanishes modulo
+// 2^32 (M = 2^22 times an odd number) and alpha = beta = 0.  Wide images keep
+// p = W + 1: a padded pitch near a power of two would alias the rows of a
+// window in the L1 sets.
+constexpr uint32_t kMagicBits = 0x4BC00000u;   // bits of 1.5 * 2^24
+__host__ __device__ inline int tex_pitch(int W) { return W + 1 >= 1029 ? W + 1 : ((W + 2 + 1023) / 1024) * 1024 - 1; }
+__host__ __device__ inline void tex_fold(int pitch, uint32_t* alpha, uint32_t* beta) {
+    const uint32_t k = 0u - kMagicBits * (uint32_t)(pitch + 1);
+    *beta = k / (uint32_t)pitch;
+    *alpha = k - *beta * (uint32_t)pitch;
+}
+
 // Bilinear-coefficient texel layout.  Texel (i, j), i in [-1, W-1],
-// j in [-1, H-1], stored at ((j + 1) * (W + 1) + (i + 1)), holds four fp16
+// j in [-1, H-1], stored at ((j + 1) * pitch + (i + 1)), holds four fp16
 // numbers computed from the clamped taps p00 = I(i, j), p01 = I(i+1, j),
 // p10 = I(i, j+1), p11 = I(i+1, j+1) on the [0, 255] scale:
 //   a = p00 + p01 + p10 + p11                 (integer in [0, 1020])
@@ -93,7 +114,7 @@ extern std::atomic<long long> g_kernel_launches;
 inline void count_launch(long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // Host-side launchers (pm_kernels.cu / phi_kernels.cu).
-cudaError_t launch_build_texture(const uint8_t* img, int W, int H, uint2* tex, cudaStream_t s);
+cudaError_t launch_build_texture(const uint8_t* img, int W, int H, uint2* tex, cudaStream_t s);   // pitch tex_pitch(W)
 cudaError_t launch_init(const RefConst& rc, float* view_cost, cudaStream_t s);
 cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, float* view_cost, cudaStream_t s);
 cudaError_t launch_phase(const RefConst& rc, int phase, cudaStream_t s);

@@ -86,19 +86,24 @@ extern "C" mvs_status mvs_measure_peaks(int32_t device, double* fp32_flops, doub
         if (e != cudaSuccess && st == MVS_OK) st = e == cudaErrorMemoryAllocation ? MVS_ENOMEM : MVS_ECUDA;
         return e == cudaSuccess;
     };
-    // times `launch` (after one warm-up run) and returns seconds
+    // times `launch` (after one warm-up run) and returns the shortest of
+    // five runs in seconds (a peak: the least disturbed run)
     auto timed = [&](auto launch) -> double {
         launch();
         if (!ck(cudaGetLastError())) return 0.0;
-        ck(cudaEventRecord(e0, s));
-        launch();
-        ck(cudaEventRecord(e1, s));
-        ck(cudaGetLastError());
-        ck(cudaEventSynchronize(e1));
-        float ms = 0.0f;
-        ck(cudaEventElapsedTime(&ms, e0, e1));
-        count_launch(2);
-        return ms * 1e-3;
+        float best = 3.0e38f;
+        for (int rep = 0; rep < 5; ++rep) {
+            ck(cudaEventRecord(e0, s));
+            launch();
+            ck(cudaEventRecord(e1, s));
+            ck(cudaGetLastError());
+            ck(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            ck(cudaEventElapsedTime(&ms, e0, e1));
+            best = std::min(best, ms);
+        }
+        count_launch(6);
+        return best * 1e-3;
     };
     const unsigned grid = (unsigned)sms * 8u;   // 8 blocks of 8 warps per SM
     if (ck(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) && ck(cudaEventCreate(&e0)) &&

@@ -262,10 +262,10 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
 // homography rows G and B of PairConst with their hi and lo parts.
 struct __align__(16) ViewSm {
     const uint2* tex;
-    // index of texel (i + 1, j + 1) = bits(1.5 * 2^24 + 2 j) * pitch
-    // + bits(1.5 * 2^24 + 2 i) + toff (mod 2^32), see tex_sample
-    uint32_t pitch, toff;
-    uint32_t last, pad_;  // last texel index (W + 1) (H + 1) - 1
+    uint32_t pitch;
+    float fold_x;         // 2 + 2 alpha: the guard texel and tex_fold's alpha in doubled coordinates
+    uint32_t last;        // last texel index pitch (H + 1) - 1
+    float fold_y;         // 2 + 2 beta
     float xmax2, ymax2;   // 2 W - 3, 2 H - 3: doubled, half-shifted image bounds
     float gx0, gx1, gy0, gy1;   // G_0, G_1 columns 0 and 1 (hi)
     float gz0, gz1, bxh, byh;   // G_2 columns 0 and 1 (hi); B_0, B_1 (hi)
@@ -275,8 +275,9 @@ struct __align__(16) ViewSm {
     float gy1l, gy2l, gz0l, gz1l;
 };
 
-static_assert(sizeof(ViewSm) == 128 && offsetof(ViewSm, pitch) == 8 && offsetof(ViewSm, toff) == 12 &&
-                  offsetof(ViewSm, last) == 16 && offsetof(ViewSm, xmax2) == 24 && offsetof(ViewSm, gx0) == 32 &&
+static_assert(sizeof(ViewSm) == 128 && offsetof(ViewSm, pitch) == 8 && offsetof(ViewSm, fold_x) == 12 &&
+                  offsetof(ViewSm, last) == 16 && offsetof(ViewSm, fold_y) == 20 && offsetof(ViewSm, xmax2) == 24 &&
+                  offsetof(ViewSm, gx0) == 32 &&
                   offsetof(ViewSm, gz0) == 48 && offsetof(ViewSm, bzh) == 64 && offsetof(ViewSm, gx2) == 80 &&
                   offsetof(ViewSm, gx0l) == 96 && offsetof(ViewSm, gy1l) == 112,
               "eval_batch and pix_views read ViewSm as 128-bit words");
@@ -287,9 +288,11 @@ __device__ __forceinline__ void load_views(const RefConst& rc, ViewSm* sv) {
         ViewSm& v = sv[j];
         v.tex = P.tex;
         v.pitch = (uint32_t)P.pitch;
-        v.toff = (uint32_t)(P.pitch + 1) * (uint32_t)(1 - kMagic2Bits);
+        uint32_t alpha, beta;
+        tex_fold(P.pitch, &alpha, &beta);
+        v.fold_x = 2.0f + 2.0f * (float)alpha;
+        v.fold_y = 2.0f + 2.0f * (float)beta;
         v.last = P.n_tex - 1u;
-        v.pad_ = 0u;
         v.xmax2 = (float)(2 * P.W - 3);
         v.ymax2 = (float)(2 * P.H - 3);
         v.gx0 = P.Gh[0]; v.gx1 = P.Gh[1]; v.gx2 = P.Gh[2];
@@ -421,8 +424,8 @@ __device__ __forceinline__ bool same_plane(const float4& a, const float4& b) {
 //      nc * n_src entries) in view-major order, with their anchored
 //      homography (PairSm);
 //   2. each group of G lanes takes the next pair: S bilinear gathers per
-//      lane, the weighted mean, then the centred moments (group reductions),
-//      ZNCC (Eq. 4),
+//      lane, the weighted moments in one pass (group reductions; a centred
+//      second pass where the one-pass form would cancel), ZNCC (Eq. 4),
 //      C(x,j) = 1 - Z; a view is excluded when its weighted variance is below
 //      1e-6 on the [0,1] scale (reading);
 //   3. lane c folds the per-view results of hypothesis c in view order
@@ -518,7 +521,10 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             float4* qw = reinterpret_cast<float4*>(pairs + count + __popc(m & ((1u << lane) - 1u)));
             qw[0] = make_float4(j0x, j0y, h0z, j1x);
             qw[1] = make_float4(j1y, h1z, nx, ny);
-            qw[2] = make_float4(pz, kMagic2 + ax, kMagic2 + ay, __int_as_float(c | (j << 8)));
+            // magic numbers with the anchor, the texture's guard texel and the
+            // index fold (tex_fold): bits(ty) pitch + bits(tx) = texel index
+            const float fx = reinterpret_cast<const float4*>(sv + j)[0].w;
+            qw[2] = make_float4(pz, kMagic2 + (ax + fx), kMagic2 + (ay + w1.y), __int_as_float(c | (j << 8)));
         } else if (act) {
             tab[c * V + j] = 0.0f;   // view excluded for this hypothesis
         }
@@ -535,12 +541,13 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         const float j1y = qb.x, h1z = qb.y, nx = qb.z, ny = qb.w;
         const float pz = qc.x, mx = qc.y, my_ = qc.z;
         const int cj = __float_as_int(qc.w), pj = cj >> 8, pc = cj & 255;
-        // view words 0 (texels, pitch, toff) and 1 (last texel)
+        // view words 0 (texels, pitch) and 1 (last texel)
         const uint4 v0 = reinterpret_cast<const uint4*>(sv + pj)[0];
         const uint32_t v_last = reinterpret_cast<const uint4*>(sv + pj)[1].x;
         const uint2* v_tex = reinterpret_cast<const uint2*>(((unsigned long long)v0.y << 32) | v0.x);
         float sa = 0.0f, sb = 0.0f, se = 0.0f;
         float sval[S], c0 = 0.0f;   // mixed precision only: the samples and their shift
+        float dv_keep[S];           // FP32: the shifted samples (for a centred second pass)
         if constexpr (!MIXED) {
             // Sample k: anchored numerators (X, Y) and depth Z; one FMA adds
             // X/Z to the pair's magic number 1.5 * 2^24 + ax, rounding to the
@@ -550,13 +557,14 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             // the source, but float positions of other samples of a plane
             // seen almost edge-on by the source need not.
             const uint2* tex = v_tex;
-            const uint32_t pitch = v0.z, toff = v0.w, last = v_last;
+            const uint32_t pitch = v0.z, last = v_last;
             // gathers in chunks of up to 8 slots (registers); the intensities
             // are shifted by c0 = the 2 x 2 texel sum at the group's first
             // sample (an intensity of this source patch), which enters through
             // the fp16 coefficient a (one mixed add)
             constexpr int CH = S <= 9 ? S : 8;
-            float nc0 = 0.0f, dv[S];
+            float nc0 = 0.0f;
+            float* dv = dv_keep;
 #pragma unroll
             for (int k0 = 0; k0 < S; k0 += CH) {
                 uint2 tq[CH];
@@ -573,7 +581,8 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                         float tx = fmaf(X, iz, mx), ty = fmaf(Y, iz, my_);
                         Us[kk] = fmaf(X, iz, mx - tx);
                         Vs[kk] = fmaf(Y, iz, my_ - ty);
-                        uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx) + toff;
+                        // (j + 1) pitch + (i + 1) modulo 2^32 (tex_fold)
+                        uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx);
                         tq[kk] = __ldg(tex + min(idx, last));
                     }
                 }
@@ -589,23 +598,18 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                         const float am = add_f16_f32(__low2half(ab), nc0);
                         dv[k] = fmaf(Vs[kk], fmaf(Us[kk], __high2float(cd), __low2float(cd)),
                                      fmaf(Us[kk], __high2float(ab), am));
-                        sa = fmaf(pw.w[k], dv[k], sa);
+                        // first and second moments in one pass, on intensities
+                        // shifted by an intensity of this patch
+                        const float t = pw.w[k] * dv[k];
+                        sa += t;
+                        sb = fmaf(t, dv[k], sb);
                         se = fmaf(pw.wr[k], dv[k], se);
                     }
                 }
             }
-            // two-pass weighted variance (the form of Eq. 4): the weighted
-            // mean first, then the centred second moment
-            sa = gsum<G>(sa);
-            const float mu = sa * geo.inv_wsum;
-#pragma unroll
-            for (int k = 0; k < S; ++k) {
-                const float e = dv[k] - mu;
-                sb = fmaf(pw.w[k] * e, e, sb);
-            }
         } else {
             const uint2* tex = v_tex;
-            const uint32_t pitch = v0.z, toff = v0.w, last = v_last;
+            const uint32_t pitch = v0.z, last = v_last;
             // mixed precision: positions and fractions in FP32 (as above), the
             // bilinear interpolation of two samples per half2 instruction, on
             // intensities shifted by the reference patch mean
@@ -625,7 +629,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                     float tx = fmaf(X, iz, mx), ty = fmaf(Y, iz, my_);
                     Us[h] = fmaf(X, iz, mx - tx);
                     Vs[h] = fmaf(Y, iz, my_ - ty);
-                    uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx) + toff;
+                    uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx);
                     q[h] = __ldg(tex + min(idx, last));
                 }
                 uint32_t ab = __byte_perm(q[0].x, q[1].x, 0x5410), bb = __byte_perm(q[0].x, q[1].x, 0x7632);
@@ -654,13 +658,29 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
-            if constexpr (MIXED) sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
             sb += __shfl_xor_sync(0xffffffffu, sb, o);
             se += __shfl_xor_sync(0xffffffffu, se, o);
         }
         const float mean_d = sa * geo.inv_wsum;
-        // sum w (s - mu)^2 (FP32: already centred; mixed: one-pass, shifted)
-        float sdd = MIXED ? fmaf(-mean_d, sa, sb) : sb;
+        // sum w (s - mu)^2 = sum w d^2 - mu_d sum w d (one pass)
+        float sdd = fmaf(-mean_d, sa, sb);
+        if constexpr (!MIXED) {
+            // when the shift lies far from the patch mean, W mu_d^2 > 8 sum
+            // w (d - mu_d)^2, the one-pass form loses bits to cancellation:
+            // take the centred second moment (the two-pass form of Eq. 4)
+            const bool centre = sa * mean_d > 8.0f * sdd;
+            if (__any_sync(0xffffffffu, centre)) {
+                float s2 = 0.0f;
+#pragma unroll
+                for (int k = 0; k < S; ++k) {
+                    const float e = dv_keep[k] - mean_d;
+                    s2 = fmaf(pw.w[k] * e, e, s2);
+                }
+                s2 = gsum<G>(s2);
+                if (centre) sdd = s2;
+            }
+        }
         // sum w r' (s - mu) = sum w r' d - mu_d sum w r'
         const float srd = fmaf(-mean_d, geo.wr_sum, se);
         if constexpr (MIXED) {

@@ -19,7 +19,7 @@ constexpr int kBlock = 128;
 // ---------------------------------------------------------------------------
 // bilinear-coefficient texture (layout documented in mvs_internal.h)
 // ---------------------------------------------------------------------------
-__global__ void k_build_texture(const uint8_t* __restrict__ img, int W, int H, uint2* __restrict__ tex) {
+__global__ void k_build_texture(const uint8_t* __restrict__ img, int W, int H, int pitch, uint2* __restrict__ tex) {
     long long n = (long long)(W + 1) * (H + 1);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
@@ -33,7 +33,7 @@ __global__ void k_build_texture(const uint8_t* __restrict__ img, int W, int H, u
         uint2 q;
         q.x = *reinterpret_cast<const uint32_t*>(&ab);
         q.y = *reinterpret_cast<const uint32_t*>(&cd);
-        tex[t] = q;
+        tex[(long long)(j + 1) * pitch + (i + 1)] = q;
     }
 }
 
@@ -222,7 +222,7 @@ struct __align__(16) PhaseWarp {
     WinGeo geo;
     float4 cur;
     float cur_c, pad_[3];
-    float4 hyp[32];
+    float4 hyp[8];     // the stage's hypotheses (at most 8: propagation groups, proposals, refinement)
     float2 off[128];   // sample offsets (ou, ov), slot-major: off[slot * G + lane_in_group], when G * S <= 128
 };
 __host__ __device__ constexpr size_t phase_smem_bytes(int n_src, int warps) {
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
                 want = lane < 3;
             }
             const int nc = stage == 0 ? 8 : (stage == 1 ? rc.n_prop : 3);
-            ws->hyp[lane] = hyp4;
+            if (lane < 8) ws->hyp[lane] = hyp4;
             Cand my = make_cand(rc, pw, geo, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
             float c = eval_batch<G, S, false, MIXED, kOffSm>(rc, views, pw, geo, pv, my, nc,
                                                               warp_pairs(smem, rc.n_src, warp), nullptr, nev,
@@ -578,7 +578,7 @@ cudaError_t prime_launch_configs(const RefConst& rc) {
 cudaError_t launch_build_texture(const uint8_t* img, int W, int H, uint2* tex, cudaStream_t s) {
     long long n = (long long)(W + 1) * (H + 1);
     unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
-    k_build_texture<<<blocks, 256, 0, s>>>(img, W, H, tex);
+    k_build_texture<<<blocks, 256, 0, s>>>(img, W, H, tex_pitch(W), tex);
     count_launch();
     return cudaGetLastError();
 }
