@@ -192,10 +192,13 @@ mvs_status mvs_patchmatch(mvs_ctx* ctx, int32_t ref, const int32_t* srcs, int32_
  *   each from the same initial state, in the view's own buffers before its
  *   real run) and keep the fastest for this window size.  With
  *   MVS_INIT_RANGE, params->init_range holds the ranges of every reference
- *   back to back in refs order (sum of H*W*2 floats).
+ *   back to back in refs order (sum of H*W*2 floats); with n_prop > 0,
+ *   params->proposals likewise holds every reference's proposals back to
+ *   back (sum of H*W*n_prop*4 floats).  The graph is keyed by the params,
+ *   so the buffers behind init_range and proposals must keep their address
+ *   between the calls that replay it.
  *   The maps stay in the context for mvs_geo_filter.
- * Errors: as mvs_patchmatch, plus MVS_EINVAL for n_ref < 1 or repeated refs,
- *   MVS_EUNSUPPORTED for learned proposals (n_prop > 0: per view only). */
+ * Errors: as mvs_patchmatch, plus MVS_EINVAL for n_ref < 1 or repeated refs. */
 mvs_status mvs_patchmatch_batch(mvs_ctx* ctx, int32_t n_ref, const int32_t* refs, const int32_t* srcs,
                                 int32_t n_src, const mvs_pm_params* params, mvs_depth_map* outs);
 

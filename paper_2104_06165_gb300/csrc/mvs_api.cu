@@ -45,7 +45,9 @@ struct BatchGraph {
     int lanes = 0;
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;
+    unsigned long long used = 0;   // call counter of the last use (least recently used is replaced)
 };
+constexpr int kBatchGraphs = 4;   // captured batches kept per context
 
 struct mvs_ctx {
     int device = 0;
@@ -62,7 +64,8 @@ struct mvs_ctx {
     // batched path
     cudaStream_t gstream = nullptr;        // private stream for graph capture / replay
     cudaEvent_t gev[2] = {nullptr, nullptr};
-    BatchGraph batch;
+    BatchGraph batch[kBatchGraphs];
+    unsigned long long batch_calls = 0;
     std::map<long long, int> tuned_lanes;  // (win_samples, n_src) -> lanes per pixel
 };
 
@@ -331,7 +334,8 @@ void mvs_destroy(mvs_ctx* c) {
     for (auto& s : c->scratch) cudaFree(s.p);
     for (auto e : c->ev) cudaEventDestroy(e);
     cudaFree(c->evals);
-    if (c->batch.exec) cudaGraphExecDestroy(c->batch.exec);
+    for (auto& b : c->batch)
+        if (b.exec) cudaGraphExecDestroy(b.exec);
     for (auto e : c->gev) if (e) cudaEventDestroy(e);
     if (c->gstream) cudaStreamDestroy(c->gstream);
     delete c;
@@ -459,7 +463,6 @@ mvs_status mvs_patchmatch_batch(mvs_ctx* c, int32_t n_ref, const int32_t* refs, 
                                 const mvs_pm_params* p, mvs_depth_map* outs) {
     if (!c) return MVS_EINVAL;
     if (n_ref < 1 || !refs || !srcs || !outs || !p) return fail(c, MVS_EINVAL, "bad batch arguments");
-    if (p->n_prop != 0) return fail(c, MVS_EUNSUPPORTED, "learned proposals are per view: use mvs_patchmatch");
     mvs_pm_params q = *p;
     const bool tune = p->lanes_per_pixel == -1;
     if (tune) q.lanes_per_pixel = 0;
@@ -498,17 +501,31 @@ mvs_status mvs_patchmatch_batch(mvs_ctx* c, int32_t n_ref, const int32_t* refs, 
     }
     std::vector<RefConst> rcs(n_ref);
     size_t range_off = 0;   // MVS_INIT_RANGE: the views' ranges lie back to back in refs order
+    size_t prop_off = 0;    // learned proposals: likewise, H * W * n_prop planes per view
     for (int r = 0; r < n_ref; ++r) {
         make_refconst(c, refs[r], srcs + (size_t)r * n_src, n_src, &q, rcs[r]);
         if (rcs[r].init_range) {
             rcs[r].init_range += range_off;
             range_off += (size_t)rcs[r].W * rcs[r].H;
         }
+        if (rcs[r].props) {
+            rcs[r].props += prop_off;
+            prop_off += (size_t)rcs[r].W * rcs[r].H * rcs[r].n_prop;
+        }
     }
-    BatchGraph& B = c->batch;
     std::vector<int32_t> kr(refs, refs + n_ref), ks(srcs, srcs + (size_t)n_ref * n_src);
-    bool same = B.exec && B.refs == kr && B.srcs == ks && B.lanes == q.lanes_per_pixel &&
-                std::memcmp(&B.params, &q, sizeof q) == 0;
+    // a graph captured for the same call, else the least recently used slot
+    BatchGraph* hit = nullptr;
+    BatchGraph* lru = &c->batch[0];
+    for (auto& b : c->batch) {
+        if (b.exec && b.refs == kr && b.srcs == ks && b.lanes == q.lanes_per_pixel &&
+            std::memcmp(&b.params, &q, sizeof q) == 0)
+            hit = &b;
+        if (!b.exec || (lru->exec && b.used < lru->used)) lru = &b;
+    }
+    BatchGraph& B = hit ? *hit : *lru;
+    B.used = ++c->batch_calls;
+    bool same = hit != nullptr;
     if (!same) {
         if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
         for (auto& rc : rcs) CK(c, prime_launch_configs(rc));

@@ -684,9 +684,22 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         // sum w r' (s - mu) = sum w r' d - mu_d sum w r'
         const float srd = fmaf(-mean_d, geo.wr_sum, se);
         if constexpr (MIXED) {
-            // a source patch near the flat limit (where the exclusion decision
-            // is taken): recompute the variance denominator in FP64
-            const bool near_flat = sdd < 2.0f * kTauVar * geo.wsum && sdd > 0.5f * kTauVar * geo.wsum;
+            // the shift far from the patch mean: the centred second moment in
+            // FP32, as in the FP32 path
+            const bool centre = sa * mean_d > 8.0f * sdd;
+            if (__any_sync(0xffffffffu, centre)) {
+                float s2 = 0.0f;
+#pragma unroll
+                for (int k = 0; k < S; ++k) {
+                    const float e = (sval[k] - c0) - mean_d;
+                    s2 = fmaf(pw.w[k] * e, e, s2);
+                }
+                s2 = gsum<G>(s2);
+                if (centre) sdd = s2;
+            }
+            // a source patch within 1 % of the flat limit (where the exclusion
+            // decision is taken): the variance denominator in FP64
+            const bool near_flat = sdd < 1.01f * kTauVar * geo.wsum && sdd > 0.99f * kTauVar * geo.wsum;
             if (__any_sync(0xffffffffu, near_flat)) {
                 const double mu_d = (double)c0 + (double)sa / (double)geo.wsum;
                 double v = 0.0;

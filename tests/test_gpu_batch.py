@@ -96,3 +96,39 @@ def test_geo_filter_across_batched_views(ring, mvs_lib, oracle_lib):
         if gt is not None:     # kept pixels are mostly right
             good = np.abs(pls[0][..., 3] - gt) / gt < 0.01
             assert good[keep == 1].mean() > 0.9
+
+
+def test_batch_takes_back_to_back_proposals(ring, mvs_lib):
+    """Learned proposals in the batched graph: every reference's H x W x K
+    planes back to back in refs order give the maps of separate
+    mvs_patchmatch calls with each view's own proposals, bit for bit, on
+    capture and on replay."""
+    import torch
+    sc, ctx, osc = ring
+    H, W, K = 96, 128, 4
+    rng = np.random.default_rng(4)
+    props = []
+    for r in REFS:
+        n = rng.normal(0, 1, (H, W, K, 3))
+        n[..., 2] = -np.abs(n[..., 2]) - 0.5
+        n /= np.linalg.norm(n, axis=-1, keepdims=True)
+        props.append(np.concatenate([n, rng.uniform(2.5, 7.5, (H, W, K, 1))], -1).astype(np.float32))
+    d_props = [torch.from_numpy(p).cuda() for p in props]
+    base = dict(win_radius=5.0, win_samples=6, iters=2, seed=31, n_prop=K)
+    sep = []
+    for r, s, dp in zip(REFS, SRCS, d_props):
+        pl = np.zeros((H, W, 4), np.float32)
+        co = np.zeros((H, W), np.float32)
+        mvs_lib.mvs_patchmatch(ctx.h, r, s, mvs_lib.PMParams(**base, proposals=dp), pl, co)
+        sep.append((pl, co))
+    both = torch.cat([dp.reshape(-1) for dp in d_props])
+    q = mvs_lib.PMParams(**base, proposals=both)
+    for _ in range(2):
+        pls = [np.zeros((H, W, 4), np.float32) for _ in REFS]
+        cos = [np.zeros((H, W), np.float32) for _ in REFS]
+        mvs_lib.mvs_patchmatch_batch(ctx.h, REFS, SRCS, q, pls, cos)
+        for (a_pl, a_co), b_pl, b_co in zip(sep, pls, cos):
+            assert np.array_equal(a_pl, b_pl) and np.array_equal(a_co, b_co)
+    # the proposals matter: without them the maps differ
+    plain = _separate(mvs_lib, ctx, mvs_lib.PMParams(win_radius=5.0, win_samples=6, iters=2, seed=31))
+    assert any(not np.array_equal(a[0], b[0]) for a, b in zip(plain, sep))
