@@ -44,7 +44,12 @@ constexpr uint32_t kBoxBytes = kTileM * 16;  // one 8-channel box of a block til
 constexpr int kHaloW = kTileM + 2, kHaloH = 3;
 constexpr uint32_t kHaloBytes = kHaloW * kHaloH * 16;            // one 8-channel box with its halo
 constexpr uint32_t kHaloStride = (kHaloBytes + 127u) & ~127u;     // boxes 128-byte aligned
-constexpr size_t kStageBudget = 200 * 1024;
+// shared memory per CTA: chunks small enough that two stages take at most
+// kChunkBudget, and at most kStageBudget of stages in all, so that two to
+// four CTAs (one tile each) share an SM and hide each other's prologue,
+// copies and epilogue
+constexpr size_t kChunkBudget = 32 * 1024;
+constexpr size_t kStageBudget = 44 * 1024;
 
 struct TcArgs {
     int W, H, Cin, Cout, taps;
@@ -364,14 +369,14 @@ int next_pow2(int v) {
 
 // input channels per chunk of a convolution with K input and N output
 // channels: the largest of 64, 32, 16 whose halo-tile stage (taps = 9) or
-// block-tile stage fits twice in the stage budget
+// block-tile stage fits twice in the chunk budget
 int conv_tc_chunk(int K, int N, int taps) {
     for (int kc : {64, 32, 16}) {
         const int k = std::min(kc, K);
         const size_t a = taps == 9 ? (size_t)(k / 8) * kHaloStride : (size_t)(k / 8) * kBoxBytes;
         const size_t b = (size_t)taps * k * N * 2;
         const size_t stage = ((a + 1023) & ~(size_t)1023) + ((b + 1023) & ~(size_t)1023);
-        if (2 * stage <= kStageBudget || kc == 16) return std::min(kc, K);
+        if (2 * stage <= kChunkBudget || kc == 16) return std::min(kc, K);
     }
     return 16;
 }
