@@ -39,7 +39,6 @@ WORKLOADS = {"highres": WORKLOAD, "mid": dict(WORKLOAD, W=1536, H=1024), "batch2
 BATCH_SIZES = ((3072, 2048),) * 8 + ((2048, 1365),) * 8 + ((1536, 1024),) * 8
 FLOP_PER_SAMPLE = 26          # algorithmic FP32 flops per window sample of one ZNCC (FMA = 2)
 GATHERS_PER_SAMPLE = 1        # one 8-byte coefficient texel per window sample
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
 def l2_bytes_per_sample(n, step):
@@ -145,6 +144,11 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi's start-up can hold up CUDA calls of this process for
+            # hundreds of ms: begin the warm-up only once it reports
+            t0 = time.perf_counter()
+            while not self.rows and self.proc.poll() is None and time.perf_counter() - t0 < 10.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -752,7 +756,8 @@ def run_learned(args):
     phase_ms, phase_n, launches, evals = prof_l
     n2 = WORKLOAD["win_samples"] ** 2
     achieved = evals * n2 * FLOP_PER_SAMPLE / (phase_ms / 1e3) / 1e12 if phase_ms > 0 else None
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peaks = measured_peaks(mvs, local)
+    peak = peaks["fp32_tflops"]
     mpix = H * W / 1e6
     line = {
         "metric": "depth-map Mpix/s (learned proposals + 4-iteration PatchMatch)", "value": mpix / (ms_l / 1e3),
@@ -768,7 +773,7 @@ def run_learned(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "kernel": "k_phase (propagation + proposals + refinement)",
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
+                     "peak_basis": "measured FFMA rate of this GPU (mvs_measure_peaks)"},
         "cnn": {"ms": cnn_ms, "achieved_tflops": cnn_tf, "peak_tflops": peak_bf16, "peak": peak_kind,
                 "frac": cnn_tf / peak_bf16, "bound": "tensor"},
         "clocks": clk.summary(),

@@ -18,10 +18,12 @@
 //    tap and group of 8 channels is one box 8 x Wt x Ht.
 // The weights come by one bulk copy per k-step from a layout prepared in the
 // operand's order, chunk-major: [chunk][tap][channels of the chunk / 8][N][8].
-// One thread issues the copies and the tcgen05.mma instructions (bf16 x bf16,
-// fp32 accumulation in tensor memory) through a ring of 2-4 stages guarded
-// by mbarriers; then every thread reads its pixel's accumulators with
-// tcgen05.ld, adds the bias, applies ReLU and stores bf16 (or fp32).
+// One thread (warp 0) issues the copies and another (warp 1) the tcgen05.mma
+// instructions (bf16 x bf16, fp32 accumulation in tensor memory), through a
+// ring of 2-8 stages guarded by mbarriers: a copy waits only for the MMAs
+// that last read its stage, an MMA only for its copies.  Then every thread
+// reads its pixel's accumulators with tcgen05.ld, adds the bias, applies
+// ReLU and stores bf16 (or fp32).
 // Every wait on an mbarrier is bounded: past the limit the CTA records
 // MVS_DEV_TIMEOUT in *status, drains what it issued (again bounded), frees
 // its tensor memory and returns.
@@ -194,85 +196,93 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int ksteps = a.halo ? a.nchunk : a.taps * a.nchunk;
     const uint32_t idesc = mma_idesc((uint32_t)a.Cout);
     const uint32_t done_bar = smem_u32(bars + 2 * S);
+    int* consumed_sm = reinterpret_cast<int*>(tmem_slot + 1);
     bool failed = false;
+    int issued = 0;
 
-    if (threadIdx.x == 0) {
-        int issued = 0, consumed = 0;
+    if (warp == 0 && lane == 0) {
+        // producer: k-step i into stage i % S once the MMAs of k-step i - S
+        // have read that stage
         if (a.force_timeout) {
             // a wait on a barrier that nothing completes (checks the timeout path)
             failed = !mbar_wait(smem_u32(bars), 0, a.wait_limit);
         }
-        for (int i = 0; i < ksteps + S - 1 && !failed; ++i) {
-            if (i < ksteps) {   // producer: stage i % S
-                const int s = i % S;
-                if (i >= S && !mbar_wait(smem_u32(bars + S + s), (uint32_t)((i / S - 1) & 1), a.wait_limit)) {
-                    failed = true;
-                    break;
-                }
-                const int tap = a.halo ? 0 : i / a.nchunk, chunk = a.halo ? i : i % a.nchunk;
-                const int kc = min(a.kc, a.Cin - chunk * a.kc);
-                const uint32_t sa = smem_u32(smem + (size_t)s * a.stage_bytes);
-                const uint32_t sb = sa + a.a_bytes;
-                const uint32_t full = smem_u32(bars + s);
-                // weights of the chunk (all taps with halo tiles, else one tap)
-                const __nv_bfloat16* wsrc =
-                    a.wt + (size_t)chunk * a.taps * a.kc * a.Cout + (size_t)tap * kc * a.Cout;
-                const uint32_t bbytes = (uint32_t)((a.halo ? a.taps : 1) * kc) * (uint32_t)a.Cout * 2u;
-                if (a.halo) {
-                    mbar_expect_tx(full, (uint32_t)(kc / 8) * kHaloBytes + bbytes);
-                    for (int b = 0; b < kc / 8; ++b)
-                        tma_load_3d(sa + (uint32_t)b * kHaloStride, &amap, chunk * a.kc + 8 * b, x0 - 1, y0 - 1, full);
-                } else {
-                    const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
-                    mbar_expect_tx(full, (uint32_t)(kc / 8) * kBoxBytes + bbytes);
-                    for (int b = 0; b < kc / 8; ++b)
-                        tma_load_3d(sa + (uint32_t)b * kBoxBytes, &amap, chunk * a.kc + 8 * b, x0 + dx, y0 + dy, full);
-                }
-                bulk_load(sb, wsrc, bbytes, full);
-                issued = i + 1;
+        for (int i = 0; i < ksteps && !failed; ++i) {
+            const int s = i % S;
+            if (i >= S && !mbar_wait(smem_u32(bars + S + s), (uint32_t)((i / S - 1) & 1), a.wait_limit)) {
+                failed = true;
+                break;
             }
-            const int j = i - (S - 1);
-            if (j >= 0 && j < ksteps) {   // consumer: stage j % S
-                const int s = j % S;
-                if (!mbar_wait(smem_u32(bars + s), (uint32_t)((j / S) & 1), a.wait_limit)) {
-                    failed = true;
-                    break;
-                }
-                tc_fence_after();
-                const int chunk = a.halo ? j : j % a.nchunk;
-                const int kc = min(a.kc, a.Cin - chunk * a.kc);
-                const uint32_t sa = smem_u32(smem + (size_t)s * a.stage_bytes);
-                const uint32_t sb = sa + a.a_bytes;
-                const uint32_t nb = (uint32_t)a.Cout * 16u;   // bytes of one 8-channel group of the weights
-                if (a.halo) {
-                    // tap (dy, dx): the 128 rows starting at halo row (dy + 1, dx + 1)
-                    for (int t = 0; t < 9; ++t) {
-                        const uint32_t shift = (uint32_t)((t / 3) * kHaloW + t % 3) * 16u;
-                        for (int kk = 0; kk < kc / 16; ++kk) {
-                            const uint64_t ad = smem_desc(sa + (uint32_t)kk * 2u * kHaloStride + shift, kHaloStride, 128u);
-                            const uint64_t bd = smem_desc(sb + ((uint32_t)t * (uint32_t)(kc / 8) + 2u * kk) * nb, nb, 128u);
-                            mma_bf16(tmem, ad, bd, idesc, (j > 0 || t > 0 || kk > 0) ? 1u : 0u);
-                        }
-                    }
-                } else {
+            const int tap = a.halo ? 0 : i / a.nchunk, chunk = a.halo ? i : i % a.nchunk;
+            const int kc = min(a.kc, a.Cin - chunk * a.kc);
+            const uint32_t sa = smem_u32(smem + (size_t)s * a.stage_bytes);
+            const uint32_t sb = sa + a.a_bytes;
+            const uint32_t full = smem_u32(bars + s);
+            // weights of the chunk (all taps with halo tiles, else one tap)
+            const __nv_bfloat16* wsrc = a.wt + (size_t)chunk * a.taps * a.kc * a.Cout + (size_t)tap * kc * a.Cout;
+            const uint32_t bbytes = (uint32_t)((a.halo ? a.taps : 1) * kc) * (uint32_t)a.Cout * 2u;
+            if (a.halo) {
+                mbar_expect_tx(full, (uint32_t)(kc / 8) * kHaloBytes + bbytes);
+                for (int b = 0; b < kc / 8; ++b)
+                    tma_load_3d(sa + (uint32_t)b * kHaloStride, &amap, chunk * a.kc + 8 * b, x0 - 1, y0 - 1, full);
+            } else {
+                const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
+                mbar_expect_tx(full, (uint32_t)(kc / 8) * kBoxBytes + bbytes);
+                for (int b = 0; b < kc / 8; ++b)
+                    tma_load_3d(sa + (uint32_t)b * kBoxBytes, &amap, chunk * a.kc + 8 * b, x0 + dx, y0 + dy, full);
+            }
+            bulk_load(sb, wsrc, bbytes, full);
+            issued = i + 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: k-step j once its copies have landed; the commit frees
+        // the stage for the producer when these MMAs have read it
+        int consumed = 0;
+        for (int j = 0; j < ksteps; ++j) {
+            const int s = j % S;
+            if (!mbar_wait(smem_u32(bars + s), (uint32_t)((j / S) & 1), a.wait_limit)) {
+                failed = true;
+                break;
+            }
+            tc_fence_after();
+            const int chunk = a.halo ? j : j % a.nchunk;
+            const int kc = min(a.kc, a.Cin - chunk * a.kc);
+            const uint32_t sa = smem_u32(smem + (size_t)s * a.stage_bytes);
+            const uint32_t sb = sa + a.a_bytes;
+            const uint32_t nb = (uint32_t)a.Cout * 16u;   // bytes of one 8-channel group of the weights
+            if (a.halo) {
+                // tap (dy, dx): the 128 rows starting at halo row (dy + 1, dx + 1)
+                for (int t = 0; t < 9; ++t) {
+                    const uint32_t shift = (uint32_t)((t / 3) * kHaloW + t % 3) * 16u;
                     for (int kk = 0; kk < kc / 16; ++kk) {
-                        const uint64_t ad = smem_desc(sa + (uint32_t)kk * 2u * kBoxBytes, kBoxBytes, 128u);
-                        const uint64_t bd = smem_desc(sb + 2u * kk * nb, nb, 128u);
-                        mma_bf16(tmem, ad, bd, idesc, (j > 0 || kk > 0) ? 1u : 0u);
+                        const uint64_t ad = smem_desc(sa + (uint32_t)kk * 2u * kHaloStride + shift, kHaloStride, 128u);
+                        const uint64_t bd = smem_desc(sb + ((uint32_t)t * (uint32_t)(kc / 8) + 2u * kk) * nb, nb, 128u);
+                        mma_bf16(tmem, ad, bd, idesc, (j > 0 || t > 0 || kk > 0) ? 1u : 0u);
                     }
                 }
-                mma_commit(smem_u32(bars + S + s));   // stage s free once these MMAs have read it
-                consumed = j + 1;
+            } else {
+                for (int kk = 0; kk < kc / 16; ++kk) {
+                    const uint64_t ad = smem_desc(sa + (uint32_t)kk * 2u * kBoxBytes, kBoxBytes, 128u);
+                    const uint64_t bd = smem_desc(sb + 2u * kk * nb, nb, 128u);
+                    mma_bf16(tmem, ad, bd, idesc, (j > 0 || kk > 0) ? 1u : 0u);
+                }
             }
+            mma_commit(smem_u32(bars + S + s));   // stage s free once these MMAs have read it
+            consumed = j + 1;
         }
-        if (failed) {
-            atomicExch(a.status, MVS_DEV_TIMEOUT);
-            // drain: copies issued but not consumed, then the MMAs in flight
-            for (int j = consumed; j < issued; ++j)
-                mbar_wait(smem_u32(bars + (j % S)), (uint32_t)((j / S) & 1), a.wait_limit);
-        }
+        *consumed_sm = consumed;
         mma_commit(done_bar);   // arrives when every MMA issued above has completed
     }
+    __syncwarp();   // lanes 1..31 wait for their lane 0 before the block barrier
+    __syncthreads();
+    if (warp == 0 && lane == 0 && issued > *consumed_sm) {
+        // the MMA issuer gave up: wait (bounded) for the copies it did not
+        // consume, so that none lands after the CTA has exited
+        failed = true;
+        for (int j = *consumed_sm; j < issued; ++j)
+            mbar_wait(smem_u32(bars + (j % S)), (uint32_t)((j / S) & 1), a.wait_limit);
+    }
+    if (failed) atomicExch(a.status, MVS_DEV_TIMEOUT);
     __syncwarp();
     // all threads: the accumulators are complete (or the CTA gave up)
     const bool ok = mbar_wait(done_bar, 0, a.wait_limit);
@@ -420,8 +430,8 @@ cudaError_t conv_tc_launch(const __nv_bfloat16* in, int Cin, int W, int H, const
     a.kc = conv_tc_chunk(Cin, Cout, taps);
     a.nchunk = (Cin + a.kc - 1) / a.kc;
     stage_bytes(Cin, Cout, taps, a.kc, a.halo, &a.a_bytes, &a.stage_bytes);
-    a.stages = (int)std::max<size_t>(2, std::min<size_t>(4, kStageBudget / a.stage_bytes));
-    const size_t smem = (size_t)a.stages * a.stage_bytes + (2 * a.stages + 1) * 8 + 16 + 1024;
+    a.stages = (int)std::max<size_t>(2, std::min<size_t>(8, kStageBudget / a.stage_bytes));
+    const size_t smem = (size_t)a.stages * a.stage_bytes + (2 * a.stages + 1) * 8 + 16 + 1024;   // + TMEM slot, count
     a.relu = relu; a.out_f32 = out_f32;
     a.wt = wt; a.bias = bias; a.out = out; a.out_ch = out_ch; a.out_off = out_off;
     a.status = status; a.force_timeout = force_timeout; a.wait_limit = wait_limit;
