@@ -171,7 +171,8 @@ struct __align__(16) WinGeo {
 // warp holds the same pixel's window (sample k = slot * G + lane_in_group).
 template <int S>
 struct PixWin {
-    float ou[S], ov[S];   // sample offsets (the first included sample for padding / excluded samples)
+    __half2 o2[S];        // sample offsets / step: (k_u - r_now, k_v - r_now), exact in fp16 (the first
+                          // included sample for padding / excluded samples)
     float w[S];           // bilateral weights (0 for padding / excluded)
     float wr[S];          // w * (I_ref - weighted mean)
     float mean;           // weighted mean of the reference samples
@@ -200,7 +201,7 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
         kv_hi = mv ? 31 - __clz(mv) : -1;
     }
     // excluded and padding samples sit on the first included sample (weight 0)
-    const float ou_pad = rc.step * ((float)ku_lo - half), ov_pad = rc.step * ((float)kv_lo - half);
+    const __half2 o2_pad = __floats2half2_rn((float)ku_lo - half, (float)kv_lo - half);
     const float rcen = exists ? 4.0f * (float)__ldg(rc.img + (long long)py * rc.W + px) : 0.0f;
     const float inv_n = rcp_approx((float)n);   // (k + 1/2) / n stays 1/(2n) away from integers
     float sw = 0.0f, swr = 0.0f;
@@ -209,7 +210,8 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
         const int k = s * G + lg;
         const int kv = (int)(((float)k + 0.5f) * inv_n), ku = k - kv * n;   // exact for k < 2^20
         bool in = exists && k < n * n && ku >= ku_lo && ku <= ku_hi && kv >= kv_lo && kv <= kv_hi;
-        float ou = rc.step * ((float)ku - half), ov = rc.step * ((float)kv - half);
+        const float ku_f = (float)ku - half, kv_f = (float)kv - half;
+        float ou = rc.step * ku_f, ov = rc.step * kv_f;
         float r = 0.0f, w = 0.0f;
         if (in) {
             r = tex_sample(rc.tex, rc.pitch, rc.n_tex, fmaf(2.0f, ou, -1.0f), fmaf(2.0f, ov, -1.0f),
@@ -217,8 +219,7 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
             float dc = r - rcen;
             w = __expf(fmaf(rc.sp_coef, ou * ou + ov * ov, rc.col_coef * dc * dc));
         }
-        pw.ou[s] = in ? ou : ou_pad;
-        pw.ov[s] = in ? ov : ov_pad;
+        pw.o2[s] = in ? __floats2half2_rn(ku_f, kv_f) : o2_pad;
         pw.w[s] = w;
         pw.wr[s] = r;   // temporarily the intensity
         sw += w;
@@ -373,8 +374,11 @@ __device__ __forceinline__ Cand make_cand(const RefConst& rc, const PixWin<S>& p
 //   xs2 = ax + (nx + ou j0x + ov j1x) / (pz + ou h0z + ov h1z),
 //   ys2 = ay + (ny + ou j0y + ov j1y) / (pz + ou h0z + ov h1z),
 // so the float arithmetic per sample works on numbers of the size of the
-// window's image, not of the source image.  The record also holds the magic
-// numbers 1.5 * 2^24 + (ax, ay) of tex_sample and (hypothesis | view << 8).
+// window's image, not of the source image.  The record holds the columns
+// per sample step, s j0 and s j1 (and s h0z, s h1z), so that a sample at
+// (k_u - r_now, k_v - r_now) steps from the pixel multiplies them by its
+// step counts directly; it also holds the magic numbers 1.5 * 2^24 +
+// (ax, ay) of tex_sample and (hypothesis | view << 8).
 struct __align__(16) PairSm {
     float j0x, j0y, h0z, j1x;
     float j1y, h1z, nx, ny;
@@ -416,6 +420,80 @@ __device__ __forceinline__ bool same_plane(const float4& a, const float4& b) {
            fabsf(a.z - b.z) <= 1e-6f;
 }
 
+// The anchored homography of one listed pair (PairSm words 0..2 without the
+// (hypothesis, view) word).
+struct PairGeo {
+    float j0x, j0y, h0z, j1x, j1y, h1z, nx, ny, pz, mx, my;
+};
+
+// One pass over a group's window samples of a listed pair (S slots per lane).
+// Sample k: anchored numerators (X, Y) and depth Z; one FMA adds X/Z to the
+// pair's magic number 1.5 * 2^24 + ax, rounding to the nearest even integer
+// 2i (its bits give i), a second gives U = ax + X/Z - 2i in [-1, 1] rounded
+// once.  The texel index is clamped into the array: the listed window
+// corners lie inside the source, but float positions of other samples of a
+// plane seen almost edge-on by the source need not.  The bilinear values
+// are shifted by c0 = the 2 x 2 texel sum at the group's first sample (an
+// intensity of this source patch, which enters through the fp16
+// coefficient a in one mixed add).
+//   CENTRED = false: nc0 = -c0 out; sa, sb, se += sum w d, sum w d^2,
+//     sum w r' d over the lane's samples, d = s - c0;
+//   CENTRED = true: nc0 in (from the first pass, so every d is the same
+//     float); sa += sum w (d - mean_d)^2.
+// The gathers run in chunks of up to 8 slots (registers).
+template <int G, int S, bool CENTRED, int CH = (S <= 9 ? S : 8)>
+__device__ __forceinline__ void window_pass(const PixWin<S>& pw, int grp,
+                                            const uint2* __restrict__ tex, uint32_t pitch, uint32_t last,
+                                            const PairGeo& g, float& nc0, float mean_d, float& sa, float& sb,
+                                            float& se) {
+#pragma unroll
+    for (int k0 = 0; k0 < S; k0 += CH) {
+        uint2 tq[CH];
+        float Us[CH], Vs[CH];
+#pragma unroll
+        for (int kk = 0; kk < CH; ++kk) {
+            const int k = k0 + kk;
+            if (k < S) {
+                const float2 o = __half22float2(pw.o2[k]);
+                const float X = fmaf(o.x, g.j0x, fmaf(o.y, g.j1x, g.nx));
+                const float Y = fmaf(o.x, g.j0y, fmaf(o.y, g.j1y, g.ny));
+                const float Z = fmaf(o.x, g.h0z, fmaf(o.y, g.h1z, g.pz));
+                const float iz = rcp_approx(Z);
+                const float tx = fmaf(X, iz, g.mx), ty = fmaf(Y, iz, g.my);
+                Us[kk] = fmaf(X, iz, g.mx - tx);
+                Vs[kk] = fmaf(Y, iz, g.my - ty);
+                // (j + 1) pitch + (i + 1) modulo 2^32 (tex_fold)
+                const uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx);
+                tq[kk] = __ldg(tex + min(idx, last));
+            }
+        }
+        if (!CENTRED && k0 == 0)
+            nc0 = -__half2float(
+                __ushort_as_half((unsigned short)(__shfl_sync(0xffffffffu, tq[0].x, grp * G) & 0xffffu)));
+#pragma unroll
+        for (int kk = 0; kk < CH; ++kk) {
+            const int k = k0 + kk;
+            if (k < S) {
+                const __half2 ab = *reinterpret_cast<const __half2*>(&tq[kk].x);
+                const __half2 cd = *reinterpret_cast<const __half2*>(&tq[kk].y);
+                const float am = add_f16_f32(__low2half(ab), nc0);
+                const float dv = fmaf(Vs[kk], fmaf(Us[kk], __high2float(cd), __low2float(cd)),
+                                      fmaf(Us[kk], __high2float(ab), am));
+                if (CENTRED) {
+                    const float e = dv - mean_d;
+                    sa = fmaf(pw.w[k] * e, e, sa);
+                } else {
+                    // first and second moments in one pass
+                    const float t = pw.w[k] * dv;
+                    sa += t;
+                    sb = fmaf(t, dv, sb);
+                    se = fmaf(pw.wr[k], dv, se);
+                }
+            }
+        }
+    }
+}
+
 // Costs C(x) (Eq. 5) of up to 8 hypotheses of the warp's pixel: lane c < nc
 // holds hypothesis c on entry and its cost on return.
 //   1. the (hypothesis, view) pairs of the usable hypotheses whose window
@@ -425,22 +503,18 @@ __device__ __forceinline__ bool same_plane(const float4& a, const float4& b) {
 //      homography (PairSm);
 //   2. each group of G lanes takes the next pair: S bilinear gathers per
 //      lane, the weighted moments in one pass (group reductions; a centred
-//      second pass where the one-pass form would cancel), ZNCC (Eq. 4),
-//      C(x,j) = 1 - Z; a view is excluded when its weighted variance is below
-//      1e-6 on the [0,1] scale (reading);
+//      second pass where the one-pass form would cancel); then one lane per
+//      pair: ZNCC (Eq. 4), C(x,j) = 1 - Z; a view is excluded when its
+//      weighted variance is below 1e-6 on the [0,1] scale (reading);
 //   3. lane c folds the per-view results of hypothesis c in view order
 //      (Eq. 5, weights 1/max(C, 1e-6)).
 // pv: the pixel's PixView records (pix_views).  Must be called by all 32
 // lanes with the same nc (warp-uniform); VIEWS (per-view costs out) needs
 // nc == 1.
-// OFF_SM: the window's sample offsets are read from shared memory, (ou, ov)
-// of slot k and lane-in-group lg at off_sm[k * G + lg] (pw.ou / pw.ov are not
-// read, so they need not stay in registers).
-template <int G, int S, bool VIEWS, bool MIXED = false, bool OFF_SM = false>
+template <int G, int S, bool VIEWS, bool MIXED = false>
 __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __restrict__ sv, const PixWin<S>& pw,
                                             const WinGeo& geo, const PixView* __restrict__ pv, const Cand& my, int nc,
-                                            PairSm* pairs, float* view_cost, unsigned& n_evals,
-                                            const float2* off_sm = nullptr) {
+                                            PairSm* pairs, float* view_cost, unsigned& n_evals) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
     const int V = rc.n_src;
@@ -519,8 +593,10 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         unsigned m = __ballot_sync(0xffffffffu, ok);
         if (ok) {
             float4* qw = reinterpret_cast<float4*>(pairs + count + __popc(m & ((1u << lane) - 1u)));
-            qw[0] = make_float4(j0x, j0y, h0z, j1x);
-            qw[1] = make_float4(j1y, h1z, nx, ny);
+            // derivatives per sample step (the offsets are in steps)
+            const float st = rc.step;
+            qw[0] = make_float4(j0x * st, j0y * st, h0z * st, j1x * st);
+            qw[1] = make_float4(j1y * st, h1z * st, nx, ny);
             // magic numbers with the anchor, the texture's guard texel and the
             // index fold (tex_fold): bits(ty) pitch + bits(tx) = texel index
             const float fx = reinterpret_cast<const float4*>(sv + j)[0].w;
@@ -531,85 +607,50 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
         count += __popc(m);
     }
     __syncwarp();
-    // ---- 2. evaluate the listed pairs, NG at a time
+    // ---- 2. evaluate the listed pairs, NG at a time: the weighted moments
+    // of each pair (group reductions), which the group's first lane writes
+    // over the pair's first record word (the record is not read again)
+    const float inv_wsum = geo.inv_wsum;
     for (int r = 0; r < count; r += NG) {
-        int it = r + grp;
-        bool has = it < count;
-        const float4* qw = reinterpret_cast<const float4*>(pairs + (has ? it : 0));
+        const int it = r + grp;
+        const bool has = it < count;
+        float4* qw = reinterpret_cast<float4*>(pairs + (has ? it : 0));
         const float4 qa = qw[0], qb = qw[1], qc = qw[2];
-        const float j0x = qa.x, j0y = qa.y, h0z = qa.z, j1x = qa.w;
-        const float j1y = qb.x, h1z = qb.y, nx = qb.z, ny = qb.w;
-        const float pz = qc.x, mx = qc.y, my_ = qc.z;
-        const int cj = __float_as_int(qc.w), pj = cj >> 8, pc = cj & 255;
+        const PairGeo pg{qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w, qc.x, qc.y, qc.z};
+        const int cj = __float_as_int(qc.w), pj = cj >> 8;
         // view words 0 (texels, pitch) and 1 (last texel)
         const uint4 v0 = reinterpret_cast<const uint4*>(sv + pj)[0];
         const uint32_t v_last = reinterpret_cast<const uint4*>(sv + pj)[1].x;
         const uint2* v_tex = reinterpret_cast<const uint2*>(((unsigned long long)v0.y << 32) | v0.x);
-        float sa = 0.0f, sb = 0.0f, se = 0.0f;
-        float sval[S], c0 = 0.0f;   // mixed precision only: the samples and their shift
-        float dv_keep[S];           // FP32: the shifted samples (for a centred second pass)
+        float sa = 0.0f, sb = 0.0f, se = 0.0f, sdd, mean_d;
         if constexpr (!MIXED) {
-            // Sample k: anchored numerators (X, Y) and depth Z; one FMA adds
-            // X/Z to the pair's magic number 1.5 * 2^24 + ax, rounding to the
-            // nearest even integer 2i (its bits give i), a second gives
-            // U = ax + X/Z - 2i in [-1, 1] rounded once.  The texel index is
-            // clamped into the array: the listed window corners lie inside
-            // the source, but float positions of other samples of a plane
-            // seen almost edge-on by the source need not.
-            const uint2* tex = v_tex;
-            const uint32_t pitch = v0.z, last = v_last;
-            // gathers in chunks of up to 8 slots (registers); the intensities
-            // are shifted by c0 = the 2 x 2 texel sum at the group's first
-            // sample (an intensity of this source patch), which enters through
-            // the fp16 coefficient a (one mixed add)
-            constexpr int CH = S <= 9 ? S : 8;
             float nc0 = 0.0f;
-            float* dv = dv_keep;
+            window_pass<G, S, false>(pw, grp, v_tex, v0.z, v_last, pg, nc0, 0.0f, sa, sb, se);
 #pragma unroll
-            for (int k0 = 0; k0 < S; k0 += CH) {
-                uint2 tq[CH];
-                float Us[CH], Vs[CH];
-#pragma unroll
-                for (int kk = 0; kk < CH; ++kk) {
-                    const int k = k0 + kk;
-                    if (k < S) {
-                        const float2 o = OFF_SM ? off_sm[k * G + lg] : make_float2(pw.ou[k], pw.ov[k]);
-                        float X = fmaf(o.x, j0x, fmaf(o.y, j1x, nx));
-                        float Y = fmaf(o.x, j0y, fmaf(o.y, j1y, ny));
-                        float Z = fmaf(o.x, h0z, fmaf(o.y, h1z, pz));
-                        float iz = rcp_approx(Z);
-                        float tx = fmaf(X, iz, mx), ty = fmaf(Y, iz, my_);
-                        Us[kk] = fmaf(X, iz, mx - tx);
-                        Vs[kk] = fmaf(Y, iz, my_ - ty);
-                        // (j + 1) pitch + (i + 1) modulo 2^32 (tex_fold)
-                        uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx);
-                        tq[kk] = __ldg(tex + min(idx, last));
-                    }
-                }
-                if (k0 == 0)
-                    nc0 = -__half2float(
-                        __ushort_as_half((unsigned short)(__shfl_sync(0xffffffffu, tq[0].x, grp * G) & 0xffffu)));
-#pragma unroll
-                for (int kk = 0; kk < CH; ++kk) {
-                    const int k = k0 + kk;
-                    if (k < S) {
-                        const __half2 ab = *reinterpret_cast<const __half2*>(&tq[kk].x);
-                        const __half2 cd = *reinterpret_cast<const __half2*>(&tq[kk].y);
-                        const float am = add_f16_f32(__low2half(ab), nc0);
-                        dv[k] = fmaf(Vs[kk], fmaf(Us[kk], __high2float(cd), __low2float(cd)),
-                                     fmaf(Us[kk], __high2float(ab), am));
-                        // first and second moments in one pass, on intensities
-                        // shifted by an intensity of this patch
-                        const float t = pw.w[k] * dv[k];
-                        sa += t;
-                        sb = fmaf(t, dv[k], sb);
-                        se = fmaf(pw.wr[k], dv[k], se);
-                    }
-                }
+            for (int o = G / 2; o > 0; o >>= 1) {
+                sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                sb += __shfl_xor_sync(0xffffffffu, sb, o);
+                se += __shfl_xor_sync(0xffffffffu, se, o);
+            }
+            mean_d = sa * inv_wsum;
+            // sum w (s - mu)^2 = sum w d^2 - mu_d sum w d (one pass)
+            sdd = fmaf(-mean_d, sa, sb);
+            // when the shift lies far from the patch mean, W mu_d^2 > 8 sum
+            // w (d - mu_d)^2, the one-pass form loses bits to cancellation:
+            // the samples are taken again for the centred second moment (the
+            // two-pass form of Eq. 4)
+            const bool centre = has && sa * mean_d > 8.0f * sdd;
+            if (__any_sync(0xffffffffu, centre)) {
+                float s2 = 0.0f, u0 = 0.0f, u1 = 0.0f;
+                window_pass<G, S, true>(pw, grp, v_tex, v0.z, v_last, pg, nc0, mean_d, s2, u0,
+                                                u1);
+                s2 = gsum<G>(s2);
+                if (centre) sdd = s2;
             }
         } else {
             const uint2* tex = v_tex;
             const uint32_t pitch = v0.z, last = v_last;
+            float sval[S];
             // mixed precision: positions and fractions in FP32 (as above), the
             // bilinear interpolation of two samples per half2 instruction, on
             // intensities shifted by the reference patch mean
@@ -621,14 +662,14 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int kk = k + h < S ? k + h : k;
-                    const float2 o = OFF_SM ? off_sm[kk * G + lg] : make_float2(pw.ou[kk], pw.ov[kk]);
-                    float X = fmaf(o.x, j0x, fmaf(o.y, j1x, nx));
-                    float Y = fmaf(o.x, j0y, fmaf(o.y, j1y, ny));
-                    float Z = fmaf(o.x, h0z, fmaf(o.y, h1z, pz));
+                    const float2 o = __half22float2(pw.o2[kk]);
+                    float X = fmaf(o.x, pg.j0x, fmaf(o.y, pg.j1x, pg.nx));
+                    float Y = fmaf(o.x, pg.j0y, fmaf(o.y, pg.j1y, pg.ny));
+                    float Z = fmaf(o.x, pg.h0z, fmaf(o.y, pg.h1z, pg.pz));
                     float iz = rcp_approx(Z);
-                    float tx = fmaf(X, iz, mx), ty = fmaf(Y, iz, my_);
-                    Us[h] = fmaf(X, iz, mx - tx);
-                    Vs[h] = fmaf(Y, iz, my_ - ty);
+                    float tx = fmaf(X, iz, pg.mx), ty = fmaf(Y, iz, pg.my);
+                    Us[h] = fmaf(X, iz, pg.mx - tx);
+                    Vs[h] = fmaf(Y, iz, pg.my - ty);
                     uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx);
                     q[h] = __ldg(tex + min(idx, last));
                 }
@@ -646,7 +687,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             // sample (an intensity of this source patch): with d = s - c0,
             // sum w (s - mu)^2 = sum w d^2 - (sum w d)^2 / W; near the flat
             // limit the denominator is recomputed in FP64 below
-            c0 = __shfl_sync(0xffffffffu, sval[0], grp * G);
+            const float c0 = __shfl_sync(0xffffffffu, sval[0], grp * G);
 #pragma unroll
             for (int k = 0; k < S; ++k) {
                 float dv = sval[k] - c0;
@@ -655,35 +696,14 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                 sb = fmaf(t, dv, sb);
                 se = fmaf(pw.wr[k], dv, se);
             }
-        }
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            sa += __shfl_xor_sync(0xffffffffu, sa, o);
-            sb += __shfl_xor_sync(0xffffffffu, sb, o);
-            se += __shfl_xor_sync(0xffffffffu, se, o);
-        }
-        const float mean_d = sa * geo.inv_wsum;
-        // sum w (s - mu)^2 = sum w d^2 - mu_d sum w d (one pass)
-        float sdd = fmaf(-mean_d, sa, sb);
-        if constexpr (!MIXED) {
-            // when the shift lies far from the patch mean, W mu_d^2 > 8 sum
-            // w (d - mu_d)^2, the one-pass form loses bits to cancellation:
-            // take the centred second moment (the two-pass form of Eq. 4)
-            const bool centre = sa * mean_d > 8.0f * sdd;
-            if (__any_sync(0xffffffffu, centre)) {
-                float s2 = 0.0f;
-#pragma unroll
-                for (int k = 0; k < S; ++k) {
-                    const float e = dv_keep[k] - mean_d;
-                    s2 = fmaf(pw.w[k] * e, e, s2);
-                }
-                s2 = gsum<G>(s2);
-                if (centre) sdd = s2;
+            for (int o = G / 2; o > 0; o >>= 1) {
+                sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                sb += __shfl_xor_sync(0xffffffffu, sb, o);
+                se += __shfl_xor_sync(0xffffffffu, se, o);
             }
-        }
-        // sum w r' (s - mu) = sum w r' d - mu_d sum w r'
-        const float srd = fmaf(-mean_d, geo.wr_sum, se);
-        if constexpr (MIXED) {
+            mean_d = sa * inv_wsum;
+            sdd = fmaf(-mean_d, sa, sb);
             // the shift far from the patch mean: the centred second moment in
             // FP32, as in the FP32 path
             const bool centre = sa * mean_d > 8.0f * sdd;
@@ -713,16 +733,22 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                 if (near_flat) sdd = (float)v;
             }
         }
-        // ZNCC, C(x, j) = 1 - Z, and its Eq. 5 weight (all lanes compute,
-        // the group's first lane stores)
-        const bool flat = !(sdd >= kTauVar * geo.wsum);
-        const float z = fminf(1.0f, fmaxf(-1.0f, srd * rsqrtf(geo.srr * sdd)));
+        if (has && lg == 0) qw[0] = make_float4(sdd, se, mean_d, __int_as_float(cj));
+    }
+    __syncwarp();
+    // ---- 2b. per evaluated pair, one per lane: ZNCC (Eq. 4), C(x, j) = 1 - Z
+    // and its Eq. 5 weight
+    for (int i = lane; i < count; i += 32) {
+        const float4 q = reinterpret_cast<const float4*>(pairs + i)[0];
+        const int cj = __float_as_int(q.w), pj = cj >> 8, pc = cj & 255;
+        // sum w r' (s - mu) = sum w r' d - mu_d sum w r'
+        const float srd = fmaf(-q.z, geo.wr_sum, q.y);
+        const bool flat = !(q.x >= kTauVar * geo.wsum);
+        const float z = fminf(1.0f, fmaxf(-1.0f, srd * rsqrtf(geo.srr * q.x)));
         const float cjv = flat ? kCmax : fminf(1.0f - z, kCmax);
-        if (has && lg == 0) {
-            if (VIEWS) tab[V + pj] = cjv;
-            tab[pc * V + pj] = cjv < kCmax ? rcp_approx(fmaxf(cjv, kEpsC)) : 0.0f;
-            n_evals++;
-        }
+        if (VIEWS) tab[V + pj] = cjv;
+        tab[pc * V + pj] = cjv < kCmax ? rcp_approx(fmaxf(cjv, kEpsC)) : 0.0f;
+        n_evals++;
     }
     __syncwarp();
     // ---- 3. fold hypothesis `lane`'s views in view order

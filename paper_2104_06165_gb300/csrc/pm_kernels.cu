@@ -223,7 +223,6 @@ struct __align__(16) PhaseWarp {
     float4 cur;
     float cur_c, pad_[3];
     float4 hyp[8];     // the stage's hypotheses (at most 8: propagation groups, proposals, refinement)
-    float2 off[128];   // sample offsets (ou, ov), slot-major: off[slot * G + lane_in_group], when G * S <= 128
 };
 __host__ __device__ constexpr size_t phase_smem_bytes(int n_src, int warps) {
     return smem_block_bytes(n_src, warps) + (size_t)warps * (32 * (sizeof(float4) + sizeof(float)) + sizeof(PhaseWarp));
@@ -321,11 +320,6 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             ws->geo = pw.geo;
             ws->cur = rc.plane[pix];
             ws->cur_c = rc.cost[pix];
-        }
-        constexpr bool kOffSm = G * S <= 128;
-        if (kOffSm && lane < G) {
-#pragma unroll
-            for (int k = 0; k < S; ++k) ws->off[k * G + lane] = make_float2(pw.ou[k], pw.ov[k]);
         }
         PixView* pv = warp_pixviews(smem, rc.n_src, warp);
         pix_views(rc, views, px, py, pv);   // (ends with a warp barrier)
@@ -426,9 +420,8 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             const int nc = stage == 0 ? 8 : (stage == 1 ? rc.n_prop : 3);
             if (lane < 8) ws->hyp[lane] = hyp4;
             Cand my = make_cand(rc, pw, geo, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
-            float c = eval_batch<G, S, false, MIXED, kOffSm>(rc, views, pw, geo, pv, my, nc,
-                                                              warp_pairs(smem, rc.n_src, warp), nullptr, nev,
-                                                              ws->off);   // (ends with a warp barrier)
+            float c = eval_batch<G, S, false, MIXED>(rc, views, pw, geo, pv, my, nc, warp_pairs(smem, rc.n_src, warp),
+                                                      nullptr, nev);   // (ends with a warp barrier)
             float bc;
             int bi = warp_argmin(my.ok ? c : 3.0e38f, nc, bc);
             if (bc < ws->cur_c && lane == 0) {
