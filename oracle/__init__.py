@@ -83,7 +83,7 @@ def lib():
             L.or_group_members.argtypes = [C.c_int, ip]
             L.or_phase.argtypes = [vp, C.c_int, ip, C.c_int, C.POINTER(_PM), C.c_int, dp, dp, ip, dp, ip, dp, dp]
             L.or_patchmatch.argtypes = [vp, C.c_int, ip, C.c_int, C.POINTER(_PM), C.c_int, dp, dp]
-            L.or_geo_filter.argtypes = [vp, C.c_int, ip, C.c_int, C.POINTER(_Filter), C.POINTER(dp), up, ip]
+            L.or_geo_filter.argtypes = [vp, C.c_int, ip, C.c_int, C.POINTER(_Filter), C.POINTER(dp), up, ip, dp]
             L.or_phi_hypotheses.argtypes = [C.c_int, C.c_int, dp, up, C.c_int, C.c_int, C.c_double, C.c_double,
                                             dp, up]
             L.or_line_fit_at.restype = C.c_double
@@ -312,9 +312,12 @@ def patchmatch(scene, ref, srcs, p, iters):
 
 
 def geo_filter(scene, ref, srcs, planes, depth_tol=0.02, depth_relative=False, max_angle_deg=30.0,
-               max_reproj=1.0, min_consistent=2):
+               max_reproj=1.0, min_consistent=2, with_margin=False):
     """Sec. III-D geometric-consistency filter. ``planes`` maps view index
-    to its (H, W, 4) plane map. Returns keep mask (uint8) and counts."""
+    to its (H, W, 4) plane map. Returns keep mask (uint8) and counts, and with
+    ``with_margin`` also each pixel's decision margin (below 1: a float
+    evaluation of the same tests may decide that pixel either way; the bands
+    are stated in or_geo_filter)."""
     H, W = scene.shape(ref)
     s = _srcs(srcs)
     arrs = [None] * scene.n
@@ -325,8 +328,9 @@ def geo_filter(scene, ref, srcs, planes, depth_tol=0.02, depth_relative=False, m
     keep = np.zeros((H, W), np.uint8)
     cnt = np.zeros((H, W), np.int32)
     f = _Filter(depth_tol, int(depth_relative), max_angle_deg, max_reproj, min_consistent)
-    lib().or_geo_filter(scene.h, ref, _i(s), len(s), C.byref(f), ptrs, _u8(keep), _i(cnt))
-    return keep, cnt
+    margin = np.zeros((H, W), np.float64)
+    lib().or_geo_filter(scene.h, ref, _i(s), len(s), C.byref(f), ptrs, _u8(keep), _i(cnt), _d(margin))
+    return (keep, cnt, margin) if with_margin else (keep, cnt)
 
 
 def phi_hypotheses(depth, known, n_fit=6, inverse=False, d_lo=0.0, d_hi=np.inf):

@@ -721,8 +721,32 @@ typedef struct {
  * view j at x'_j; a tap without depth makes the view inconsistent; the
  * normal of view j is taken at the rounded coordinate, brought into the
  * reference frame and compared sign-agnostically */
+/* Test support: margin_out (or NULL) receives per pixel the smallest
+ * distance of any decision taken for it to that decision's boundary, in
+ * units of a band: 1e-3 px for positions (image bounds, the reprojection
+ * limit), 1e-5 for the depth test (in its own units), 1e-5 for the cosine of
+ * the angle test.  A position within 1e-3 px of a pixel boundary of the
+ * bilinear depth's tap cell, or of the nearest-pixel rounding of the normal
+ * lookup, counts only where the neighbouring choice would change a decision
+ * (a tap without depth, an angle test on the other side).  A pixel whose
+ * margin is below 1 can be decided either way by a float evaluation of the
+ * same tests. */
+static double frac_dist(double a) {     /* distance of a to the nearest integer */
+    double t = a - floor(a);
+    return t < 0.5 ? t : 1.0 - t;
+}
+
+/* all four taps of the cell with corner (x0, y0) (clamped) have depth */
+static int cell_has_depth(const double* Pj, int W, int H, int x0, int y0) {
+    x0 = x0 < 0 ? 0 : (x0 > W - 1 ? W - 1 : x0);
+    y0 = y0 < 0 ? 0 : (y0 > H - 1 ? H - 1 : y0);
+    int x1 = x0 + 1 < W ? x0 + 1 : W - 1, y1 = y0 + 1 < H ? y0 + 1 : H - 1;
+    return Pj[4 * ((long)y0 * W + x0) + 3] > 0 && Pj[4 * ((long)y0 * W + x1) + 3] > 0 &&
+           Pj[4 * ((long)y1 * W + x0) + 3] > 0 && Pj[4 * ((long)y1 * W + x1) + 3] > 0;
+}
+
 void or_geo_filter(const or_scene* s, int ref, const int* srcs, int ns, const or_filter* f,
-                   const double* const* planes, unsigned char* keep, int* count_out) {
+                   const double* const* planes, unsigned char* keep, int* count_out, double* margin_out) {
     const or_view* V = &s->v[ref];
     const double* P = planes[ref];
     double cos_max = cos(f->max_angle_deg * OR_PI / 180.0);
@@ -731,6 +755,8 @@ void or_geo_filter(const or_scene* s, int ref, const int* srcs, int ns, const or
             long i = (long)y * V->W + x;
             double d = P[4 * i + 3];
             int cnt = 0;
+            double mg = 1e300;
+#define OR_MG(v) do { double m_ = (v); if (m_ < mg) mg = m_; } while (0)
             if (d > 0) {
                 double xt[3] = {(double)x, (double)y, 1.0}, r[3], X[3];
                 m3_vec(V->Kinv, xt, r);
@@ -746,8 +772,18 @@ void or_geo_filter(const or_scene* s, int ref, const int* srcs, int ns, const or
                     if (!(Xj[2] > 0)) continue;
                     m3_vec(S->K, Xj, q);
                     double u = q[0] / q[2], v = q[1] / q[2];
+                    OR_MG(fmin(fmin(fabs(u), fabs(S->W - 1 - u)), fmin(fabs(v), fabs(S->H - 1 - v))) / 1e-3);
                     if (!(u >= 0 && u <= S->W - 1 && v >= 0 && v <= S->H - 1)) continue;
                     int x0 = (int)floor(u), y0 = (int)floor(v);
+                    {   /* a float position on the other side of a pixel boundary picks the
+                         * neighbouring cell: fragile where its taps' depth presence differs */
+                        const int here = cell_has_depth(Pj, S->W, S->H, x0, y0);
+                        const int ax = u - x0 < 0.5 ? x0 - 1 : x0 + 1, ay = v - y0 < 0.5 ? y0 - 1 : y0 + 1;
+                        if (frac_dist(u) < 1e-3 && cell_has_depth(Pj, S->W, S->H, ax, y0) != here) OR_MG(0.0);
+                        if (frac_dist(v) < 1e-3 && cell_has_depth(Pj, S->W, S->H, x0, ay) != here) OR_MG(0.0);
+                        if (frac_dist(u) < 1e-3 && frac_dist(v) < 1e-3 &&
+                            cell_has_depth(Pj, S->W, S->H, ax, ay) != here) OR_MG(0.0);
+                    }
                     int x1 = x0 + 1 < S->W ? x0 + 1 : S->W - 1, y1 = y0 + 1 < S->H ? y0 + 1 : S->H - 1;
                     double da = Pj[4 * ((long)y0 * S->W + x0) + 3], db = Pj[4 * ((long)y0 * S->W + x1) + 3];
                     double dc = Pj[4 * ((long)y1 * S->W + x0) + 3], de = Pj[4 * ((long)y1 * S->W + x1) + 3];
@@ -756,6 +792,7 @@ void or_geo_filter(const or_scene* s, int ref, const int* srcs, int ns, const or
                     double dj = (1 - fy) * ((1 - fx) * da + fx * db) + fy * ((1 - fx) * dc + fx * de);
                     double diff = fabs(dj - Xj[2]);
                     if (f->depth_relative) diff /= Xj[2];
+                    OR_MG(fabs(diff - f->depth_tol) / 1e-5);
                     if (!(diff < f->depth_tol)) continue;
                     int xn = (int)floor(u + 0.5), yn = (int)floor(v + 0.5);
                     if (xn > S->W - 1) xn = S->W - 1;
@@ -766,6 +803,22 @@ void or_geo_filter(const or_scene* s, int ref, const int* srcs, int ns, const or
                     m3_vec(RrT, nj, nr);
                     const double* nx = P + 4 * i;
                     double cs = fabs(dot3(nx, nr)) / sqrt(dot3(nx, nx) * dot3(nr, nr));
+                    OR_MG(fabs(cs - cos_max) / 1e-5);
+                    /* a float position on the other side of a rounding boundary takes the
+                     * neighbouring pixel's normal: its angle test counts too */
+                    for (int alt = 1; alt <= 3; ++alt) {
+                        const int bx = (alt & 1) && frac_dist(u + 0.5) < 1e-3, by = (alt & 2) && frac_dist(v + 0.5) < 1e-3;
+                        if (((alt & 1) && !bx) || ((alt & 2) && !by)) continue;
+                        int xa = xn, ya = yn;
+                        if (bx) xa = u + 0.5 - xn < 0.5 ? xn - 1 : xn + 1;
+                        if (by) ya = v + 0.5 - yn < 0.5 ? yn - 1 : yn + 1;
+                        xa = xa < 0 ? 0 : (xa > S->W - 1 ? S->W - 1 : xa);
+                        ya = ya < 0 ? 0 : (ya > S->H - 1 ? S->H - 1 : ya);
+                        double na[3];
+                        m3_vec(RrT, Pj + 4 * ((long)ya * S->W + xa), na);
+                        const double ca = fabs(dot3(nx, na)) / sqrt(dot3(nx, nx) * dot3(na, na));
+                        OR_MG((ca > cos_max) != (cs > cos_max) ? 0.0 : fabs(ca - cos_max) / 1e-5);
+                    }
                     if (!(cs > cos_max)) continue;
                     /* reprojection: back-project x'_j with d_j, into the reference */
                     double ut[3] = {u, v, 1.0}, rj[3], Y[3], Yr[3], qr[3];
@@ -775,10 +828,13 @@ void or_geo_filter(const or_scene* s, int ref, const int* srcs, int ns, const or
                     if (!(Yr[2] > 0)) continue;
                     m3_vec(V->K, Yr, qr);
                     double eu = qr[0] / qr[2] - x, ev = qr[1] / qr[2] - y;
+                    OR_MG(fabs(sqrt(eu * eu + ev * ev) - f->max_reproj) / 1e-3);
                     if (!(sqrt(eu * eu + ev * ev) < f->max_reproj)) continue;
                     cnt++;
                 }
             }
+#undef OR_MG
+            if (margin_out) margin_out[i] = mg;
             if (count_out) count_out[i] = cnt;
             keep[i] = (unsigned char)(d > 0 && cnt >= f->min_consistent);
         }

@@ -511,10 +511,13 @@ __device__ __forceinline__ void window_pass(const PixWin<S>& pw, int grp,
 // pv: the pixel's PixView records (pix_views).  Must be called by all 32
 // lanes with the same nc (warp-uniform); VIEWS (per-view costs out) needs
 // nc == 1.
-template <int G, int S, bool VIEWS, bool MIXED = false>
+// OFF_SM (fp16 path only): the sample offsets come from the per-warp table
+// off_sm (slot k, lane-in-group lg at [k * G + lg]) instead of pw.o2.
+template <int G, int S, bool VIEWS, bool MIXED = false, bool OFF_SM = false>
 __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __restrict__ sv, const PixWin<S>& pw,
                                             const WinGeo& geo, const PixView* __restrict__ pv, const Cand& my, int nc,
-                                            PairSm* pairs, float* view_cost, unsigned& n_evals) {
+                                            PairSm* pairs, float* view_cost, unsigned& n_evals,
+                                            const float2* off_sm = nullptr) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
     const int V = rc.n_src;
@@ -662,7 +665,7 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int kk = k + h < S ? k + h : k;
-                    const float2 o = __half22float2(pw.o2[kk]);
+                    const float2 o = OFF_SM ? off_sm[kk * G + lg] : __half22float2(pw.o2[kk]);
                     float X = fmaf(o.x, pg.j0x, fmaf(o.y, pg.j1x, pg.nx));
                     float Y = fmaf(o.x, pg.j0y, fmaf(o.y, pg.j1y, pg.ny));
                     float Z = fmaf(o.x, pg.h0z, fmaf(o.y, pg.h1z, pg.pz));

@@ -224,8 +224,14 @@ struct __align__(16) PhaseWarp {
     float cur_c, pad_[3];
     float4 hyp[8];     // the stage's hypotheses (at most 8: propagation groups, proposals, refinement)
 };
-__host__ __device__ constexpr size_t phase_smem_bytes(int n_src, int warps) {
-    return smem_block_bytes(n_src, warps) + (size_t)warps * (32 * (sizeof(float4) + sizeof(float)) + sizeof(PhaseWarp));
+// The fp16 path keeps the window's sample offsets in a per-warp table after
+// the PhaseWarp records (offset (k_u - r_now, k_v - r_now) of slot k and
+// lane-in-group lg at [k * G + lg], when G * S <= 128): its samples take
+// fewer registers than the FP32 path's, so the offsets leave the registers.
+constexpr int kOffWords = 128;
+__host__ __device__ constexpr size_t phase_smem_bytes(int n_src, int warps, bool mixed) {
+    return smem_block_bytes(n_src, warps) + (size_t)warps * (32 * (sizeof(float4) + sizeof(float)) + sizeof(PhaseWarp)) +
+           (mixed ? (size_t)warps * kOffWords * sizeof(float2) : 0);
 }
 
 // Rows of warps of a phase block: PhaseTile<S>::TY, or fewer when the
@@ -241,9 +247,9 @@ int max_block_smem() {
     return bytes;
 }
 template <int S>
-int phase_rows(int n_src) {
+int phase_rows(int n_src, bool mixed) {
     int ty = PhaseTile<S>::TY;
-    while (ty > 1 && phase_smem_bytes(n_src, PhaseTile<S>::TX * ty) > (size_t)max_block_smem()) --ty;
+    while (ty > 1 && phase_smem_bytes(n_src, PhaseTile<S>::TX * ty, mixed) > (size_t)max_block_smem()) --ty;
     return ty;
 }
 
@@ -275,7 +281,7 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
     constexpr int kTileX = PhaseTile<S>::TX;
     const int kTileY = (int)(blockDim.x >> 5) / kTileX;
     const int kWarpsB = kTileX * kTileY;
-    extern __shared__ __align__(16) unsigned char smem[];   // phase_smem_bytes(n_src, kWarpsB)
+    extern __shared__ __align__(16) unsigned char smem[];   // phase_smem_bytes(n_src, kWarpsB, MIXED)
     ViewSm* views = reinterpret_cast<ViewSm*>(smem);
     load_views(rc, views);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -285,6 +291,10 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
                                             kWarpsB * 32) + warp * 32;
     PhaseWarp* ws = reinterpret_cast<PhaseWarp*>(smem + smem_block_bytes(rc.n_src, kWarpsB) +
                                                  (size_t)kWarpsB * 32 * (sizeof(float4) + sizeof(float))) + warp;
+    constexpr bool kOffSm = MIXED && G * S <= kOffWords;
+    float2* off_sm = reinterpret_cast<float2*>(reinterpret_cast<PhaseWarp*>(
+                         smem + smem_block_bytes(rc.n_src, kWarpsB) +
+                         (size_t)kWarpsB * 32 * (sizeof(float4) + sizeof(float))) + kWarpsB) + warp * kOffWords;
     const int Wa = (rc.W + 1) >> 1;
     const int ntx = (Wa + kTileX - 1) / kTileX, nty = (rc.H + kTileY - 1) / kTileY;
     const int nstx = (ntx + 7) / 8, nsty = (nty + 15) / 16;
@@ -320,6 +330,10 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             ws->geo = pw.geo;
             ws->cur = rc.plane[pix];
             ws->cur_c = rc.cost[pix];
+        }
+        if (kOffSm && lane < G) {
+#pragma unroll
+            for (int k = 0; k < S; ++k) off_sm[k * G + lane] = __half22float2(pw.o2[k]);
         }
         PixView* pv = warp_pixviews(smem, rc.n_src, warp);
         pix_views(rc, views, px, py, pv);   // (ends with a warp barrier)
@@ -420,8 +434,9 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             const int nc = stage == 0 ? 8 : (stage == 1 ? rc.n_prop : 3);
             if (lane < 8) ws->hyp[lane] = hyp4;
             Cand my = make_cand(rc, pw, geo, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
-            float c = eval_batch<G, S, false, MIXED>(rc, views, pw, geo, pv, my, nc, warp_pairs(smem, rc.n_src, warp),
-                                                      nullptr, nev);   // (ends with a warp barrier)
+            float c = eval_batch<G, S, false, MIXED, kOffSm>(rc, views, pw, geo, pv, my, nc,
+                                                              warp_pairs(smem, rc.n_src, warp), nullptr, nev,
+                                                              off_sm);   // (ends with a warp barrier)
             float bc;
             int bi = warp_argmin(my.ok ? c : 3.0e38f, nc, bc);
             if (bc < ws->cur_c && lane == 0) {
@@ -554,8 +569,8 @@ cudaError_t prime_launch_configs(const RefConst& rc) {
         pm_grid_for((const void*)k_init<G, S, MX>, 1, smem, kBlock);                                  \
         pm_grid_for((const void*)k_cost<G, S, MX>, 1, smem, kBlock);                                  \
         pm_grid_for((const void*)k_phase<G, S, MX>, 1,                                                \
-                    phase_smem_bytes(rc.n_src, PhaseTile<S>::TX * phase_rows<S>(rc.n_src)),          \
-                    32 * PhaseTile<S>::TX * phase_rows<S>(rc.n_src));                                  \
+                    phase_smem_bytes(rc.n_src, PhaseTile<S>::TX * phase_rows<S>(rc.n_src, MX), MX),  \
+                    32 * PhaseTile<S>::TX * phase_rows<S>(rc.n_src, MX));                              \
     } while (0)
     if (rc.precision) {
         constexpr bool MX = true;
@@ -616,9 +631,9 @@ cudaError_t launch_cost(const RefConst& rc, const float4* plane, float* cost, fl
 template <int G, int S, bool MX>
 void phase_launch(const RefConst& rc, int phase, cudaStream_t s) {
     using T = PhaseTile<S>;
-    const int ty = phase_rows<S>(rc.n_src), block = 32 * T::TX * ty;
+    const int ty = phase_rows<S>(rc.n_src, MX), block = 32 * T::TX * ty;
     const long long ntiles = (long long)(((rc.W + 1) / 2 + T::TX - 1) / T::TX) * ((rc.H + ty - 1) / ty);
-    const size_t smem = phase_smem_bytes(rc.n_src, T::TX * ty);
+    const size_t smem = phase_smem_bytes(rc.n_src, T::TX * ty, MX);
     k_phase<G, S, MX><<<pm_grid_for((const void*)k_phase<G, S, MX>, ntiles, smem, block), block, smem, s>>>(rc,
                                                                                                            phase);
 }

@@ -89,9 +89,11 @@ def test_geo_filter_across_batched_views(ring, mvs_lib, oracle_lib):
         keep = np.zeros((96, 128), np.uint8)
         cnt = np.zeros((96, 128), np.int32)
         mvs_lib.mvs_geo_filter(ctx.h, r, others, fp, keep, cnt)
-        okeep, ocnt = oracle_lib.geo_filter(osc, r, others, maps, min_consistent=1)
+        okeep, ocnt, mg = oracle_lib.geo_filter(osc, r, others, maps, min_consistent=1, with_margin=True)
         assert keep.mean() > 0.3
-        assert (cnt != ocnt).mean() <= 1e-3 and (keep != okeep).mean() <= 1e-3
+        firm = mg >= 1.0       # outside the oracle's fragile band: identical
+        assert np.array_equal(cnt[firm], ocnt[firm]) and np.array_equal(keep[firm], okeep[firm])
+        assert firm.mean() > 0.99
         gt = sc.gt_depth if r == 0 else None
         if gt is not None:     # kept pixels are mostly right
             good = np.abs(pls[0][..., 3] - gt) / gt < 0.01

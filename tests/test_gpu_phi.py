@@ -47,10 +47,15 @@ def test_geo_filter_parity(multi, mvs_lib, oracle_lib):
     keep = np.zeros((96, 128), np.uint8)
     cnt = np.zeros((96, 128), np.int32)
     mvs_lib.mvs_geo_filter(ctx.h, 0, [1, 2, 3], mvs_lib.FilterParams(), keep, cnt)
-    okeep, ocnt = oracle_lib.geo_filter(osc, 0, [1, 2, 3], {v: noisy[v].astype(np.float64) for v in range(4)})
+    okeep, ocnt, mg = oracle_lib.geo_filter(osc, 0, [1, 2, 3], {v: noisy[v].astype(np.float64) for v in range(4)},
+                                            with_margin=True)
     assert 0.05 < keep.mean() < 0.98                 # a real mix of kept and dropped pixels
-    assert (cnt != ocnt).mean() <= 5e-4
-    assert (keep != okeep).mean() <= 5e-4
+    # identical outside the fragile band (a decision within 1e-3 px, 1e-5 in
+    # depth or 1e-5 in cosine of its boundary, as the oracle reports it)
+    firm = mg >= 1.0
+    print(f"geo filter: fragile pixels {1 - firm.mean():.4%}")
+    assert np.array_equal(cnt[firm], ocnt[firm]) and np.array_equal(keep[firm], okeep[firm])
+    assert firm.mean() > 0.99
 
 
 def test_geo_filter_needs_source_maps(mvs_lib):

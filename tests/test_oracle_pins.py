@@ -348,6 +348,13 @@ def test_geo_filter_keeps_consistent_and_drops_shifted(oracle_lib):
     one[3] = planes[3] + np.array([0, 0, 0, 0.03])
     keep3, cnt3 = oracle_lib.geo_filter(osc, 0, [1, 2, 3], one)
     assert not keep3.any() and (cnt3[inner] == 1).all()     # "more than one" view needed
+    # the decision margin follows the depth test: sources 5e-6 beyond the
+    # 0.02 tolerance (band 1e-5) make every interior pixel fragile, sources
+    # 0.01 beyond it almost none
+    for dz, fragile in ((0.020005, 1.0), (0.03, 0.0)):
+        sh = {v: (pl.copy() if v == 0 else pl + np.array([0, 0, 0, dz])) for v, pl in planes.items()}
+        _, _, mg = oracle_lib.geo_filter(osc, 0, [1, 2, 3], sh, with_margin=True)
+        assert abs((mg[inner] < 1.0).mean() - fragile) < 0.05
 
 
 # --------------------------------------------------------------------------
