@@ -259,8 +259,10 @@ __device__ __forceinline__ void build_window(const RefConst& rc, int px, int py,
 }
 
 // Source-view constants copied to shared memory once per block (128 bytes,
-// read as 16-byte words): the texture, and the doubled, half-shifted
-// homography rows G and B of PairConst with their hi and lo parts.
+// read as 16-byte words, and 16 bytes of padding: lanes that read different
+// views' records at the same offset then fall on different banks): the
+// texture, and the doubled, half-shifted homography rows G and B of
+// PairConst with their hi and lo parts.
 struct __align__(16) ViewSm {
     const uint2* tex;
     uint32_t pitch;
@@ -274,9 +276,10 @@ struct __align__(16) ViewSm {
     float gx2, gy2, gz2, gz2l;  // column 2 of G (hi), G_2 column 2 (lo)
     float gx0l, gx1l, gx2l, gy0l;
     float gy1l, gy2l, gz0l, gz1l;
+    float pad_[4];
 };
 
-static_assert(sizeof(ViewSm) == 128 && offsetof(ViewSm, pitch) == 8 && offsetof(ViewSm, fold_x) == 12 &&
+static_assert(sizeof(ViewSm) == 144 && offsetof(ViewSm, pitch) == 8 && offsetof(ViewSm, fold_x) == 12 &&
                   offsetof(ViewSm, last) == 16 && offsetof(ViewSm, fold_y) == 20 && offsetof(ViewSm, xmax2) == 24 &&
                   offsetof(ViewSm, gx0) == 32 &&
                   offsetof(ViewSm, gz0) == 48 && offsetof(ViewSm, bzh) == 64 && offsetof(ViewSm, gx2) == 80 &&
@@ -310,10 +313,12 @@ __device__ __forceinline__ void load_views(const RefConst& rc, ViewSm* sv) {
 
 // Per (reference pixel, source view): G x~ of the pixel (the source point at
 // infinite depth in doubled, half-shifted homogeneous coordinates) as hi + lo
-// floats, computed once per pixel by lane j for view j.
+// floats, computed once per pixel by lane j for view j (48 bytes: lanes
+// reading eight different views' records touch eight different bank groups).
 struct __align__(16) PixView {
     float gxh, gxl, gyh, gyl;
     float gzh, gzl, pad0_, pad1_;
+    float pad2_[4];
 };
 
 __device__ __forceinline__ void pix_views(const RefConst& rc, const ViewSm* __restrict__ sv, int px, int py,
@@ -327,8 +332,9 @@ __device__ __forceinline__ void pix_views(const RefConst& rc, const ViewSm* __re
         df_affine(w2.x, w2.y, w5.x, w6.x, w6.y, w6.z, x, y, r.gxh, r.gxl);
         df_affine(w2.z, w2.w, w5.y, w6.w, w7.x, w7.y, x, y, r.gyh, r.gyl);
         df_affine(w3.x, w3.y, w5.z, w7.z, w7.w, w5.w, x, y, r.gzh, r.gzl);
-        r.pad0_ = r.pad1_ = 0.0f;
-        pv[j] = r;
+        float4* o = reinterpret_cast<float4*>(pv + j);   // the padding is never read
+        o[0] = make_float4(r.gxh, r.gxl, r.gyh, r.gyl);
+        o[1] = make_float4(r.gzh, r.gzl, 0.0f, 0.0f);
     }
     __syncwarp();
 }
@@ -397,7 +403,7 @@ __host__ __device__ constexpr size_t smem_views_bytes(int n_src) {
     return (size_t)n_src * sizeof(ViewSm);
 }
 __host__ __device__ constexpr size_t smem_warp_bytes(int n_src) {
-    return (size_t)8 * n_src * (sizeof(PairSm) + sizeof(float)) + (size_t)n_src * sizeof(PixView);   // 448 n_src
+    return (size_t)8 * n_src * (sizeof(PairSm) + sizeof(float)) + (size_t)n_src * sizeof(PixView);   // 464 n_src
 }
 __host__ __device__ constexpr size_t smem_block_bytes(int n_src, int warps) {
     return smem_views_bytes(n_src) + (size_t)warps * smem_warp_bytes(n_src);
