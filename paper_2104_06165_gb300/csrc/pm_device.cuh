@@ -439,9 +439,11 @@ struct PairGeo {
 // once.  The texel index is clamped into the array: the listed window
 // corners lie inside the source, but float positions of other samples of a
 // plane seen almost edge-on by the source need not.  The bilinear values
-// are shifted by c0 = the 2 x 2 texel sum at the group's first sample (an
-// intensity of this source patch, which enters through the fp16
-// coefficient a in one mixed add).
+// are shifted by c0 = the 2 x 2 texel sum at the pair's anchor, next to the
+// image of the window centre (an intensity of this source patch, which
+// enters through the fp16 coefficient a in one mixed add): the bilateral
+// weights favour samples like the centre, so the weighted mean lies near c0
+// and the one-pass moments rarely cancel.
 //   CENTRED = false: nc0 = -c0 out; sa, sb, se += sum w d, sum w d^2,
 //     sum w r' d over the lane's samples, d = s - c0;
 //   CENTRED = true: nc0 in (from the first pass, so every d is the same
@@ -452,6 +454,12 @@ __device__ __forceinline__ void window_pass(const PixWin<S>& pw, int grp,
                                             const uint2* __restrict__ tex, uint32_t pitch, uint32_t last,
                                             const PairGeo& g, float& nc0, float mean_d, float& sa, float& sb,
                                             float& se) {
+    if (!CENTRED) {
+        // the texel at the anchor: X / Z = 0 in the sample formula below
+        const uint32_t ia = (uint32_t)__float_as_int(g.my) * pitch + (uint32_t)__float_as_int(g.mx);
+        const uint2 qa = __ldg(tex + min(ia, last));
+        nc0 = -__half2float(__ushort_as_half((unsigned short)(qa.x & 0xffffu)));
+    }
 #pragma unroll
     for (int k0 = 0; k0 < S; k0 += CH) {
         uint2 tq[CH];
@@ -473,9 +481,6 @@ __device__ __forceinline__ void window_pass(const PixWin<S>& pw, int grp,
                 tq[kk] = __ldg(tex + min(idx, last));
             }
         }
-        if (!CENTRED && k0 == 0)
-            nc0 = -__half2float(
-                __ushort_as_half((unsigned short)(__shfl_sync(0xffffffffu, tq[0].x, grp * G) & 0xffffu)));
 #pragma unroll
         for (int kk = 0; kk < CH; ++kk) {
             const int k = k0 + kk;

@@ -4,6 +4,7 @@
 //   Sec. III-C  Eq. 4 weighted ZNCC, Eq. 5 aggregation, refinement
 //   Sec. III    red-black checkerboard updating
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <unordered_map>
@@ -237,14 +238,19 @@ __host__ __device__ constexpr size_t phase_smem_bytes(int n_src, int warps, bool
 // Rows of warps of a phase block: PhaseTile<S>::TY, or fewer when the
 // block's pair lists (which grow with the number of sources) would exceed the
 // per-block shared memory.
+// The limit is a property of the current device (queried once per device;
+// a failed query leaves 48 KB, the limit without the opt-in).
 int max_block_smem() {
-    static const int bytes = [] {
-        int dev = 0, v = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        return v;
-    }();
-    return bytes;
+    static std::atomic<int> bytes[128];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return 48 * 1024;
+    int v = bytes[dev].load();
+    if (v == 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+            return 48 * 1024;
+        bytes[dev].store(v);
+    }
+    return v;
 }
 template <int S>
 int phase_rows(int n_src, bool mixed) {
