@@ -505,6 +505,84 @@ __device__ __forceinline__ void window_pass(const PixWin<S>& pw, int grp,
     }
 }
 
+// Mixed-precision form of window_pass: positions, fractions and texel
+// indices in FP32 exactly as there, the bilinear value of two slots per
+// half2 instruction (fp16 products of the exact fp16 coefficients), moments
+// accumulated in FP32.  The coefficient a is shifted by c0 in fp16 (both
+// are integers up to 1020, so a - c0 is exact); c0 is the anchor texel's a,
+// as in window_pass.
+//   MODE 0: nc0 = -c0 out; sa, sb, se += sum w d, sum w d^2, sum w r' d;
+//   MODE 1: sa += sum w (d - mean_d)^2 in FP32;
+//   MODE 2: sd += the same in FP64 (the variance denominator near the
+//           flat-patch limit).
+// d is the same value in every mode (the same half2 operations).
+template <int G, int S, int MODE, int CH = (S <= 9 ? S : 8)>
+__device__ __forceinline__ void window_pass_h2(const PixWin<S>& pw, const uint2* __restrict__ tex, uint32_t pitch,
+                                               uint32_t last, const PairGeo& g, float& nc0, float mean_d, float& sa,
+                                               float& sb, float& se, double& sd) {
+    const uint32_t ia = (uint32_t)__float_as_int(g.my) * pitch + (uint32_t)__float_as_int(g.mx);
+    if (MODE == 0) {
+        const uint2 qa = __ldg(tex + min(ia, last));
+        nc0 = -__half2float(__ushort_as_half((unsigned short)(qa.x & 0xffffu)));
+    }
+    const __half2 c2 = __float2half2_rn(-nc0);   // exact: an integer <= 1020
+#pragma unroll
+    for (int k0 = 0; k0 < S; k0 += CH) {
+        uint2 tq[CH];
+        float Us[CH], Vs[CH];
+#pragma unroll
+        for (int kk = 0; kk < CH; ++kk) {
+            const int k = k0 + kk;
+            if (k < S) {
+                const float2 o = __half22float2(pw.o2[k]);
+                const float X = fmaf(o.x, g.j0x, fmaf(o.y, g.j1x, g.nx));
+                const float Y = fmaf(o.x, g.j0y, fmaf(o.y, g.j1y, g.ny));
+                const float Z = fmaf(o.x, g.h0z, fmaf(o.y, g.h1z, g.pz));
+                const float iz = rcp_approx(Z);
+                const float tx = fmaf(X, iz, g.mx), ty = fmaf(Y, iz, g.my);
+                Us[kk] = fmaf(X, iz, g.mx - tx);
+                Vs[kk] = fmaf(Y, iz, g.my - ty);
+                const uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx);
+                tq[kk] = __ldg(tex + min(idx, last));
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < CH; kk += 2) {
+            const int k = k0 + kk;
+            if (k < S) {
+                const bool two = k + 1 < S;   // compile-time
+                const uint2 q0 = tq[kk], q1 = two ? tq[kk + 1] : tq[kk];
+                uint32_t ab = __byte_perm(q0.x, q1.x, 0x5410), bb = __byte_perm(q0.x, q1.x, 0x7632);
+                uint32_t cb = __byte_perm(q0.y, q1.y, 0x5410), db = __byte_perm(q0.y, q1.y, 0x7632);
+                const __half2 A = __hsub2(*reinterpret_cast<__half2*>(&ab), c2);
+                const __half2 B = *reinterpret_cast<__half2*>(&bb), C = *reinterpret_cast<__half2*>(&cb);
+                const __half2 D = *reinterpret_cast<__half2*>(&db);
+                const __half2 U2 = __floats2half2_rn(Us[kk], two ? Us[kk + 1] : Us[kk]);
+                const __half2 V2 = __floats2half2_rn(Vs[kk], two ? Vs[kk + 1] : Vs[kk]);
+                const float2 dv = __half22float2(__hfma2(V2, __hfma2(U2, D, C), __hfma2(U2, B, A)));
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && !two) break;
+                    const float d = h ? dv.y : dv.x;
+                    const float w = pw.w[k + h];
+                    if (MODE == 0) {
+                        const float t = w * d;
+                        sa += t;
+                        sb = fmaf(t, d, sb);
+                        se = fmaf(pw.wr[k + h], d, se);
+                    } else if (MODE == 1) {
+                        const float e = d - mean_d;
+                        sa = fmaf(w * e, e, sa);
+                    } else {
+                        const double e = (double)d - (double)mean_d;
+                        sd = fma((double)w * e, e, sd);
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Costs C(x) (Eq. 5) of up to 8 hypotheses of the warp's pixel: lane c < nc
 // holds hypothesis c on entry and its cost on return.
 //   1. the (hypothesis, view) pairs of the usable hypotheses whose window
@@ -522,13 +600,10 @@ __device__ __forceinline__ void window_pass(const PixWin<S>& pw, int grp,
 // pv: the pixel's PixView records (pix_views).  Must be called by all 32
 // lanes with the same nc (warp-uniform); VIEWS (per-view costs out) needs
 // nc == 1.
-// OFF_SM (fp16 path only): the sample offsets come from the per-warp table
-// off_sm (slot k, lane-in-group lg at [k * G + lg]) instead of pw.o2.
-template <int G, int S, bool VIEWS, bool MIXED = false, bool OFF_SM = false>
+template <int G, int S, bool VIEWS, bool MIXED = false>
 __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __restrict__ sv, const PixWin<S>& pw,
                                             const WinGeo& geo, const PixView* __restrict__ pv, const Cand& my, int nc,
-                                            PairSm* pairs, float* view_cost, unsigned& n_evals,
-                                            const float2* off_sm = nullptr) {
+                                            PairSm* pairs, float* view_cost, unsigned& n_evals) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
     const int V = rc.n_src;
@@ -662,53 +737,10 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
                 if (centre) sdd = s2;
             }
         } else {
-            const uint2* tex = v_tex;
-            const uint32_t pitch = v0.z, last = v_last;
-            float sval[S];
-            // mixed precision: positions and fractions in FP32 (as above), the
-            // bilinear interpolation of two samples per half2 instruction, on
-            // intensities shifted by the reference patch mean
-            const __half2 mu2 = __float2half2_rn(pw.mean);
-#pragma unroll
-            for (int k = 0; k < S; k += 2) {
-                float Us[2], Vs[2];
-                uint2 q[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int kk = k + h < S ? k + h : k;
-                    const float2 o = OFF_SM ? off_sm[kk * G + lg] : __half22float2(pw.o2[kk]);
-                    float X = fmaf(o.x, pg.j0x, fmaf(o.y, pg.j1x, pg.nx));
-                    float Y = fmaf(o.x, pg.j0y, fmaf(o.y, pg.j1y, pg.ny));
-                    float Z = fmaf(o.x, pg.h0z, fmaf(o.y, pg.h1z, pg.pz));
-                    float iz = rcp_approx(Z);
-                    float tx = fmaf(X, iz, pg.mx), ty = fmaf(Y, iz, pg.my);
-                    Us[h] = fmaf(X, iz, pg.mx - tx);
-                    Vs[h] = fmaf(Y, iz, pg.my - ty);
-                    uint32_t idx = (uint32_t)__float_as_int(ty) * pitch + (uint32_t)__float_as_int(tx);
-                    q[h] = __ldg(tex + min(idx, last));
-                }
-                uint32_t ab = __byte_perm(q[0].x, q[1].x, 0x5410), bb = __byte_perm(q[0].x, q[1].x, 0x7632);
-                uint32_t cb = __byte_perm(q[0].y, q[1].y, 0x5410), db = __byte_perm(q[0].y, q[1].y, 0x7632);
-                __half2 A = __hsub2(*reinterpret_cast<__half2*>(&ab), mu2);
-                __half2 B = *reinterpret_cast<__half2*>(&bb), Cc = *reinterpret_cast<__half2*>(&cb);
-                __half2 D = *reinterpret_cast<__half2*>(&db);
-                __half2 U2 = __floats2half2_rn(Us[0], Us[1]), V2 = __floats2half2_rn(Vs[0], Vs[1]);
-                float2 s2 = __half22float2(__hfma2(V2, __hfma2(U2, D, Cc), __hfma2(U2, B, A)));
-                sval[k] = s2.x;
-                if (k + 1 < S) sval[k + 1] = s2.y;
-            }
-            // weighted moments in one pass, shifted by the group's first
-            // sample (an intensity of this source patch): with d = s - c0,
-            // sum w (s - mu)^2 = sum w d^2 - (sum w d)^2 / W; near the flat
-            // limit the denominator is recomputed in FP64 below
-            const float c0 = __shfl_sync(0xffffffffu, sval[0], grp * G);
-#pragma unroll
-            for (int k = 0; k < S; ++k) {
-                float dv = sval[k] - c0;
-                float t = pw.w[k] * dv;
-                sa += t;
-                sb = fmaf(t, dv, sb);
-                se = fmaf(pw.wr[k], dv, se);
+            float nc0 = 0.0f;
+            {
+                double unused = 0.0;
+                window_pass_h2<G, S, 0>(pw, v_tex, v0.z, v_last, pg, nc0, 0.0f, sa, sb, se, unused);
             }
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) {
@@ -719,29 +751,22 @@ __device__ __forceinline__ float eval_batch(const RefConst& rc, const ViewSm* __
             mean_d = sa * inv_wsum;
             sdd = fmaf(-mean_d, sa, sb);
             // the shift far from the patch mean: the centred second moment in
-            // FP32, as in the FP32 path
-            const bool centre = sa * mean_d > 8.0f * sdd;
+            // FP32 from a second gather pass, as in the FP32 path
+            const bool centre = has && sa * mean_d > 8.0f * sdd;
             if (__any_sync(0xffffffffu, centre)) {
-                float s2 = 0.0f;
-#pragma unroll
-                for (int k = 0; k < S; ++k) {
-                    const float e = (sval[k] - c0) - mean_d;
-                    s2 = fmaf(pw.w[k] * e, e, s2);
-                }
+                float s2 = 0.0f, u0 = 0.0f, u1 = 0.0f;
+                double unused = 0.0;
+                window_pass_h2<G, S, 1>(pw, v_tex, v0.z, v_last, pg, nc0, mean_d, s2, u0, u1, unused);
                 s2 = gsum<G>(s2);
                 if (centre) sdd = s2;
             }
             // a source patch within 1 % of the flat limit (where the exclusion
             // decision is taken): the variance denominator in FP64
-            const bool near_flat = sdd < 1.01f * kTauVar * geo.wsum && sdd > 0.99f * kTauVar * geo.wsum;
+            const bool near_flat = has && sdd < 1.01f * kTauVar * geo.wsum && sdd > 0.99f * kTauVar * geo.wsum;
             if (__any_sync(0xffffffffu, near_flat)) {
-                const double mu_d = (double)c0 + (double)sa / (double)geo.wsum;
                 double v = 0.0;
-#pragma unroll
-                for (int k = 0; k < S; ++k) {
-                    double dd = (double)sval[k] - mu_d;
-                    v = fma((double)pw.w[k] * dd, dd, v);
-                }
+                float s0 = 0.0f, u0 = 0.0f, u1 = 0.0f;
+                window_pass_h2<G, S, 2, 2>(pw, v_tex, v0.z, v_last, pg, nc0, mean_d, s0, u0, u1, v);
 #pragma unroll
                 for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (near_flat) sdd = (float)v;

@@ -225,14 +225,10 @@ struct __align__(16) PhaseWarp {
     float cur_c, pad_[3];
     float4 hyp[8];     // the stage's hypotheses (at most 8: propagation groups, proposals, refinement)
 };
-// The fp16 path keeps the window's sample offsets in a per-warp table after
-// the PhaseWarp records (offset (k_u - r_now, k_v - r_now) of slot k and
-// lane-in-group lg at [k * G + lg], when G * S <= 128): its samples take
-// fewer registers than the FP32 path's, so the offsets leave the registers.
-constexpr int kOffWords = 128;
+// Shared memory of a phase block (the same for both precisions).
 __host__ __device__ constexpr size_t phase_smem_bytes(int n_src, int warps, bool mixed) {
-    return smem_block_bytes(n_src, warps) + (size_t)warps * (32 * (sizeof(float4) + sizeof(float)) + sizeof(PhaseWarp)) +
-           (mixed ? (size_t)warps * kOffWords * sizeof(float2) : 0);
+    return (void)mixed,
+           smem_block_bytes(n_src, warps) + (size_t)warps * (32 * (sizeof(float4) + sizeof(float)) + sizeof(PhaseWarp));
 }
 
 // Rows of warps of a phase block: PhaseTile<S>::TY, or fewer when the
@@ -297,10 +293,6 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
                                             kWarpsB * 32) + warp * 32;
     PhaseWarp* ws = reinterpret_cast<PhaseWarp*>(smem + smem_block_bytes(rc.n_src, kWarpsB) +
                                                  (size_t)kWarpsB * 32 * (sizeof(float4) + sizeof(float))) + warp;
-    constexpr bool kOffSm = MIXED && G * S <= kOffWords;
-    float2* off_sm = reinterpret_cast<float2*>(reinterpret_cast<PhaseWarp*>(
-                         smem + smem_block_bytes(rc.n_src, kWarpsB) +
-                         (size_t)kWarpsB * 32 * (sizeof(float4) + sizeof(float))) + kWarpsB) + warp * kOffWords;
     const int Wa = (rc.W + 1) >> 1;
     const int ntx = (Wa + kTileX - 1) / kTileX, nty = (rc.H + kTileY - 1) / kTileY;
     const int nstx = (ntx + 7) / 8, nsty = (nty + 15) / 16;
@@ -336,10 +328,6 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             ws->geo = pw.geo;
             ws->cur = rc.plane[pix];
             ws->cur_c = rc.cost[pix];
-        }
-        if (kOffSm && lane < G) {
-#pragma unroll
-            for (int k = 0; k < S; ++k) off_sm[k * G + lane] = __half22float2(pw.o2[k]);
         }
         PixView* pv = warp_pixviews(smem, rc.n_src, warp);
         pix_views(rc, views, px, py, pv);   // (ends with a warp barrier)
@@ -440,9 +428,9 @@ __global__ void __launch_bounds__(PhaseTile<S>::BLOCK, PhaseTile<S>::MIN_BLOCKS)
             const int nc = stage == 0 ? 8 : (stage == 1 ? rc.n_prop : 3);
             if (lane < 8) ws->hyp[lane] = hyp4;
             Cand my = make_cand(rc, pw, geo, hyp4.x, hyp4.y, hyp4.z, hyp4.w, want);
-            float c = eval_batch<G, S, false, MIXED, kOffSm>(rc, views, pw, geo, pv, my, nc,
-                                                              warp_pairs(smem, rc.n_src, warp), nullptr, nev,
-                                                              off_sm);   // (ends with a warp barrier)
+            float c = eval_batch<G, S, false, MIXED>(rc, views, pw, geo, pv, my, nc,
+                                                     warp_pairs(smem, rc.n_src, warp), nullptr,
+                                                     nev);   // (ends with a warp barrier)
             float bc;
             int bi = warp_argmin(my.ok ? c : 3.0e38f, nc, bc);
             if (bc < ws->cur_c && lane == 0) {
