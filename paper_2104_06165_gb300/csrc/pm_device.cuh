@@ -574,8 +574,10 @@ __device__ __forceinline__ void window_pass_h2(const PixWin<S>& pw, const uint2*
                         const float e = d - mean_d;
                         sa = fmaf(w * e, e, sa);
                     } else {
-                        const double e = (double)d - (double)mean_d;
-                        sd = fma((double)w * e, e, sd);
+                        // e and w e rounded once each in FP32; their product
+                        // and the sum exact or in FP64
+                        const float e = d - mean_d;
+                        sd = fma((double)(w * e), (double)e, sd);
                     }
                 }
             }
