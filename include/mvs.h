@@ -79,10 +79,11 @@ typedef struct {
     uint64_t seed;         /* Philox4x64-10 key word 0 (word 1 = ref index)  */
     int32_t precision;     /* 0 = FP32; 1 = mixed: the bilinear interpolation
                               of two window samples per half2 instruction on
-                              intensities shifted by the reference patch mean,
-                              moments in FP32, near-flat variance denominators
-                              recomputed in FP64 (results differ from FP32 by
-                              the fp16 rounding of the interpolated values)  */
+                              intensities shifted by an intensity of the
+                              source patch, moments in FP32, near-flat
+                              variance denominators recomputed in FP64
+                              (results differ from FP32 by the fp16 rounding
+                              of the interpolated values)                    */
     int32_t lanes_per_pixel; /* work layout of the ZNCC kernels: lanes that
                               share one window (4, 8, 16 or 32; 0 = default;
                               -1 = timed choice, mvs_patchmatch_batch only).
