@@ -375,6 +375,9 @@ def run_ours(args):
                      "kernel": "k_phase (checkerboard propagation + refinement)",
                      "peak_basis": "measured FFMA rate of this GPU (mvs_measure_peaks), see peaks",
                      "fractions": {k: round(v, 4) for k, v in fracs.items()}, "binding": binding,
+                     "binding_note": "the largest of the three fractions from algorithmic counts; the L2 count "
+                                     "assumes no L1 reuse across pairs, while the kernel's measured limiter is "
+                                     "instruction issue (ncu: 75 % of issue slots, L2 at 20 % of its peak)",
                      "fraction_basis": {"fp32": f"{FLOP_PER_SAMPLE} flop per window sample / measured FFMA peak",
                                         "l1": f"{GATHERS_PER_SAMPLE} 8-byte gather per window sample / measured "
                                               "L1 gather peak in the same pattern",
